@@ -1,0 +1,73 @@
+"""Workload definitions: material data, wall conditions and seeded UQ inputs.
+
+Plain data only (no finite-volume arithmetic).  The numbers are the synthetic
+stand-ins for the paper's castings (Sections 3-5 use an Sn-Bi ingot, a clamp
+and a pulley whose geometry and data are not available): an Al-like alloy in a
+0.1 x 0.1 x 0.0125 m cavity.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from .mesh import box_mesh
+
+# wall types of a boundary patch
+BC_ADIABATIC = 0      # no heat flux, no-slip
+BC_DIRICHLET = 1      # fixed temperature, no-slip
+
+AL_ALLOY = dict(
+    rho=2700.0, k=150.0, cp=900.0, latent=3.9e5,
+    T_sol=833.0, T_liq=913.0, mu=1.3e-3, beta=1e-4,
+    T_ref=913.0, g=(0.0, -9.81, 0.0),
+    darcy_C=1e8, darcy_eps=1e-3,
+)
+
+CAVITY = (0.1, 0.1, 0.0125)
+
+
+def cavity_walls(T_cold=700.0, T_hot=950.0):
+    """x = 0 wall held cold, x = L wall held hot, the other four adiabatic."""
+    return [(BC_DIRICHLET, T_cold), (BC_DIRICHLET, T_hot),
+            (BC_ADIABATIC, 0.0), (BC_ADIABATIC, 0.0),
+            (BC_ADIABATIC, 0.0), (BC_ADIABATIC, 0.0)]
+
+
+def all_walls(T_wall):
+    return [(BC_DIRICHLET, float(T_wall))] * 6
+
+
+def props(material=None, walls=None, T_init=950.0, p_rtol=1e-8, precision=0, **tol):
+    """Solver settings in the layout of ``fvs_props`` (see include/fvs.h)."""
+    p = dict(material=dict(AL_ALLOY if material is None else material),
+             walls=list(cavity_walls() if walls is None else walls),
+             T_init=float(T_init), p_rtol=float(p_rtol), precision=int(precision),
+             mom_rtol=1e-10, e_rtol=1e-10, e_tol_T=1e-8, max_e_iters=40)
+    p.update(tol)
+    return p
+
+
+def config_small():
+    """32x32x4 orthogonal cavity, dt 1e-3 s, 200 steps."""
+    return dict(mesh=box_mesh(32, 32, 4, CAVITY), dt=1e-3, steps=200, props=props())
+
+
+def config_jittered(n=128, steps=500, seed_jitter=1810, seed_perm=8572):
+    """n^3 cavity, interior nodes jittered by +-0.2 cell widths, cells permuted."""
+    return dict(mesh=box_mesh(n, n, n, CAVITY, jitter=0.2, jitter_seed=seed_jitter,
+                              permute_seed=seed_perm),
+                dt=1e-3, steps=steps, props=props())
+
+
+def uq_inputs(n_samples, seed):
+    """Stochastic inputs per sample: melt temperature ~ N(950, 10) K, wall
+    temperature ~ U(650, 750) K, solute C0 ~ U(3, 5) wt%.  Returns [S, 3]."""
+    rng = np.random.default_rng(seed)
+    T_melt = rng.normal(950.0, 10.0, n_samples)
+    T_wall = rng.uniform(650.0, 750.0, n_samples)
+    C0 = rng.uniform(3.0, 5.0, n_samples)
+    return np.stack([T_melt, T_wall, C0], axis=1)
+
+
+def liquidus_of(C0):
+    """Liquidus shifted linearly by -5 K per wt% about 913 K at 4 wt%."""
+    return 913.0 - 5.0 * (np.asarray(C0) - 4.0)

@@ -1,0 +1,484 @@
+"""Plain FP64 CPU oracle of the fractional-step finite-volume solidification step.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the product path may import this file:
+only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` use it.  It shares no code with the CUDA library.
+
+Everything is written as sparse matrices built from the definitions, assembled
+with scipy.sparse and solved with a sparse direct solver, so that a reader can
+check each operator against the paper by eye.  Section, equation and algorithm
+numbers refer to Shahane et al., "Finite Volume Simulation Framework for Die
+Casting with Uncertainty Quantification" (arXiv:1810.08572).
+
+Readings of points the paper leaves open (each is listed in the design doc too):
+ * face vector area S_f = 1/2 (x_V3 - x_V1) x (x_V4 - x_V2); cell and face
+   centres are vertex means; volume = 1/3 sum_f x_f . S_f (outward)
+ * the local Jacobian of Eq. 12 has rows d = C1C2, V1V3, V2V4; on a boundary
+   face C2 is the face centre
+ * vertex values are arithmetic means of the cells around the vertex
+   (Section 2.3); wall vertices take the wall value for velocity (no slip)
+   and for temperature on fixed-temperature walls
+ * convection uses the arithmetic mean of the two owner values (Section 2.3)
+ * Darcy drag D = C fs^2 / ((1 - fs)^3 + eps) (Blake-Kozeny form of Eq. 3 with
+   lambda folded into C)
+ * the energy equation uses the same Crank-Nicolson diffusion and
+   Adams-Bashforth convection as the momentum predictor (Eq. 6), with the
+   flux level matching each temperature level
+ * the solid fraction is linear between solidus and liquidus; at the kinks
+   the derivative is taken from the mushy side
+ * an LM cell none of whose faces carries flow is left out of the pressure
+   system (its pressure is 0) and is treated like a solid cell when face
+   gradients are smeared
+ * the pressure of each connected part of the pressure system is fixed by
+   zero mean; the right side is projected to zero sum on each part
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+from scipy.sparse.csgraph import connected_components
+
+BC_ADIABATIC = 0
+BC_DIRICHLET = 1
+
+
+# ----------------------------------------------------------------------------
+# Geometry (Section 2.3, Fig. 1, Eq. 11-12)
+# ----------------------------------------------------------------------------
+class Geometry:
+    """Face and cell geometry of an unstructured hexahedral mesh."""
+
+    def __init__(self, nodes, cells, faces, face_cells, patch):
+        X = np.asarray(nodes, dtype=np.float64)
+        self.nodes = X
+        self.cells = np.asarray(cells, dtype=np.int64)
+        self.faces = np.asarray(faces, dtype=np.int64)
+        self.face_cells = np.asarray(face_cells, dtype=np.int64)
+        self.patch = np.asarray(patch, dtype=np.int64)
+        self.Nc, self.Nf, self.Nv = len(self.cells), len(self.faces), len(X)
+        self.owner = self.face_cells[:, 0]
+        self.neigh = self.face_cells[:, 1]
+        self.interior = self.neigh >= 0
+        Vx = [X[self.faces[:, k]] for k in range(4)]          # V1..V4
+        self.Sf = 0.5 * np.cross(Vx[2] - Vx[0], Vx[3] - Vx[1])
+        self.Af = np.linalg.norm(self.Sf, axis=1)
+        self.n = self.Sf / self.Af[:, None]
+        self.xf = X[self.faces].mean(axis=1)
+        self.xc = X[self.cells].mean(axis=1)
+        # volume by the divergence theorem, div x = 3
+        xs = np.einsum("fi,fi->f", self.xf, self.Sf) / 3.0
+        self.V = np.zeros(self.Nc)
+        np.add.at(self.V, self.owner, xs)
+        np.add.at(self.V, self.neigh[self.interior], -xs[self.interior])
+        # d = C1 -> C2 (face centre on the boundary)
+        c2 = np.where(self.interior[:, None], self.xc[np.maximum(self.neigh, 0)], self.xf)
+        self.d = c2 - self.xc[self.owner]
+        self.ndotd = np.einsum("fi,fi->f", self.n, self.d)
+        # local frame xi: C1C2, eta: V1V3, zeta: V2V4 (Eq. 12); rows of J
+        self.J = np.stack([self.d, Vx[2] - Vx[0], Vx[3] - Vx[1]], axis=1)
+        self.Jinv = np.linalg.inv(self.J)
+        # cross-diffusion vector of Eq. 11 and its weights on the local
+        # differences: t . (J^-1 delta) = (J^-T t) . delta
+        t = self.n - self.d / self.ndotd[:, None]
+        self.w = np.einsum("fij,fi->fj", self.Jinv, t)
+        # incidences
+        rows = np.repeat(np.arange(self.Nc), 8)
+        self.Pc = sp.csr_matrix((np.ones(8 * self.Nc), (self.cells.ravel(), rows)),
+                                shape=(self.Nv, self.Nc))          # vertex x cell
+        self.Pc.data[:] = 1.0                                      # repeated corners count once
+        self.nv = np.asarray(self.Pc.sum(axis=1)).ravel()
+        self.Pavg = sp.diags(1.0 / self.nv) @ self.Pc
+        fr = np.repeat(np.arange(self.Nf), 4)
+        self.Fv = sp.csr_matrix((np.ones(4 * self.Nf), (fr, self.faces.ravel())),
+                                shape=(self.Nf, self.Nv))
+        self.E31 = self._vdiff(2, 0)
+        self.E42 = self._vdiff(3, 1)
+        # neighbour set N(f): cells sharing a vertex with the face (Section 2.4.2)
+        NB = (self.Fv @ self.Pc).tocsr()
+        NB.data[:] = 1.0
+        self.NB = NB
+        # signed face -> cell sum (outward from each cell)
+        fi = np.arange(self.Nf)
+        r = np.concatenate([self.owner, self.neigh[self.interior]])
+        c = np.concatenate([fi, fi[self.interior]])
+        v = np.concatenate([np.ones(self.Nf), -np.ones(self.interior.sum())])
+        self.Div = sp.csr_matrix((v, (r, c)), shape=(self.Nc, self.Nf))
+        # C2 - C1 difference (boundary rows carry only -C1; the wall value is added separately)
+        r = np.concatenate([fi, fi[self.interior]])
+        c = np.concatenate([self.owner, self.neigh[self.interior]])
+        v = np.concatenate([-np.ones(self.Nf), np.ones(self.interior.sum())])
+        self.Dxi = sp.csr_matrix((v, (r, c)), shape=(self.Nf, self.Nc))
+        # owner mean (1/2 each owner) used for convection and u*_f
+        r = np.concatenate([fi, fi[self.interior]])
+        c = np.concatenate([self.owner, self.neigh[self.interior]])
+        vals = np.concatenate([np.full(self.Nf, 0.5), np.full(self.interior.sum(), 0.5)])
+        self.Avg = sp.csr_matrix((vals, (r, c)), shape=(self.Nf, self.Nc))
+        self.boundary_vertex = np.zeros(self.Nv, bool)
+        self.boundary_vertex[self.faces[~self.interior].ravel()] = True
+
+    def _vdiff(self, a, b):
+        fi = np.arange(self.Nf)
+        r = np.concatenate([fi, fi])
+        c = np.concatenate([self.faces[:, a], self.faces[:, b]])
+        v = np.concatenate([np.ones(self.Nf), -np.ones(self.Nf)])
+        return sp.csr_matrix((v, (r, c)), shape=(self.Nf, self.Nv))
+
+    # -- face normal derivative (Eq. 11) -------------------------------------
+    def normal_derivative_rows(self, Dxi, Deta, Dzeta):
+        """A_f (n . grad phi)_f as rows over cells, from the three local differences."""
+        A = self.Af
+        return (sp.diags(A * (1.0 / self.ndotd + self.w[:, 0])) @ Dxi
+                + sp.diags(A * self.w[:, 1]) @ Deta
+                + sp.diags(A * self.w[:, 2]) @ Dzeta).tocsr()
+
+
+# ----------------------------------------------------------------------------
+# Diffusion operators with wall data (Eq. 10-12)
+# ----------------------------------------------------------------------------
+def vertex_operator(g, fixed_mask, fixed_value):
+    """phi_v = mean of the cells around v, or a fixed wall value where masked.
+    Returns (P [Nv x Nc], c [Nv]) with phi_v = P phi + c."""
+    keep = sp.diags((~fixed_mask).astype(np.float64))
+    return (keep @ g.Pavg).tocsr(), np.where(fixed_mask, fixed_value, 0.0)
+
+
+def diffusion_operator(g, face_mask, vP, vc, phi_b):
+    """Affine operator L phi + l = sum over masked faces of sigma A_f (n . grad phi)_f.
+
+    ``phi_b`` is the value at boundary faces (C2 := face centre)."""
+    Deta = g.E31 @ vP
+    Dzeta = g.E42 @ vP
+    N = g.normal_derivative_rows(g.Dxi, Deta, Dzeta)
+    k = g.Af * ((1.0 / g.ndotd + g.w[:, 0]) * np.where(g.interior, 0.0, phi_b)
+                + g.w[:, 1] * (g.E31 @ vc) + g.w[:, 2] * (g.E42 @ vc))
+    M = g.Div @ sp.diags(face_mask.astype(np.float64))
+    return (M @ N).tocsr(), M @ k
+
+
+def velocity_diffusion(g):
+    """No-slip walls: wall vertices and wall faces carry u = 0."""
+    vP, vc = vertex_operator(g, g.boundary_vertex, 0.0)
+    return diffusion_operator(g, np.ones(g.Nf, bool), vP, vc, np.zeros(g.Nf))
+
+
+def temperature_diffusion(g, walls):
+    """Fixed-temperature walls enter through their vertices and faces;
+    adiabatic walls carry no flux."""
+    btype = np.full(g.Nf, -1)
+    bval = np.zeros(g.Nf)
+    for pid, (typ, T) in enumerate(walls):
+        m = g.patch == pid
+        btype[m] = typ
+        bval[m] = T
+    dir_face = btype == BC_DIRICHLET
+    # a vertex on fixed-temperature walls takes the mean of the values of the
+    # fixed-temperature wall faces that contain it (each face counted once)
+    cnt = np.zeros(g.Nv)
+    acc = np.zeros(g.Nv)
+    for f in np.nonzero(dir_face)[0]:
+        for v in set(g.faces[f].tolist()):
+            cnt[v] += 1
+            acc[v] += bval[f]
+    fixed = cnt > 0
+    val = np.where(fixed, acc / np.maximum(cnt, 1), 0.0)
+    vP, vc = vertex_operator(g, fixed, val)
+    face_mask = g.interior | dir_face
+    return diffusion_operator(g, face_mask, vP, vc, bval)
+
+
+# ----------------------------------------------------------------------------
+# Material laws (Eq. 3, Eq. 5 in its linear form, Eq. 22-23)
+# ----------------------------------------------------------------------------
+def solid_fraction(T, T_sol, T_liq):
+    return np.clip((T_liq - T) / (T_liq - T_sol), 0.0, 1.0)
+
+
+def solid_fraction_slope(T, T_sol, T_liq):
+    """dfs/dT, taken from the mushy side at the kinks."""
+    return np.where((T >= T_sol) & (T <= T_liq), -1.0 / (T_liq - T_sol), 0.0)
+
+
+def darcy_coefficient(fs, C, eps):
+    return C * fs * fs / ((1.0 - fs) ** 3 + eps)
+
+
+def sdas_um(cooling_rate):
+    """Eq. 22: lambda_2 = 39.4 (dT/dt)^-0.317 micrometres."""
+    return 39.4 * np.power(cooling_rate, -0.317)
+
+
+def yield_strength_mpa(sdas):
+    """Eq. 23: sigma_0.2 = 59.0 lambda_2^-1/2 + 120.3 MPa."""
+    return 59.0 / np.sqrt(sdas) + 120.3
+
+
+# ----------------------------------------------------------------------------
+# Linear solves
+# ----------------------------------------------------------------------------
+def solve(A, b):
+    x = spla.spsolve(A.tocsc(), b)
+    return np.atleast_1d(x)
+
+
+def pressure_components(App):
+    """Connected parts of the pressure system (symmetric closure of its pattern)."""
+    S = (abs(App) + abs(App).T).tocsr()
+    S.eliminate_zeros()
+    return connected_components(S, directed=False)
+
+
+def solve_singular(App, b):
+    """Solve A p = b on each connected part: project b to zero sum, pin the
+    first unknown of each part, then shift p to zero mean (Section 2.5 notes
+    the disjoint liquid pockets; each pocket is a separate singular block)."""
+    n = App.shape[0]
+    if n == 0:
+        return np.zeros(0), 0
+    ncomp, lab = pressure_components(App)
+    b = b.copy()
+    for c in range(ncomp):
+        m = lab == c
+        b[m] -= b[m].mean()
+    A = App.tolil()
+    rhs = b.copy()
+    for c in range(ncomp):
+        i = np.nonzero(lab == c)[0][0]
+        A.rows[i] = [i]
+        A.data[i] = [1.0]
+        rhs[i] = 0.0
+    p = solve(A.tocsr(), rhs)
+    for c in range(ncomp):
+        m = lab == c
+        p[m] -= p[m].mean()
+    return p, ncomp
+
+
+# ----------------------------------------------------------------------------
+# The solver state and one time step (Section 2.2, steps 1-5)
+# ----------------------------------------------------------------------------
+class Oracle:
+    """One deterministic run of the method on one mesh."""
+
+    def __init__(self, mesh, props):
+        self.g = g = Geometry(mesh["nodes"], mesh["cells"], mesh["faces"],
+                              mesh["face_cells"], mesh["patch"])
+        self.m = dict(props["material"])
+        self.walls = list(props["walls"])
+        self.props = props
+        self.Lu, _ = velocity_diffusion(g)
+        self.LT, self.lT = temperature_diffusion(g, self.walls)
+        self.Deta_p = (g.E31 @ g.Pavg).tocsr()
+        self.Dzeta_p = (g.E42 @ g.Pavg).tocsr()
+        m = self.m
+        self.T = np.full(g.Nc, props["T_init"])
+        self.fs = solid_fraction(self.T, m["T_sol"], m["T_liq"])
+        self.T_old = self.T.copy()
+        self.u = np.zeros((g.Nc, 3))
+        self.u_old = np.zeros((g.Nc, 3))
+        self.F = np.zeros(g.Nf)
+        self.F_old = np.zeros(g.Nf)
+        self.p = np.zeros(g.Nc)
+        self.time = 0.0
+        self.nstep = 0
+        self.t_liq = np.where(self.T <= m["T_liq"], 0.0, -1.0)
+        self.t_sol = np.where(self.T <= m["T_sol"], 0.0, -1.0)
+        self.stats = {}
+
+    # -- helpers ---------------------------------------------------------------
+    def conv(self, phi, F):
+        """Conv(phi, F)_c = sum_f sigma F_f (phi_C1 + phi_C2)/2 (walls carry F = 0)."""
+        return self.g.Div @ (F * (self.g.Avg @ phi))
+
+    def face_cases(self, lm):
+        """Section 2.4.2: 0 wall, 1 no solid neighbour, 2 solid neighbour only,
+        3 solid owner.  Returns (case, ppe_active)."""
+        g = self.g
+        own_ok = lm[g.owner] & np.where(g.interior, lm[np.maximum(g.neigh, 0)], False)
+        case = np.where(g.interior, np.where(own_ok, 1, 3), 0)
+        # LM cells with no flow face are removed from the pressure system
+        flow = np.zeros(g.Nc, bool)
+        f12 = case == 1
+        flow[g.owner[f12]] = True
+        flow[g.neigh[f12]] = True
+        ppe = lm & flow
+        nsolid = g.NB @ (~ppe).astype(np.float64)
+        case = np.where((case == 1) & (nsolid > 0), 2, case)
+        return case, ppe
+
+    def smeared_rows(self, case, ppe):
+        """Section 2.4.2, Eq. 15-16: on case-2 faces the deleted (solid)
+        neighbours' coefficients are spread equally over the remaining ones."""
+        g = self.g
+        De = self.Deta_p.tolil(copy=True)
+        Dz = self.Dzeta_p.tolil(copy=True)
+        NB = g.NB
+        for f in np.nonzero(case == 2)[0]:
+            nbr = NB.indices[NB.indptr[f]:NB.indptr[f + 1]]
+            keep = nbr[ppe[nbr]]
+            gone = nbr[~ppe[nbr]]
+            for D in (De, Dz):
+                row = dict(zip(D.rows[f], D.data[f]))
+                s = sum(row.get(j, 0.0) for j in gone)
+                for j in gone:
+                    row.pop(j, None)
+                for j in keep:
+                    row[j] = row.get(j, 0.0) + s / len(keep)
+                cols = sorted(row)
+                D.rows[f] = cols
+                D.data[f] = [row[j] for j in cols]
+        return De.tocsr(), Dz.tocsr()
+
+    # -- the step ------------------------------------------------------------------
+    def step(self, dt):
+        g, m = self.g, self.m
+        rho, mu = m["rho"], m["mu"]
+        T_n, fs_n = self.T, self.fs
+        # 1. tags from the previous temperature (Section 2.4)
+        lm = T_n > m["T_sol"]
+        solid = ~lm
+        u_n = self.u.copy(); u_n[solid] = 0.0
+        u_o = self.u_old.copy(); u_o[solid] = 0.0
+        blocked = ~(lm[g.owner] & np.where(g.interior, lm[np.maximum(g.neigh, 0)], False))
+        F_n = np.where(blocked, 0.0, self.F)
+        F_o = np.where(blocked, 0.0, self.F_old)
+
+        # 2. momentum predictor on LM cells, Eq. 6 with Section 2.4.1 row deletion
+        act = np.nonzero(lm)[0]
+        Lu = self.Lu[act][:, act]
+        V = g.V[act]
+        D = darcy_coefficient(fs_n[act], m["darcy_C"], m["darcy_eps"])
+        M = (sp.diags(rho * V / dt + D * V) - 0.5 * mu * Lu).tocsr()
+        gvec = np.asarray(m["g"], dtype=np.float64)
+        buoy = -rho * m["beta"] * (T_n[act] - m["T_ref"])[:, None] * gvec[None, :] * V[:, None]
+        u_star = np.zeros((g.Nc, 3))
+        for k in range(3):
+            conv = 1.5 * self.conv(u_n[:, k], F_n) - 0.5 * self.conv(u_o[:, k], F_o)
+            rhs = (rho * V / dt * u_n[act, k] - rho * conv[act]
+                   + 0.5 * mu * (self.Lu @ u_n[:, k])[act] + buoy[:, k])
+            u_star[act, k] = solve(M, rhs)
+
+        # 3. pressure Poisson equation on the flowing LM cells (Eq. 9, Section 2.4.2)
+        case, ppe = self.face_cases(lm)
+        De, Dz = self.smeared_rows(case, ppe)
+        Nrow = g.normal_derivative_rows(g.Dxi, De, Dz)           # A_f (n . grad p)_f^mod
+        flow = (case == 1) | (case == 2)
+        Mdiv = g.Div @ sp.diags(flow.astype(np.float64))
+        App_full = (Mdiv @ Nrow / rho).tocsr()
+        uf = g.Avg @ u_star                                        # u*_f, owner mean
+        Fstar = g.Af * np.einsum("fi,fi->f", g.n, uf) * flow
+        b_full = (g.Div @ Fstar) / dt
+        pa = np.nonzero(ppe)[0]
+        App = App_full[pa][:, pa]
+        p_act, ncomp = solve_singular(App, b_full[pa])
+        p = np.zeros(g.Nc)
+        p[pa] = p_act
+        resid = b_full[pa] - App @ p_act
+        self.stats = dict(n_active=int(lm.sum()), n_ppe=int(ppe.sum()), ncomp=ncomp,
+                          ppe_relres=float(np.linalg.norm(resid) / max(np.linalg.norm(b_full[pa]), 1e-300)))
+
+        # 4. face flux and cell velocity correction (Eq. 8, Eq. 17)
+        F_new = (Fstar - dt / rho * (Nrow @ p)) * flow
+        dxi, deta, dzeta = g.Dxi @ p, De @ p, Dz @ p
+        grad_f = np.einsum("fij,fj->fi", g.Jinv, np.stack([dxi, deta, dzeta], axis=1))
+        cnt = np.abs(g.Div) @ flow.astype(np.float64)
+        gsum = np.abs(g.Div) @ (grad_f * flow[:, None])
+        grad_c = np.where(cnt[:, None] > 0, gsum / np.maximum(cnt, 1)[:, None], 0.0)
+        u_new = np.zeros((g.Nc, 3))
+        u_new[act] = u_star[act] - dt / rho * grad_c[act]
+
+        # 5. energy with latent heat on all cells (Eq. 4, Eq. 18-20)
+        T_new, fs_new, e_its = self.energy(dt, T_n, fs_n, self.T_old, F_n, F_o)
+
+        # 6. microstructure bookkeeping (Eq. 22-23 use the local cooling rate)
+        self.update_crossings(T_n, T_new, dt)
+
+        self.stats.update(e_its=e_its, n_faces_case2=int((case == 2).sum()),
+                          n_faces_case3=int((case == 3).sum()))
+        self.T_old, self.T, self.fs = T_n, T_new, fs_new
+        self.u_old, self.u = u_n, u_new
+        self.F_old, self.F = F_n, F_new
+        self.p = p
+        self.u_star = u_star
+        self.case, self.ppe, self.lm = case, ppe, lm
+        self.b_ppe = b_full
+        self.time += dt
+        self.nstep += 1
+        return self.stats
+
+    def energy_residual(self, T, dt, T_n, fs_n, T_o, F_n, F_o):
+        """R(T) of the discrete energy equation (all terms moved to the left)."""
+        g, m = self.g, self.m
+        rho, cp, k, L = m["rho"], m["cp"], m["k"], m["latent"]
+        conv = 1.5 * self.conv(T_n, F_n) - 0.5 * self.conv(T_o, F_o)
+        fs = solid_fraction(T, m["T_sol"], m["T_liq"])
+        return (rho * cp * g.V / dt * (T - T_n) + rho * cp * conv
+                - 0.5 * k * (self.LT @ T + self.lT) - 0.5 * k * (self.LT @ T_n + self.lT)
+                - rho * L * g.V / dt * (fs - fs_n))
+
+    def energy(self, dt, T_n, fs_n, T_o, F_n, F_o):
+        """Section 2.4.4 iteration: S_p, S_c from the last iterate, solve,
+        update fs with lambda = 1; stop when T and fs stop changing.  After 20
+        passes without convergence the temperature is taken from the
+        linearised enthalpy instead (same fixed point)."""
+        g, m = self.g, self.m
+        rho, cp, k, L = m["rho"], m["cp"], m["k"], m["latent"]
+        Ts, Tl = m["T_sol"], m["T_liq"]
+        conv = 1.5 * self.conv(T_n, F_n) - 0.5 * self.conv(T_o, F_o)
+        base = (rho * cp * g.V / dt * T_n - rho * cp * conv
+                + 0.5 * k * (self.LT @ T_n + self.lT) + 0.5 * k * self.lT)
+        K = (-0.5 * k * self.LT).tocsr()
+        T, fs = T_n.copy(), fs_n.copy()
+        tolT = self.props.get("oracle_tol_T", 1e-11)
+        for it in range(1, 200):
+            dfs = solid_fraction_slope(T, Ts, Tl)
+            Sp = rho * L * g.V / dt * dfs
+            Sc = rho * L * g.V / dt * (fs - fs_n - dfs * T)
+            A = (K + sp.diags(rho * cp * g.V / dt - Sp)).tocsr()
+            T_lin = solve(A, base + Sc)
+            if it <= 20:
+                T_next = T_lin
+            else:
+                H = cp * T_lin + L * (1.0 - fs - dfs * (T_lin - T))
+                T_next = temperature_from_enthalpy(H, cp, L, Ts, Tl)
+            fs_next = solid_fraction(T_next, Ts, Tl)
+            dT = np.max(np.abs(T_next - T))
+            dF = np.max(np.abs(fs_next - fs))
+            T, fs = T_next, fs_next
+            if dT <= tolT and dF <= 1e-12:
+                break
+        return T, fs, it
+
+    def update_crossings(self, T_n, T_new, dt):
+        m = self.m
+        for which, Tc in (("t_liq", m["T_liq"]), ("t_sol", m["T_sol"])):
+            arr = getattr(self, which)
+            hit = (arr < 0) & (T_n > Tc) & (T_new <= Tc)
+            frac = (T_n - Tc) / np.where(hit, T_n - T_new, 1.0)
+            arr[hit] = self.time + dt * frac[hit]
+
+    def qoi(self):
+        """Local solidification time, cooling rate, SDAS and yield strength
+        per cell (NaN where the cell has not yet passed the solidus)."""
+        m = self.m
+        done = (self.t_sol >= 0) & (self.t_liq >= 0)
+        tf = np.where(done, self.t_sol - self.t_liq, np.nan)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            cr = (m["T_liq"] - m["T_sol"]) / tf
+            lam = sdas_um(cr)
+            ys = yield_strength_mpa(lam)
+        return dict(t_f=tf, cooling_rate=cr, sdas=lam, yield_strength=ys)
+
+    def run(self, dt, nsteps):
+        for _ in range(nsteps):
+            self.step(dt)
+        return self
+
+
+def temperature_from_enthalpy(H, cp, L, T_sol, T_liq):
+    """Invert H(T) = cp T + L (1 - fs(T)) with linear fs: piecewise linear,
+    strictly increasing."""
+    H_sol = cp * T_sol
+    H_liq = cp * T_liq + L
+    T_mush = T_sol + (H - H_sol) / (H_liq - H_sol) * (T_liq - T_sol)
+    return np.where(H <= H_sol, H / cp, np.where(H >= H_liq, (H - L) / cp, T_mush))
