@@ -1,0 +1,320 @@
+"""Benchmark: active cell-steps/s of the finite-volume solidification step.
+
+Default workload: the 128^3 cavity (0.1 x 0.1 x 0.0125 m, 2,097,152 hex
+cells) with interior nodes jittered by +-0.2 cell widths and cells, faces and
+nodes randomly renumbered; Al-like alloy from 950 K at rest, x = 0 wall at
+700 K, x = L wall at 950 K; dt = 1e-3 s; pressure solved to a relative
+residual of 1e-8.  A step is one pass of the whole method (tags and
+compaction, momentum predictor, pressure Poisson solve with AMG-Krylov, flux
+and velocity correction, latent-heat energy loop, crossing times).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl fvs|reference]
+                  [--precision fp64|mixed] [--n 128]
+
+Prints one JSON line.  ``--impl reference`` times the CPU oracle (the plain
+FP64 implementation written from the paper) on a bounded sample of the same
+workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "active cell-steps/s at 1e-8 pressure residual (mixed vs FP64) + UQ samples/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fvs", choices=["fvs", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--n", type=int, default=128, help="cells per axis of the cavity")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-n", type=int, default=20, help="cells per axis of the oracle sample")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    return ap.parse_args()
+
+
+def workload(n):
+    from fvs_inputs import cases
+    return cases.config_jittered(n=n)
+
+
+def bench_props(precision):
+    from fvs_inputs import cases
+    return cases.props(p_rtol=1e-8, mom_rtol=1e-10, e_rtol=1e-10, e_tol_T=1e-6, max_e_iters=40,
+                       max_krylov_iters=1000, precision=1 if precision == "mixed" else 0)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline key)
+# ---------------------------------------------------------------------------
+def _oracle_worker(n, steps, q):
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    os.environ.setdefault("OMP_NUM_THREADS", "1")
+    import warnings
+    warnings.filterwarnings("ignore")
+    from fvs_inputs import cases
+    from oracle.fv import Oracle
+    c = cases.config_jittered(n=n)
+    o = Oracle(c["mesh"], bench_props("fp64"))
+    o.step(c["dt"])            # first step outside the timing (imports, caches)
+    t0 = time.perf_counter()
+    act = 0
+    for _ in range(steps):
+        st = o.step(c["dt"])
+        act += st["n_active"]
+    dt = time.perf_counter() - t0
+    q.put(dict(active_cell_steps=act, seconds=dt))
+
+
+def cpu_oracle(n, steps):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    env_keep = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_keep:
+        os.environ[k] = "1"
+    p = ctx.Process(target=_oracle_worker, args=(n, steps, q))
+    p.start()
+    r = q.get(timeout=1800)
+    p.join()
+    for k, v in env_keep.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
+    value = r["active_cell_steps"] / r["seconds"]
+    return dict(value=value, unit="active cell-steps/s", cores=1, kind="oracle",
+                sample=f"{n}^3 jittered permuted cavity (same physics and dt), {steps} steps after one "
+                       f"untimed step, single-threaded scipy oracle, {r['seconds']:.1f} s")
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0]],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return dict(sm_mhz=statistics.median(sm), sm_max_mhz=mx, reasons=sorted(reasons), samples=len(sm))
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_gpu(args):
+    import numpy as np
+    import torch
+    from paper_1810_08572_gb300 import LIB_PATH, build
+    if not os.path.exists(LIB_PATH):
+        build()
+    from paper_1810_08572_gb300 import fvs
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    c = workload(args.n)
+    props = bench_props(args.precision)
+    stream = torch.cuda.Stream()
+    mesh = fvs.Mesh(c["mesh"], stream=stream)
+    S = fvs.Solver(mesh, props, stream=stream)
+    dt = c["dt"]
+    for _ in range(args.warmup):
+        S.step(dt, 1, allow_not_converged=True)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    S.profile(True)
+    clocks = Clocks(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
+                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/fvs_clocks.csv")
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    act = 0
+    its = []
+    torch.cuda.synchronize()
+    n_launch0 = fvs.fvs_launch_count()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        st = S.step(dt, 1, allow_not_converged=True)
+        act += st["n_active"]
+        its.append(st)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    n_launch = fvs.fvs_launch_count() - n_launch0
+    ms = ev0.elapsed_time(ev1)
+    ck = clocks.stop()
+    prof = S.profile_read()
+    S.profile(False)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        a = torch.tensor([act], device="cuda", dtype=torch.float64)
+        dist.all_reduce(a)
+        act = float(a.item())
+    value = act / (ms / 1e3)
+
+    # roofline of the kernel class with the largest total time
+    peak, peak_kind = load_peaks()
+    top = max(prof, key=lambda r: r["total_ms"]) if prof else None
+    roof = None
+    if top:
+        per_launch_bytes = top["bytes"] / top["launches"]
+        per_launch_s = top["total_ms"] / top["launches"] / 1e3
+        ach = per_launch_bytes / per_launch_s / 1e9
+        roof = dict(bound="hbm", kernel=top["name"], achieved=round(ach, 1), peak=peak, unit="GB/s",
+                    frac=round(ach / peak, 4), traffic=None, peak_source=f"{peak_kind} copy bandwidth",
+                    launches=top["launches"], share_of_step=round(top["total_ms"] / ms, 3),
+                    bytes_per_launch=per_launch_bytes)
+
+    e2e = None
+    if not args.no_e2e and rank == 0:
+        e2e = run_e2e(fvs, c, props, args, stream, torch)
+
+    cpu = None
+    if not args.no_cpu and rank == 0 and world == 1:
+        cpu = cpu_oracle(args.cpu_n, args.cpu_steps)
+
+    nkern = sum(r["launches"] for r in prof)
+    line = dict(
+        metric=METRIC, value=round(value, 1), unit="active cell-steps/s", n_gpus=world, steps=args.steps,
+        warmup=args.warmup, ms_per_step=round(ms / args.steps, 3), higher_is_better=True, scaling="weak",
+        vs_baseline=None, dtype="f64" if args.precision == "fp64" else "f64+f32",
+        data="synthetic",
+        config=dict(workload=f"cavity {args.n}^3 jittered+permuted, dt 1e-3 s, p_rtol 1e-8, "
+                             f"{args.precision}", cells=args.n ** 3, dt=dt, p_rtol=1e-8,
+                    precision=args.precision, l2="inputs larger than L2 (matrices ~1 GB)",
+                    parallelism="replicas" if world > 1 else "single GPU"),
+        roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=ck,
+        gpu_launches=int(n_launch),
+        kernel_profile=sorted(prof, key=lambda r: -r["total_ms"])[:8],
+        step_stats=dict(p_its=[s["p_its"] for s in its], e_its=[s["e_its"] for s in its],
+                        e_lin_its=[s["e_lin_its"] for s in its], mom_its=[s["mom_its"] for s in its],
+                        p_relres=max(s["p_relres"] for s in its), fallback=sum(s["fallback"] for s in its),
+                        amg_levels=its[-1]["amg_levels"], n_active_last=its[-1]["n_active"]),
+    )
+    line["gpu_launches_profiled"] = nkern
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_e2e(fvs, c, props, args, stream, torch):
+    """Same metric through the public API from host buffers: mesh upload and
+    set-up, the steps, and the fields read back, all inside the timed region."""
+    import numpy as np
+    m = c["mesh"]
+    h2d = sum(np.asarray(m[k]).nbytes for k in ("nodes", "cells", "faces", "face_cells", "patch"))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mesh = fvs.Mesh(m, stream=stream)
+    S = fvs.Solver(mesh, props, stream=stream)
+    act = 0
+    k = max(1, args.steps)
+    for _ in range(k):
+        act += S.step(c["dt"], 1, allow_not_converged=True)["n_active"]
+    T = S.query("T")
+    U = S.query("U")
+    P = S.query("P")
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    d2h = T.nbytes + U.nbytes + P.nbytes
+    S.close()
+    mesh.close()
+    return dict(value=round(act / sec, 1), unit="active cell-steps/s", h2d_bytes_per_step=int(h2d / k),
+                d2h_bytes_per_step=int(d2h / k), steps=k,
+                note="mesh upload, renumbering and geometry, solver set-up, steps, T/u/p read back")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cpu = cpu_oracle(args.cpu_n, max(1, args.steps // 10 or 1) if args.steps > 0 else 1)
+    line = dict(impl="reference", metric=METRIC, value=round(cpu["value"], 2), unit="active cell-steps/s",
+                n_gpus=args.gpus, steps=args.steps, warmup=args.warmup, higher_is_better=True,
+                scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
+                config=dict(workload=f"cavity {args.n}^3 jittered+permuted, dt 1e-3 s, p_rtol 1e-8, "
+                                     f"{args.precision}", cpu_sample_cells=args.cpu_n ** 3),
+                cpu_baseline=cpu,
+                e2e=dict(value=round(cpu["value"], 2), unit="active cell-steps/s", h2d_bytes_per_step=0,
+                         d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,231 @@
+/*
+ * fvs.h - C ABI of the GB300 finite-volume solidification solver.
+ *
+ * The library advances the fractional-step method of Shahane et al.,
+ * "Finite Volume Simulation Framework for Die Casting with Uncertainty
+ * Quantification" (arXiv:1810.08572), on unstructured hexahedral meshes:
+ * momentum predictor with Boussinesq buoyancy and Darcy drag (Section 2.2,
+ * Eq. 6), pressure Poisson equation on the liquid/mushy cells with the
+ * coefficient smearing of Section 2.4.2 (Eq. 9, Eq. 15-16), consistent face
+ * flux and velocity correction (Eq. 8, Eq. 17), and the energy equation with
+ * latent heat by source linearisation (Eq. 4, Eq. 18-20, Section 2.4.4).
+ *
+ * Conventions for every entry point:
+ *  - Every function returns an fvs_status; FVS_OK (0) on success.  No entry
+ *    point aborts, traps or exits; fvs_last_error() gives a message for the
+ *    last failure on the calling thread.
+ *  - "host" pointers are plain CPU memory, "device" pointers are CUDA device
+ *    memory of the GPU that was current when the object was created.
+ *  - Inputs are copied; the caller keeps ownership of every buffer it
+ *    passes.  The library owns (and frees in the destroy calls) all device
+ *    memory it allocates.
+ *  - A stream argument is a cudaStream_t passed as void* (NULL = legacy
+ *    default stream).  All work of an object runs in order on its stream.
+ *  - Field arrays exchanged with the caller are in the caller's (input)
+ *    numbering of cells and faces, whatever reordering the mesh applied.
+ *  - There is no CPU fallback: without a usable GPU the calls fail with
+ *    FVS_ERR_CUDA.
+ */
+#ifndef FVS_H
+#define FVS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FVS_OK = 0,
+  FVS_ERR_ARG = 1,           /* bad argument (NULL, size, range)                 */
+  FVS_ERR_MESH = 2,          /* mesh failed validation                          */
+  FVS_ERR_CUDA = 3,          /* CUDA runtime error                              */
+  FVS_ERR_NOMEM = 4,         /* device allocation failed                        */
+  FVS_ERR_NOT_CONVERGED = 5, /* a solve stopped at its iteration limit; fields
+                                are left consistent and the residual reported   */
+  FVS_ERR_TIMEOUT = 6,       /* a bounded device wait ran out                   */
+  FVS_ERR_STATE = 7          /* call out of order (e.g. step before properties) */
+} fvs_status;
+
+typedef struct fvs_mesh_s* fvs_mesh;
+typedef struct fvs_solver_s* fvs_solver;
+
+/* Message for the last non-OK status returned on this thread (never NULL). */
+const char* fvs_last_error(void);
+
+/* Library version string, e.g. "fvs 0.1 sm_103a". */
+const char* fvs_version(void);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all objects, all threads). */
+int64_t fvs_launch_count(void);
+
+/* ------------------------------------------------------------------------
+ * Mesh (Section 2.3, Fig. 1).
+ *   nodes_xyz      host  double [n_nodes*3]
+ *   cell_nodes     host  int32  [n_cells*8]  hexahedron corners (VTK order)
+ *   face_nodes     host  int32  [n_faces*4]  corners V1..V4 in cyclic order
+ *                  with the right-hand normal 1/2 (V3-V1) x (V4-V2) pointing
+ *                  from the owner C1 to the neighbour C2 (outward on walls);
+ *                  V1V3 and V2V4 are the local eta and zeta axes of Eq. 12
+ *   face_cells     host  int32  [n_faces*2]  (owner, neighbour), neighbour -1
+ *                  on the boundary
+ *   boundary_patch host  int32  [n_faces]    -1 interior, else wall patch id
+ *                  0..63 (wall data are given per patch in fvs_props)
+ *   reorder        1: renumber cells (Morton order of centres), vertices
+ *                  and faces (by owner) for coalesced access; 0: keep input
+ *                  order
+ * Fails with FVS_ERR_MESH unless every cell has exactly six faces, every
+ * interior face has two distinct owners, all ids are in range, and all
+ * volumes and face areas are positive.
+ * ------------------------------------------------------------------------ */
+fvs_status fvs_mesh_create(const double* nodes_xyz, int64_t n_nodes,
+                           const int32_t* cell_nodes, int64_t n_cells,
+                           const int32_t* face_nodes, int64_t n_faces,
+                           const int32_t* face_cells, const int32_t* boundary_patch,
+                           int reorder, void* stream, fvs_mesh* out);
+fvs_status fvs_mesh_destroy(fvs_mesh mesh);
+
+typedef struct {
+  int64_t n_cells, n_faces, n_nodes, n_interior_faces;
+  int32_t max_cell_neighbours; /* width of the vertex-neighbour stencil       */
+  int32_t max_face_neighbours; /* largest neighbour set N(f) of a face        */
+  int32_t n_patches;           /* 1 + largest patch id                        */
+  int32_t orthogonal;          /* 1 if no face carries cross diffusion        */
+  double total_volume;
+} fvs_mesh_info;
+fvs_status fvs_mesh_get_info(fvs_mesh mesh, fvs_mesh_info* info);
+
+/* Geometry in input numbering, for checking: which = 0 cell volumes [n_cells],
+ * 1 face areas [n_faces]; dst is host memory of dst_len doubles. */
+fvs_status fvs_mesh_geometry(fvs_mesh mesh, int which, double* dst, int64_t dst_len);
+
+/* ------------------------------------------------------------------------
+ * Material and run settings.
+ *  Darcy drag D = darcy_C fs^2 / ((1 - fs)^3 + darcy_eps) (Eq. 3 with the
+ *  dendrite spacing folded into darcy_C); solid fraction linear between
+ *  T_sol and T_liq (Eq. 5 in its linear form); buoyancy -rho beta (T - T_ref) g.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double rho, k, cp, latent, T_sol, T_liq, mu, beta, T_ref;
+  double g[3];
+  double darcy_C, darcy_eps;
+} fvs_material;
+
+enum { FVS_BC_ADIABATIC = 0, FVS_BC_DIRICHLET = 1 };
+typedef struct {
+  int32_t type; /* FVS_BC_ADIABATIC or FVS_BC_DIRICHLET; every wall is no-slip */
+  double T;     /* wall temperature for FVS_BC_DIRICHLET                       */
+} fvs_patch_bc;
+
+enum { FVS_PREC_FP64 = 0, FVS_PREC_MIXED = 1 };
+enum { FVS_PSOLVER_AMG = 0, FVS_PSOLVER_JACOBI = 1 };
+
+typedef struct {
+  fvs_material mat;
+  int32_t n_patches;            /* entries in bc (>= the mesh's n_patches)      */
+  const fvs_patch_bc* bc;       /* host, indexed by patch id                    */
+  double T_init;                /* uniform initial temperature; fluid at rest   */
+  double p_rtol;                /* pressure: ||b - A p||_2 / ||b||_2 target     */
+  double mom_rtol;              /* momentum predictor relative residual target  */
+  double e_rtol;                /* energy inner solve relative residual target  */
+  double e_tol_T;               /* latent-heat loop: max |dT| stop rule (K)     */
+  int32_t max_e_iters;          /* latent-heat loop limit                       */
+  int32_t max_krylov_iters;     /* per linear solve                             */
+  int32_t precision;            /* FVS_PREC_FP64 or FVS_PREC_MIXED              */
+  int32_t p_solver;             /* FVS_PSOLVER_AMG (AMG-preconditioned Krylov,
+                                   falling back to Jacobi BiCGStab on failure as
+                                   in Section 2.5) or FVS_PSOLVER_JACOBI         */
+} fvs_props;
+
+fvs_status fvs_solver_create(fvs_mesh mesh, void* stream, fvs_solver* out);
+fvs_status fvs_solver_destroy(fvs_solver solver);
+
+/* Copies the settings and resets the state to the initial condition
+ * (uniform T_init, u = 0, zero fluxes, time 0). */
+fvs_status fvs_set_properties(fvs_solver solver, const fvs_props* props);
+
+/* Overwrite the state with a given temperature field (and velocity, or NULL
+ * for rest): T^n = T^{n-1} = T, fs = fs(T), u^n = u^{n-1} = u (zero in solid
+ * cells), fluxes and pressure zero, time 0, crossing times reset.
+ * T [n_cells], u [n_cells*3] (x,y,z per cell); on_device selects the memory
+ * space of both. */
+fvs_status fvs_set_state(fvs_solver solver, const double* T, const double* u, int on_device);
+
+typedef struct {
+  int64_t n_active;   /* liquid + mushy cells (rows of momentum)            */
+  int64_t n_ppe;      /* cells in the pressure system                        */
+  int32_t mom_its;    /* Krylov iterations, sum of the three components      */
+  int32_t p_its;      /* pressure Krylov iterations                          */
+  int32_t e_its;      /* latent-heat loop passes                             */
+  int32_t e_lin_its;  /* energy Krylov iterations, summed over passes        */
+  double p_relres;    /* final pressure relative residual                    */
+  int32_t fallback;   /* 1 if the pressure solve fell back to Jacobi BiCGStab */
+  int32_t n_components; /* connected parts of the pressure system            */
+  int32_t amg_levels;
+  int32_t status;     /* fvs_status of the step                              */
+} fvs_step_stats;
+
+/* Advance n_steps time steps of size dt (Section 2.2, steps 1-5 plus the
+ * crossing-time bookkeeping for Eq. 22-23).  'last' (nullable, host) gets the
+ * statistics of the final step.  Returns FVS_ERR_NOT_CONVERGED if a solve hit
+ * its iteration limit (the step is still completed). */
+fvs_status fvs_step(fvs_solver solver, double dt, int32_t n_steps, fvs_step_stats* last);
+
+/* Solve the pressure system of the current state's active set (tags of the
+ * last step, Section 2.4.2) for a given right side.
+ *   rhs    device double [n_cells], input numbering; entries of cells outside
+ *          the pressure system are ignored
+ *   p_out  device double [n_cells]; zero outside the pressure system, zero
+ *          mean on each connected part
+ * The right side is projected to zero sum on each connected part.  The
+ * system is A p = rhs with A p = sum over flowing faces of
+ * (A_f / rho) (n . grad p)_f (Eq. 9 left side). */
+fvs_status fvs_pressure_solve(fvs_solver solver, const double* rhs, double* p_out,
+                              double rtol, int32_t* iters, double* relres);
+
+typedef enum {
+  FVS_T = 0,       /* temperature [n_cells]                                   */
+  FVS_FS = 1,      /* solid fraction [n_cells]                                */
+  FVS_U = 2,       /* velocity [n_cells*3]                                    */
+  FVS_P = 3,       /* pressure [n_cells]                                      */
+  FVS_FLUX = 4,    /* face volume flux owner->neighbour [n_faces]             */
+  FVS_TAG = 5,     /* 1 liquid/mushy, 0 solid, as double [n_cells]            */
+  FVS_QOI = 6,     /* per cell: t_f, cooling rate, SDAS (um), yield (MPa)
+                      [n_cells*4]; NaN where the cell has not solidified      */
+  FVS_USTAR = 7,   /* predictor velocity u* of the last step [n_cells*3]      */
+  FVS_CROSS = 8,   /* liquidus / solidus crossing times [n_cells*2], -1 unset */
+  FVS_FACE_CASE = 9 /* pressure face case 0 wall,1,2,3 as double [n_faces]   */
+} fvs_field;
+
+/* Copy a field (double values, input numbering) into dst (dst_len doubles,
+ * host or device per dst_on_device). */
+fvs_status fvs_query_fields(fvs_solver solver, fvs_field field, double* dst,
+                            int64_t dst_len, int dst_on_device);
+
+/* ------------------------------------------------------------------------
+ * Kernel timing (not part of the method; for roofline measurement).
+ * While enabled, every launch of the SpMV, residual and Jacobi kernels on the
+ * fine pressure, energy and momentum matrices inside fvs_step is bracketed by
+ * CUDA events on the solver's stream and credited with its algorithmic bytes
+ * (matrix values and column ids once, each vector entry once).
+ * fvs_profile_enable clears the records.  fvs_profile_read waits for the
+ * stream, then writes up to max_records aggregates (host memory) and sets
+ * *n_records to the number of kernel classes seen.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  char name[48];      /* kernel@matrix, e.g. "spmv@pressure"               */
+  int64_t launches;
+  double total_ms;    /* summed event time of the launches                 */
+  double bytes;       /* summed algorithmic bytes of the launches          */
+} fvs_kernel_time;
+fvs_status fvs_profile_enable(fvs_solver solver, int on);
+fvs_status fvs_profile_read(fvs_solver solver, fvs_kernel_time* out, int32_t max_records, int32_t* n_records);
+
+/* Current simulated time and step count. */
+fvs_status fvs_get_time(fvs_solver solver, double* time, int64_t* steps);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FVS_H */

@@ -1,0 +1,71 @@
+// Aggregation algebraic multigrid for the pressure system (Section 2.5: the
+// paper preconditions its Krylov solver with BoomerAMG; this GPU-native
+// replacement aggregates by a parallel maximal independent set on the strong
+// connections, builds Galerkin coarse operators with piecewise-constant
+// transfers, and solves the coarsest level densely with one pinned unknown
+// per singular connected part -- the disjoint liquid pockets of Section 2.5).
+#pragma once
+
+#include <memory>
+#include <vector>
+
+#include "la.cuh"
+#include "scan.cuh"
+
+namespace fvs {
+
+struct AmgLevel {
+  Ell own;              // coarse operator (levels >= 1)
+  const Ell* A = nullptr;
+  DBuf<double> dinv;    // 1 / diagonal
+  DBuf<float> dinvf;
+  DBuf<int32_t> agg;    // row -> aggregate (row of the next level)
+  DBuf<int32_t> mptr, midx;   // members of each aggregate of the next level (CSR)
+  DBuf<double> b, x, y, r;    // V-cycle work
+  DBuf<float> bf, xf, yf, rf; // FP32 V-cycle work
+  int64_t n = 0;
+};
+
+struct AmgOptions {
+  double theta = 0.08;     // strength threshold
+  double omega = 0.7;      // Jacobi damping
+  double coarse_scale = 1.0;
+  int max_levels = 20;
+  int coarsest = 256;      // stop coarsening at or below this size
+  int npre = 1, npost = 1;
+  bool fp32 = false;       // V-cycle in single precision
+};
+
+struct Amg : Precond {
+  AmgOptions opt;
+  std::vector<std::unique_ptr<AmgLevel>> lv;
+  int nc = 0;                    // coarsest size
+  DBuf<double> Ainv;             // [nc*nc] pinned inverse of the coarsest operator
+  DBuf<float> Ainvf;
+  DBuf<int32_t> clab;            // coarsest component labels
+  DBuf<uint8_t> csing;           // per component: 1 if singular (row sums zero)
+  DBuf<int32_t> fine_lab;        // labels of the fine rows
+  int ncomp = 0;
+  std::vector<uint8_t> sing_host;
+  DBuf<double> csum, ccnt;       // per-component sums / counts (fine)
+  DBuf<double> cpart;            // block partials for component sums
+  ScanWork sw;
+  bool ready = false;
+
+  fvs_status setup(cudaStream_t s, const Ell& A);
+  fvs_status apply(cudaStream_t s, const double* r, double* z) override;
+  // subtract the component mean on every singular component (fine level)
+  fvs_status project(cudaStream_t s, double* v);
+  int levels() const { return (int)lv.size(); }
+
+ private:
+  fvs_status vcycle(cudaStream_t s, int l, const double* b, double* y);
+  fvs_status coarsest_setup(cudaStream_t s);
+};
+
+struct AmgProjector : Projector {
+  Amg* amg = nullptr;
+  fvs_status apply(cudaStream_t s, double* v) override { return amg->project(s, v); }
+};
+
+}  // namespace fvs

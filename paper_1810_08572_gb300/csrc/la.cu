@@ -1,0 +1,395 @@
+// Sparse linear algebra kernels and Krylov drivers (Section 2.5: the paper
+// uses AMG-preconditioned Krylov solvers; these are the GPU-native ones).
+#include "la.cuh"
+
+namespace fvs {
+
+static constexpr int RB = 256;  // threads per reduction block
+
+// ---------------------------------------------------------------------------
+// SpMV and residual (ELL, one thread per row, slot-major coalesced loads)
+// ---------------------------------------------------------------------------
+__global__ void k_spmv(int64_t n, int w, const int32_t* __restrict__ col, const double* __restrict__ val,
+                       const double* __restrict__ x, double* __restrict__ y,
+                       const double* __restrict__ dextra) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = dextra ? dextra[i] * x[i] : 0.0;
+    for (int k = 0; k < w; ++k) {
+      const int64_t e = (int64_t)k * n + i;
+      acc = fma(val[e], x[col[e]], acc);
+    }
+    y[i] = acc;
+  }
+}
+
+__global__ void k_residual(int64_t n, int w, const int32_t* __restrict__ col, const double* __restrict__ val,
+                           const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ r,
+                           const double* __restrict__ dextra) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = dextra ? dextra[i] * x[i] : 0.0;
+    for (int k = 0; k < w; ++k) {
+      const int64_t e = (int64_t)k * n + i;
+      acc = fma(val[e], x[col[e]], acc);
+    }
+    r[i] = b[i] - acc;
+  }
+}
+
+fvs_status spmv(cudaStream_t s, const Ell& A, const double* x, double* y, const double* dextra) {
+  if (A.n == 0) return FVS_OK;
+  ProfScope ps(&A, "spmv", (double)A.n * (12.0 * A.w + 16.0 + (dextra ? 8.0 : 0.0)), s);
+  k_spmv<<<stride_grid(A.n, 256), 256, 0, s>>>(A.n, A.w, A.col, A.val, x, y, dextra); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
+fvs_status residual(cudaStream_t s, const Ell& A, const double* x, const double* b, double* r,
+                    const double* dextra) {
+  if (A.n == 0) return FVS_OK;
+  ProfScope ps(&A, "residual", (double)A.n * (12.0 * A.w + 24.0 + (dextra ? 8.0 : 0.0)), s);
+  k_residual<<<stride_grid(A.n, 256), 256, 0, s>>>(A.n, A.w, A.col, A.val, x, b, r, dextra); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic reductions: fixed grid, block partials, single-block final sum
+// ---------------------------------------------------------------------------
+__global__ void k_dot2_part(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                            const double* __restrict__ c, const double* __restrict__ d, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    s0 = fma(a[i], b[i], s0);
+    if (c) s1 = fma(c[i], d[i], s1);
+  }
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0;
+    part[gridDim.x + blockIdx.x] = s1;
+  }
+}
+
+__global__ void k_maxdiff2_part(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                                const double* __restrict__ c, const double* __restrict__ d, double* __restrict__ part) {
+  __shared__ double sh[32];
+  double s0 = 0.0, s1 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    s0 = fmax(s0, fabs(a[i] - b[i]));
+    if (c) s1 = fmax(s1, fabs(c[i] - d[i]));
+  }
+  s0 = block_max(s0, sh);
+  s1 = block_max(s1, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = s0;
+    part[gridDim.x + blockIdx.x] = s1;
+  }
+}
+
+// Final sum of partials into slots; mode 1 = max.  Before overwriting s0,
+// the previous value is moved to s0_old (if >= 0): the Krylov drivers keep
+// rho_{k-1} that way without a separate launch.
+__global__ void k_final2(int nb, const double* __restrict__ part, double* __restrict__ sc, int s0, int s1,
+                         int s0_old, int mode) {
+  __shared__ double sh[32];
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    if (mode) {
+      a = fmax(a, part[i]);
+      b = fmax(b, part[nb + i]);
+    } else {
+      a += part[i];
+      b += part[nb + i];
+    }
+  }
+  if (mode) {
+    a = block_max(a, sh);
+    b = block_max(b, sh);
+  } else {
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+  }
+  if (threadIdx.x == 0) {
+    if (s0_old >= 0) sc[s0_old] = sc[s0];
+    sc[s0] = a;
+    if (s1 >= 0) sc[s1] = b;
+  }
+}
+
+fvs_status Reducer::init() {
+  blocks = 2 * sm_count();
+  if (blocks > 1024) blocks = 1024;
+  FVS_TRY(part.alloc(2 * (size_t)blocks));
+  FVS_TRY(sc.alloc(S_NSLOT));
+  FVS_TRY(sc.zero(0));
+  if (!host) FVS_CUDA(cudaMallocHost(&host, S_NSLOT * sizeof(double)));
+  return FVS_OK;
+}
+
+fvs_status Reducer::dot(cudaStream_t s, int64_t n, const double* x, const double* y, int slot) {
+  k_dot2_part<<<blocks, RB, 0, s>>>(n, x, y, nullptr, nullptr, part); FVS_COUNT_LAUNCH();
+  k_final2<<<1, 1024, 0, s>>>(blocks, part, sc, slot, -1, -1, 0); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
+fvs_status Reducer::dot2(cudaStream_t s, int64_t n, const double* a, const double* b, const double* c,
+                         const double* d, int s0, int s1) {
+  k_dot2_part<<<blocks, RB, 0, s>>>(n, a, b, c, d, part); FVS_COUNT_LAUNCH();
+  k_final2<<<1, 1024, 0, s>>>(blocks, part, sc, s0, s1, -1, 0); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
+fvs_status Reducer::max_abs_diff2(cudaStream_t s, int64_t n, const double* a, const double* b,
+                                  const double* c, const double* d, int s0, int s1) {
+  k_maxdiff2_part<<<blocks, RB, 0, s>>>(n, a, b, c, d, part); FVS_COUNT_LAUNCH();
+  k_final2<<<1, 1024, 0, s>>>(blocks, part, sc, s0, s1, -1, 1); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
+fvs_status Reducer::fetch(cudaStream_t s) {
+  FVS_CUDA(cudaMemcpyAsync(host, sc.p, S_NSLOT * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FVS_CUDA(cudaStreamSynchronize(s));
+  return FVS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// vector kernels
+// ---------------------------------------------------------------------------
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+__global__ void k_copy(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  GRID_STRIDE(i, n) b[i] = a[i];
+}
+__global__ void k_fill(int64_t n, double v, double* __restrict__ a) {
+  GRID_STRIDE(i, n) a[i] = v;
+}
+fvs_status vcopy(cudaStream_t s, int64_t n, const double* a, double* b) {
+  if (n <= 0) return FVS_OK;
+  k_copy<<<stride_grid(n, 256), 256, 0, s>>>(n, a, b); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+fvs_status vfill(cudaStream_t s, int64_t n, double v, double* a) {
+  if (n <= 0) return FVS_OK;
+  k_fill<<<stride_grid(n, 256), 256, 0, s>>>(n, v, a); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
+__global__ void k_jacobi_apply(int64_t n, const double* __restrict__ diag, const double* __restrict__ dextra,
+                               const double* __restrict__ r, double* __restrict__ z) {
+  GRID_STRIDE(i, n) {
+    const double d = diag[i] + (dextra ? dextra[i] : 0.0);
+    z[i] = r[i] / d;
+  }
+}
+
+fvs_status JacobiPrecond::apply(cudaStream_t s, const double* r, double* z) {
+  if (A->n == 0) return FVS_OK;
+  k_jacobi_apply<<<stride_grid(A->n, 256), 256, 0, s>>>(A->n, A->diag, dextra, r, z); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
+fvs_status KrylovWork::ensure(int64_t n) {
+  const size_t m = (size_t)n + 1;
+  FVS_TRY(r.alloc(m)); FVS_TRY(rh.alloc(m)); FVS_TRY(p.alloc(m)); FVS_TRY(ph.alloc(m));
+  FVS_TRY(v.alloc(m)); FVS_TRY(sv.alloc(m)); FVS_TRY(sh.alloc(m)); FVS_TRY(t.alloc(m));
+  FVS_TRY(z.alloc(m)); FVS_TRY(q.alloc(m));
+  return FVS_OK;
+}
+
+// safe quotient for Krylov scalars (a breakdown shows up as a stalled residual)
+__device__ __forceinline__ double sdiv(double a, double b) { return b != 0.0 ? a / b : 0.0; }
+
+// BiCGStab: p = r + beta (p - omega v), beta = (rho/rho_old)(alpha/omega)
+__global__ void k_bicg_p(int64_t n, const double* __restrict__ sc, const double* __restrict__ r,
+                         const double* __restrict__ v, double* __restrict__ p, int first) {
+  const double beta = first ? 0.0 : sdiv(sc[S_RHO], sc[S_RHO_OLD]) * sdiv(sc[S_ALPHA], sc[S_OMEGA]);
+  const double om = sc[S_OMEGA];
+  GRID_STRIDE(i, n) p[i] = first ? r[i] : r[i] + beta * (p[i] - om * v[i]);
+}
+// s = r - alpha v, alpha = rho / (rh . v)
+__global__ void k_bicg_s(int64_t n, const double* __restrict__ sc, const double* __restrict__ r,
+                         const double* __restrict__ v, double* __restrict__ sv) {
+  const double alpha = sdiv(sc[S_RHO], sc[S_RV]);
+  GRID_STRIDE(i, n) sv[i] = r[i] - alpha * v[i];
+}
+// x += alpha ph + omega sh ; r = s - omega t
+__global__ void k_bicg_xr(int64_t n, double* __restrict__ sc, const double* __restrict__ ph,
+                          const double* __restrict__ sh, const double* __restrict__ sv,
+                          const double* __restrict__ t, double* __restrict__ x, double* __restrict__ r) {
+  const double alpha = sdiv(sc[S_RHO], sc[S_RV]);
+  const double omega = sdiv(sc[S_TS], sc[S_TT]);
+  GRID_STRIDE(i, n) {
+    x[i] += alpha * ph[i] + omega * sh[i];
+    r[i] = sv[i] - omega * t[i];
+  }
+}
+// alpha and omega are kept for the next iteration's beta by a one-thread
+// launch after the update (the update kernel itself still reads rho/rv, ts/tt)
+__global__ void k_store_ao(double* __restrict__ sc) {
+  sc[S_ALPHA] = sdiv(sc[S_RHO], sc[S_RV]);
+  sc[S_OMEGA] = sdiv(sc[S_TS], sc[S_TT]);
+}
+
+static inline bool bad(double v) { return !(v == v) || v > 1e300 || v < -1e300; }
+
+fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, const double* dextra,
+                    Precond& M, const double* b, double* x, double rtol, int maxit, Projector* proj,
+                    SolveResult& res) {
+  const int64_t n = A.n;
+  res = SolveResult();
+  if (n == 0) {
+    res.converged = true;
+    return FVS_OK;
+  }
+  FVS_TRY(w.ensure(n));
+  const int grid = stride_grid(n, 256);
+  FVS_TRY(residual(s, A, x, b, w.r, dextra));
+  if (proj) FVS_TRY(proj->apply(s, w.r));
+  FVS_TRY(vcopy(s, n, w.r, w.rh));
+  // ||b|| of the (projected) right side
+  if (proj) {
+    FVS_TRY(vcopy(s, n, b, w.q));
+    FVS_TRY(proj->apply(s, w.q));
+    FVS_TRY(red.dot2(s, n, w.q, w.q, w.r, w.r, S_BB, S_RR));
+  } else {
+    FVS_TRY(red.dot2(s, n, b, b, w.r, w.r, S_BB, S_RR));
+  }
+  FVS_TRY(red.fetch(s));
+  double bnorm = sqrt(red.host[S_BB]);
+  if (bnorm == 0.0) bnorm = 1.0;
+  double rn = sqrt(red.host[S_RR]);
+  res.relres = rn / bnorm;
+  if (res.relres <= rtol) {
+    res.converged = true;
+    return FVS_OK;
+  }
+  for (int it = 0; it < maxit; ++it) {
+    // rho = rh . r (previous rho moved to rho_old by the final kernel)
+    k_dot2_part<<<red.blocks, RB, 0, s>>>(n, w.rh, w.r, nullptr, nullptr, red.part); FVS_COUNT_LAUNCH();
+    k_final2<<<1, 1024, 0, s>>>(red.blocks, red.part, red.sc, S_RHO, -1, S_RHO_OLD, 0); FVS_COUNT_LAUNCH();
+    k_bicg_p<<<grid, 256, 0, s>>>(n, red.sc, w.r, w.v, w.p, it == 0); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+    FVS_TRY(M.apply(s, w.p, w.ph));
+    FVS_TRY(spmv(s, A, w.ph, w.v, dextra));
+    if (proj) FVS_TRY(proj->apply(s, w.v));
+    FVS_TRY(red.dot(s, n, w.rh, w.v, S_RV));
+    k_bicg_s<<<grid, 256, 0, s>>>(n, red.sc, w.r, w.v, w.sv); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+    FVS_TRY(M.apply(s, w.sv, w.sh));
+    FVS_TRY(spmv(s, A, w.sh, w.t, dextra));
+    if (proj) FVS_TRY(proj->apply(s, w.t));
+    FVS_TRY(red.dot2(s, n, w.t, w.sv, w.t, w.t, S_TS, S_TT));
+    k_bicg_xr<<<grid, 256, 0, s>>>(n, red.sc, w.ph, w.sh, w.sv, w.t, x, w.r); FVS_COUNT_LAUNCH();
+    k_store_ao<<<1, 1, 0, s>>>(red.sc); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+    FVS_TRY(red.dot(s, n, w.r, w.r, S_RR));
+    FVS_TRY(red.fetch(s));
+    rn = sqrt(red.host[S_RR]);
+    res.iters = it + 1;
+    res.relres = rn / bnorm;
+    if (bad(rn)) return FVS_OK;
+    if (res.relres <= rtol) {
+      res.converged = true;
+      break;
+    }
+    // restart on breakdown of the shadow residual
+    if (red.host[S_TT] == 0.0 || red.host[S_RV] == 0.0) {
+      FVS_TRY(residual(s, A, x, b, w.r, dextra));
+      if (proj) FVS_TRY(proj->apply(s, w.r));
+      FVS_TRY(vcopy(s, n, w.r, w.rh));
+    }
+  }
+  // recompute the true residual (the recursive one drifts)
+  FVS_TRY(residual(s, A, x, b, w.r, dextra));
+  if (proj) FVS_TRY(proj->apply(s, w.r));
+  FVS_TRY(red.dot(s, n, w.r, w.r, S_RR));
+  FVS_TRY(red.fetch(s));
+  res.relres = sqrt(red.host[S_RR]) / bnorm;
+  res.converged = res.relres <= rtol * 10.0 && !bad(res.relres);
+  return FVS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// preconditioned CG (symmetric systems)
+// ---------------------------------------------------------------------------
+__global__ void k_cg_xr(int64_t n, const double* __restrict__ sc, const double* __restrict__ p,
+                        const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r) {
+  const double alpha = sdiv(sc[S_RZ], sc[S_PQ]);
+  GRID_STRIDE(i, n) {
+    x[i] += alpha * p[i];
+    r[i] -= alpha * q[i];
+  }
+}
+__global__ void k_cg_p(int64_t n, const double* __restrict__ sc, const double* __restrict__ z,
+                       double* __restrict__ p, int first) {
+  const double beta = first ? 0.0 : sdiv(sc[S_RZ], sc[S_RZ_OLD]);
+  GRID_STRIDE(i, n) p[i] = first ? z[i] : z[i] + beta * p[i];
+}
+
+fvs_status pcg(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, Precond& M, const double* b,
+               double* x, double rtol, int maxit, Projector* proj, SolveResult& res) {
+  const int64_t n = A.n;
+  res = SolveResult();
+  if (n == 0) {
+    res.converged = true;
+    return FVS_OK;
+  }
+  FVS_TRY(w.ensure(n));
+  const int grid = stride_grid(n, 256);
+  FVS_TRY(residual(s, A, x, b, w.r, nullptr));
+  if (proj) FVS_TRY(proj->apply(s, w.r));
+  if (proj) {
+    FVS_TRY(vcopy(s, n, b, w.q));
+    FVS_TRY(proj->apply(s, w.q));
+    FVS_TRY(red.dot2(s, n, w.q, w.q, w.r, w.r, S_BB, S_RR));
+  } else {
+    FVS_TRY(red.dot2(s, n, b, b, w.r, w.r, S_BB, S_RR));
+  }
+  FVS_TRY(red.fetch(s));
+  double bnorm = sqrt(red.host[S_BB]);
+  if (bnorm == 0.0) bnorm = 1.0;
+  res.relres = sqrt(red.host[S_RR]) / bnorm;
+  if (res.relres <= rtol) {
+    res.converged = true;
+    return FVS_OK;
+  }
+  for (int it = 0; it < maxit; ++it) {
+    FVS_TRY(M.apply(s, w.r, w.z));
+    if (proj) FVS_TRY(proj->apply(s, w.z));
+    k_dot2_part<<<red.blocks, RB, 0, s>>>(n, w.r, w.z, nullptr, nullptr, red.part); FVS_COUNT_LAUNCH();
+    k_final2<<<1, 1024, 0, s>>>(red.blocks, red.part, red.sc, S_RZ, -1, S_RZ_OLD, 0); FVS_COUNT_LAUNCH();
+    k_cg_p<<<grid, 256, 0, s>>>(n, red.sc, w.z, w.p, it == 0); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+    FVS_TRY(spmv(s, A, w.p, w.q, nullptr));
+    FVS_TRY(red.dot(s, n, w.p, w.q, S_PQ));
+    k_cg_xr<<<grid, 256, 0, s>>>(n, red.sc, w.p, w.q, x, w.r); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+    FVS_TRY(red.dot(s, n, w.r, w.r, S_RR));
+    FVS_TRY(red.fetch(s));
+    const double rn = sqrt(red.host[S_RR]);
+    res.iters = it + 1;
+    res.relres = rn / bnorm;
+    if (bad(rn)) return FVS_OK;
+    if (res.relres <= rtol) {
+      res.converged = true;
+      break;
+    }
+  }
+  FVS_TRY(residual(s, A, x, b, w.r, nullptr));
+  if (proj) FVS_TRY(proj->apply(s, w.r));
+  FVS_TRY(red.dot(s, n, w.r, w.r, S_RR));
+  FVS_TRY(red.fetch(s));
+  res.relres = sqrt(red.host[S_RR]) / bnorm;
+  res.converged = res.relres <= rtol * 10.0 && !bad(res.relres);
+  return FVS_OK;
+}
+
+}  // namespace fvs

@@ -1,0 +1,103 @@
+// Sparse linear algebra of the solver: ELL matrices, SpMV, deterministic
+// reductions, Jacobi, and the Krylov drivers (BiCGStab, CG).
+#pragma once
+
+#include "common.cuh"
+
+namespace fvs {
+
+// ELL matrix stored slot-major: entry k of row i at [k*n + i], so that one
+// thread per row reads consecutive addresses across a warp.  Unused slots
+// hold col = i and val = 0.
+struct Ell {
+  int64_t n = 0;
+  int w = 0;
+  DBuf<int32_t> col;
+  DBuf<double> val;
+  DBuf<double> diag;   // diagonal (Jacobi)
+  DBuf<float> valf;    // FP32 copies for the mixed-precision V-cycle
+  DBuf<float> diagf;
+  fvs_status alloc(int64_t rows, int width) {
+    n = rows;
+    w = width;
+    FVS_TRY(col.alloc((size_t)rows * width + 1));
+    FVS_TRY(val.alloc((size_t)rows * width + 1));
+    FVS_TRY(diag.alloc((size_t)rows + 1));
+    return FVS_OK;
+  }
+};
+
+// Scalar slots of the Krylov drivers (device memory).
+enum Slot {
+  S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_RV, S_TS, S_TT, S_RR, S_BB, S_RZ, S_RZ_OLD, S_PQ,
+  S_TMP0, S_TMP1, S_NSLOT
+};
+
+// Reduction scratch owned by a solver: block partials + scalar slots +
+// pinned host mirror.
+struct Reducer {
+  int blocks = 0;
+  DBuf<double> part;   // [2*blocks]
+  DBuf<double> sc;     // [S_NSLOT]
+  double* host = nullptr;  // pinned [S_NSLOT]
+  fvs_status init();
+  ~Reducer() { if (host) cudaFreeHost(host); }
+  // out[slot] = x . y  (deterministic: fixed blocks, fixed order)
+  fvs_status dot(cudaStream_t s, int64_t n, const double* x, const double* y, int slot);
+  // two dots in one pass: sc[s0] = a.b, sc[s1] = c.d
+  fvs_status dot2(cudaStream_t s, int64_t n, const double* a, const double* b,
+                  const double* c, const double* d, int s0, int s1);
+  fvs_status max_abs_diff2(cudaStream_t s, int64_t n, const double* a, const double* b,
+                           const double* c, const double* d, int s0, int s1);
+  fvs_status fetch(cudaStream_t s);   // copies sc -> host and waits
+};
+
+// y = A x (+ dextra .* x if dextra)
+fvs_status spmv(cudaStream_t s, const Ell& A, const double* x, double* y, const double* dextra = nullptr);
+// r = b - A x (- dextra .* x)
+fvs_status residual(cudaStream_t s, const Ell& A, const double* x, const double* b, double* r,
+                    const double* dextra = nullptr);
+
+// Preconditioner interface: z = M^-1 r.
+struct Precond {
+  virtual ~Precond() {}
+  virtual fvs_status apply(cudaStream_t s, const double* r, double* z) = 0;
+};
+
+// Jacobi: z = r / (diag + dextra)
+struct JacobiPrecond : Precond {
+  const Ell* A = nullptr;
+  const double* dextra = nullptr;
+  fvs_status apply(cudaStream_t s, const double* r, double* z) override;
+};
+
+struct KrylovWork {
+  DBuf<double> r, rh, p, ph, v, sv, sh, t, z, q;
+  fvs_status ensure(int64_t n);
+};
+
+struct SolveResult {
+  int iters = 0;
+  double relres = 0.0;
+  bool converged = false;
+};
+
+// Right-preconditioned BiCGStab on A x = b (x holds the initial guess).
+// proj: optional projection applied to the right side and residual updates
+// (null-space handling of the pressure system).
+struct Projector {
+  virtual ~Projector() {}
+  virtual fvs_status apply(cudaStream_t s, double* v) = 0;
+};
+
+fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, const double* dextra,
+                    Precond& M, const double* b, double* x, double rtol, int maxit,
+                    Projector* proj, SolveResult& res);
+fvs_status pcg(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, Precond& M,
+               const double* b, double* x, double rtol, int maxit, Projector* proj, SolveResult& res);
+
+// small vector kernels
+fvs_status vcopy(cudaStream_t s, int64_t n, const double* a, double* b);
+fvs_status vfill(cudaStream_t s, int64_t n, double v, double* a);
+
+}  // namespace fvs

@@ -1,0 +1,975 @@
+// The fractional step of Section 2.2 on the GPU:
+//  1. tags from T^n (S / LM, Section 2.4), compaction of the LM cells
+//  2. momentum predictor u* on LM cells (Eq. 6; rows and columns of solid
+//     cells deleted, Section 2.4.1)
+//  3. pressure Poisson equation on the flowing LM cells (Eq. 9) with face
+//     cases 1/2/3 and smeared gradient coefficients (Section 2.4.2, Eq. 15-16),
+//     solved by AMG-preconditioned CG/BiCGStab (Section 2.5)
+//  4. face flux and cell velocity correction (Eq. 8, Eq. 17)
+//  5. energy with latent heat on all cells (Eq. 4, Eq. 18-20, Section 2.4.4)
+//  6. liquidus/solidus crossing times for the microstructure relations (Eq. 22-23)
+#include <algorithm>
+#include <cmath>
+
+#include "solver.cuh"
+
+namespace fvs {
+
+#define GS(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+struct Mat {
+  double rho, k, cp, L, Ts, Tl, mu, beta, Tref, g0, g1, g2, C, eps;
+};
+static Mat mat_of(const fvs_props& p) {
+  const fvs_material& m = p.mat;
+  return Mat{m.rho, m.k, m.cp, m.latent, m.T_sol, m.T_liq, m.mu, m.beta, m.T_ref, m.g[0], m.g[1], m.g[2],
+             m.darcy_C, m.darcy_eps};
+}
+
+__device__ __forceinline__ double solid_fraction(double T, double Ts, double Tl) {
+  return fmin(fmax((Tl - T) / (Tl - Ts), 0.0), 1.0);
+}
+__device__ __forceinline__ double solid_fraction_slope(double T, double Ts, double Tl) {
+  return (T >= Ts && T <= Tl) ? -1.0 / (Tl - Ts) : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// 1. tags and compaction
+// ---------------------------------------------------------------------------
+__global__ void k_tag(int64_t Nc, const double* T, double Ts, uint8_t* lm, int32_t* flag, double* u, double* uold) {
+  GS(c, Nc) {
+    const bool l = T[c] > Ts;
+    lm[c] = l;
+    flag[c] = l;
+    if (!l) {
+      for (int d = 0; d < 3; ++d) {
+        u[d * Nc + c] = 0.0;
+        uold[d * Nc + c] = 0.0;
+      }
+    }
+  }
+}
+__global__ void k_compact(int64_t Nc, const uint8_t* lm, const int32_t* excl, int32_t* map, int32_t* act) {
+  GS(c, Nc) {
+    if (lm[c]) {
+      map[c] = excl[c];
+      act[excl[c]] = (int32_t)c;
+    } else {
+      map[c] = -1;
+    }
+  }
+}
+// faces with a solid owner (and walls) carry no flux; mark cells with a flowing face
+__global__ void k_faces_open(int64_t Nf, const int32_t* own, const int32_t* nei, const uint8_t* lm, double* F,
+                             double* Fold, uint8_t* flow) {
+  GS(f, Nf) {
+    const int32_t o = own[f], q = nei[f];
+    const bool open = q >= 0 && lm[o] && lm[q];
+    if (!open) {
+      F[f] = 0.0;
+      Fold[f] = 0.0;
+    } else {
+      flow[o] = 1;
+      flow[q] = 1;
+    }
+  }
+}
+__global__ void k_ppe_cells(int64_t Nc, const uint8_t* lm, const uint8_t* flow, uint8_t* ppe) {
+  GS(c, Nc) ppe[c] = lm[c] && flow[c];
+}
+__global__ void k_vertex_nonppe(int64_t Nv, const int32_t* vptr, const int32_t* vidx, const uint8_t* ppe, int32_t* nS) {
+  GS(v, Nv) {
+    int n = 0;
+    for (int32_t e = vptr[v]; e < vptr[v + 1]; ++e) n += ppe[vidx[e]] ? 0 : 1;
+    nS[v] = n;
+  }
+}
+// Section 2.4.2: 0 wall, 1 no solid neighbour, 2 solid neighbour only, 3 solid owner
+__global__ void k_face_case(int64_t Nf, const int32_t* own, const int32_t* nei, const int32_t* fv, const uint8_t* lm,
+                            const int32_t* nS, uint8_t* fcase) {
+  GS(f, Nf) {
+    const int32_t o = own[f], q = nei[f];
+    uint8_t c;
+    if (q < 0) c = 0;
+    else if (!(lm[o] && lm[q])) c = 3;
+    else {
+      int s = 0;
+      for (int k = 0; k < 4; ++k) s += nS[fv[k * Nf + f]];
+      c = s > 0 ? 2 : 1;
+    }
+    fcase[f] = c;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2. momentum predictor (Eq. 6)
+// ---------------------------------------------------------------------------
+__global__ void k_mom_matrix(int64_t nact, int64_t Nc, int W, const int32_t* act, const int32_t* map,
+                             const int32_t* Lcol, const double* Lval, const double* V, const double* fs, Mat m,
+                             double dt, int32_t* col, double* val, double* diag) {
+  GS(r, nact) {
+    const int32_t c = act[r];
+    const double f = fs[c];
+    const double D = m.C * f * f / ((1.0 - f) * (1.0 - f) * (1.0 - f) + m.eps);
+    const double dterm = (m.rho / dt + D) * V[c];
+    for (int k = 0; k < W; ++k) {
+      const int32_t j = Lcol[(int64_t)k * Nc + c];
+      const double a = Lval[(int64_t)k * Nc + c];
+      int32_t cc = (int32_t)r;
+      double v = 0.0;
+      if (j == c) {
+        v = dterm - 0.5 * m.mu * a;
+        diag[r] = v;
+      } else if (map[j] >= 0) {
+        cc = map[j];
+        v = -0.5 * m.mu * a;
+      }
+      col[(int64_t)k * nact + r] = cc;
+      val[(int64_t)k * nact + r] = v;
+    }
+  }
+}
+
+__global__ void k_mom_rhs(int64_t nact, int64_t Nc, int W, const int32_t* act, const int32_t* cf, const int8_t* cfs,
+                          const int32_t* own, const int32_t* nei, const double* F, const double* Fold,
+                          const double* u, const double* uold, const int32_t* Lcol, const double* Lval,
+                          const double* V, const double* T, Mat m, double dt, double* rhs, double* x) {
+  GS(r, nact) {
+    const int32_t c = act[r];
+    double cn[3] = {0, 0, 0}, co[3] = {0, 0, 0};
+    for (int s = 0; s < 6; ++s) {
+      const int32_t f = cf[s * Nc + c];
+      const int32_t o = own[f], q = nei[f];
+      if (q < 0) continue;
+      const double sg = (double)cfs[s * Nc + c];
+      const double fn = sg * F[f], fo = sg * Fold[f];
+      for (int d = 0; d < 3; ++d) {
+        cn[d] += fn * 0.5 * (u[d * Nc + o] + u[d * Nc + q]);
+        co[d] += fo * 0.5 * (uold[d * Nc + o] + uold[d * Nc + q]);
+      }
+    }
+    double lu[3] = {0, 0, 0};
+    for (int k = 0; k < W; ++k) {
+      const int32_t j = Lcol[(int64_t)k * Nc + c];
+      const double a = Lval[(int64_t)k * Nc + c];
+      for (int d = 0; d < 3; ++d) lu[d] += a * u[d * Nc + j];
+    }
+    const double Vc = V[c];
+    const double bf = -m.rho * m.beta * (T[c] - m.Tref) * Vc;
+    const double g[3] = {m.g0, m.g1, m.g2};
+    for (int d = 0; d < 3; ++d) {
+      rhs[d * nact + r] = m.rho * Vc / dt * u[d * Nc + c] - m.rho * (1.5 * cn[d] - 0.5 * co[d]) +
+                          0.5 * m.mu * lu[d] + bf * g[d];
+      x[d * nact + r] = u[d * Nc + c];
+    }
+  }
+}
+
+__global__ void k_scatter3(int64_t Nc, int64_t nact, const int32_t* map, const double* x, double* full) {
+  GS(c, Nc) {
+    const int32_t r = map[c];
+    for (int d = 0; d < 3; ++d) full[d * Nc + c] = r >= 0 ? x[d * nact + r] : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3. pressure system K = -A on LM cells (Eq. 9, Section 2.4.2)
+// ---------------------------------------------------------------------------
+struct PpeCtx {
+  int64_t Nc, Nf, nact;
+  int W;
+  const int32_t *act, *map, *cf, *own, *nei, *fv, *vc_ptr, *vc_idx, *nb, *nnb, *fnb, *nfnb, *nS;
+  const int8_t* cfs;
+  const uint8_t *ppe, *fcase;
+  const double *cd, *ce, *cz, *Pbval;
+  const int32_t* Pbcol;
+  double rho;
+  int WF;
+};
+
+__device__ __forceinline__ void ppe_vertex(const PpeCtx& x, int64_t c, int nn, int32_t v, double coef, double* acc) {
+  const int32_t lo = x.vc_ptr[v], hi = x.vc_ptr[v + 1];
+  const double share = coef / (double)(hi - lo);
+  for (int32_t e = lo; e < hi; ++e) {
+    const int32_t j = x.vc_idx[e];
+    if (!x.ppe[j]) continue;            // deleted column (solid or non-flowing)
+    const int p = find_sorted(x.nb + c, x.Nc, nn, j);
+    if (p >= 0) acc[p] += share;
+  }
+}
+
+__global__ void k_ppe_matrix(PpeCtx x, int32_t* col, double* val, double* diag, int* err) {
+  double acc[FVS_MAX_NB];
+  GS(r, x.nact) {
+    const int32_t c = x.act[r];
+    const int nn = x.nnb[c];
+    if (!x.ppe[c]) {
+      // an LM cell with no flowing face: p = 0 (identity row)
+      for (int k = 0; k < x.W; ++k) {
+        col[(int64_t)k * x.nact + r] = (int32_t)r;
+        val[(int64_t)k * x.nact + r] = k == 0 ? 1.0 : 0.0;
+      }
+      diag[r] = 1.0;
+      continue;
+    }
+    bool modified = false;
+    for (int s = 0; s < 6; ++s) {
+      const uint8_t fc = x.fcase[x.cf[s * x.Nc + c]];
+      modified |= (fc == 2 || fc == 3);
+    }
+    if (!modified) {
+      // unchanged row: the base coefficients, renumbered
+      double dg = 0.0;
+      for (int k = 0; k < x.W; ++k) {
+        const int32_t j = x.Pbcol[(int64_t)k * x.Nc + c];
+        const double a = -x.Pbval[(int64_t)k * x.Nc + c] / x.rho;
+        const int32_t mj = x.map[j];
+        int32_t cc = (int32_t)r;
+        double v = 0.0;
+        if (k < nn) {
+          if (mj >= 0) { cc = mj; v = a; }
+          else if (a != 0.0) atomicOr(err, 1);
+        }
+        if (j == c) dg = v;
+        col[(int64_t)k * x.nact + r] = cc;
+        val[(int64_t)k * x.nact + r] = v;
+      }
+      diag[r] = dg;
+      continue;
+    }
+    // re-assembly from the faces (Section 2.4.2, step 3)
+    for (int k = 0; k < nn; ++k) acc[k] = 0.0;
+    for (int s = 0; s < 6; ++s) {
+      const int32_t f = x.cf[s * x.Nc + c];
+      const uint8_t fc = x.fcase[f];
+      if (fc != 1 && fc != 2) continue;
+      const double sg = (double)x.cfs[s * x.Nc + c];
+      const int32_t o = x.own[f], q = x.nei[f];
+      { const int pq = find_sorted(x.nb + c, x.Nc, nn, q); if (pq >= 0) acc[pq] += sg * x.cd[f]; else atomicOr(err, 8); }
+      { const int po = find_sorted(x.nb + c, x.Nc, nn, o); if (po >= 0) acc[po] -= sg * x.cd[f]; else atomicOr(err, 8); }
+      const int32_t v1 = x.fv[f], v2 = x.fv[x.Nf + f], v3 = x.fv[2 * x.Nf + f], v4 = x.fv[3 * x.Nf + f];
+      const double ce = sg * x.ce[f], cz = sg * x.cz[f];
+      ppe_vertex(x, c, nn, v3, ce, acc);
+      ppe_vertex(x, c, nn, v1, -ce, acc);
+      ppe_vertex(x, c, nn, v4, cz, acc);
+      ppe_vertex(x, c, nn, v2, -cz, acc);
+      if (fc == 2) {
+        // Eq. 16: the deleted neighbours' coefficients, spread equally over
+        // the remaining members of N(f)
+        auto frac = [&](int32_t v) {
+          return (double)x.nS[v] / (double)(x.vc_ptr[v + 1] - x.vc_ptr[v]);
+        };
+        const double sdel = ce * (frac(v3) - frac(v1)) + cz * (frac(v4) - frac(v2));
+        const int nf = x.nfnb[f];
+        int nrem = 0;
+        for (int k = 0; k < nf; ++k) nrem += x.ppe[x.fnb[(int64_t)k * x.Nf + f]] ? 1 : 0;
+        const double add = sdel / (double)nrem;
+        for (int k = 0; k < nf; ++k) {
+          const int32_t j = x.fnb[(int64_t)k * x.Nf + f];
+          if (!x.ppe[j]) continue;
+          const int p = find_sorted(x.nb + c, x.Nc, nn, j);
+          if (p >= 0) acc[p] += add; else atomicOr(err, 2);
+        }
+      }
+    }
+    double dg = 0.0;
+    for (int k = 0; k < x.W; ++k) {
+      int32_t cc = (int32_t)r;
+      double v = 0.0;
+      if (k < nn) {
+        const int32_t j = x.nb[(int64_t)k * x.Nc + c];
+        const double a = -acc[k] / x.rho;
+        const int32_t mj = x.map[j];
+        if (mj >= 0 && x.ppe[j]) { cc = mj; v = a; }
+        else if (a != 0.0) atomicOr(err, 4);
+        if (j == c) dg = v;
+      }
+      col[(int64_t)k * x.nact + r] = cc;
+      val[(int64_t)k * x.nact + r] = v;
+    }
+    diag[r] = dg;
+  }
+}
+
+// b = (1/dt) sum over flowing faces of sigma A n . (u*_C1 + u*_C2)/2;  K rhs = -b
+__global__ void k_ppe_rhs(int64_t nact, int64_t Nc, int64_t Nf, const int32_t* act, const uint8_t* ppe,
+                          const int32_t* cf, const int8_t* cfs, const uint8_t* fcase, const int32_t* own,
+                          const int32_t* nei, const double* A, const double* nrm, const double* us, double dt,
+                          const double* p, double* rhs, double* x) {
+  GS(r, nact) {
+    const int32_t c = act[r];
+    double b = 0.0;
+    if (ppe[c]) {
+      for (int s = 0; s < 6; ++s) {
+        const int32_t f = cf[s * Nc + c];
+        const uint8_t fc = fcase[f];
+        if (fc != 1 && fc != 2) continue;
+        const int32_t o = own[f], q = nei[f];
+        double un = 0.0;
+        for (int d = 0; d < 3; ++d) un += nrm[d * Nf + f] * 0.5 * (us[d * Nc + o] + us[d * Nc + q]);
+        b += (double)cfs[s * Nc + c] * A[f] * un;
+      }
+      b /= dt;
+    }
+    rhs[r] = -b;
+    x[r] = ppe[c] ? p[c] : 0.0;
+  }
+}
+
+__global__ void k_scatter1(int64_t Nc, const int32_t* map, const uint8_t* ppe, const double* x, double* full) {
+  GS(c, Nc) {
+    const int32_t r = map[c];
+    full[c] = (r >= 0 && ppe[c]) ? x[r] : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 4. correction (Eq. 17 and the cell-centred gradient of Section 2.4.3)
+// ---------------------------------------------------------------------------
+__global__ void k_vertex_p(int64_t Nv, const int32_t* vptr, const int32_t* vidx, const uint8_t* ppe, const double* p,
+                           const int32_t* nS, double* pv, double* fS) {
+  GS(v, Nv) {
+    const int32_t lo = vptr[v], hi = vptr[v + 1];
+    double s = 0.0;
+    for (int32_t e = lo; e < hi; ++e) {
+      const int32_t j = vidx[e];
+      if (ppe[j]) s += p[j];
+    }
+    const double n = (double)(hi - lo);
+    pv[v] = s / n;
+    fS[v] = (double)nS[v] / n;
+  }
+}
+
+__global__ void k_face_correct(int64_t Nf, int64_t Nc, const int32_t* own, const int32_t* nei, const int32_t* fv,
+                               const uint8_t* fcase, const int32_t* fnb, const int32_t* nfnb, const uint8_t* ppe,
+                               const double* p, const double* pv, const double* fS, const double* A,
+                               const double* nrm, const double* cd, const double* ce, const double* cz,
+                               const double* Jinv, const double* us, double dt, double rho, double* Fnew,
+                               double* gradf) {
+  GS(f, Nf) {
+    const uint8_t fc = fcase[f];
+    if (fc != 1 && fc != 2) {
+      Fnew[f] = 0.0;
+      for (int d = 0; d < 3; ++d) gradf[d * Nf + f] = 0.0;
+      continue;
+    }
+    const int32_t o = own[f], q = nei[f];
+    const int32_t v1 = fv[f], v2 = fv[Nf + f], v3 = fv[2 * Nf + f], v4 = fv[3 * Nf + f];
+    const double dxi = p[q] - p[o];
+    double deta = pv[v3] - pv[v1];
+    double dzeta = pv[v4] - pv[v2];
+    if (fc == 2) {
+      // deleted neighbours take the mean of the remaining ones (Eq. 16)
+      const int nf = nfnb[f];
+      double s = 0.0;
+      int n = 0;
+      for (int k = 0; k < nf; ++k) {
+        const int32_t j = fnb[(int64_t)k * Nf + f];
+        if (ppe[j]) { s += p[j]; ++n; }
+      }
+      const double pbar = s / (double)n;
+      deta += (fS[v3] - fS[v1]) * pbar;
+      dzeta += (fS[v4] - fS[v2]) * pbar;
+    }
+    const double nd = cd[f] * dxi + ce[f] * deta + cz[f] * dzeta;   // A (n . grad p)
+    double un = 0.0;
+    for (int d = 0; d < 3; ++d) un += nrm[d * Nf + f] * 0.5 * (us[d * Nc + o] + us[d * Nc + q]);
+    Fnew[f] = A[f] * un - dt / rho * nd;
+    for (int d = 0; d < 3; ++d)
+      gradf[d * Nf + f] = Jinv[(3 * d + 0) * Nf + f] * dxi + Jinv[(3 * d + 1) * Nf + f] * deta +
+                          Jinv[(3 * d + 2) * Nf + f] * dzeta;
+  }
+}
+
+__global__ void k_cell_correct(int64_t Nc, int64_t Nf, const uint8_t* lm, const int32_t* cf, const uint8_t* fcase,
+                               const double* gradf, const double* us, double dt, double rho, double* unew) {
+  GS(c, Nc) {
+    if (!lm[c]) {
+      for (int d = 0; d < 3; ++d) unew[d * Nc + c] = 0.0;
+      continue;
+    }
+    double g[3] = {0, 0, 0};
+    int n = 0;
+    for (int s = 0; s < 6; ++s) {
+      const int32_t f = cf[s * Nc + c];
+      const uint8_t fc = fcase[f];
+      if (fc != 1 && fc != 2) continue;
+      ++n;
+      for (int d = 0; d < 3; ++d) g[d] += gradf[d * Nf + f];
+    }
+    for (int d = 0; d < 3; ++d)
+      unew[d * Nc + c] = us[d * Nc + c] - (n > 0 ? dt / rho * g[d] / (double)n : 0.0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 5. energy with latent heat (Eq. 4, Eq. 18-20)
+// ---------------------------------------------------------------------------
+__global__ void k_energy_base(int64_t Nc, int W, const int32_t* cf, const int8_t* cfs, const int32_t* own,
+                              const int32_t* nei, const double* F, const double* Fold, const double* T,
+                              const double* Told, const int32_t* Lcol, const double* Lval, const double* lT,
+                              const double* V, Mat m, double dt, double* base) {
+  GS(c, Nc) {
+    double cn = 0.0, co = 0.0;
+    for (int s = 0; s < 6; ++s) {
+      const int32_t f = cf[s * Nc + c];
+      const int32_t o = own[f], q = nei[f];
+      if (q < 0) continue;
+      const double sg = (double)cfs[s * Nc + c];
+      cn += sg * F[f] * 0.5 * (T[o] + T[q]);
+      co += sg * Fold[f] * 0.5 * (Told[o] + Told[q]);
+    }
+    double lt = 0.0;
+    for (int k = 0; k < W; ++k) lt += Lval[(int64_t)k * Nc + c] * T[Lcol[(int64_t)k * Nc + c]];
+    base[c] = m.rho * m.cp * V[c] / dt * T[c] - m.rho * m.cp * (1.5 * cn - 0.5 * co) + 0.5 * m.k * lt +
+              m.k * lT[c];
+  }
+}
+
+// source linearisation at the current iterate (Eq. 20): S_p, S_c
+__global__ void k_energy_lin(int64_t Nc, const double* V, Mat m, double dt, const double* Tm, const double* fsm,
+                             const double* fsn, const double* base, double* dextra, double* rhs, double* x) {
+  GS(c, Nc) {
+    const double t = Tm[c];
+    const double dfs = solid_fraction_slope(t, m.Ts, m.Tl);
+    const double a = m.rho * m.L * V[c] / dt;
+    const double Sp = a * dfs;
+    const double Sc = a * (fsm[c] - fsn[c] - dfs * t);
+    dextra[c] = m.rho * m.cp * V[c] / dt - Sp;
+    rhs[c] = base[c] + Sc;
+    x[c] = t;
+  }
+}
+
+// enthalpy-to-temperature inversion of the linearised update:
+// H = cp T_lin + L (1 - fs^m - dfs (T_lin - T^m)), T = H^-1(H), fs = fs(T)
+__global__ void k_energy_update(int64_t Nc, Mat m, const double* Tlin, const double* Tm, const double* fsm,
+                                double* Tnext, double* fsnext) {
+  GS(c, Nc) {
+    const double t = Tm[c];
+    const double dfs = solid_fraction_slope(t, m.Ts, m.Tl);
+    const double H = m.cp * Tlin[c] + m.L * (1.0 - fsm[c] - dfs * (Tlin[c] - t));
+    const double Hs = m.cp * m.Ts, Hl = m.cp * m.Tl + m.L;
+    double T;
+    if (H <= Hs) T = H / m.cp;
+    else if (H >= Hl) T = (H - m.L) / m.cp;
+    else T = m.Ts + (H - Hs) / (Hl - Hs) * (m.Tl - m.Ts);
+    Tnext[c] = T;
+    fsnext[c] = solid_fraction(T, m.Ts, m.Tl);
+  }
+}
+
+__global__ void k_count_u8(int64_t n, const uint8_t* a, int* out) {
+  int c = 0;
+  GS(i, n) c += a[i] ? 1 : 0;
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+  if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+__global__ void k_crossings(int64_t Nc, const double* Tn, const double* Tnew, double Ts, double Tl, double time,
+                            double dt, double* tliq, double* tsol) {
+  GS(c, Nc) {
+    const double a = Tn[c], b = Tnew[c];
+    if (tliq[c] < 0.0 && a > Tl && b <= Tl) tliq[c] = time + dt * (a - Tl) / (a - b);
+    if (tsol[c] < 0.0 && a > Ts && b <= Ts) tsol[c] = time + dt * (a - Ts) / (a - b);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// state set-up and queries
+// ---------------------------------------------------------------------------
+__global__ void k_init_state(int64_t Nc, const int32_t* cell_in, const double* Tin, double Tuni, const double* uin,
+                             Mat m, double* T, double* Told, double* fs, double* u, double* uold, double* p,
+                             double* tliq, double* tsol) {
+  GS(c, Nc) {
+    const int32_t o = cell_in[c];
+    const double t = Tin ? Tin[o] : Tuni;
+    T[c] = t;
+    Told[c] = t;
+    fs[c] = solid_fraction(t, m.Ts, m.Tl);
+    const bool solid = !(t > m.Ts);
+    for (int d = 0; d < 3; ++d) {
+      const double v = (uin && !solid) ? uin[3 * (int64_t)o + d] : 0.0;
+      u[d * Nc + c] = v;
+      uold[d * Nc + c] = v;
+    }
+    p[c] = 0.0;
+    tliq[c] = t <= m.Tl ? 0.0 : -1.0;
+    tsol[c] = t <= m.Ts ? 0.0 : -1.0;
+  }
+}
+
+__global__ void k_gather_out(int64_t n, int comps, const int32_t* to_in, const double* src, double* dst) {
+  GS(i, n) {
+    const int64_t o = to_in[i];
+    for (int d = 0; d < comps; ++d) dst[comps * o + d] = src[d * n + i];
+  }
+}
+__global__ void k_gather_u8(int64_t n, const int32_t* to_in, const uint8_t* src, double* dst) {
+  GS(i, n) dst[to_in[i]] = (double)src[i];
+}
+__global__ void k_qoi(int64_t Nc, const int32_t* to_in, const double* tliq, const double* tsol, double Ts, double Tl,
+                      double* dst) {
+  GS(c, Nc) {
+    const int64_t o = to_in[c];
+    double tf = __longlong_as_double(0x7ff8000000000000LL), cr = tf, lam = tf, ys = tf;
+    if (tliq[c] >= 0.0 && tsol[c] >= 0.0) {
+      tf = tsol[c] - tliq[c];
+      cr = (Tl - Ts) / tf;
+      lam = 39.4 * pow(cr, -0.317);          // Eq. 22 (micrometres)
+      ys = 59.0 / sqrt(lam) + 120.3;         // Eq. 23 (MPa)
+    }
+    dst[4 * o] = tf;
+    dst[4 * o + 1] = cr;
+    dst[4 * o + 2] = lam;
+    dst[4 * o + 3] = ys;
+  }
+}
+__global__ void k_scale_ell(int64_t n, int w, double a, const double* val, const double* diag, double* oval,
+                            double* odiag) {
+  GS(i, n) {
+    for (int k = 0; k < w; ++k) oval[(int64_t)k * n + i] = a * val[(int64_t)k * n + i];
+    odiag[i] = a * diag[i];
+  }
+}
+__global__ void k_copy_i(int64_t n, const int32_t* a, int32_t* b) {
+  GS(i, n) b[i] = a[i];
+}
+__global__ void k_rhs_in(int64_t nact, const int32_t* act, const uint8_t* ppe, const int32_t* cell_in,
+                         const double* rhs_in, double* rhs, double* x) {
+  GS(r, nact) {
+    const int32_t c = act[r];
+    rhs[r] = ppe[c] ? -rhs_in[cell_in[c]] : 0.0;
+    x[r] = 0.0;
+  }
+}
+__global__ void k_p_out(int64_t Nc, const int32_t* map, const uint8_t* ppe, const int32_t* cell_in, const double* x,
+                        double* out) {
+  GS(c, Nc) {
+    const int32_t r = map[c];
+    out[cell_in[c]] = (r >= 0 && ppe[c]) ? x[r] : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host orchestration
+// ---------------------------------------------------------------------------
+fvs_status solver_alloc(fvs_solver s) {
+  fvs_mesh m = s->mesh;
+  const int64_t Nc = m->Nc, Nf = m->Nf, Nv = m->Nv;
+  FVS_TRY(s->T.alloc(Nc)); FVS_TRY(s->Told.alloc(Nc)); FVS_TRY(s->Tnew.alloc(Nc));
+  FVS_TRY(s->fs.alloc(Nc)); FVS_TRY(s->fsnew.alloc(Nc));
+  FVS_TRY(s->u.alloc(3 * Nc)); FVS_TRY(s->uold.alloc(3 * Nc)); FVS_TRY(s->unew.alloc(3 * Nc));
+  FVS_TRY(s->ustar.alloc(3 * Nc));
+  FVS_TRY(s->F.alloc(Nf)); FVS_TRY(s->Fold.alloc(Nf)); FVS_TRY(s->Fnew.alloc(Nf));
+  FVS_TRY(s->p.alloc(Nc)); FVS_TRY(s->tliq.alloc(Nc)); FVS_TRY(s->tsol.alloc(Nc));
+  FVS_TRY(s->lm.alloc(Nc)); FVS_TRY(s->ppe.alloc(Nc)); FVS_TRY(s->flow.alloc(Nc)); FVS_TRY(s->fcase.alloc(Nf));
+  FVS_TRY(s->flag.alloc(Nc + 1)); FVS_TRY(s->excl.alloc(Nc + 1)); FVS_TRY(s->map.alloc(Nc));
+  FVS_TRY(s->act.alloc(Nc + 1)); FVS_TRY(s->nS.alloc(Nv));
+  FVS_TRY(s->pv.alloc(Nv)); FVS_TRY(s->fSv.alloc(Nv)); FVS_TRY(s->gradf.alloc(3 * Nf));
+  FVS_TRY(s->ebase.alloc(Nc)); FVS_TRY(s->erhs.alloc(Nc)); FVS_TRY(s->edx.alloc(Nc)); FVS_TRY(s->Tlin.alloc(Nc));
+  FVS_TRY(s->lT.alloc(Nc));
+  FVS_TRY(s->Tit.alloc(Nc)); FVS_TRY(s->fsit.alloc(Nc));
+  FVS_TRY(s->cnt.alloc(2));
+  FVS_TRY(s->red.init());
+  FVS_TRY(s->ustar.zero(s->stream));
+  FVS_TRY(s->fcase.zero(s->stream));
+  s->aproj.amg = &s->amg;
+  return FVS_OK;
+}
+
+fvs_status solver_set_properties(fvs_solver s, const fvs_props* p) {
+  fvs_mesh m = s->mesh;
+  if (p->n_patches < m->npatch || (p->n_patches > 0 && !p->bc)) {
+    set_error("props give %d wall patches, the mesh uses %d", p->n_patches, m->npatch);
+    return FVS_ERR_ARG;
+  }
+  const fvs_material& mt = p->mat;
+  if (!(mt.rho > 0 && mt.k > 0 && mt.cp > 0 && mt.T_liq > mt.T_sol && mt.mu >= 0 && mt.latent >= 0)) {
+    set_error("invalid material data");
+    return FVS_ERR_ARG;
+  }
+  s->props = *p;
+  s->bc.assign(p->bc, p->bc + p->n_patches);
+  s->props.bc = nullptr;
+  if (s->props.max_krylov_iters <= 0) s->props.max_krylov_iters = 500;
+  if (s->props.max_e_iters <= 0) s->props.max_e_iters = 40;
+  if (!(s->props.p_rtol > 0)) s->props.p_rtol = 1e-8;
+  if (!(s->props.mom_rtol > 0)) s->props.mom_rtol = 1e-10;
+  if (!(s->props.e_rtol > 0)) s->props.e_rtol = 1e-10;
+  if (!(s->props.e_tol_T > 0)) s->props.e_tol_T = 1e-8;
+  const int np = std::max(1, p->n_patches);
+  std::vector<int32_t> ht(np, 0);
+  std::vector<double> hT(np, 0.0);
+  for (int i = 0; i < p->n_patches; ++i) {
+    ht[i] = p->bc[i].type;
+    hT[i] = p->bc[i].T;
+  }
+  FVS_TRY(s->bc_type.alloc(np));
+  FVS_TRY(s->bc_T.alloc(np));
+  FVS_CUDA(cudaMemcpyAsync(s->bc_type.p, ht.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, s->stream));
+  FVS_CUDA(cudaMemcpyAsync(s->bc_T.p, hT.data(), np * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  FVS_TRY(assemble_temperature_operator(m, s->bc_type, s->bc_T, s->LT, s->lT, s->stream));
+  // Ke = -k/2 LT with the same pattern
+  FVS_TRY(s->Ke.alloc(m->Nc, m->W));
+  k_copy_i<<<stride_grid((int64_t)m->Nc * m->W, 256), 256, 0, s->stream>>>((int64_t)m->Nc * m->W, s->LT.col,
+                                                                            s->Ke.col); FVS_COUNT_LAUNCH();
+  k_scale_ell<<<stride_grid(m->Nc, 256), 256, 0, s->stream>>>(m->Nc, m->W, -0.5 * mt.k, s->LT.val, s->LT.diag,
+                                                             s->Ke.val, s->Ke.diag); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  s->have_props = true;
+  return solver_set_state(s, nullptr, nullptr, 0);
+}
+
+fvs_status solver_set_state(fvs_solver s, const double* T, const double* u, int on_device) {
+  if (!s->have_props) {
+    set_error("fvs_set_properties must come first");
+    return FVS_ERR_STATE;
+  }
+  fvs_mesh m = s->mesh;
+  const int64_t Nc = m->Nc;
+  cudaStream_t st = s->stream;
+  DBuf<double> dT, du;
+  const double* pT = T;
+  const double* pu = u;
+  if (T && !on_device) {
+    FVS_TRY(dT.alloc(Nc));
+    FVS_CUDA(cudaMemcpyAsync(dT.p, T, Nc * sizeof(double), cudaMemcpyHostToDevice, st));
+    pT = dT.p;
+  }
+  if (u && !on_device) {
+    FVS_TRY(du.alloc(3 * Nc));
+    FVS_CUDA(cudaMemcpyAsync(du.p, u, 3 * Nc * sizeof(double), cudaMemcpyHostToDevice, st));
+    pu = du.p;
+  }
+  const Mat mt = mat_of(s->props);
+  k_init_state<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, m->cell_in, pT, s->props.T_init, pu, mt, s->T, s->Told,
+                                                     s->fs, s->u, s->uold, s->p, s->tliq, s->tsol); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  FVS_TRY(s->F.zero(st)); FVS_TRY(s->Fold.zero(st)); FVS_TRY(s->Fnew.zero(st));
+  FVS_TRY(s->ustar.zero(st));
+  FVS_CUDA(cudaStreamSynchronize(st));
+  s->time = 0.0;
+  s->nstep = 0;
+  s->have_step = false;
+  return FVS_OK;
+}
+
+// tags, compaction and face cases for the current temperature
+static fvs_status classify(fvs_solver s) {
+  fvs_mesh m = s->mesh;
+  cudaStream_t st = s->stream;
+  const int64_t Nc = m->Nc, Nf = m->Nf, Nv = m->Nv;
+  const Mat mt = mat_of(s->props);
+  FVS_TRY(s->flag.zero(st));
+  k_tag<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, mt.Ts, s->lm, s->flag, s->u, s->uold); FVS_COUNT_LAUNCH();
+  FVS_TRY(exclusive_scan(st, s->sw, Nc + 1, s->flag, s->excl));
+  k_compact<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->lm, s->excl, s->map, s->act); FVS_COUNT_LAUNCH();
+  FVS_TRY(s->flow.zero(st));
+  k_faces_open<<<stride_grid(Nf, 256), 256, 0, st>>>(Nf, m->own, m->nei, s->lm, s->F, s->Fold, s->flow); FVS_COUNT_LAUNCH();
+  k_ppe_cells<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->lm, s->flow, s->ppe); FVS_COUNT_LAUNCH();
+  k_vertex_nonppe<<<stride_grid(Nv, 256), 256, 0, st>>>(Nv, m->vc_ptr, m->vc_idx, s->ppe, s->nS); FVS_COUNT_LAUNCH();
+  k_face_case<<<stride_grid(Nf, 256), 256, 0, st>>>(Nf, m->own, m->nei, m->fv, s->lm, s->nS, s->fcase); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  FVS_TRY(s->cnt.zero(st));
+  k_count_u8<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->ppe, s->cnt); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  int32_t na = 0;
+  int hc[2];
+  FVS_CUDA(cudaMemcpyAsync(&na, s->excl.p + Nc, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  FVS_CUDA(cudaMemcpyAsync(hc, s->cnt.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  FVS_CUDA(cudaStreamSynchronize(st));
+  s->nact = na;
+  s->nppe = hc[0];
+  return FVS_OK;
+}
+
+static PpeCtx ppe_ctx(fvs_solver s) {
+  fvs_mesh m = s->mesh;
+  PpeCtx x;
+  x.Nc = m->Nc; x.Nf = m->Nf; x.nact = s->nact; x.W = m->W; x.WF = m->WF;
+  x.act = s->act; x.map = s->map; x.cf = m->cf; x.own = m->own; x.nei = m->nei; x.fv = m->fv;
+  x.vc_ptr = m->vc_ptr; x.vc_idx = m->vc_idx; x.nb = m->nb; x.nnb = m->nnb; x.fnb = m->fnb; x.nfnb = m->nfnb;
+  x.nS = s->nS; x.cfs = m->cfs; x.ppe = s->ppe; x.fcase = s->fcase;
+  x.cd = m->cd; x.ce = m->ce; x.cz = m->cz; x.Pbval = m->Pb.val; x.Pbcol = m->Pb.col;
+  x.rho = s->props.mat.rho;
+  return x;
+}
+
+static fvs_status assemble_pressure(fvs_solver s) {
+  fvs_mesh m = s->mesh;
+  cudaStream_t st = s->stream;
+  FVS_TRY(s->K.alloc(s->nact, m->W));
+  DBuf<int> err;
+  FVS_TRY(err.alloc(1));
+  FVS_TRY(err.zero(st));
+  if (s->nact > 0) {
+    k_ppe_matrix<<<stride_grid(s->nact, 128, 4), 128, 0, st>>>(ppe_ctx(s), s->K.col, s->K.val, s->K.diag, err); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+  }
+  int h = 0;
+  FVS_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FVS_CUDA(cudaStreamSynchronize(st));
+  if (h) {
+    set_error("pressure assembly referenced a deleted column (flags 0x%x)", h);
+    return FVS_ERR_STATE;
+  }
+  // AMG hierarchy for the new active set (Section 2.5); on failure the
+  // solve falls back to single-grid Jacobi BiCGStab
+  s->amg_ok = false;
+  if (s->props.p_solver == FVS_PSOLVER_AMG && s->nact > 0) {
+    fvs_status r = s->amg.setup(st, s->K);
+    if (r == FVS_OK) {
+      s->amg_ok = true;
+      s->amg_levels = s->amg.levels();
+      s->ncomp = s->amg.ncomp;
+    } else if (r != FVS_ERR_NOT_CONVERGED) {
+      return r;
+    }
+  }
+  return FVS_OK;
+}
+
+// solve K x = rhs (compact) with the configured method; fills stats
+static fvs_status solve_pressure(fvs_solver s, double rtol, SolveResult& res, int& fallback) {
+  cudaStream_t st = s->stream;
+  fallback = 0;
+  const int maxit = s->props.max_krylov_iters;
+  if (s->amg_ok) {
+    if (s->mesh->orthogonal)
+      FVS_TRY(pcg(st, s->red, s->kw, s->K, s->amg, s->prhs, s->px, rtol, maxit, &s->aproj, res));
+    else
+      FVS_TRY(bicgstab(st, s->red, s->kw, s->K, nullptr, s->amg, s->prhs, s->px, rtol, maxit, &s->aproj, res));
+    if (res.converged) {
+      FVS_TRY(s->amg.project(st, s->px));
+      return FVS_OK;
+    }
+  }
+  // single-grid fallback (Section 2.5); the null space is handled by the
+  // AMG's component labels when they exist, else by a global mean
+  fallback = 1;
+  JacobiPrecond J;
+  J.A = &s->K;
+  Projector* pj = s->amg_ok ? (Projector*)&s->aproj : nullptr;
+  FVS_TRY(bicgstab(st, s->red, s->kw, s->K, nullptr, J, s->prhs, s->px, rtol, maxit * 4, pj, res));
+  if (pj) FVS_TRY(s->amg.project(st, s->px));
+  return FVS_OK;
+}
+
+fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
+  if (!s->have_props) {
+    set_error("fvs_set_properties must come first");
+    return FVS_ERR_STATE;
+  }
+  if (!(dt > 0)) {
+    set_error("dt must be positive");
+    return FVS_ERR_ARG;
+  }
+  fvs_mesh m = s->mesh;
+  cudaStream_t st = s->stream;
+  const int64_t Nc = m->Nc, Nf = m->Nf, Nv = m->Nv;
+  const Mat mt = mat_of(s->props);
+  fvs_step_stats S{};
+  fvs_status status = FVS_OK;
+
+  // 1. tags, compaction, face cases
+  FVS_TRY(classify(s));
+  const int64_t na = s->nact;
+  S.n_active = na;
+
+  // 2. momentum predictor
+  FVS_TRY(s->M.alloc(na, m->W));
+  FVS_TRY(s->mrhs.alloc(3 * na + 1));
+  FVS_TRY(s->mx.alloc(3 * na + 1));
+  if (na > 0) {
+    k_mom_matrix<<<stride_grid(na, 256), 256, 0, st>>>(na, Nc, m->W, s->act, s->map, m->Lu.col, m->Lu.val, m->V,
+                                                       s->fs, mt, dt, s->M.col, s->M.val, s->M.diag); FVS_COUNT_LAUNCH();
+    k_mom_rhs<<<stride_grid(na, 256), 256, 0, st>>>(na, Nc, m->W, s->act, m->cf, m->cfs, m->own, m->nei, s->F,
+                                                    s->Fold, s->u, s->uold, m->Lu.col, m->Lu.val, m->V, s->T, mt, dt,
+                                                    s->mrhs, s->mx); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+    JacobiPrecond J;
+    J.A = &s->M;
+    for (int d = 0; d < 3; ++d) {
+      SolveResult r;
+      FVS_TRY(bicgstab(st, s->red, s->kw, s->M, nullptr, J, s->mrhs.p + d * na, s->mx.p + d * na,
+                       s->props.mom_rtol, s->props.max_krylov_iters, nullptr, r));
+      S.mom_its += r.iters;
+      if (!r.converged) status = FVS_ERR_NOT_CONVERGED;
+    }
+  }
+  k_scatter3<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, na, s->map, s->mx, s->ustar); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+
+  // 3. pressure system
+  FVS_TRY(assemble_pressure(s));
+  FVS_TRY(s->prhs.alloc(na + 1));
+  FVS_TRY(s->px.alloc(na + 1));
+  if (na > 0) {
+    k_ppe_rhs<<<stride_grid(na, 256), 256, 0, st>>>(na, Nc, Nf, s->act, s->ppe, m->cf, m->cfs, s->fcase, m->own,
+                                                    m->nei, m->A, m->nrm, s->ustar, dt, s->p, s->prhs, s->px); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+    SolveResult r;
+    int fb = 0;
+    FVS_TRY(solve_pressure(s, s->props.p_rtol, r, fb));
+    S.p_its = r.iters;
+    S.p_relres = r.relres;
+    S.fallback = fb;
+    if (!r.converged) status = FVS_ERR_NOT_CONVERGED;
+  }
+  k_scatter1<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->map, s->ppe, s->px, s->p); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+
+  // 4. correction
+  k_vertex_p<<<stride_grid(Nv, 256), 256, 0, st>>>(Nv, m->vc_ptr, m->vc_idx, s->ppe, s->p, s->nS, s->pv, s->fSv); FVS_COUNT_LAUNCH();
+  k_face_correct<<<stride_grid(Nf, 256), 256, 0, st>>>(Nf, Nc, m->own, m->nei, m->fv, s->fcase, m->fnb, m->nfnb,
+                                                       s->ppe, s->p, s->pv, s->fSv, m->A, m->nrm, m->cd, m->ce,
+                                                       m->cz, m->Jinv, s->ustar, dt, mt.rho, s->Fnew, s->gradf); FVS_COUNT_LAUNCH();
+  k_cell_correct<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, Nf, s->lm, m->cf, s->fcase, s->gradf, s->ustar, dt,
+                                                       mt.rho, s->unew); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+
+  // 5. energy: linearised latent heat, inner solve, enthalpy inversion
+  k_energy_base<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, m->W, m->cf, m->cfs, m->own, m->nei, s->F, s->Fold, s->T,
+                                                      s->Told, s->LT.col, s->LT.val, s->lT, m->V, mt, dt, s->ebase); FVS_COUNT_LAUNCH();
+  FVS_TRY(vcopy(st, Nc, s->T, s->Tnew));
+  FVS_TRY(vcopy(st, Nc, s->fs, s->fsnew));
+  {
+    JacobiPrecond J;
+    J.A = &s->Ke;
+    J.dextra = s->edx;
+    // Tnew / fsnew hold the iterate m; Tlin the linear solution
+    DBuf<double>& Tm = s->Tnew;
+    DBuf<double>& fsm = s->fsnew;
+    int it = 0;
+    bool conv = false;
+    for (it = 1; it <= s->props.max_e_iters; ++it) {
+      k_energy_lin<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, m->V, mt, dt, Tm, fsm, s->fs, s->ebase, s->edx,
+                                                          s->erhs, s->Tlin); FVS_COUNT_LAUNCH();
+      FVS_LAUNCH_CHECK();
+      SolveResult r;
+      FVS_TRY(bicgstab(st, s->red, s->kw, s->Ke, s->edx, J, s->erhs, s->Tlin, s->props.e_rtol,
+                       s->props.max_krylov_iters, nullptr, r));
+      S.e_lin_its += r.iters;
+      if (!r.converged) status = FVS_ERR_NOT_CONVERGED;
+      // next iterate, then its change against the current one
+      k_energy_update<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, mt, s->Tlin, Tm, fsm, s->Tit, s->fsit); FVS_COUNT_LAUNCH();
+      FVS_LAUNCH_CHECK();
+      FVS_TRY(s->red.max_abs_diff2(st, Nc, s->Tit, Tm, s->fsit, fsm, S_TMP0, S_TMP1));
+      dswap(s->Tit, Tm);
+      dswap(s->fsit, fsm);
+      FVS_TRY(s->red.fetch(st));
+      if (s->red.host[S_TMP0] <= s->props.e_tol_T && s->red.host[S_TMP1] <= 1e-12) {
+        conv = true;
+        break;
+      }
+    }
+    S.e_its = std::min(it, s->props.max_e_iters);
+    if (!conv) status = FVS_ERR_NOT_CONVERGED;
+  }
+
+  // 6. crossing times, then rotate the time levels
+  k_crossings<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, s->Tnew, mt.Ts, mt.Tl, s->time, dt, s->tliq, s->tsol); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  dswap(s->Told, s->T);     // Told <- T^n
+  dswap(s->T, s->Tnew);     // T <- T^{n+1}
+  dswap(s->fs, s->fsnew);
+  dswap(s->uold, s->u);     // uold <- u^n
+  dswap(s->u, s->unew);     // u <- u^{n+1}
+  dswap(s->Fold, s->F);     // Fold <- F^n
+  dswap(s->F, s->Fnew);     // F <- F^{n+1}
+  FVS_CUDA(cudaStreamSynchronize(st));
+  s->time += dt;
+  s->nstep += 1;
+  s->have_step = true;
+
+  S.n_ppe = s->nppe;
+  S.n_components = s->amg_ok ? s->ncomp : -1;
+  S.amg_levels = s->amg_ok ? s->amg_levels : 0;
+  S.status = status;
+  s->last = S;
+  if (stats) *stats = S;
+  return status;
+}
+
+fvs_status solver_pressure_solve(fvs_solver s, const double* rhs, double* p_out, double rtol, int* iters,
+                                 double* relres) {
+  if (!s->have_step) {
+    set_error("fvs_pressure_solve needs the active set of a completed step");
+    return FVS_ERR_STATE;
+  }
+  fvs_mesh m = s->mesh;
+  cudaStream_t st = s->stream;
+  FVS_TRY(s->prhs.alloc(s->nact + 1));
+  FVS_TRY(s->px.alloc(s->nact + 1));
+  if (s->nact > 0) {
+    k_rhs_in<<<stride_grid(s->nact, 256), 256, 0, st>>>(s->nact, s->act, s->ppe, m->cell_in, rhs, s->prhs, s->px); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+  }
+  SolveResult r;
+  int fb = 0;
+  FVS_TRY(solve_pressure(s, rtol, r, fb));
+  k_p_out<<<stride_grid(m->Nc, 256), 256, 0, st>>>(m->Nc, s->map, s->ppe, m->cell_in, s->px, p_out); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  FVS_CUDA(cudaStreamSynchronize(st));
+  if (iters) *iters = r.iters;
+  if (relres) *relres = r.relres;
+  return r.converged ? FVS_OK : FVS_ERR_NOT_CONVERGED;
+}
+
+fvs_status solver_query(fvs_solver s, fvs_field f, double* dst, int64_t len, int on_device) {
+  fvs_mesh m = s->mesh;
+  cudaStream_t st = s->stream;
+  const int64_t Nc = m->Nc, Nf = m->Nf;
+  int64_t need = 0;
+  switch (f) {
+    case FVS_T: case FVS_FS: case FVS_P: case FVS_TAG: need = Nc; break;
+    case FVS_U: case FVS_USTAR: need = 3 * Nc; break;
+    case FVS_QOI: need = 4 * Nc; break;
+    case FVS_CROSS: need = 2 * Nc; break;
+    case FVS_FLUX: case FVS_FACE_CASE: need = Nf; break;
+    default: set_error("unknown field %d", (int)f); return FVS_ERR_ARG;
+  }
+  if (len < need) {
+    set_error("destination holds %lld values, field needs %lld", (long long)len, (long long)need);
+    return FVS_ERR_ARG;
+  }
+  DBuf<double> tmp;
+  double* out = dst;
+  if (!on_device) {
+    FVS_TRY(tmp.alloc(need));
+    out = tmp.p;
+  }
+  const int gc = stride_grid(Nc, 256), gf = stride_grid(Nf, 256);
+  const Mat mt = mat_of(s->props);
+  switch (f) {
+    case FVS_T: k_gather_out<<<gc, 256, 0, st>>>(Nc, 1, m->cell_in, s->T, out); break;
+    case FVS_FS: k_gather_out<<<gc, 256, 0, st>>>(Nc, 1, m->cell_in, s->fs, out); break;
+    case FVS_P: k_gather_out<<<gc, 256, 0, st>>>(Nc, 1, m->cell_in, s->p, out); break;
+    case FVS_U: k_gather_out<<<gc, 256, 0, st>>>(Nc, 3, m->cell_in, s->u, out); break;
+    case FVS_USTAR: k_gather_out<<<gc, 256, 0, st>>>(Nc, 3, m->cell_in, s->ustar, out); break;
+    case FVS_FLUX: k_gather_out<<<gf, 256, 0, st>>>(Nf, 1, m->face_in, s->F, out); break;
+    case FVS_TAG: k_gather_u8<<<gc, 256, 0, st>>>(Nc, m->cell_in, s->lm, out); break;
+    case FVS_FACE_CASE: k_gather_u8<<<gf, 256, 0, st>>>(Nf, m->face_in, s->fcase, out); break;
+    case FVS_QOI: k_qoi<<<gc, 256, 0, st>>>(Nc, m->cell_in, s->tliq, s->tsol, mt.Ts, mt.Tl, out); break;
+    case FVS_CROSS: {
+      DBuf<double> both;
+      FVS_TRY(both.alloc(2 * Nc));
+      FVS_CUDA(cudaMemcpyAsync(both.p, s->tliq.p, Nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      FVS_CUDA(cudaMemcpyAsync(both.p + Nc, s->tsol.p, Nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+      k_gather_out<<<gc, 256, 0, st>>>(Nc, 2, m->cell_in, both, out); FVS_COUNT_LAUNCH();
+      FVS_LAUNCH_CHECK();
+      FVS_CUDA(cudaStreamSynchronize(st));
+      break;
+    }
+    default: break;
+  }
+  if (f != FVS_CROSS) FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  if (!on_device) FVS_CUDA(cudaMemcpyAsync(dst, out, need * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FVS_CUDA(cudaStreamSynchronize(st));
+  return FVS_OK;
+}
+
+}  // namespace fvs

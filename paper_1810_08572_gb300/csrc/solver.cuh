@@ -1,0 +1,75 @@
+// Solver state and the time step (Section 2.2, steps 1-5).
+#pragma once
+
+#include "amg.cuh"
+#include "mesh.cuh"
+#include "scan.cuh"
+
+template <typename T>
+inline void dswap(fvs::DBuf<T>& a, fvs::DBuf<T>& b) {
+  T* p = a.p; size_t n = a.n;
+  a.p = b.p; a.n = b.n;
+  b.p = p; b.n = n;
+}
+
+struct fvs_solver_s {
+  fvs_mesh mesh = nullptr;
+  cudaStream_t stream = nullptr;
+  bool have_props = false;
+  bool have_step = false;     // tags / compact systems of a step exist
+  fvs_props props{};
+  std::vector<fvs_patch_bc> bc;
+  double time = 0.0;
+  int64_t nstep = 0;
+
+  // state (mesh numbering); vectors of 3 are stored component-major [3*Nc]
+  fvs::DBuf<double> T, Told, Tnew, fs, fsnew;
+  fvs::DBuf<double> u, uold, unew, ustar;
+  fvs::DBuf<double> F, Fold, Fnew;
+  fvs::DBuf<double> p, tliq, tsol;
+
+  // wall data and the energy operator (-k/2 times the unit operator)
+  fvs::DBuf<int32_t> bc_type;
+  fvs::DBuf<double> bc_T;
+  fvs::Ell LT;            // unit temperature operator
+  fvs::DBuf<double> lT;   // its constant part from fixed-temperature walls
+  fvs::Ell Ke;            // -k/2 LT
+
+  // active set
+  fvs::DBuf<uint8_t> lm, ppe, flow, fcase;
+  fvs::DBuf<int32_t> flag, excl, map, act, nS;
+  int64_t nact = 0, nppe = 0;
+  fvs::ScanWork sw;
+
+  // compact systems
+  fvs::Ell M;             // momentum predictor on LM cells
+  fvs::Ell K;             // pressure: K = -A on LM cells (identity rows for non-flowing)
+  fvs::DBuf<double> mrhs, mx;     // [3*nact]
+  fvs::DBuf<double> prhs, px;     // [nact]
+  fvs::DBuf<double> pv, fSv;      // vertex pressure sums / solid fractions [Nv]
+  fvs::DBuf<double> gradf;        // [3*Nf]
+
+  // energy work
+  fvs::DBuf<double> ebase, erhs, edx, Tlin, Tit, fsit;
+  fvs::DBuf<int> cnt;
+
+  fvs::Reducer red;
+  fvs::KrylovWork kw;
+  fvs::Amg amg;
+  fvs::AmgProjector aproj;
+  bool amg_ok = false;
+  int amg_levels = 0;
+  int ncomp = 0;
+  fvs_step_stats last{};
+  fvs::Prof prof;
+};
+
+namespace fvs {
+fvs_status solver_alloc(fvs_solver s);
+fvs_status solver_set_properties(fvs_solver s, const fvs_props* p);
+fvs_status solver_set_state(fvs_solver s, const double* T, const double* u, int on_device);
+fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* st);
+fvs_status solver_pressure_solve(fvs_solver s, const double* rhs, double* p_out, double rtol, int* iters,
+                                 double* relres);
+fvs_status solver_query(fvs_solver s, fvs_field f, double* dst, int64_t len, int on_device);
+}  // namespace fvs

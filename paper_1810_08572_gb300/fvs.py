@@ -1,0 +1,277 @@
+"""Thin ctypes binding of the C ABI in include/fvs.h.
+
+Argument marshalling only: every step of the method runs in the CUDA
+library libfvs.so.  The functions keep the C names (fvs_mesh_create,
+fvs_step, ...); ``Mesh`` and ``Solver`` are small conveniences that own the
+handles.  There is no CPU fallback: importing this module fails if the
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfvs.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -m paper_1810_08572_gb300.build)")
+_lib = C.CDLL(LIB_PATH)
+
+# status codes
+FVS_OK, FVS_ERR_ARG, FVS_ERR_MESH, FVS_ERR_CUDA, FVS_ERR_NOMEM, FVS_ERR_NOT_CONVERGED, \
+    FVS_ERR_TIMEOUT, FVS_ERR_STATE = range(8)
+STATUS = {0: "FVS_OK", 1: "FVS_ERR_ARG", 2: "FVS_ERR_MESH", 3: "FVS_ERR_CUDA", 4: "FVS_ERR_NOMEM",
+          5: "FVS_ERR_NOT_CONVERGED", 6: "FVS_ERR_TIMEOUT", 7: "FVS_ERR_STATE"}
+FVS_BC_ADIABATIC, FVS_BC_DIRICHLET = 0, 1
+FVS_PREC_FP64, FVS_PREC_MIXED = 0, 1
+FVS_PSOLVER_AMG, FVS_PSOLVER_JACOBI = 0, 1
+FIELDS = dict(T=0, FS=1, U=2, P=3, FLUX=4, TAG=5, QOI=6, USTAR=7, CROSS=8, FACE_CASE=9)
+
+
+class FvsError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {fvs_last_error()}")
+
+
+class fvs_material(C.Structure):
+    _fields_ = [("rho", C.c_double), ("k", C.c_double), ("cp", C.c_double), ("latent", C.c_double),
+                ("T_sol", C.c_double), ("T_liq", C.c_double), ("mu", C.c_double), ("beta", C.c_double),
+                ("T_ref", C.c_double), ("g", C.c_double * 3), ("darcy_C", C.c_double),
+                ("darcy_eps", C.c_double)]
+
+
+class fvs_patch_bc(C.Structure):
+    _fields_ = [("type", C.c_int32), ("T", C.c_double)]
+
+
+class fvs_props(C.Structure):
+    _fields_ = [("mat", fvs_material), ("n_patches", C.c_int32), ("bc", C.POINTER(fvs_patch_bc)),
+                ("T_init", C.c_double), ("p_rtol", C.c_double), ("mom_rtol", C.c_double),
+                ("e_rtol", C.c_double), ("e_tol_T", C.c_double), ("max_e_iters", C.c_int32),
+                ("max_krylov_iters", C.c_int32), ("precision", C.c_int32), ("p_solver", C.c_int32)]
+
+
+class fvs_step_stats(C.Structure):
+    _fields_ = [("n_active", C.c_int64), ("n_ppe", C.c_int64), ("mom_its", C.c_int32), ("p_its", C.c_int32),
+                ("e_its", C.c_int32), ("e_lin_its", C.c_int32), ("p_relres", C.c_double),
+                ("fallback", C.c_int32), ("n_components", C.c_int32), ("amg_levels", C.c_int32),
+                ("status", C.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fvs_mesh_info(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("n_faces", C.c_int64), ("n_nodes", C.c_int64),
+                ("n_interior_faces", C.c_int64), ("max_cell_neighbours", C.c_int32),
+                ("max_face_neighbours", C.c_int32), ("n_patches", C.c_int32), ("orthogonal", C.c_int32),
+                ("total_volume", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fvs_kernel_time(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("launches", C.c_int64), ("total_ms", C.c_double),
+                ("bytes", C.c_double)]
+
+
+_P = C.c_void_p
+_SIGS = {
+    "fvs_last_error": ([], C.c_char_p),
+    "fvs_version": ([], C.c_char_p),
+    "fvs_launch_count": ([], C.c_int64),
+    "fvs_mesh_create": ([_P, C.c_int64, _P, C.c_int64, _P, C.c_int64, _P, _P, C.c_int, _P, C.POINTER(_P)],
+                        C.c_int),
+    "fvs_mesh_destroy": ([_P], C.c_int),
+    "fvs_mesh_get_info": ([_P, C.POINTER(fvs_mesh_info)], C.c_int),
+    "fvs_mesh_geometry": ([_P, C.c_int, _P, C.c_int64], C.c_int),
+    "fvs_solver_create": ([_P, _P, C.POINTER(_P)], C.c_int),
+    "fvs_solver_destroy": ([_P], C.c_int),
+    "fvs_set_properties": ([_P, C.POINTER(fvs_props)], C.c_int),
+    "fvs_set_state": ([_P, _P, _P, C.c_int], C.c_int),
+    "fvs_step": ([_P, C.c_double, C.c_int32, C.POINTER(fvs_step_stats)], C.c_int),
+    "fvs_pressure_solve": ([_P, _P, _P, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double)], C.c_int),
+    "fvs_query_fields": ([_P, C.c_int, _P, C.c_int64, C.c_int], C.c_int),
+    "fvs_get_time": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
+    "fvs_profile_enable": ([_P, C.c_int], C.c_int),
+    "fvs_profile_read": ([_P, C.POINTER(fvs_kernel_time), C.c_int32, C.POINTER(C.c_int32)], C.c_int),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _res
+    globals()[_name] = _f
+EXPORTED = sorted(_SIGS)
+
+
+def fvs_last_error_str():
+    return _lib.fvs_last_error().decode()
+
+
+def fvs_last_error():   # noqa: F811  (string form for messages)
+    return _lib.fvs_last_error().decode()
+
+
+def check(status, where):
+    if status != FVS_OK:
+        raise FvsError(status, where)
+    return status
+
+
+def _ptr(a):
+    """Host numpy array or device tensor -> void pointer."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(C.c_void_p)
+    return C.c_void_p(a.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def make_props(p):
+    """fvs_props from the plain-dict settings of fvs_inputs.cases.props()."""
+    m = p["material"]
+    mat = fvs_material(m["rho"], m["k"], m["cp"], m["latent"], m["T_sol"], m["T_liq"], m["mu"], m["beta"],
+                       m["T_ref"], (C.c_double * 3)(*m["g"]), m["darcy_C"], m["darcy_eps"])
+    walls = p["walls"]
+    bcs = (fvs_patch_bc * max(1, len(walls)))(*[fvs_patch_bc(int(t), float(T)) for t, T in walls])
+    props = fvs_props(mat, len(walls), C.cast(bcs, C.POINTER(fvs_patch_bc)), p["T_init"], p["p_rtol"],
+                      p.get("mom_rtol", 1e-10), p.get("e_rtol", 1e-10), p.get("e_tol_T", 1e-8),
+                      int(p.get("max_e_iters", 40)), int(p.get("max_krylov_iters", 500)),
+                      int(p.get("precision", 0)), int(p.get("p_solver", 0)))
+    props._keep = bcs
+    return props
+
+
+class Mesh:
+    """Owns an fvs_mesh handle built from host arrays (see fvs_inputs.mesh)."""
+
+    def __init__(self, mesh, reorder=True, stream=None):
+        self.nodes = np.ascontiguousarray(mesh["nodes"], dtype=np.float64)
+        cells = np.ascontiguousarray(mesh["cells"], dtype=np.int32)
+        faces = np.ascontiguousarray(mesh["faces"], dtype=np.int32)
+        fcells = np.ascontiguousarray(mesh["face_cells"], dtype=np.int32)
+        patch = np.ascontiguousarray(mesh["patch"], dtype=np.int32)
+        h = C.c_void_p()
+        check(fvs_mesh_create(_ptr(self.nodes), len(self.nodes), _ptr(cells), len(cells), _ptr(faces),
+                              len(faces), _ptr(fcells), _ptr(patch), int(reorder), _stream_ptr(stream),
+                              C.byref(h)), "fvs_mesh_create")
+        self.h = h
+        info = fvs_mesh_info()
+        check(fvs_mesh_get_info(h, C.byref(info)), "fvs_mesh_get_info")
+        self.info = info.as_dict()
+        self.n_cells = info.n_cells
+        self.n_faces = info.n_faces
+
+    def geometry(self, which):
+        n = self.n_cells if which == 0 else self.n_faces
+        out = np.empty(n, dtype=np.float64)
+        check(fvs_mesh_geometry(self.h, which, _ptr(out), n), "fvs_mesh_geometry")
+        return out
+
+    def close(self):
+        if self.h:
+            fvs_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver:
+    """Owns an fvs_solver handle on a Mesh."""
+
+    def __init__(self, mesh, props, stream=None):
+        self.mesh = mesh
+        h = C.c_void_p()
+        check(fvs_solver_create(mesh.h, _stream_ptr(stream), C.byref(h)), "fvs_solver_create")
+        self.h = h
+        self.set_properties(props)
+
+    def set_properties(self, props):
+        self._props = make_props(props)
+        check(fvs_set_properties(self.h, C.byref(self._props)), "fvs_set_properties")
+
+    def set_state(self, T, u=None):
+        """T [n_cells], u [n_cells, 3] (host numpy or device tensors, input numbering)."""
+        on_dev = not isinstance(T, np.ndarray)
+        if not on_dev:
+            T = np.ascontiguousarray(T, dtype=np.float64)
+            u = None if u is None else np.ascontiguousarray(u, dtype=np.float64)
+        check(fvs_set_state(self.h, _ptr(T), _ptr(u), int(on_dev)), "fvs_set_state")
+
+    def step(self, dt, n=1, allow_not_converged=False):
+        st = fvs_step_stats()
+        r = fvs_step(self.h, float(dt), int(n), C.byref(st))
+        if r != FVS_OK and not (allow_not_converged and r == FVS_ERR_NOT_CONVERGED):
+            raise FvsError(r, "fvs_step")
+        return st.as_dict()
+
+    def query(self, name, out=None):
+        """Field in input numbering: host numpy array, or into a device tensor ``out``."""
+        f = FIELDS[name]
+        nc, nf = self.mesh.n_cells, self.mesh.n_faces
+        n = {0: nc, 1: nc, 2: 3 * nc, 3: nc, 4: nf, 5: nc, 6: 4 * nc, 7: 3 * nc, 8: 2 * nc, 9: nf}[f]
+        if out is None:
+            a = np.empty(n, dtype=np.float64)
+            check(fvs_query_fields(self.h, f, _ptr(a), n, 0), "fvs_query_fields")
+            if f in (2, 7):
+                a = a.reshape(nc, 3)
+            elif f == 6:
+                a = a.reshape(nc, 4)
+            elif f == 8:
+                a = a.reshape(nc, 2)
+            return a
+        check(fvs_query_fields(self.h, f, _ptr(out), out.numel(), 1), "fvs_query_fields")
+        return out
+
+    def pressure_solve(self, rhs, p_out, rtol):
+        """rhs, p_out: device tensors [n_cells] (input numbering)."""
+        it = C.c_int32()
+        rr = C.c_double()
+        r = fvs_pressure_solve(self.h, _ptr(rhs), _ptr(p_out), float(rtol), C.byref(it), C.byref(rr))
+        return r, it.value, rr.value
+
+    def profile(self, on=True):
+        check(fvs_profile_enable(self.h, int(on)), "fvs_profile_enable")
+
+    def profile_read(self):
+        recs = (fvs_kernel_time * 64)()
+        n = C.c_int32()
+        check(fvs_profile_read(self.h, recs, 64, C.byref(n)), "fvs_profile_read")
+        return [dict(name=r.name.decode(), launches=r.launches, total_ms=r.total_ms, bytes=r.bytes)
+                for r in recs[:min(n.value, 64)]]
+
+    def time(self):
+        t = C.c_double()
+        n = C.c_int64()
+        check(fvs_get_time(self.h, C.byref(t), C.byref(n)), "fvs_get_time")
+        return t.value, n.value
+
+    def close(self):
+        if self.h:
+            fvs_solver_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,150 @@
+"""GPU path against the CPU oracle, element by element, through the C ABI.
+
+Bar (FP64 path): <= 1e-10 relative after one step, <= 1e-6 K in temperature
+after 200 steps of the 32x32x4 cavity.  Relative errors are measured against
+the largest magnitude of each field.
+"""
+import numpy as np
+import pytest
+
+from fvs_inputs import box_mesh, cases
+from oracle.fv import Oracle
+from tests.helpers import frozen_corner_field, set_state
+
+pytestmark = [pytest.mark.gpu, pytest.mark.filterwarnings("ignore::RuntimeWarning")]
+
+TIGHT = dict(p_rtol=1e-13, mom_rtol=1e-14, e_rtol=1e-14, e_tol_T=1e-11, max_krylov_iters=2000)
+
+
+@pytest.fixture(scope="module")
+def fvs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1810_08572_gb300 import LIB_PATH, build
+    import os
+    if not os.path.exists(LIB_PATH):
+        build()
+    from paper_1810_08572_gb300 import fvs as f
+    return f
+
+
+def rel(a, b):
+    scale = np.abs(b).max()
+    return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
+
+
+def make_pair(fvs, mesh, props, T0=None, u0=None, reorder=True):
+    o = Oracle(mesh, props)
+    M = fvs.Mesh(mesh, reorder=reorder)
+    S = fvs.Solver(M, props)
+    if T0 is not None:
+        set_state(o, T0, u0)
+        S.set_state(T0, u0)
+    return o, M, S
+
+
+def compare(o, S, tol, fields=("T", "U", "P", "FLUX", "USTAR")):
+    ref = dict(T=o.T, U=o.u, P=o.p, FLUX=o.F, USTAR=o.u_star, FS=o.fs)
+    out = {}
+    for name in fields:
+        out[name] = rel(S.query(name), ref[name])
+    bad = {k: v for k, v in out.items() if not v <= tol}
+    assert not bad, out
+    return out
+
+
+def test_geometry_matches(fvs):
+    m = box_mesh(9, 7, 5, cases.CAVITY, jitter=0.2, jitter_seed=4, permute_seed=5)
+    o = Oracle(m, cases.props())
+    M = fvs.Mesh(m)
+    assert rel(M.geometry(0), o.g.V) < 1e-13
+    assert rel(M.geometry(1), o.g.Af) < 1e-13
+    assert M.info["orthogonal"] == 0
+    assert abs(M.info["total_volume"] - 0.1 * 0.1 * 0.0125) < 1e-15
+    M2 = fvs.Mesh(box_mesh(6, 5, 4, cases.CAVITY))
+    assert M2.info["orthogonal"] == 1 and M2.info["max_cell_neighbours"] == 27
+
+
+def test_one_step_cavity(fvs):
+    """32x32x4 cavity, cold x = 0 wall: one step from rest at 950 K."""
+    c = cases.config_small()
+    props = cases.props(**TIGHT)
+    o, M, S = make_pair(fvs, c["mesh"], props)
+    o.step(1e-3)
+    S.step(1e-3)
+    compare(o, S, 1e-10)
+
+
+@pytest.mark.parametrize("reorder", [True, False])
+def test_one_step_jittered_with_solid(fvs, reorder):
+    """Jittered, permuted 16x16x2 mesh with a frozen block and a lone solid
+    cell, a random initial velocity: every face case, cross diffusion,
+    smearing and renumbering are exercised."""
+    m = box_mesh(16, 16, 2, cases.CAVITY, jitter=0.2, jitter_seed=21, permute_seed=22)
+    T0 = frozen_corner_field(m)
+    rng = np.random.default_rng(3)
+    u0 = rng.normal(scale=2e-3, size=(len(T0), 3))
+    props = cases.props(**TIGHT)
+    o, M, S = make_pair(fvs, m, props, T0, u0, reorder=reorder)
+    o.step(1e-3)
+    st = S.step(1e-3)
+    assert st["n_active"] == int(o.lm.sum())
+    assert st["n_ppe"] == int(o.ppe.sum())
+    cases_gpu = S.query("FACE_CASE")
+    assert np.array_equal(cases_gpu.astype(int), o.case)
+    assert np.array_equal(S.query("TAG").astype(bool), o.lm)
+    compare(o, S, 1e-10)
+    # a second step uses the Adams-Bashforth history of the first
+    o.step(1e-3)
+    S.step(1e-3)
+    compare(o, S, 1e-10)
+
+
+def test_pressure_solve_matches_oracle(fvs):
+    """fvs_pressure_solve on the oracle's right side of the last step."""
+    import torch
+    m = box_mesh(12, 12, 3, cases.CAVITY, jitter=0.2, jitter_seed=31, permute_seed=32)
+    T0 = frozen_corner_field(m, seed=2)
+    rng = np.random.default_rng(5)
+    u0 = rng.normal(scale=2e-3, size=(len(T0), 3))
+    o, M, S = make_pair(fvs, m, cases.props(**TIGHT), T0, u0)
+    o.step(1e-3)
+    S.step(1e-3)
+    rhs = torch.tensor(o.b_ppe, dtype=torch.float64, device="cuda")
+    p = torch.zeros_like(rhs)
+    status, its, rr = S.pressure_solve(rhs, p, 1e-13)
+    assert status == 0 and rr <= 1e-12
+    assert rel(p.cpu().numpy(), o.p) < 1e-10
+
+
+def test_two_hundred_steps_cavity(fvs):
+    """The 32x32x4 configuration for its 200 steps: temperature within 1e-6 K."""
+    c = cases.config_small()
+    props = cases.props(**dict(TIGHT, p_rtol=1e-12))
+    o, M, S = make_pair(fvs, c["mesh"], props)
+    for _ in range(200):
+        o.step(1e-3)
+    S.step(1e-3, 200)
+    assert np.abs(S.query("T") - o.T).max() <= 1e-6
+    assert rel(S.query("U"), o.u) <= 1e-6
+    np.testing.assert_allclose(S.query("CROSS"), np.stack([o.t_liq, o.t_sol], 1), atol=1e-9)
+
+
+def test_crossings_and_microstructure(fvs):
+    """A small cavity cooled on all walls freezes within the run; per-cell
+    solidification times, cooling rates, SDAS and yield strength (Eq. 22-23)
+    follow the oracle's."""
+    m = box_mesh(8, 8, 2, (0.01, 0.01, 0.0025))
+    props = cases.props(walls=cases.all_walls(700.0), T_init=920.0, **TIGHT)
+    o, M, S = make_pair(fvs, m, props)
+    for _ in range(120):
+        o.step(2e-3)
+    S.step(2e-3, 120)
+    q = S.query("QOI")
+    ref = o.qoi()
+    done = np.isfinite(ref["t_f"])
+    assert done.sum() > 20
+    assert np.array_equal(np.isfinite(q[:, 0]), done)
+    for k, name in enumerate(("t_f", "cooling_rate", "sdas", "yield_strength")):
+        assert rel(q[done, k], ref[name][done]) < 1e-8, name
