@@ -3,6 +3,7 @@
 // V-cycle (damped Jacobi, piecewise-constant restriction / prolongation).
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 
 #include "amg.cuh"
 
@@ -337,56 +338,75 @@ __global__ void k_coarsest(int n, int w, const int32_t* col, const double* val, 
     const int i = e / n, j = e - i * n;
     Ainv[e] = M[(int64_t)i * n2 + n + j];
   }
+  __syncthreads();
+  // fold the projections onto zero-mean parts into the inverse:
+  // Ainv <- P Ainv P, P v = v - (mean of v on each singular part)
+  int* order = (int*)fac;           // rows grouped by part (n ints)
+  __shared__ int ncs;
+  if (threadIdx.x == 0) {
+    ncs = *ncomp_out;
+    int pos = 0;
+    for (int c = 0; c < ncs; ++c)
+      for (int i = 0; i < n; ++i)
+        if (lab[i] == c) order[pos++] = i;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {      // left: column j
+    int pos = 0;
+    for (int c = 0; c < ncs; ++c) {
+      int cnt = 0;
+      double sum = 0.0;
+      for (int q = pos; q < n && lab[order[q]] == c; ++q, ++cnt) sum += Ainv[(int64_t)order[q] * n + j];
+      if (sing[c]) {
+        const double m = sum / (double)cnt;
+        for (int q = pos; q < pos + cnt; ++q) Ainv[(int64_t)order[q] * n + j] -= m;
+      }
+      pos += cnt;
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {      // right: row i
+    int pos = 0;
+    for (int c = 0; c < ncs; ++c) {
+      int cnt = 0;
+      double sum = 0.0;
+      for (int q = pos; q < n && lab[order[q]] == c; ++q, ++cnt) sum += Ainv[(int64_t)i * n + order[q]];
+      if (sing[c]) {
+        const double m = sum / (double)cnt;
+        for (int q = pos; q < pos + cnt; ++q) Ainv[(int64_t)i * n + order[q]] -= m;
+      }
+      pos += cnt;
+    }
+  }
 }
 
-// y = P (Ainv (P b)), P = subtract the mean on singular parts (one block)
-__global__ void k_coarse_solve(int n, const double* Ainv, const int32_t* lab, const uint8_t* sing, int ncomp,
-                               const double* b, double* y, double scale) {
-  extern __shared__ double sh[];
-  double* rb = sh;            // [n]
-  double* cs = sh + n;        // [ncomp] sums
-  double* cc = cs + ncomp;    // [ncomp] counts
-  for (int i = threadIdx.x; i < n; i += blockDim.x) rb[i] = b[i];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < ncomp; ++c) { cs[c] = 0.0; cc[c] = 0.0; }
-    for (int i = 0; i < n; ++i) { cs[lab[i]] += rb[i]; cc[lab[i]] += 1.0; }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x)
-    if (sing[lab[i]]) rb[i] -= cs[lab[i]] / cc[lab[i]];
-  __syncthreads();
-  double* yy = y;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double a = 0.0;
-    for (int j = 0; j < n; ++j) a = fma(Ainv[(int64_t)i * n + j], rb[j], a);
-    yy[i] = a;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int c = 0; c < ncomp; ++c) cs[c] = 0.0;
-    for (int i = 0; i < n; ++i) cs[lab[i]] += yy[i];
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double a = yy[i];
-    if (sing[lab[i]]) a -= cs[lab[i]] / cc[lab[i]];
-    yy[i] = scale * a;
-  }
+// coarsest solve: y = Ainv b with the projections already folded into Ainv;
+// one warp per row, FP64 arithmetic whatever the vector type
+template <typename T>
+__global__ void k_coarse_solve(int n, const double* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= n) return;
+  double a = 0.0;
+  for (int j = lane; j < n; j += 32) a = fma(Ainv[(int64_t)row * n + j], (double)b[j], a);
+  a = warp_sum(a);
+  if (lane == 0) y[row] = (T)a;
 }
 
 // ---------------------------------------------------------------------------
 // V-cycle kernels
 // ---------------------------------------------------------------------------
-__global__ void k_jac0(int64_t n, double omega, const double* dinv, const double* b, double* x) {
+template <typename T>
+__global__ void k_jac0(int64_t n, T omega, const T* dinv, const T* b, T* x) {
   GS(i, n) x[i] = omega * dinv[i] * b[i];
 }
 // y = x + omega D^-1 (b - A x)
-__global__ void k_jac(int64_t n, int w, const int32_t* __restrict__ col, const double* __restrict__ val,
-                      double omega, const double* __restrict__ dinv, const double* __restrict__ b,
-                      const double* __restrict__ x, double* __restrict__ y) {
+template <typename T>
+__global__ void k_jac(int64_t n, int w, const int32_t* __restrict__ col, const T* __restrict__ val, T omega,
+                      const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
+                      T* __restrict__ y) {
   GS(i, n) {
-    double acc = 0.0;
+    T acc = 0;
     for (int k = 0; k < w; ++k) {
       const int64_t e = (int64_t)k * n + i;
       acc = fma(val[e], x[col[e]], acc);
@@ -394,15 +414,33 @@ __global__ void k_jac(int64_t n, int w, const int32_t* __restrict__ col, const d
     y[i] = x[i] + omega * dinv[i] * (b[i] - acc);
   }
 }
-__global__ void k_restrict(int64_t nc, const int32_t* mptr, const int32_t* midx, const double* r, double* bc) {
+template <typename T>
+__global__ void k_resid(int64_t n, int w, const int32_t* __restrict__ col, const T* __restrict__ val,
+                        const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r) {
+  GS(i, n) {
+    T acc = 0;
+    for (int k = 0; k < w; ++k) {
+      const int64_t e = (int64_t)k * n + i;
+      acc = fma(val[e], x[col[e]], acc);
+    }
+    r[i] = b[i] - acc;
+  }
+}
+template <typename T>
+__global__ void k_restrict(int64_t nc, const int32_t* mptr, const int32_t* midx, const T* r, T* bc) {
   GS(I, nc) {
-    double s = 0.0;
+    T s = 0;
     for (int32_t m = mptr[I]; m < mptr[I + 1]; ++m) s += r[midx[m]];
     bc[I] = s;
   }
 }
-__global__ void k_prolong(int64_t n, const int32_t* agg, const double* yc, double* x) {
-  GS(i, n) x[i] += yc[agg[i]];
+template <typename T>
+__global__ void k_prolong(int64_t n, const int32_t* agg, const T* yc, T scale, T* x) {
+  GS(i, n) x[i] += scale * yc[agg[i]];
+}
+template <typename A, typename B>
+__global__ void k_convert(int64_t n, const A* a, B* b) {
+  GS(i, n) b[i] = (B)a[i];
 }
 
 // label propagation down the hierarchy and per-component counts
@@ -454,9 +492,22 @@ static fvs_status read_int(cudaStream_t s, const int* d, int* h) {
   return FVS_OK;
 }
 
+static double env_num(const char* name, double dflt) {
+  const char* v = getenv(name);
+  return (v && *v) ? atof(v) : dflt;
+}
+
 fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
   ready = false;
   lv.clear();
+  opt.theta = env_num("FVS_AMG_THETA", opt.theta);
+  opt.omega = env_num("FVS_AMG_OMEGA", opt.omega);
+  opt.coarse_scale = env_num("FVS_AMG_SCALE", opt.coarse_scale);
+  opt.npre = (int)env_num("FVS_AMG_NPRE", opt.npre);
+  opt.npost = (int)env_num("FVS_AMG_NPOST", opt.npost);
+  opt.coarsest = (int)env_num("FVS_AMG_COARSEST", opt.coarsest);
+  if (opt.npre < 1) opt.npre = 1;
+  if (opt.npost < 1) opt.npost = 1;
   DBuf<int> err, cnt;
   FVS_TRY(err.alloc(1));
   FVS_TRY(cnt.alloc(2));
@@ -473,6 +524,7 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
     L->n = n;
     FVS_TRY(L->dinv.alloc(n + 1));
     FVS_TRY(L->b.alloc(n + 1)); FVS_TRY(L->x.alloc(n + 1)); FVS_TRY(L->y.alloc(n + 1)); FVS_TRY(L->r.alloc(n + 1));
+    FVS_TRY(L->t.alloc(n + 1));
     DBuf<double> mo;
     FVS_TRY(mo.alloc(n + 1));
     if (n > 0) {
@@ -555,6 +607,12 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
     }
   }
   FVS_TRY(coarsest_setup(s));
+  if (opt.fp32) FVS_TRY(setup_fp32(s));
+  if (getenv("FVS_DEBUG")) {
+    fprintf(stderr, "[fvs amg] levels %d:", (int)lv.size());
+    for (auto& L : lv) fprintf(stderr, " %lld(w%d)", (long long)L->n, L->A->w);
+    fprintf(stderr, " coarsest %d parts %d\n", nc, ncomp);
+  }
   ready = true;
   return FVS_OK;
 }
@@ -637,38 +695,85 @@ fvs_status Amg::project(cudaStream_t s, double* v) {
   return FVS_OK;
 }
 
-fvs_status Amg::vcycle(cudaStream_t s, int l, const double* b, double* y) {
+template <typename T>
+fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
   AmgLevel* L = lv[l].get();
   const Ell& A = *L->A;
   const int64_t n = L->n;
   if (n == 0) return FVS_OK;
   if (l + 1 == (int)lv.size()) {
-    const size_t sh = (size_t)(nc + 2 * ncomp + 2) * sizeof(double);
-    k_coarse_solve<<<1, 256, sh, s>>>(nc, Ainv, clab, csing, ncomp, b, y, 1.0); FVS_COUNT_LAUNCH();
+    k_coarse_solve<T><<<(nc + 7) / 8, 256, 0, s>>>(nc, Ainv.p, b, y); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
     return FVS_OK;
   }
   AmgLevel* C = lv[l + 1].get();
+  const bool f32 = sizeof(T) == 4;
+  const T* val = f32 ? (const T*)L->valf.p : (const T*)A.val.p;
+  const T* dinv = f32 ? (const T*)L->dinvf.p : (const T*)L->dinv.p;
+  T* xa = f32 ? (T*)L->xf.p : (T*)L->x.p;
+  T* xb = f32 ? (T*)L->tf.p : (T*)L->t.p;
+  T* r = f32 ? (T*)L->rf.p : (T*)L->r.p;
+  T* cb = f32 ? (T*)C->bf.p : (T*)C->b.p;
+  T* cy = f32 ? (T*)C->yf.p : (T*)C->y.p;
+  const double vb = (double)sizeof(T);
+  const double jac_bytes = (double)n * ((4.0 + vb) * A.w + 4.0 * vb);
   const int g = stride_grid(n, 256);
   {
-    ProfScope ps(L->A, "jacobi0", 24.0 * (double)n, s);
-    k_jac0<<<g, 256, 0, s>>>(n, opt.omega, L->dinv, b, L->x); FVS_COUNT_LAUNCH();
+    ProfScope ps(L->A, f32 ? "jacobi0_f32" : "jacobi0", 3.0 * vb * (double)n, s);
+    k_jac0<T><<<g, 256, 0, s>>>(n, (T)opt.omega, dinv, b, xa); FVS_COUNT_LAUNCH();
   }
-  FVS_TRY(residual(s, A, L->x, b, L->r));
-  k_restrict<<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, L->r, C->b); FVS_COUNT_LAUNCH();
-  FVS_LAUNCH_CHECK();
-  FVS_TRY(vcycle(s, l + 1, C->b, C->y));
-  k_prolong<<<g, 256, 0, s>>>(n, L->agg, C->y, L->x); FVS_COUNT_LAUNCH();
+  for (int k = 1; k < opt.npre; ++k) {
+    ProfScope ps(L->A, f32 ? "jacobi_f32" : "jacobi", jac_bytes, s);
+    k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xa, xb); FVS_COUNT_LAUNCH();
+    T* t = xa; xa = xb; xb = t;
+  }
   {
-    ProfScope ps(L->A, "jacobi", (double)n * (12.0 * A.w + 32.0), s);
-    k_jac<<<g, 256, 0, s>>>(n, A.w, A.col, A.val, opt.omega, L->dinv, b, L->x, y); FVS_COUNT_LAUNCH();
+    ProfScope ps(L->A, f32 ? "residual_f32" : "residual_vc", (double)n * ((4.0 + vb) * A.w + 3.0 * vb), s);
+    k_resid<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, xa, b, r); FVS_COUNT_LAUNCH();
+  }
+  k_restrict<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cb); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  FVS_TRY(vcycle_t<T>(s, l + 1, cb, cy));
+  k_prolong<T><<<g, 256, 0, s>>>(n, L->agg, cy, (T)opt.coarse_scale, xa); FVS_COUNT_LAUNCH();
+  for (int k = 0; k < opt.npost; ++k) {
+    T* out = (k == opt.npost - 1) ? y : xb;
+    ProfScope ps(L->A, f32 ? "jacobi_f32" : "jacobi", jac_bytes, s);
+    k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xa, out); FVS_COUNT_LAUNCH();
+    xb = xa;
+    xa = out;
   }
   FVS_LAUNCH_CHECK();
   return FVS_OK;
 }
 
 fvs_status Amg::apply(cudaStream_t s, const double* r, double* z) {
-  return vcycle(s, 0, r, z);
+  if (!opt.fp32) return vcycle_t<double>(s, 0, r, z);
+  // mixed precision: the V-cycle runs in FP32, the Krylov method around it in FP64
+  AmgLevel* L = lv[0].get();
+  const int64_t n = L->n;
+  k_convert<double, float><<<stride_grid(n, 256), 256, 0, s>>>(n, r, L->bf.p); FVS_COUNT_LAUNCH();
+  FVS_TRY(vcycle_t<float>(s, 0, L->bf.p, L->yf.p));
+  k_convert<float, double><<<stride_grid(n, 256), 256, 0, s>>>(n, L->yf.p, z); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
+// FP32 copies of the level operators and vectors (mixed precision)
+fvs_status Amg::setup_fp32(cudaStream_t s) {
+  for (auto& up : lv) {
+    AmgLevel* L = up.get();
+    const int64_t n = L->n;
+    const int64_t nz = n * (int64_t)L->A->w;
+    FVS_TRY(L->valf.alloc(nz + 1)); FVS_TRY(L->dinvf.alloc(n + 1));
+    FVS_TRY(L->bf.alloc(n + 1)); FVS_TRY(L->xf.alloc(n + 1)); FVS_TRY(L->yf.alloc(n + 1)); FVS_TRY(L->rf.alloc(n + 1));
+    FVS_TRY(L->tf.alloc(n + 1));
+    if (n > 0) {
+      k_convert<double, float><<<stride_grid(nz, 256), 256, 0, s>>>(nz, L->A->val.p, L->valf.p); FVS_COUNT_LAUNCH();
+      k_convert<double, float><<<stride_grid(n, 256), 256, 0, s>>>(n, L->dinv.p, L->dinvf.p); FVS_COUNT_LAUNCH();
+    }
+  }
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
 }
 
 }  // namespace fvs

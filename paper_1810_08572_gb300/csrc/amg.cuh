@@ -19,10 +19,11 @@ struct AmgLevel {
   const Ell* A = nullptr;
   DBuf<double> dinv;    // 1 / diagonal
   DBuf<float> dinvf;
+  DBuf<float> valf;     // FP32 copy of the operator values (mixed precision)
   DBuf<int32_t> agg;    // row -> aggregate (row of the next level)
   DBuf<int32_t> mptr, midx;   // members of each aggregate of the next level (CSR)
-  DBuf<double> b, x, y, r;    // V-cycle work
-  DBuf<float> bf, xf, yf, rf; // FP32 V-cycle work
+  DBuf<double> b, x, y, r, t;    // V-cycle work
+  DBuf<float> bf, xf, yf, rf, tf; // FP32 V-cycle work
   int64_t n = 0;
 };
 
@@ -59,8 +60,10 @@ struct Amg : Precond {
   int levels() const { return (int)lv.size(); }
 
  private:
-  fvs_status vcycle(cudaStream_t s, int l, const double* b, double* y);
+  template <typename T>
+  fvs_status vcycle_t(cudaStream_t s, int l, const T* b, T* y);
   fvs_status coarsest_setup(cudaStream_t s);
+  fvs_status setup_fp32(cudaStream_t s);
 };
 
 struct AmgProjector : Projector {

@@ -118,11 +118,13 @@ __global__ void k_final2(int nb, const double* __restrict__ part, double* __rest
 }
 
 fvs_status Reducer::init() {
-  blocks = 2 * sm_count();
+  blocks = 4 * sm_count();
   if (blocks > 1024) blocks = 1024;
   FVS_TRY(part.alloc(2 * (size_t)blocks));
   FVS_TRY(sc.alloc(S_NSLOT));
   FVS_TRY(sc.zero(0));
+  FVS_TRY(ticket.alloc(1));
+  FVS_TRY(ticket.zero(0));
   if (!host) FVS_CUDA(cudaMallocHost(&host, S_NSLOT * sizeof(double)));
   return FVS_OK;
 }
@@ -207,6 +209,114 @@ fvs_status KrylovWork::ensure(int64_t n) {
 // safe quotient for Krylov scalars (a breakdown shows up as a stalled residual)
 __device__ __forceinline__ double sdiv(double a, double b) { return b != 0.0 ? a / b : 0.0; }
 
+// ---------------------------------------------------------------------------
+// Fused reductions: every block writes its partial sums; the last block to
+// finish (ticket) adds the partials in block order, so the result does not
+// depend on scheduling, and then applies the scalar bookkeeping.
+// ---------------------------------------------------------------------------
+enum { FIN_RV = 0, FIN_TSTT = 1, FIN_RR_RHO = 2, FIN_PQ = 3, FIN_RR = 4, FIN_RZ = 5 };
+
+__device__ void finish2(double a, double b, double* part, unsigned int* ticket, double* sc, int mode) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  a = block_sum(a, sh);
+  b = block_sum(b, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = a;
+    part[gridDim.x + blockIdx.x] = b;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+    x += ((volatile double*)part)[i];
+    y += ((volatile double*)part)[gridDim.x + i];
+  }
+  x = block_sum(x, sh);
+  y = block_sum(y, sh);
+  if (threadIdx.x == 0) {
+    switch (mode) {
+      case FIN_RV: sc[S_RV] = x; break;
+      case FIN_TSTT: sc[S_TS] = x; sc[S_TT] = y; break;
+      case FIN_RR_RHO:
+        // alpha and omega of this iteration are kept for the next beta
+        sc[S_ALPHA] = sdiv(sc[S_RHO], sc[S_RV]);
+        sc[S_OMEGA] = sdiv(sc[S_TS], sc[S_TT]);
+        sc[S_RR] = x;
+        sc[S_RHO_OLD] = sc[S_RHO];
+        sc[S_RHO] = y;
+        break;
+      case FIN_PQ: sc[S_PQ] = x; break;
+      case FIN_RR: sc[S_RR] = x; break;
+      case FIN_RZ: sc[S_RZ_OLD] = sc[S_RZ]; sc[S_RZ] = x; break;
+    }
+    *ticket = 0u;
+  }
+}
+
+// y = A x (+ dextra x); sums d.y (and y.y when yy)
+__global__ void k_spmv_dot(int64_t n, int w, const int32_t* __restrict__ col, const double* __restrict__ val,
+                           const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ dextra,
+                           const double* __restrict__ d, int yy, double* part, unsigned int* ticket, double* sc,
+                           int mode) {
+  double a = 0.0, b = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = dextra ? dextra[i] * x[i] : 0.0;
+    for (int k = 0; k < w; ++k) {
+      const int64_t e = (int64_t)k * n + i;
+      acc = fma(val[e], x[col[e]], acc);
+    }
+    y[i] = acc;
+    a = fma(d[i], acc, a);
+    if (yy) b = fma(acc, acc, b);
+  }
+  finish2(a, b, part, ticket, sc, mode);
+}
+
+// BiCGStab: x += alpha ph + omega sh ; r = s - omega t ; sums r.r and rh.r
+__global__ void k_bicg_xr_dot(int64_t n, double* __restrict__ sc, const double* __restrict__ ph,
+                              const double* __restrict__ sh, const double* __restrict__ sv,
+                              const double* __restrict__ t, const double* __restrict__ rh, double* __restrict__ x,
+                              double* __restrict__ r, double* part, unsigned int* ticket) {
+  const double alpha = sdiv(sc[S_RHO], sc[S_RV]);
+  const double omega = sdiv(sc[S_TS], sc[S_TT]);
+  double a = 0.0, b = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * ph[i] + omega * sh[i];
+    const double ri = sv[i] - omega * t[i];
+    r[i] = ri;
+    a = fma(ri, ri, a);
+    b = fma(rh[i], ri, b);
+  }
+  finish2(a, b, part, ticket, sc, FIN_RR_RHO);
+}
+
+// CG: x += alpha p ; r -= alpha q ; sums r.r
+__global__ void k_cg_xr_dot(int64_t n, double* __restrict__ sc, const double* __restrict__ p,
+                            const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r,
+                            double* part, unsigned int* ticket) {
+  const double alpha = sdiv(sc[S_RZ], sc[S_PQ]);
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] += alpha * p[i];
+    const double ri = r[i] - alpha * q[i];
+    r[i] = ri;
+    a = fma(ri, ri, a);
+  }
+  finish2(a, 0.0, part, ticket, sc, FIN_RR);
+}
+// sums r.z (rz moved to rz_old)
+__global__ void k_dot_rz(int64_t n, const double* __restrict__ r, const double* __restrict__ z, double* part,
+                         unsigned int* ticket, double* sc) {
+  double a = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    a = fma(r[i], z[i], a);
+  finish2(a, 0.0, part, ticket, sc, FIN_RZ);
+}
+
 // BiCGStab: p = r + beta (p - omega v), beta = (rho/rho_old)(alpha/omega)
 __global__ void k_bicg_p(int64_t n, const double* __restrict__ sc, const double* __restrict__ r,
                          const double* __restrict__ v, double* __restrict__ p, int first) {
@@ -220,25 +330,22 @@ __global__ void k_bicg_s(int64_t n, const double* __restrict__ sc, const double*
   const double alpha = sdiv(sc[S_RHO], sc[S_RV]);
   GRID_STRIDE(i, n) sv[i] = r[i] - alpha * v[i];
 }
-// x += alpha ph + omega sh ; r = s - omega t
-__global__ void k_bicg_xr(int64_t n, double* __restrict__ sc, const double* __restrict__ ph,
-                          const double* __restrict__ sh, const double* __restrict__ sv,
-                          const double* __restrict__ t, double* __restrict__ x, double* __restrict__ r) {
-  const double alpha = sdiv(sc[S_RHO], sc[S_RV]);
-  const double omega = sdiv(sc[S_TS], sc[S_TT]);
-  GRID_STRIDE(i, n) {
-    x[i] += alpha * ph[i] + omega * sh[i];
-    r[i] = sv[i] - omega * t[i];
-  }
-}
-// alpha and omega are kept for the next iteration's beta by a one-thread
-// launch after the update (the update kernel itself still reads rho/rv, ts/tt)
-__global__ void k_store_ao(double* __restrict__ sc) {
-  sc[S_ALPHA] = sdiv(sc[S_RHO], sc[S_RV]);
-  sc[S_OMEGA] = sdiv(sc[S_TS], sc[S_TT]);
+__global__ void k_cg_p(int64_t n, const double* __restrict__ sc, const double* __restrict__ z,
+                       double* __restrict__ p, int first) {
+  const double beta = first ? 0.0 : sdiv(sc[S_RZ], sc[S_RZ_OLD]);
+  GRID_STRIDE(i, n) p[i] = first ? z[i] : z[i] + beta * p[i];
 }
 
 static inline bool bad(double v) { return !(v == v) || v > 1e300 || v < -1e300; }
+
+static fvs_status spmv_dot(cudaStream_t s, Reducer& red, const Ell& A, const double* x, double* y,
+                           const double* dextra, const double* d, bool yy, int mode) {
+  ProfScope ps(&A, "spmv", (double)A.n * (12.0 * A.w + 24.0 + (dextra ? 8.0 : 0.0)), s);
+  k_spmv_dot<<<red.blocks, 256, 0, s>>>(A.n, A.w, A.col, A.val, x, y, dextra, d, yy ? 1 : 0, red.part,
+                                         red.ticket, red.sc, mode); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
 
 fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, const double* dextra,
                     Precond& M, const double* b, double* x, double rtol, int maxit, Projector* proj,
@@ -254,14 +361,15 @@ fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, c
   FVS_TRY(residual(s, A, x, b, w.r, dextra));
   if (proj) FVS_TRY(proj->apply(s, w.r));
   FVS_TRY(vcopy(s, n, w.r, w.rh));
-  // ||b|| of the (projected) right side
+  // ||b|| of the (projected) right side; rho_0 = rh . r
+  const double* bb = b;
   if (proj) {
     FVS_TRY(vcopy(s, n, b, w.q));
     FVS_TRY(proj->apply(s, w.q));
-    FVS_TRY(red.dot2(s, n, w.q, w.q, w.r, w.r, S_BB, S_RR));
-  } else {
-    FVS_TRY(red.dot2(s, n, b, b, w.r, w.r, S_BB, S_RR));
+    bb = w.q;
   }
+  FVS_TRY(red.dot2(s, n, bb, bb, w.r, w.r, S_BB, S_RR));
+  FVS_TRY(red.dot(s, n, w.rh, w.r, S_RHO));
   FVS_TRY(red.fetch(s));
   double bnorm = sqrt(red.host[S_BB]);
   if (bnorm == 0.0) bnorm = 1.0;
@@ -271,26 +379,20 @@ fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, c
     res.converged = true;
     return FVS_OK;
   }
+  // K x has zero sum on every singular part (zero column sums), so the
+  // Krylov vectors stay in the range once r is projected
   for (int it = 0; it < maxit; ++it) {
-    // rho = rh . r (previous rho moved to rho_old by the final kernel)
-    k_dot2_part<<<red.blocks, RB, 0, s>>>(n, w.rh, w.r, nullptr, nullptr, red.part); FVS_COUNT_LAUNCH();
-    k_final2<<<1, 1024, 0, s>>>(red.blocks, red.part, red.sc, S_RHO, -1, S_RHO_OLD, 0); FVS_COUNT_LAUNCH();
     k_bicg_p<<<grid, 256, 0, s>>>(n, red.sc, w.r, w.v, w.p, it == 0); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
     FVS_TRY(M.apply(s, w.p, w.ph));
-    FVS_TRY(spmv(s, A, w.ph, w.v, dextra));
-    if (proj) FVS_TRY(proj->apply(s, w.v));
-    FVS_TRY(red.dot(s, n, w.rh, w.v, S_RV));
+    FVS_TRY(spmv_dot(s, red, A, w.ph, w.v, dextra, w.rh, false, FIN_RV));
     k_bicg_s<<<grid, 256, 0, s>>>(n, red.sc, w.r, w.v, w.sv); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
     FVS_TRY(M.apply(s, w.sv, w.sh));
-    FVS_TRY(spmv(s, A, w.sh, w.t, dextra));
-    if (proj) FVS_TRY(proj->apply(s, w.t));
-    FVS_TRY(red.dot2(s, n, w.t, w.sv, w.t, w.t, S_TS, S_TT));
-    k_bicg_xr<<<grid, 256, 0, s>>>(n, red.sc, w.ph, w.sh, w.sv, w.t, x, w.r); FVS_COUNT_LAUNCH();
-    k_store_ao<<<1, 1, 0, s>>>(red.sc); FVS_COUNT_LAUNCH();
+    FVS_TRY(spmv_dot(s, red, A, w.sh, w.t, dextra, w.sv, true, FIN_TSTT));
+    k_bicg_xr_dot<<<red.blocks, 256, 0, s>>>(n, red.sc, w.ph, w.sh, w.sv, w.t, w.rh, x, w.r, red.part,
+                                              red.ticket); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
-    FVS_TRY(red.dot(s, n, w.r, w.r, S_RR));
     FVS_TRY(red.fetch(s));
     rn = sqrt(red.host[S_RR]);
     res.iters = it + 1;
@@ -301,10 +403,13 @@ fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, c
       break;
     }
     // restart on breakdown of the shadow residual
-    if (red.host[S_TT] == 0.0 || red.host[S_RV] == 0.0) {
+    if (red.host[S_TT] == 0.0 || red.host[S_RV] == 0.0 || red.host[S_RHO] == 0.0) {
       FVS_TRY(residual(s, A, x, b, w.r, dextra));
       if (proj) FVS_TRY(proj->apply(s, w.r));
       FVS_TRY(vcopy(s, n, w.r, w.rh));
+      FVS_TRY(red.dot(s, n, w.rh, w.r, S_RHO));
+      it = -1 + it;   // keep counting iterations, restart the recurrence
+      k_bicg_p<<<grid, 256, 0, s>>>(n, red.sc, w.r, w.v, w.p, 1); FVS_COUNT_LAUNCH();
     }
   }
   // recompute the true residual (the recursive one drifts)
@@ -320,20 +425,6 @@ fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, c
 // ---------------------------------------------------------------------------
 // preconditioned CG (symmetric systems)
 // ---------------------------------------------------------------------------
-__global__ void k_cg_xr(int64_t n, const double* __restrict__ sc, const double* __restrict__ p,
-                        const double* __restrict__ q, double* __restrict__ x, double* __restrict__ r) {
-  const double alpha = sdiv(sc[S_RZ], sc[S_PQ]);
-  GRID_STRIDE(i, n) {
-    x[i] += alpha * p[i];
-    r[i] -= alpha * q[i];
-  }
-}
-__global__ void k_cg_p(int64_t n, const double* __restrict__ sc, const double* __restrict__ z,
-                       double* __restrict__ p, int first) {
-  const double beta = first ? 0.0 : sdiv(sc[S_RZ], sc[S_RZ_OLD]);
-  GRID_STRIDE(i, n) p[i] = first ? z[i] : z[i] + beta * p[i];
-}
-
 fvs_status pcg(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, Precond& M, const double* b,
                double* x, double rtol, int maxit, Projector* proj, SolveResult& res) {
   const int64_t n = A.n;
@@ -346,13 +437,13 @@ fvs_status pcg(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, Precon
   const int grid = stride_grid(n, 256);
   FVS_TRY(residual(s, A, x, b, w.r, nullptr));
   if (proj) FVS_TRY(proj->apply(s, w.r));
+  const double* bb = b;
   if (proj) {
     FVS_TRY(vcopy(s, n, b, w.q));
     FVS_TRY(proj->apply(s, w.q));
-    FVS_TRY(red.dot2(s, n, w.q, w.q, w.r, w.r, S_BB, S_RR));
-  } else {
-    FVS_TRY(red.dot2(s, n, b, b, w.r, w.r, S_BB, S_RR));
+    bb = w.q;
   }
+  FVS_TRY(red.dot2(s, n, bb, bb, w.r, w.r, S_BB, S_RR));
   FVS_TRY(red.fetch(s));
   double bnorm = sqrt(red.host[S_BB]);
   if (bnorm == 0.0) bnorm = 1.0;
@@ -364,15 +455,12 @@ fvs_status pcg(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, Precon
   for (int it = 0; it < maxit; ++it) {
     FVS_TRY(M.apply(s, w.r, w.z));
     if (proj) FVS_TRY(proj->apply(s, w.z));
-    k_dot2_part<<<red.blocks, RB, 0, s>>>(n, w.r, w.z, nullptr, nullptr, red.part); FVS_COUNT_LAUNCH();
-    k_final2<<<1, 1024, 0, s>>>(red.blocks, red.part, red.sc, S_RZ, -1, S_RZ_OLD, 0); FVS_COUNT_LAUNCH();
+    k_dot_rz<<<red.blocks, 256, 0, s>>>(n, w.r, w.z, red.part, red.ticket, red.sc); FVS_COUNT_LAUNCH();
     k_cg_p<<<grid, 256, 0, s>>>(n, red.sc, w.z, w.p, it == 0); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
-    FVS_TRY(spmv(s, A, w.p, w.q, nullptr));
-    FVS_TRY(red.dot(s, n, w.p, w.q, S_PQ));
-    k_cg_xr<<<grid, 256, 0, s>>>(n, red.sc, w.p, w.q, x, w.r); FVS_COUNT_LAUNCH();
+    FVS_TRY(spmv_dot(s, red, A, w.p, w.q, nullptr, w.p, false, FIN_PQ));
+    k_cg_xr_dot<<<red.blocks, 256, 0, s>>>(n, red.sc, w.p, w.q, x, w.r, red.part, red.ticket); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
-    FVS_TRY(red.dot(s, n, w.r, w.r, S_RR));
     FVS_TRY(red.fetch(s));
     const double rn = sqrt(red.host[S_RR]);
     res.iters = it + 1;

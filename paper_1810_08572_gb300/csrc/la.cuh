@@ -39,6 +39,7 @@ struct Reducer {
   int blocks = 0;
   DBuf<double> part;   // [2*blocks]
   DBuf<double> sc;     // [S_NSLOT]
+  DBuf<unsigned int> ticket;   // last-block counter of the fused reductions
   double* host = nullptr;  // pinned [S_NSLOT]
   fvs_status init();
   ~Reducer() { if (host) cudaFreeHost(host); }

@@ -36,9 +36,12 @@ __device__ __forceinline__ double solid_fraction_slope(double T, double Ts, doub
 // ---------------------------------------------------------------------------
 // 1. tags and compaction
 // ---------------------------------------------------------------------------
-__global__ void k_tag(int64_t Nc, const double* T, double Ts, uint8_t* lm, int32_t* flag, double* u, double* uold) {
+__global__ void k_tag(int64_t Nc, const double* T, double Ts, uint8_t* lm, int32_t* flag, double* u, double* uold,
+                      int* changed) {
+  int ch = 0;
   GS(c, Nc) {
     const bool l = T[c] > Ts;
+    ch += (lm[c] != (uint8_t)l) ? 1 : 0;
     lm[c] = l;
     flag[c] = l;
     if (!l) {
@@ -48,6 +51,7 @@ __global__ void k_tag(int64_t Nc, const double* T, double Ts, uint8_t* lm, int32
       }
     }
   }
+  if (ch) atomicAdd(changed, ch);
 }
 __global__ void k_compact(int64_t Nc, const uint8_t* lm, const int32_t* excl, int32_t* map, int32_t* act) {
   GS(c, Nc) {
@@ -112,14 +116,18 @@ __global__ void k_mom_matrix(int64_t nact, int64_t Nc, int W, const int32_t* act
     const double f = fs[c];
     const double D = m.C * f * f / ((1.0 - f) * (1.0 - f) * (1.0 - f) + m.eps);
     const double dterm = (m.rho / dt + D) * V[c];
+    bool seen_diag = false;   // padding slots also carry col = c (value 0)
     for (int k = 0; k < W; ++k) {
       const int32_t j = Lcol[(int64_t)k * Nc + c];
       const double a = Lval[(int64_t)k * Nc + c];
       int32_t cc = (int32_t)r;
       double v = 0.0;
       if (j == c) {
-        v = dterm - 0.5 * m.mu * a;
-        diag[r] = v;
+        if (!seen_diag) {
+          v = dterm - 0.5 * m.mu * a;
+          diag[r] = v;
+          seen_diag = true;
+        }
       } else if (map[j] >= 0) {
         cc = map[j];
         v = -0.5 * m.mu * a;
@@ -229,8 +237,8 @@ __global__ void k_ppe_matrix(PpeCtx x, int32_t* col, double* val, double* diag, 
         if (k < nn) {
           if (mj >= 0) { cc = mj; v = a; }
           else if (a != 0.0) atomicOr(err, 1);
+          if (j == c) dg = v;
         }
-        if (j == c) dg = v;
         col[(int64_t)k * x.nact + r] = cc;
         val[(int64_t)k * x.nact + r] = v;
       }
@@ -653,6 +661,7 @@ fvs_status solver_set_state(fvs_solver s, const double* T, const double* u, int 
   s->time = 0.0;
   s->nstep = 0;
   s->have_step = false;
+  s->k_valid = false;
   return FVS_OK;
 }
 
@@ -663,7 +672,9 @@ static fvs_status classify(fvs_solver s) {
   const int64_t Nc = m->Nc, Nf = m->Nf, Nv = m->Nv;
   const Mat mt = mat_of(s->props);
   FVS_TRY(s->flag.zero(st));
-  k_tag<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, mt.Ts, s->lm, s->flag, s->u, s->uold); FVS_COUNT_LAUNCH();
+  FVS_TRY(s->cnt.zero(st));
+  k_tag<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, mt.Ts, s->lm, s->flag, s->u, s->uold, s->cnt.p + 1);
+  FVS_COUNT_LAUNCH();
   FVS_TRY(exclusive_scan(st, s->sw, Nc + 1, s->flag, s->excl));
   k_compact<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->lm, s->excl, s->map, s->act); FVS_COUNT_LAUNCH();
   FVS_TRY(s->flow.zero(st));
@@ -672,7 +683,6 @@ static fvs_status classify(fvs_solver s) {
   k_vertex_nonppe<<<stride_grid(Nv, 256), 256, 0, st>>>(Nv, m->vc_ptr, m->vc_idx, s->ppe, s->nS); FVS_COUNT_LAUNCH();
   k_face_case<<<stride_grid(Nf, 256), 256, 0, st>>>(Nf, m->own, m->nei, m->fv, s->lm, s->nS, s->fcase); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
-  FVS_TRY(s->cnt.zero(st));
   k_count_u8<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->ppe, s->cnt); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   int32_t na = 0;
@@ -682,6 +692,9 @@ static fvs_status classify(fvs_solver s) {
   FVS_CUDA(cudaStreamSynchronize(st));
   s->nact = na;
   s->nppe = hc[0];
+  // the pressure system depends on the tags only: keep it (and its AMG
+  // hierarchy) while no cell changed phase
+  if (hc[1] != 0) s->k_valid = false;
   return FVS_OK;
 }
 
@@ -719,6 +732,7 @@ static fvs_status assemble_pressure(fvs_solver s) {
   // solve falls back to single-grid Jacobi BiCGStab
   s->amg_ok = false;
   if (s->props.p_solver == FVS_PSOLVER_AMG && s->nact > 0) {
+    s->amg.opt.fp32 = s->props.precision == FVS_PREC_MIXED;
     fvs_status r = s->amg.setup(st, s->K);
     if (r == FVS_OK) {
       s->amg_ok = true;
@@ -796,14 +810,21 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
       FVS_TRY(bicgstab(st, s->red, s->kw, s->M, nullptr, J, s->mrhs.p + d * na, s->mx.p + d * na,
                        s->props.mom_rtol, s->props.max_krylov_iters, nullptr, r));
       S.mom_its += r.iters;
-      if (!r.converged) status = FVS_ERR_NOT_CONVERGED;
+      if (!r.converged) {
+        status = FVS_ERR_NOT_CONVERGED;
+        set_error("momentum component %d: relative residual %.3e after %d iterations", d, r.relres, r.iters);
+      }
     }
   }
   k_scatter3<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, na, s->map, s->mx, s->ustar); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
 
   // 3. pressure system
-  FVS_TRY(assemble_pressure(s));
+  if (!s->k_valid) {
+    FVS_TRY(assemble_pressure(s));
+    s->k_valid = true;
+    S.p_rebuilt = 1;
+  }
   FVS_TRY(s->prhs.alloc(na + 1));
   FVS_TRY(s->px.alloc(na + 1));
   if (na > 0) {
@@ -816,7 +837,10 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
     S.p_its = r.iters;
     S.p_relres = r.relres;
     S.fallback = fb;
-    if (!r.converged) status = FVS_ERR_NOT_CONVERGED;
+    if (!r.converged) {
+      status = FVS_ERR_NOT_CONVERGED;
+      set_error("pressure: relative residual %.3e after %d iterations (fallback %d)", r.relres, r.iters, fb);
+    }
   }
   k_scatter1<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->map, s->ppe, s->px, s->p); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
@@ -852,7 +876,10 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
       FVS_TRY(bicgstab(st, s->red, s->kw, s->Ke, s->edx, J, s->erhs, s->Tlin, s->props.e_rtol,
                        s->props.max_krylov_iters, nullptr, r));
       S.e_lin_its += r.iters;
-      if (!r.converged) status = FVS_ERR_NOT_CONVERGED;
+      if (!r.converged) {
+        status = FVS_ERR_NOT_CONVERGED;
+        set_error("energy pass %d: relative residual %.3e after %d iterations", it, r.relres, r.iters);
+      }
       // next iterate, then its change against the current one
       k_energy_update<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, mt, s->Tlin, Tm, fsm, s->Tit, s->fsit); FVS_COUNT_LAUNCH();
       FVS_LAUNCH_CHECK();
@@ -866,7 +893,10 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
       }
     }
     S.e_its = std::min(it, s->props.max_e_iters);
-    if (!conv) status = FVS_ERR_NOT_CONVERGED;
+    if (!conv) {
+      status = FVS_ERR_NOT_CONVERGED;
+      set_error("latent-heat loop: max|dT| %.3e after %d passes", s->red.host[S_TMP0], S.e_its);
+    }
   }
 
   // 6. crossing times, then rotate the time levels

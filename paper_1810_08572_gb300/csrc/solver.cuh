@@ -17,6 +17,7 @@ struct fvs_solver_s {
   cudaStream_t stream = nullptr;
   bool have_props = false;
   bool have_step = false;     // tags / compact systems of a step exist
+  bool k_valid = false;       // pressure system and AMG match the current tags
   fvs_props props{};
   std::vector<fvs_patch_bc> bc;
   double time = 0.0;
