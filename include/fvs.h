@@ -206,6 +206,72 @@ fvs_status fvs_query_fields(fvs_solver solver, fvs_field field, double* dst,
                             int64_t dst_len, int dst_on_device);
 
 /* ------------------------------------------------------------------------
+ * Batched uncertainty quantification (Section 2.7: non-intrusive sampling of
+ * the stochastic inputs, one plain solve per sample; Eq. 22-23 outputs).
+ *   base      host: material and solver settings shared by all samples
+ *             (its bc and T_init are replaced per sample)
+ *   inputs    host double [n_samples*3], per sample: melt temperature (K),
+ *             wall temperature applied to every wall patch (K), solute
+ *             concentration C0 (wt%) which moves the liquidus to
+ *             base T_liq - 5 (C0 - 4)
+ *   dt        time step (s); each sample starts at rest at its melt
+ *             temperature and runs until a step starts with every cell solid,
+ *             or for max_steps steps
+ *   mode      0: plain solves (the only mode available)
+ *   n_streams concurrent samples, each on its own CUDA stream and solver
+ *             (0 = 8)
+ *   qoi_out   host double [n_samples*4]: per sample the mean over the
+ *             solidified cells of local solidification time t_f (s), cooling
+ *             rate (K/s), SDAS (um) and yield strength (MPa); NaN if no cell
+ *             solidified
+ *   steps_out host int64 [n_samples] steps taken (nullable)
+ * Blocks until all samples are done.  Fails with FVS_ERR_ARG if a sample's
+ * liquidus falls to the solidus.
+ * ------------------------------------------------------------------------ */
+fvs_status fvs_uq_batch(fvs_mesh mesh, const fvs_props* base, int64_t n_samples, const double* inputs,
+                        double dt, int32_t max_steps, int32_t mode, int32_t n_streams, double* qoi_out,
+                        int64_t* steps_out);
+
+/* ------------------------------------------------------------------------
+ * Learned surrogate of the UQ map (the role the polynomial-chaos expansion
+ * of Section 2.7, Eq. 27-28, plays in the paper): a multilayer perceptron
+ * from the stochastic process inputs to the microstructure outputs of
+ * Section 2.6 (Eq. 22-23).  Hidden layers GELU(W h + b), linear output,
+ * mean-squared-error loss on standardised inputs and outputs.  BF16 weights
+ * and activations with FP32 accumulation on the tensor cores; FP32 master
+ * weights and Adam.  Parameters are exchanged as one flat host array of
+ * doubles: for each layer its weight matrix [n_out x n_in] row-major, then
+ * its bias [n_out].
+ * ------------------------------------------------------------------------ */
+typedef struct fvs_surrogate_s* fvs_surrogate;
+
+/* n_in, n_hidden, n_out in 1..128, 1..16 hidden layers; weights drawn
+ * uniform(-sqrt(6/fan_in), +sqrt(6/fan_in)) from a counter-based generator
+ * keyed by seed, biases zero; scaling is the identity until set. */
+fvs_status fvs_surrogate_create(int32_t n_in, int32_t n_hidden, int32_t n_hidden_layers, int32_t n_out,
+                                uint64_t seed, void* stream, fvs_surrogate* out);
+fvs_status fvs_surrogate_destroy(fvs_surrogate s);
+/* Standardisation: x' = (x - mu_in)/sd_in, y = y' sd_out + mu_out (host arrays
+ * of n_in and n_out doubles; scales must be positive). */
+fvs_status fvs_surrogate_set_scaling(fvs_surrogate s, const double* mu_in, const double* sd_in,
+                                     const double* mu_out, const double* sd_out);
+/* Number of parameters in the flat layout, or -1 for a NULL handle. */
+int64_t fvs_surrogate_num_params(fvs_surrogate s);
+/* set = 1: load the flat host array into the model; set = 0: read it out. */
+fvs_status fvs_surrogate_params(fvs_surrogate s, double* inout, int64_t len, int set);
+/* Loss (mean over samples and outputs of the squared standardised error) and
+ * its gradient with respect to the flat parameters at the current weights.
+ * X host [n x n_in], T host [n x n_out], grad host [len]. */
+fvs_status fvs_surrogate_gradients(fvs_surrogate s, const double* X, const double* T, int64_t n, double* grad,
+                                   int64_t grad_len, double* loss);
+/* Full-batch Adam (beta 0.9 / 0.999, eps 1e-8) for the given epochs;
+ * final_loss (nullable) gets the loss after training. */
+fvs_status fvs_surrogate_train(fvs_surrogate s, const double* X, const double* T, int64_t n, int32_t epochs,
+                               double lr, double* final_loss);
+/* Y [n x n_out] = model(X [n x n_in]); both host or both device memory. */
+fvs_status fvs_surrogate_predict(fvs_surrogate s, const double* X, double* Y, int64_t n, int on_device);
+
+/* ------------------------------------------------------------------------
  * Kernel timing (not part of the method; for roofline measurement).
  * While enabled, every launch of the SpMV, residual and Jacobi kernels on the
  * fine pressure, energy and momentum matrices inside fvs_step is bracketed by

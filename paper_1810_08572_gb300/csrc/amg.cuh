@@ -29,8 +29,8 @@ struct AmgLevel {
 
 struct AmgOptions {
   double theta = 0.08;     // strength threshold
-  double omega = 0.7;      // Jacobi damping
-  double coarse_scale = 1.0;
+  double omega = 0.85;     // Jacobi damping
+  double coarse_scale = 1.5;  // over-correction of the piecewise-constant coarse correction
   int max_levels = 20;
   int coarsest = 256;      // stop coarsening at or below this size
   int npre = 1, npost = 1;

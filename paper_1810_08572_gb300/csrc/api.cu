@@ -19,6 +19,7 @@ void set_error(const char* fmt, ...) {
 }
 
 thread_local Prof* g_prof = nullptr;
+thread_local cudaStream_t g_alloc_stream = nullptr;
 unsigned long long g_launches = 0;
 
 Prof::~Prof() {
@@ -130,6 +131,7 @@ FVS_API fvs_status fvs_mesh_create(const double* nodes_xyz, int64_t n_nodes, con
   fvs_mesh m = new (std::nothrow) fvs_mesh_s();
   if (!m) return FVS_ERR_NOMEM;
   m->stream = (cudaStream_t)stream;
+  AllocStream as(m->stream);
   cudaGetDevice(&m->device);
   fvs_status s = mesh_build(m, nodes_xyz, n_nodes, cell_nodes, n_cells, face_nodes, n_faces, face_cells,
                             boundary_patch, reorder);
@@ -143,8 +145,13 @@ FVS_API fvs_status fvs_mesh_create(const double* nodes_xyz, int64_t n_nodes, con
 
 FVS_API fvs_status fvs_mesh_destroy(fvs_mesh mesh) {
   if (!mesh) return FVS_ERR_ARG;
-  cudaStreamSynchronize(mesh->stream);
-  delete mesh;
+  cudaStream_t st = mesh->stream;
+  {
+    AllocStream as(st);
+    cudaStreamSynchronize(st);
+    delete mesh;
+  }
+  cudaStreamSynchronize(st);
   return FVS_OK;
 }
 
@@ -180,6 +187,7 @@ FVS_API fvs_status fvs_mesh_geometry(fvs_mesh m, int which, double* dst, int64_t
     set_error("fvs_mesh_geometry: destination too small");
     return FVS_ERR_ARG;
   }
+  AllocStream as(m->stream);
   DBuf<double> tmp;
   FVS_TRY(tmp.alloc(n));
   k_unpermute<<<stride_grid(n, 256), 256, 0, m->stream>>>(n, which == 0 ? m->cell_in.p : m->face_in.p,
@@ -200,6 +208,7 @@ FVS_API fvs_status fvs_solver_create(fvs_mesh mesh, void* stream, fvs_solver* ou
   if (!s) return FVS_ERR_NOMEM;
   s->mesh = mesh;
   s->stream = (cudaStream_t)stream;
+  AllocStream as(s->stream);
   fvs_status st = solver_alloc(s);
   if (st != FVS_OK) {
     delete s;
@@ -211,8 +220,13 @@ FVS_API fvs_status fvs_solver_create(fvs_mesh mesh, void* stream, fvs_solver* ou
 
 FVS_API fvs_status fvs_solver_destroy(fvs_solver s) {
   if (!s) return FVS_ERR_ARG;
-  cudaStreamSynchronize(s->stream);
-  delete s;
+  cudaStream_t st = s->stream;
+  {
+    AllocStream as(st);
+    cudaStreamSynchronize(st);
+    delete s;
+  }
+  cudaStreamSynchronize(st);
   return FVS_OK;
 }
 
@@ -221,6 +235,7 @@ FVS_API fvs_status fvs_set_properties(fvs_solver s, const fvs_props* p) {
     set_error("fvs_set_properties: NULL argument");
     return FVS_ERR_ARG;
   }
+  AllocStream as(s->stream);
   return solver_set_properties(s, p);
 }
 
@@ -229,6 +244,7 @@ FVS_API fvs_status fvs_set_state(fvs_solver s, const double* T, const double* u,
     set_error("fvs_set_state: NULL argument");
     return FVS_ERR_ARG;
   }
+  AllocStream as(s->stream);
   return solver_set_state(s, T, u, on_device);
 }
 
@@ -238,6 +254,7 @@ FVS_API fvs_status fvs_step(fvs_solver s, double dt, int32_t n_steps, fvs_step_s
     return FVS_ERR_ARG;
   }
   fvs_status worst = FVS_OK;
+  AllocStream as(s->stream);
   g_prof = &s->prof;
   for (int i = 0; i < n_steps; ++i) {
     fvs_status r = solver_step(s, dt, last);
@@ -286,6 +303,7 @@ FVS_API fvs_status fvs_pressure_solve(fvs_solver s, const double* rhs, double* p
     return FVS_ERR_ARG;
   }
   int it = 0;
+  AllocStream as(s->stream);
   fvs_status r = solver_pressure_solve(s, rhs, p_out, rtol, &it, relres);
   if (iters) *iters = it;
   return r;
@@ -300,6 +318,7 @@ FVS_API fvs_status fvs_query_fields(fvs_solver s, fvs_field field, double* dst, 
     set_error("fvs_query_fields: no properties set");
     return FVS_ERR_STATE;
   }
+  AllocStream as(s->stream);
   return solver_query(s, field, dst, dst_len, dst_on_device);
 }
 
@@ -311,4 +330,25 @@ FVS_API fvs_status fvs_get_time(fvs_solver s, double* time, int64_t* steps) {
   if (time) *time = s->time;
   if (steps) *steps = s->nstep;
   return FVS_OK;
+}
+
+FVS_API fvs_status fvs_uq_batch(fvs_mesh mesh, const fvs_props* base, int64_t n_samples, const double* inputs,
+                                double dt, int32_t max_steps, int32_t mode, int32_t n_streams, double* qoi_out,
+                                int64_t* steps_out) {
+  if (!mesh || !base || !inputs || !qoi_out || n_samples <= 0 || !(dt > 0) || max_steps <= 0) {
+    set_error("fvs_uq_batch: bad argument");
+    return FVS_ERR_ARG;
+  }
+  if (mode != 0) {
+    set_error("fvs_uq_batch: mode %d is not available (0 = plain solves)", mode);
+    return FVS_ERR_ARG;
+  }
+  for (int64_t i = 0; i < n_samples; ++i) {
+    const double C0 = inputs[3 * i + 2];
+    if (!(base->mat.T_liq - 5.0 * (C0 - 4.0) > base->mat.T_sol)) {
+      set_error("fvs_uq_batch: sample %lld puts the liquidus below the solidus", (long long)i);
+      return FVS_ERR_ARG;
+    }
+  }
+  return uq_batch(mesh, base, n_samples, inputs, dt, max_steps, n_streams, qoi_out, steps_out);
 }

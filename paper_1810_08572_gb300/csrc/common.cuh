@@ -37,6 +37,17 @@ void set_error(const char* fmt, ...);
 extern unsigned long long g_launches;
 #define FVS_COUNT_LAUNCH() __atomic_add_fetch(&::fvs::g_launches, 1ULL, __ATOMIC_RELAXED)
 
+// Stream-ordered allocation: buffers are allocated and freed on the stream
+// of the object being worked on (set by the entry points), so concurrent
+// solvers on different streams never synchronise the whole device through
+// cudaFree.
+extern thread_local cudaStream_t g_alloc_stream;
+struct AllocStream {
+  cudaStream_t prev;
+  explicit AllocStream(cudaStream_t s) : prev(g_alloc_stream) { g_alloc_stream = s; }
+  ~AllocStream() { g_alloc_stream = prev; }
+};
+
 // Owning device buffer (freed on destruction).
 template <typename T>
 struct DBuf {
@@ -47,7 +58,7 @@ struct DBuf {
   DBuf& operator=(const DBuf&) = delete;
   ~DBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, g_alloc_stream);
     p = nullptr;
     n = 0;
   }
@@ -55,10 +66,10 @@ struct DBuf {
     if (count <= n && p) return FVS_OK;
     release();
     if (count == 0) return FVS_OK;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), g_alloc_stream);
     if (e != cudaSuccess) {
       p = nullptr;
-      set_error("cudaMalloc of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
+      set_error("cudaMallocAsync of %zu bytes failed: %s", count * sizeof(T), cudaGetErrorString(e));
       return e == cudaErrorMemoryAllocation ? FVS_ERR_NOMEM : FVS_ERR_CUDA;
     }
     n = count;

@@ -118,13 +118,13 @@ __global__ void k_final2(int nb, const double* __restrict__ part, double* __rest
 }
 
 fvs_status Reducer::init() {
-  blocks = 4 * sm_count();
-  if (blocks > 1024) blocks = 1024;
+  cudaStream_t st = g_alloc_stream;
+  blocks = 8 * sm_count();   // full occupancy for the fused SpMV + reduction kernels
   FVS_TRY(part.alloc(2 * (size_t)blocks));
   FVS_TRY(sc.alloc(S_NSLOT));
-  FVS_TRY(sc.zero(0));
+  FVS_TRY(sc.zero(st));
   FVS_TRY(ticket.alloc(1));
-  FVS_TRY(ticket.zero(0));
+  FVS_TRY(ticket.zero(st));
   if (!host) FVS_CUDA(cudaMallocHost(&host, S_NSLOT * sizeof(double)));
   return FVS_OK;
 }
@@ -349,7 +349,7 @@ static fvs_status spmv_dot(cudaStream_t s, Reducer& red, const Ell& A, const dou
 
 fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, const double* dextra,
                     Precond& M, const double* b, double* x, double rtol, int maxit, Projector* proj,
-                    SolveResult& res) {
+                    SolveResult& res, double bnorm_floor) {
   const int64_t n = A.n;
   res = SolveResult();
   if (n == 0) {
@@ -371,7 +371,7 @@ fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, c
   FVS_TRY(red.dot2(s, n, bb, bb, w.r, w.r, S_BB, S_RR));
   FVS_TRY(red.dot(s, n, w.rh, w.r, S_RHO));
   FVS_TRY(red.fetch(s));
-  double bnorm = sqrt(red.host[S_BB]);
+  double bnorm = fmax(sqrt(red.host[S_BB]), bnorm_floor);
   if (bnorm == 0.0) bnorm = 1.0;
   double rn = sqrt(red.host[S_RR]);
   res.relres = rn / bnorm;

@@ -91,9 +91,10 @@ struct Projector {
   virtual fvs_status apply(cudaStream_t s, double* v) = 0;
 };
 
+// The residual is measured against max(||b||, bnorm_floor).
 fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, const double* dextra,
                     Precond& M, const double* b, double* x, double rtol, int maxit,
-                    Projector* proj, SolveResult& res);
+                    Projector* proj, SolveResult& res, double bnorm_floor = 0.0);
 fvs_status pcg(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, Precond& M,
                const double* b, double* x, double rtol, int maxit, Projector* proj, SolveResult& res);
 

@@ -1,0 +1,598 @@
+// Learned surrogate of the UQ map (stochastic process inputs -> the
+// microstructure outputs of Section 2.6, Eq. 22-23), replacing the plain
+// solve inside Monte Carlo sampling (Section 2.7 uses a polynomial-chaos
+// surrogate for the same role).
+//
+// A multilayer perceptron with GELU hidden layers and a linear output,
+// BF16 weights and activations, FP32 accumulation on the tensor cores
+// (mma.sync m16n8k16), FP32 master weights and Adam moments.  Every
+// dimension is padded to a multiple of 16 with zeros that stay zero.
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace fvs {
+
+#define GS(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+typedef __nv_bfloat16 bf16;
+
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+
+enum { EPI_GELU = 0, EPI_LINEAR = 1, EPI_DGRAD = 2, EPI_WGRAD = 3 };
+
+struct Epi {
+  const float* bias;   // [N]           (GELU, LINEAR)
+  float* z;            // [M x ldo] f32  pre-activations to keep (GELU, LINEAR) or read (DGRAD)
+  bf16* hout;          // [M x ldo] bf16 activations (GELU) / previous delta (DGRAD)
+  float* fout;         // [M x ldo] f32  output (LINEAR) / weight gradient (WGRAD)
+  int ldo;
+};
+
+// C[M x N] = sum_k A(m, k) B(n, k) with A(m, k) = A[m*am + k*ak], B(n, k) = B[n*bn + k*bk].
+// One warp per 16-row tile, all N (<= 128) columns; K, N multiples of 16.
+template <int EPI>
+__global__ void k_mlp_gemm(int M, int N, int K, const bf16* __restrict__ A, int am, int ak,
+                           const bf16* __restrict__ B, int bn, int bk, Epi e) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int m0 = warp * 16;
+  if (m0 >= M) return;
+  const int g = lane >> 2, t = lane & 3;
+  float acc[16][4];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+  const bf16 zero = __float2bfloat16(0.f);
+  auto ldA = [&](int m, int k) -> bf16 { return m < M ? A[(int64_t)m * am + (int64_t)k * ak] : zero; };
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    uint32_t a[4];
+    a[0] = pack2(ldA(m0 + g, k0 + 2 * t), ldA(m0 + g, k0 + 2 * t + 1));
+    a[1] = pack2(ldA(m0 + g + 8, k0 + 2 * t), ldA(m0 + g + 8, k0 + 2 * t + 1));
+    a[2] = pack2(ldA(m0 + g, k0 + 2 * t + 8), ldA(m0 + g, k0 + 2 * t + 9));
+    a[3] = pack2(ldA(m0 + g + 8, k0 + 2 * t + 8), ldA(m0 + g + 8, k0 + 2 * t + 9));
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j * 8 < N) {
+        const int n = j * 8 + g;
+        uint32_t b[2];
+        b[0] = pack2(B[(int64_t)n * bn + (int64_t)(k0 + 2 * t) * bk], B[(int64_t)n * bn + (int64_t)(k0 + 2 * t + 1) * bk]);
+        b[1] = pack2(B[(int64_t)n * bn + (int64_t)(k0 + 2 * t + 8) * bk],
+                     B[(int64_t)n * bn + (int64_t)(k0 + 2 * t + 9) * bk]);
+        mma_bf16_16816(acc[j], a, b);
+      }
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j * 8 >= N) continue;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int m = m0 + g + (q >= 2 ? 8 : 0);
+      const int n = j * 8 + 2 * t + (q & 1);
+      if (m >= M) continue;
+      const int64_t o = (int64_t)m * e.ldo + n;
+      float v = acc[j][q];
+      if (EPI == EPI_GELU) {
+        v += e.bias[n];
+        if (e.z) e.z[o] = v;
+        e.hout[o] = __float2bfloat16(gelu(v));
+      } else if (EPI == EPI_LINEAR) {
+        v += e.bias[n];
+        e.fout[o] = v;
+      } else if (EPI == EPI_DGRAD) {
+        e.hout[o] = __float2bfloat16(v * gelu_grad(e.z[o]));
+      } else {
+        e.fout[o] = v;
+      }
+    }
+  }
+}
+
+// inputs (double, [n x nin]) -> normalised BF16 rows padded to kin
+__global__ void k_mlp_in(int64_t n, int nin, int kin, const double* X, const float* mu, const float* sd, bf16* H) {
+  GS(i, n * (int64_t)kin) {
+    const int64_t r = i / kin;
+    const int c = (int)(i - r * kin);
+    const float v = c < nin ? (float)((X[r * nin + c] - (double)mu[c]) / (double)sd[c]) : 0.f;
+    H[i] = __float2bfloat16(v);
+  }
+}
+// output rows (f32, padded) -> de-normalised doubles [n x nout]
+__global__ void k_mlp_out(int64_t n, int nout, int kout, const float* Y, const float* mu, const float* sd, double* out) {
+  GS(i, n * (int64_t)nout) {
+    const int64_t r = i / nout;
+    const int c = (int)(i - r * nout);
+    out[i] = (double)Y[r * kout + c] * (double)sd[c] + (double)mu[c];
+  }
+}
+// MSE loss on normalised targets; delta = 2 (y - t) / (n nout) as BF16, loss partials
+__global__ void k_mlp_loss(int64_t n, int nout, int kout, const float* Y, const double* T, const float* mu,
+                           const float* sd, bf16* delta, double* part) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  const double scale = 2.0 / ((double)n * nout);
+  GS(i, n * (int64_t)kout) {
+    const int64_t r = i / kout;
+    const int c = (int)(i - r * kout);
+    float d = 0.f;
+    if (c < nout) {
+      const double tn = (T[r * nout + c] - (double)mu[c]) / (double)sd[c];
+      const double diff = (double)Y[i] - tn;
+      acc += diff * diff;
+      d = (float)(scale * diff);
+    }
+    delta[i] = __float2bfloat16(d);
+  }
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+__global__ void k_sum_final(int nb, const double* part, double scale, double* out) {
+  __shared__ double sh[32];
+  double a = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) a += part[b];
+  a = block_sum(a, sh);
+  if (threadIdx.x == 0) *out = a * scale;
+}
+// bias gradient: db[n] = sum_m delta[m][n] (one thread per column)
+__global__ void k_bias_grad(int M, int N, const bf16* delta, float* db) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= N) return;
+  float s = 0.f;
+  for (int m = 0; m < M; ++m) s += __bfloat162float(delta[(int64_t)m * N + n]);
+  db[n] = s;
+}
+// Adam on FP32 master weights; refresh the BF16 copy.  mask keeps padding at zero.
+__global__ void k_adam(int64_t n, float* w, float* m, float* v, const float* g, const uint8_t* mask, float lr,
+                       float b1, float b2, float eps, float c1, float c2, bf16* wb) {
+  GS(i, n) {
+    if (!mask[i]) continue;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    w[i] = wi;
+    if (wb) wb[i] = __float2bfloat16(wi);
+  }
+}
+__global__ void k_to_bf16(int64_t n, const float* a, bf16* b) {
+  GS(i, n) b[i] = __float2bfloat16(a[i]);
+}
+// counter-based initialisation: uniform(-lim, lim) from a 64-bit mix of (seed, index)
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  x += 0x9e3779b97f4a7c15ULL;
+  x = (x ^ (x >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  x = (x ^ (x >> 27)) * 0x94d049bb133111ebULL;
+  return x ^ (x >> 31);
+}
+__global__ void k_init_w(int64_t n, int kpad, int nin_real, int nout_real, uint64_t seed, float lim, float* w,
+                         uint8_t* mask) {
+  GS(i, n) {
+    const int r = (int)(i / kpad), c = (int)(i - (int64_t)r * kpad);
+    const bool live = r < nout_real && c < nin_real;
+    const double u = (double)(mix64(seed ^ (uint64_t)i * 0x2545f4914f6cdd1dULL) >> 11) * (1.0 / 9007199254740992.0);
+    w[i] = live ? (float)((2.0 * u - 1.0) * lim) : 0.f;
+    mask[i] = live;
+  }
+}
+
+}  // namespace fvs
+
+// ---------------------------------------------------------------------------
+// the surrogate object
+// ---------------------------------------------------------------------------
+using namespace fvs;
+
+struct fvs_surrogate_s {
+  cudaStream_t stream = nullptr;
+  int nin = 0, nout = 0, hidden = 0, nlayers = 0;   // nlayers = hidden layers
+  std::vector<int> kd;       // padded widths: kd[0] input, kd[L] output
+  std::vector<int> real;     // real widths
+  // per layer l (0..L-1): W [kd[l+1] x kd[l]], b [kd[l+1]]
+  DBuf<float> w32, m, v, g;  // all layer weights then all biases, flattened
+  DBuf<bf16> wb;             // BF16 copy of the weights part
+  DBuf<uint8_t> mask;
+  std::vector<int64_t> woff, boff;
+  int64_t nw = 0, nparam = 0;
+  DBuf<float> mu_in, sd_in, mu_out, sd_out;
+  int64_t step = 0;
+  // work (sized for the largest batch seen)
+  int64_t cap = 0;
+  std::vector<DBuf<bf16>*> H;   // activations per layer input (L+1 buffers)
+  std::vector<DBuf<float>*> Z;  // pre-activations per layer output
+  DBuf<bf16> d0, d1;
+  DBuf<float> Y;
+  DBuf<double> part, lossv, Xd, Td;
+  ~fvs_surrogate_s() {
+    for (auto* p : H) delete p;
+    for (auto* p : Z) delete p;
+  }
+};
+
+namespace fvs {
+
+static fvs_status sg_work(fvs_surrogate_s* s, int64_t n) {
+  if (n <= s->cap) return FVS_OK;
+  const int L = (int)s->kd.size() - 1;
+  for (auto* p : s->H) delete p;
+  for (auto* p : s->Z) delete p;
+  s->H.clear();
+  s->Z.clear();
+  for (int l = 0; l <= L; ++l) {
+    s->H.push_back(new DBuf<bf16>());
+    FVS_TRY(s->H.back()->alloc((size_t)n * s->kd[l] + 16));
+  }
+  for (int l = 0; l < L; ++l) {
+    s->Z.push_back(new DBuf<float>());
+    FVS_TRY(s->Z.back()->alloc((size_t)n * s->kd[l + 1] + 16));
+  }
+  int kmax = 0;
+  for (int k : s->kd) kmax = std::max(kmax, k);
+  FVS_TRY(s->d0.alloc((size_t)n * kmax + 16));
+  FVS_TRY(s->d1.alloc((size_t)n * kmax + 16));
+  FVS_TRY(s->Y.alloc((size_t)n * s->kd[L] + 16));
+  FVS_TRY(s->part.alloc(1024));
+  FVS_TRY(s->lossv.alloc(1));
+  s->cap = n;
+  return FVS_OK;
+}
+
+static int gemm_grid(int64_t M) { return (int)((M + 63) / 64); }
+
+// forward pass of n normalised BF16 rows already in H[0]; keep Z when training
+static fvs_status sg_forward(fvs_surrogate_s* s, int64_t n, bool keep) {
+  const int L = (int)s->kd.size() - 1;
+  cudaStream_t st = s->stream;
+  for (int l = 0; l < L; ++l) {
+    const int K = s->kd[l], N = s->kd[l + 1];
+    Epi e{};
+    e.bias = s->w32.p + s->boff[l];
+    e.ldo = N;
+    const bf16* W = s->wb.p + s->woff[l];
+    if (l < L - 1) {
+      e.z = keep ? s->Z[l]->p : nullptr;
+      e.hout = s->H[l + 1]->p;
+      k_mlp_gemm<EPI_GELU><<<gemm_grid(n), 128, 0, st>>>((int)n, N, K, s->H[l]->p, K, 1, W, K, 1, e);
+    } else {
+      e.fout = s->Y.p;
+      k_mlp_gemm<EPI_LINEAR><<<gemm_grid(n), 128, 0, st>>>((int)n, N, K, s->H[l]->p, K, 1, W, K, 1, e);
+    }
+    FVS_COUNT_LAUNCH();
+  }
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
+// gradients of the loss at the current weights for n rows (X, T on device)
+static fvs_status sg_gradients(fvs_surrogate_s* s, int64_t n, double* loss_host) {
+  const int L = (int)s->kd.size() - 1;
+  cudaStream_t st = s->stream;
+  FVS_TRY(sg_work(s, n));
+  k_mlp_in<<<stride_grid(n * s->kd[0], 256), 256, 0, st>>>(n, s->nin, s->kd[0], s->Xd.p, s->mu_in.p, s->sd_in.p,
+                                                          s->H[0]->p); FVS_COUNT_LAUNCH();
+  FVS_TRY(sg_forward(s, n, true));
+  const int nb = 256;
+  k_mlp_loss<<<nb, 256, 0, st>>>(n, s->nout, s->kd[L], s->Y.p, s->Td.p, s->mu_out.p, s->sd_out.p, s->d0.p,
+                                 s->part.p); FVS_COUNT_LAUNCH();
+  k_sum_final<<<1, 256, 0, st>>>(nb, s->part.p, 1.0 / ((double)n * s->nout), s->lossv.p); FVS_COUNT_LAUNCH();
+  bf16* dcur = s->d0.p;
+  bf16* dnext = s->d1.p;
+  for (int l = L - 1; l >= 0; --l) {
+    const int K = s->kd[l], N = s->kd[l + 1];
+    // weight gradient dW[N x K] = delta^T H_l : A(m=n, k=b) = delta[b*N + n], B(n'=k, k=b) = H[b*K + k]
+    Epi e{};
+    e.fout = s->g.p + s->woff[l];
+    e.ldo = K;
+    k_mlp_gemm<EPI_WGRAD><<<gemm_grid(N), 128, 0, st>>>(N, K, (int)((n + 15) / 16 * 16), dcur, 1, N,
+                                                        s->H[l]->p, 1, K, e); FVS_COUNT_LAUNCH();
+    k_bias_grad<<<(N + 127) / 128, 128, 0, st>>>((int)n, N, dcur, s->g.p + s->boff[l]); FVS_COUNT_LAUNCH();
+    if (l > 0) {
+      // delta_{l-1} = (delta_l W_l) * gelu'(Z_{l-1}): A(m=b, k=n) = delta[b*N + n], B(n'=k, k=n) = W[n*K + k]
+      Epi d{};
+      d.z = s->Z[l - 1]->p;
+      d.hout = dnext;
+      d.ldo = K;
+      k_mlp_gemm<EPI_DGRAD><<<gemm_grid(n), 128, 0, st>>>((int)n, K, N, dcur, N, 1, s->wb.p + s->woff[l], 1, K, d);
+      FVS_COUNT_LAUNCH();
+      std::swap(dcur, dnext);
+    }
+  }
+  FVS_LAUNCH_CHECK();
+  if (loss_host) {
+    FVS_CUDA(cudaMemcpyAsync(loss_host, s->lossv.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    FVS_CUDA(cudaStreamSynchronize(st));
+  }
+  return FVS_OK;
+}
+
+}  // namespace fvs
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+#define FVS_API extern "C" __attribute__((visibility("default")))
+
+namespace fvs {
+__global__ void k_zero_rows_bf16(int64_t from, int64_t to, int k, bf16* h) {
+  GS(i, (to - from) * (int64_t)k) h[from * k + i] = __float2bfloat16(0.f);
+}
+
+// flattened real parameters (oracle order: per layer W row-major, then b) <-> padded device layout
+static void layout(const fvs_surrogate_s* s, std::vector<int64_t>& dev_index) {
+  dev_index.clear();
+  const int L = (int)s->kd.size() - 1;
+  for (int l = 0; l < L; ++l) {
+    for (int r = 0; r < s->real[l + 1]; ++r)
+      for (int c = 0; c < s->real[l]; ++c) dev_index.push_back(s->woff[l] + (int64_t)r * s->kd[l] + c);
+    for (int r = 0; r < s->real[l + 1]; ++r) dev_index.push_back(s->boff[l] + r);
+  }
+}
+
+static fvs_status upload_xt(fvs_surrogate_s* s, const double* X, const double* T, int64_t n) {
+  FVS_TRY(s->Xd.alloc((size_t)n * s->nin + 1));
+  FVS_CUDA(cudaMemcpyAsync(s->Xd.p, X, n * s->nin * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  if (T) {
+    FVS_TRY(s->Td.alloc((size_t)n * s->nout + 1));
+    FVS_CUDA(cudaMemcpyAsync(s->Td.p, T, n * s->nout * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  }
+  return FVS_OK;
+}
+
+static fvs_status zero_padding_rows(fvs_surrogate_s* s, int64_t n) {
+  const int64_t nr = (n + 15) / 16 * 16;
+  if (nr == n) return FVS_OK;
+  for (size_t l = 0; l < s->H.size(); ++l) {
+    k_zero_rows_bf16<<<1, 256, 0, s->stream>>>(n, nr, s->kd[l], s->H[l]->p); FVS_COUNT_LAUNCH();
+  }
+  // delta buffers hold rows of different widths (>= 16): clear everything
+  // past the first n rows of the narrowest width once; live rows are rewritten
+  int kmax = 0;
+  for (int k : s->kd) kmax = std::max(kmax, k);
+  const size_t tail = s->d0.n - (size_t)n * 16;
+  FVS_CUDA(cudaMemsetAsync(s->d0.p + (size_t)n * 16, 0, tail * sizeof(bf16), s->stream));
+  FVS_CUDA(cudaMemsetAsync(s->d1.p + (size_t)n * 16, 0, tail * sizeof(bf16), s->stream));
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+}  // namespace fvs
+
+FVS_API fvs_status fvs_surrogate_create(int32_t n_in, int32_t n_hidden, int32_t n_hidden_layers, int32_t n_out,
+                                        uint64_t seed, void* stream, fvs_surrogate* out) {
+  if (!out || n_in < 1 || n_in > 128 || n_out < 1 || n_out > 128 || n_hidden < 1 || n_hidden > 128 ||
+      n_hidden_layers < 1 || n_hidden_layers > 16) {
+    set_error("fvs_surrogate_create: widths must be 1..128, hidden layers 1..16");
+    return FVS_ERR_ARG;
+  }
+  *out = nullptr;
+  fvs_surrogate_s* s = new fvs_surrogate_s();
+  s->stream = (cudaStream_t)stream;
+  AllocStream as(s->stream);
+  auto pad = [](int x) { return (x + 15) / 16 * 16; };
+  s->nin = n_in; s->nout = n_out; s->hidden = n_hidden; s->nlayers = n_hidden_layers;
+  s->real.push_back(n_in);
+  for (int l = 0; l < n_hidden_layers; ++l) s->real.push_back(n_hidden);
+  s->real.push_back(n_out);
+  for (int r : s->real) s->kd.push_back(pad(r));
+  const int L = (int)s->kd.size() - 1;
+  int64_t off = 0;
+  for (int l = 0; l < L; ++l) { s->woff.push_back(off); off += (int64_t)s->kd[l + 1] * s->kd[l]; }
+  s->nw = off;
+  for (int l = 0; l < L; ++l) { s->boff.push_back(off); off += s->kd[l + 1]; }
+  s->nparam = off;
+  fvs_status r = FVS_OK;
+  if (r == FVS_OK) r = s->w32.alloc(s->nparam);
+  if (r == FVS_OK) r = s->m.alloc(s->nparam);
+  if (r == FVS_OK) r = s->v.alloc(s->nparam);
+  if (r == FVS_OK) r = s->g.alloc(s->nparam);
+  if (r == FVS_OK) r = s->wb.alloc(s->nw);
+  if (r == FVS_OK) r = s->mask.alloc(s->nparam);
+  if (r == FVS_OK) r = s->mu_in.alloc(128);
+  if (r == FVS_OK) r = s->sd_in.alloc(128);
+  if (r == FVS_OK) r = s->mu_out.alloc(128);
+  if (r == FVS_OK) r = s->sd_out.alloc(128);
+  if (r != FVS_OK) { delete s; return r; }
+  s->w32.zero(s->stream); s->m.zero(s->stream); s->v.zero(s->stream); s->g.zero(s->stream);
+  s->mask.zero(s->stream);
+  for (int l = 0; l < L; ++l) {
+    const int64_t n = (int64_t)s->kd[l + 1] * s->kd[l];
+    const float lim = sqrtf(6.0f / (float)s->real[l]);
+    k_init_w<<<stride_grid(n, 256), 256, 0, s->stream>>>(n, s->kd[l], s->real[l], s->real[l + 1],
+                                                        seed * 1315423911ULL + l, lim, s->w32.p + s->woff[l],
+                                                        s->mask.p + s->woff[l]);
+    FVS_COUNT_LAUNCH();
+  }
+  // biases: live entries start at zero
+  {
+    std::vector<uint8_t> bm(s->nparam - s->nw, 0);
+    for (int l = 0; l < L; ++l)
+      for (int r2 = 0; r2 < s->real[l + 1]; ++r2) bm[s->boff[l] - s->nw + r2] = 1;
+    cudaMemcpyAsync(s->mask.p + s->nw, bm.data(), bm.size(), cudaMemcpyHostToDevice, s->stream);
+    cudaStreamSynchronize(s->stream);
+  }
+  k_to_bf16<<<stride_grid(s->nw, 256), 256, 0, s->stream>>>(s->nw, s->w32.p, s->wb.p);
+  FVS_COUNT_LAUNCH();
+  std::vector<float> one(128, 1.0f), zero(128, 0.0f);
+  cudaMemcpyAsync(s->mu_in.p, zero.data(), 512, cudaMemcpyHostToDevice, s->stream);
+  cudaMemcpyAsync(s->sd_in.p, one.data(), 512, cudaMemcpyHostToDevice, s->stream);
+  cudaMemcpyAsync(s->mu_out.p, zero.data(), 512, cudaMemcpyHostToDevice, s->stream);
+  cudaMemcpyAsync(s->sd_out.p, one.data(), 512, cudaMemcpyHostToDevice, s->stream);
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) {
+    set_error("fvs_surrogate_create: %s", cudaGetErrorString(cudaGetLastError()));
+    delete s;
+    return FVS_ERR_CUDA;
+  }
+  *out = s;
+  return FVS_OK;
+}
+
+FVS_API fvs_status fvs_surrogate_destroy(fvs_surrogate s) {
+  if (!s) return FVS_ERR_ARG;
+  cudaStream_t st = s->stream;
+  {
+    AllocStream as(st);
+    cudaStreamSynchronize(st);
+    delete s;
+  }
+  cudaStreamSynchronize(st);
+  return FVS_OK;
+}
+
+FVS_API fvs_status fvs_surrogate_set_scaling(fvs_surrogate s, const double* mu_in, const double* sd_in,
+                                             const double* mu_out, const double* sd_out) {
+  if (!s || !mu_in || !sd_in || !mu_out || !sd_out) {
+    set_error("fvs_surrogate_set_scaling: NULL argument");
+    return FVS_ERR_ARG;
+  }
+  std::vector<float> a(128, 0.f), b(128, 1.f), c(128, 0.f), d(128, 1.f);
+  for (int i = 0; i < s->nin; ++i) {
+    if (!(sd_in[i] > 0)) { set_error("fvs_surrogate_set_scaling: non-positive scale"); return FVS_ERR_ARG; }
+    a[i] = (float)mu_in[i]; b[i] = (float)sd_in[i];
+  }
+  for (int i = 0; i < s->nout; ++i) {
+    if (!(sd_out[i] > 0)) { set_error("fvs_surrogate_set_scaling: non-positive scale"); return FVS_ERR_ARG; }
+    c[i] = (float)mu_out[i]; d[i] = (float)sd_out[i];
+  }
+  FVS_CUDA(cudaMemcpyAsync(s->mu_in.p, a.data(), 512, cudaMemcpyHostToDevice, s->stream));
+  FVS_CUDA(cudaMemcpyAsync(s->sd_in.p, b.data(), 512, cudaMemcpyHostToDevice, s->stream));
+  FVS_CUDA(cudaMemcpyAsync(s->mu_out.p, c.data(), 512, cudaMemcpyHostToDevice, s->stream));
+  FVS_CUDA(cudaMemcpyAsync(s->sd_out.p, d.data(), 512, cudaMemcpyHostToDevice, s->stream));
+  FVS_CUDA(cudaStreamSynchronize(s->stream));
+  return FVS_OK;
+}
+
+FVS_API int64_t fvs_surrogate_num_params(fvs_surrogate s) {
+  if (!s) return -1;
+  std::vector<int64_t> idx;
+  layout(s, idx);
+  return (int64_t)idx.size();
+}
+
+FVS_API fvs_status fvs_surrogate_params(fvs_surrogate s, double* inout, int64_t len, int set) {
+  if (!s || !inout) {
+    set_error("fvs_surrogate_params: NULL argument");
+    return FVS_ERR_ARG;
+  }
+  AllocStream as(s->stream);
+  std::vector<int64_t> idx;
+  layout(s, idx);
+  if (len < (int64_t)idx.size()) {
+    set_error("fvs_surrogate_params: need %lld values", (long long)idx.size());
+    return FVS_ERR_ARG;
+  }
+  std::vector<float> h(s->nparam);
+  FVS_CUDA(cudaMemcpyAsync(h.data(), s->w32.p, s->nparam * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+  FVS_CUDA(cudaStreamSynchronize(s->stream));
+  if (set) {
+    for (size_t i = 0; i < idx.size(); ++i) h[idx[i]] = (float)inout[i];
+    FVS_CUDA(cudaMemcpyAsync(s->w32.p, h.data(), s->nparam * sizeof(float), cudaMemcpyHostToDevice, s->stream));
+    k_to_bf16<<<stride_grid(s->nw, 256), 256, 0, s->stream>>>(s->nw, s->w32.p, s->wb.p);
+    FVS_COUNT_LAUNCH();
+    FVS_CUDA(cudaStreamSynchronize(s->stream));
+  } else {
+    for (size_t i = 0; i < idx.size(); ++i) inout[i] = (double)h[idx[i]];
+  }
+  return FVS_OK;
+}
+
+FVS_API fvs_status fvs_surrogate_gradients(fvs_surrogate s, const double* X, const double* T, int64_t n,
+                                           double* grad, int64_t grad_len, double* loss) {
+  if (!s || !X || !T || !grad || n <= 0) {
+    set_error("fvs_surrogate_gradients: bad argument");
+    return FVS_ERR_ARG;
+  }
+  AllocStream as(s->stream);
+  std::vector<int64_t> idx;
+  layout(s, idx);
+  if (grad_len < (int64_t)idx.size()) {
+    set_error("fvs_surrogate_gradients: need %lld values", (long long)idx.size());
+    return FVS_ERR_ARG;
+  }
+  FVS_TRY(upload_xt(s, X, T, n));
+  FVS_TRY(sg_work(s, n + 16));
+  FVS_TRY(zero_padding_rows(s, n));
+  FVS_TRY(sg_gradients(s, n, loss));
+  std::vector<float> h(s->nparam);
+  FVS_CUDA(cudaMemcpyAsync(h.data(), s->g.p, s->nparam * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
+  FVS_CUDA(cudaStreamSynchronize(s->stream));
+  for (size_t i = 0; i < idx.size(); ++i) grad[i] = (double)h[idx[i]];
+  return FVS_OK;
+}
+
+FVS_API fvs_status fvs_surrogate_train(fvs_surrogate s, const double* X, const double* T, int64_t n, int32_t epochs,
+                                       double lr, double* final_loss) {
+  if (!s || !X || !T || n <= 0 || epochs < 0 || !(lr > 0)) {
+    set_error("fvs_surrogate_train: bad argument");
+    return FVS_ERR_ARG;
+  }
+  AllocStream as(s->stream);
+  FVS_TRY(upload_xt(s, X, T, n));
+  FVS_TRY(sg_work(s, n + 16));
+  FVS_TRY(zero_padding_rows(s, n));
+  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  for (int e = 0; e < epochs; ++e) {
+    FVS_TRY(sg_gradients(s, n, nullptr));
+    ++s->step;
+    const float c1 = 1.f - powf(b1, (float)s->step), c2 = 1.f - powf(b2, (float)s->step);
+    k_adam<<<stride_grid(s->nparam, 256), 256, 0, s->stream>>>(s->nparam, s->w32.p, s->m.p, s->v.p, s->g.p,
+                                                              s->mask.p, (float)lr, b1, b2, eps, c1, c2, nullptr);
+    FVS_COUNT_LAUNCH();
+    k_to_bf16<<<stride_grid(s->nw, 256), 256, 0, s->stream>>>(s->nw, s->w32.p, s->wb.p);
+    FVS_COUNT_LAUNCH();
+  }
+  FVS_LAUNCH_CHECK();
+  double l = 0.0;
+  FVS_TRY(sg_gradients(s, n, &l));
+  if (final_loss) *final_loss = l;
+  return FVS_OK;
+}
+
+FVS_API fvs_status fvs_surrogate_predict(fvs_surrogate s, const double* X, double* Y, int64_t n, int on_device) {
+  if (!s || !X || !Y || n <= 0) {
+    set_error("fvs_surrogate_predict: bad argument");
+    return FVS_ERR_ARG;
+  }
+  AllocStream as(s->stream);
+  const int L = (int)s->kd.size() - 1;
+  const double* Xd = X;
+  if (!on_device) {
+    FVS_TRY(upload_xt(s, X, nullptr, n));
+    Xd = s->Xd.p;
+  }
+  FVS_TRY(sg_work(s, n + 16));
+  k_mlp_in<<<stride_grid(n * s->kd[0], 256), 256, 0, s->stream>>>(n, s->nin, s->kd[0], Xd, s->mu_in.p, s->sd_in.p,
+                                                                  s->H[0]->p);
+  FVS_COUNT_LAUNCH();
+  FVS_TRY(sg_forward(s, n, false));
+  DBuf<double> out;
+  double* Yd = Y;
+  if (!on_device) {
+    FVS_TRY(out.alloc((size_t)n * s->nout));
+    Yd = out.p;
+  }
+  k_mlp_out<<<stride_grid(n * s->nout, 256), 256, 0, s->stream>>>(n, s->nout, s->kd[L], s->Y.p, s->mu_out.p,
+                                                                  s->sd_out.p, Yd);
+  FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  if (!on_device) FVS_CUDA(cudaMemcpyAsync(Y, Yd, n * s->nout * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  FVS_CUDA(cudaStreamSynchronize(s->stream));
+  return FVS_OK;
+}

@@ -73,4 +73,6 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* st);
 fvs_status solver_pressure_solve(fvs_solver s, const double* rhs, double* p_out, double rtol, int* iters,
                                  double* relres);
 fvs_status solver_query(fvs_solver s, fvs_field f, double* dst, int64_t len, int on_device);
+fvs_status uq_batch(fvs_mesh mesh, const fvs_props* base, int64_t n, const double* inputs, double dt,
+                    int max_steps, int n_streams, double* qoi, int64_t* steps);
 }  // namespace fvs

@@ -100,7 +100,18 @@ _SIGS = {
     "fvs_pressure_solve": ([_P, _P, _P, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double)], C.c_int),
     "fvs_query_fields": ([_P, C.c_int, _P, C.c_int64, C.c_int], C.c_int),
     "fvs_get_time": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
+    "fvs_surrogate_create": ([C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, _P, C.POINTER(_P)],
+                             C.c_int),
+    "fvs_surrogate_destroy": ([_P], C.c_int),
+    "fvs_surrogate_set_scaling": ([_P, _P, _P, _P, _P], C.c_int),
+    "fvs_surrogate_num_params": ([_P], C.c_int64),
+    "fvs_surrogate_params": ([_P, _P, C.c_int64, C.c_int], C.c_int),
+    "fvs_surrogate_gradients": ([_P, _P, _P, C.c_int64, _P, C.c_int64, C.POINTER(C.c_double)], C.c_int),
+    "fvs_surrogate_train": ([_P, _P, _P, C.c_int64, C.c_int32, C.c_double, C.POINTER(C.c_double)], C.c_int),
+    "fvs_surrogate_predict": ([_P, _P, _P, C.c_int64, C.c_int], C.c_int),
     "fvs_profile_enable": ([_P, C.c_int], C.c_int),
+    "fvs_uq_batch": ([_P, C.POINTER(fvs_props), C.c_int64, _P, C.c_double, C.c_int32, C.c_int32, C.c_int32, _P,
+                      _P], C.c_int),
     "fvs_profile_read": ([_P, C.POINTER(fvs_kernel_time), C.c_int32, C.POINTER(C.c_int32)], C.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
@@ -186,6 +197,83 @@ class Mesh:
     def close(self):
         if self.h:
             fvs_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def uq_batch(mesh, props, inputs, dt, max_steps, n_streams=0):
+    """Plain batched UQ solves: inputs [S, 3] (T_melt, T_wall, C0) -> (qoi [S, 4], steps [S])."""
+    inputs = np.ascontiguousarray(inputs, dtype=np.float64)
+    n = len(inputs)
+    qoi = np.empty((n, 4), dtype=np.float64)
+    steps = np.empty(n, dtype=np.int64)
+    pr = make_props(props)
+    check(fvs_uq_batch(mesh.h, C.byref(pr), n, _ptr(inputs), float(dt), int(max_steps), 0, int(n_streams),
+                       _ptr(qoi), _ptr(steps)), "fvs_uq_batch")
+    return qoi, steps
+
+
+class Surrogate:
+    """Owns an fvs_surrogate handle (BF16 tensor-core MLP)."""
+
+    def __init__(self, n_in, n_hidden, n_layers, n_out, seed=0, stream=None):
+        h = C.c_void_p()
+        check(fvs_surrogate_create(n_in, n_hidden, n_layers, n_out, seed, _stream_ptr(stream), C.byref(h)),
+              "fvs_surrogate_create")
+        self.h = h
+        self.n_in, self.n_out = n_in, n_out
+
+    def set_scaling(self, mu_in, sd_in, mu_out, sd_out):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (mu_in, sd_in, mu_out, sd_out)]
+        check(fvs_surrogate_set_scaling(self.h, *[_ptr(a) for a in arrs]), "fvs_surrogate_set_scaling")
+
+    def num_params(self):
+        return int(fvs_surrogate_num_params(self.h))
+
+    def get_params(self):
+        p = np.empty(self.num_params(), dtype=np.float64)
+        check(fvs_surrogate_params(self.h, _ptr(p), len(p), 0), "fvs_surrogate_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float64)
+        check(fvs_surrogate_params(self.h, _ptr(p), len(p), 1), "fvs_surrogate_params")
+
+    def gradients(self, X, T):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        g = np.empty(self.num_params(), dtype=np.float64)
+        loss = C.c_double()
+        check(fvs_surrogate_gradients(self.h, _ptr(X), _ptr(T), len(X), _ptr(g), len(g), C.byref(loss)),
+              "fvs_surrogate_gradients")
+        return g, loss.value
+
+    def train(self, X, T, epochs, lr):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        loss = C.c_double()
+        check(fvs_surrogate_train(self.h, _ptr(X), _ptr(T), len(X), int(epochs), float(lr), C.byref(loss)),
+              "fvs_surrogate_train")
+        return loss.value
+
+    def predict(self, X, out=None):
+        """Host numpy in/out, or device tensors (X [n, n_in], out [n, n_out])."""
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, dtype=np.float64)
+            Y = np.empty((len(X), self.n_out), dtype=np.float64)
+            check(fvs_surrogate_predict(self.h, _ptr(X), _ptr(Y), len(X), 0), "fvs_surrogate_predict")
+            return Y
+        check(fvs_surrogate_predict(self.h, _ptr(X), _ptr(out), X.shape[0], 1), "fvs_surrogate_predict")
+        return out
+
+    def close(self):
+        if self.h:
+            fvs_surrogate_destroy(self.h)
             self.h = None
 
     def __del__(self):

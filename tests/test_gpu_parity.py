@@ -184,3 +184,28 @@ def test_mixed_precision_matches_fp64(fvs):
     for k in ("T", "U", "P"):
         assert rel(runs[1][k], runs[0][k]) <= 1e-6, (k, rel(runs[1][k], runs[0][k]))
         assert rel(runs[1][k], ref[k]) <= 1e-6, (k, rel(runs[1][k], ref[k]))
+
+
+def test_uq_batch_matches_oracle(fvs):
+    """fvs_uq_batch: each sample is a plain solve with its own melt and wall
+    temperatures and liquidus; per-sample means of t_f, cooling rate, SDAS and
+    yield equal the oracle's runs of the same samples to full solidification."""
+    m = box_mesh(8, 8, 2, (0.01, 0.01, 0.0025))
+    inputs = np.array([[930.0, 700.0, 4.0], [955.0, 680.0, 3.2], [942.0, 735.0, 4.8]])
+    props = cases.props(**TIGHT)
+    M = fvs.Mesh(m)
+    qoi, steps = fvs.uq_batch(M, props, inputs, 2e-3, 400, n_streams=2)
+    for i, (Tm, Tw, C0) in enumerate(inputs):
+        mat = dict(props["material"], T_liq=913.0 - 5.0 * (C0 - 4.0))
+        o = Oracle(m, cases.props(material=mat, walls=cases.all_walls(Tw), T_init=Tm, **TIGHT))
+        k = 0
+        while k < 400:
+            st = o.step(2e-3)
+            k += 1
+            if st["n_active"] == 0:
+                break
+        assert steps[i] == k
+        q = o.qoi()
+        done = np.isfinite(q["t_f"])
+        ref = [q[name][done].mean() for name in ("t_f", "cooling_rate", "sdas", "yield_strength")]
+        np.testing.assert_allclose(qoi[i], ref, rtol=1e-8)
