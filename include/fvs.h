@@ -290,6 +290,25 @@ typedef struct {
 fvs_status fvs_profile_enable(fvs_solver solver, int on);
 fvs_status fvs_profile_read(fvs_solver solver, fvs_kernel_time* out, int32_t max_records, int32_t* n_records);
 
+/* Same values and argument meaning as fvs_query_fields with a host
+ * destination, for callers that must not allocate GPU memory (the paper has
+ * no counterpart: this is a service of the library).  fvs_query_fields
+ * stages the reordered field in a temporary device buffer; a caller that
+ * samples a running simulation from a thread that must not block on or fail
+ * in the allocator, or that runs with its device memory already fully
+ * committed, cannot afford that.  This entry point stages the field in a
+ * fixed device array built into the library instead, and calls no
+ * allocating routine.
+ *   dst  host memory of dst_len doubles
+ * Limit: fields of at most 1,048,576 values (8 MiB of staging, held by every
+ * GPU that loads the library until the process exits); larger fields fail
+ * with FVS_ERR_ARG (use fvs_query_fields).  The first call on a device looks
+ * up the array's device address (make that first call before any CUDA stream
+ * capture).  All calls share the array: each call overwrites every value it
+ * returns, and calls whose GPU work overlaps (other streams, other threads)
+ * race on it. */
+fvs_status fvs_query_fields_noalloc(fvs_solver solver, fvs_field field, double* dst, int64_t dst_len);
+
 /* Current simulated time and step count. */
 fvs_status fvs_get_time(fvs_solver solver, double* time, int64_t* steps);
 

@@ -100,6 +100,7 @@ _SIGS = {
     "fvs_pressure_solve": ([_P, _P, _P, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double)], C.c_int),
     "fvs_query_fields": ([_P, C.c_int, _P, C.c_int64, C.c_int], C.c_int),
     "fvs_get_time": ([_P, C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
+    "fvs_query_fields_noalloc": ([_P, C.c_int, _P, C.c_int64], C.c_int),
     "fvs_surrogate_create": ([C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_uint64, _P, C.POINTER(_P)],
                              C.c_int),
     "fvs_surrogate_destroy": ([_P], C.c_int),
