@@ -44,6 +44,12 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-n", type=int, default=20, help="cells per axis of the oracle sample")
     ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--no-uq", action="store_true")
+    ap.add_argument("--prof-steps", type=int, default=3, help="steps with per-kernel event timing")
+    ap.add_argument("--uq-n", type=int, default=32, help="cells per axis of the UQ cavity")
+    ap.add_argument("--uq-samples", type=int, default=32)
+    ap.add_argument("--uq-streams", type=int, default=16)
+    ap.add_argument("--uq-dt", type=float, default=2e-3)
     return ap.parse_args()
 
 
@@ -189,7 +195,6 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    S.profile(True)
     clocks = Clocks(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
                     if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/fvs_clocks.csv")
     clocks.start()
@@ -208,6 +213,11 @@ def run_gpu(args):
     n_launch = fvs.fvs_launch_count() - n_launch0
     ms = ev0.elapsed_time(ev1)
     ck = clocks.stop()
+    # per-kernel event timing right after the timed region, on the same
+    # stream, for --prof-steps further steps (kernels run eagerly while timed)
+    S.profile(True)
+    for _ in range(args.prof_steps):
+        S.step(dt, 1, allow_not_converged=True)
     prof = S.profile_read()
     S.profile(False)
     if dist:
@@ -229,12 +239,17 @@ def run_gpu(args):
         ach = per_launch_bytes / per_launch_s / 1e9
         roof = dict(bound="hbm", kernel=top["name"], achieved=round(ach, 1), peak=peak, unit="GB/s",
                     frac=round(ach / peak, 4), traffic=None, peak_source=f"{peak_kind} copy bandwidth",
-                    launches=top["launches"], share_of_step=round(top["total_ms"] / ms, 3),
+                    launches=top["launches"],
+                    share_of_step=round(top["total_ms"] / max(1, args.prof_steps) / (ms / args.steps), 3),
                     bytes_per_launch=per_launch_bytes)
 
     e2e = None
     if not args.no_e2e and rank == 0:
         e2e = run_e2e(fvs, c, props, args, stream, torch)
+
+    uq = None
+    if not args.no_uq and rank == 0:
+        uq = run_uq(fvs, args)
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
@@ -250,19 +265,50 @@ def run_gpu(args):
                              f"{args.precision}", cells=args.n ** 3, dt=dt, p_rtol=1e-8,
                     precision=args.precision, l2="inputs larger than L2 (matrices ~1 GB)",
                     parallelism="replicas" if world > 1 else "single GPU"),
-        roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=ck,
+        roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=ck, uq=uq,
         gpu_launches=int(n_launch),
         kernel_profile=sorted(prof, key=lambda r: -r["total_ms"])[:8],
         step_stats=dict(p_its=[s["p_its"] for s in its], e_its=[s["e_its"] for s in its],
                         e_lin_its=[s["e_lin_its"] for s in its], mom_its=[s["mom_its"] for s in its],
                         p_relres=max(s["p_relres"] for s in its), fallback=sum(s["fallback"] for s in its),
-                        amg_levels=its[-1]["amg_levels"], n_active_last=its[-1]["n_active"]),
+                        amg_levels=its[-1]["amg_levels"], n_active_last=its[-1]["n_active"],
+                        p_rebuilt=[s["p_rebuilt"] for s in its], setup_ms=[round(s["setup_ms"], 2) for s in its]),
     )
     line["gpu_launches_profiled"] = nkern
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def run_uq(fvs, args):
+    """UQ samples/s: plain batched solves to full solidification, then the
+    surrogate trained on them evaluated on 1e6 Monte Carlo inputs."""
+    import numpy as np
+    from fvs_inputs import box_mesh, cases
+    n = args.uq_n
+    m = box_mesh(n, n, n, cases.CAVITY)
+    M = fvs.Mesh(m)
+    props = bench_props("mixed")
+    X = cases.uq_inputs(args.uq_samples, seed=2018)
+    t0 = time.perf_counter()
+    Y, steps = fvs.uq_batch(M, props, X, args.uq_dt, 20000, n_streams=args.uq_streams)
+    sec = time.perf_counter() - t0
+    plain = args.uq_samples / sec
+    S = fvs.Surrogate(3, 128, 4, 4, seed=1)
+    S.set_scaling(X.mean(0), X.std(0), Y.mean(0), Y.std(0))
+    S.train(X, Y, 2000, 1e-3)
+    Xmc = cases.uq_inputs(1000000, seed=4)
+    S.predict(Xmc[:4096])
+    t1 = time.perf_counter()
+    Ymc = S.predict(Xmc)
+    sur = len(Xmc) / (time.perf_counter() - t1)
+    return dict(plain_samples_per_s=round(plain, 3), surrogate_samples_per_s=round(sur, 1), unit="samples/s",
+                samples=args.uq_samples, mesh=f"cavity {n}^3, all walls at the sampled temperature",
+                dt=args.uq_dt, mean_steps=float(np.mean(steps)), streams=args.uq_streams,
+                qoi_mean_plain=[float(v) for v in Y.mean(0)], qoi_mean_surrogate_1e6=[float(v) for v in Ymc.mean(0)],
+                note="plain: fvs_uq_batch to full solidification (mixed precision); surrogate: BF16 MLP "
+                     "trained on those solves, inference on 1e6 inputs (host in/out)")
 
 
 def run_e2e(fvs, c, props, args, stream, torch):

@@ -164,8 +164,12 @@ typedef struct {
   int32_t n_components; /* connected parts of the pressure system            */
   int32_t amg_levels;
   int32_t status;     /* fvs_status of the step                              */
-  int32_t p_rebuilt;  /* 1 if the pressure system and its AMG were rebuilt
-                         (some cell changed phase), 0 if reused               */
+  int32_t p_rebuilt;  /* pressure system of this step: 0 reused unchanged
+                         (no cell changed phase), 1 renumbered with the AMG
+                         hierarchy built anew, 2 reassembled on the kept
+                         numbering with the hierarchy refreshed on its fine
+                         level (cells only froze)                             */
+  double setup_ms;    /* host wall time of that rebuild (0 if reused)        */
 } fvs_step_stats;
 
 /* Advance n_steps time steps of size dt (Section 2.2, steps 1-5 plus the

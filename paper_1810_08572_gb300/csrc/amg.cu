@@ -2,6 +2,7 @@
 // coarse operators, pinned dense coarsest inverse, component labels) and the
 // V-cycle (damped Jacobi, piecewise-constant restriction / prolongation).
 #include <algorithm>
+#include <chrono>
 #include <climits>
 #include <cstdlib>
 
@@ -12,6 +13,7 @@ namespace fvs {
 #define GS(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
 static constexpr int GAL_CAP = 2048;   // entries gathered per coarse row
+static constexpr int GAL_SMALL = 256;  // rows up to this many entries: the many-warp kernel
 
 // ---------------------------------------------------------------------------
 // strength of connection: j is strong for i if -a_ij >= theta max_k(-a_ik)
@@ -26,31 +28,25 @@ __global__ void k_maxoff(int64_t n, int w, const int32_t* col, const double* val
       if (col[e] != (int32_t)i) m = fmax(m, -val[e]);
     }
     mo[i] = m;
-    dinv[i] = 1.0 / diag[i];
+    dinv[i] = diag[i] != 0.0 ? 1.0 / diag[i] : 0.0;   // empty rows (refresh) stay untouched
   }
 }
 
 __global__ void k_strong(int64_t n, int w, const int32_t* col, const double* val, const double* mo, double theta,
                          uint64_t* mask) {
   GS(i, n) {
+    // judged from row i alone (the strength graph may be slightly
+    // asymmetric; the independent-set rounds and the assignment only ever
+    // look at a node's own mask, so that stays consistent).  Slots beyond 64
+    // are never strong.
     uint64_t msk = 0;
-    for (int k = 0; k < w; ++k) {
+    const int wk = w < 64 ? w : 64;
+    for (int k = 0; k < wk; ++k) {
       const int64_t e = (int64_t)k * n + i;
       const int32_t j = col[e];
       if (j == (int32_t)i) continue;
       const double a = -val[e];
-      bool s = a > 0.0 && a >= theta * mo[i];
-      if (!s) {
-        for (int q = 0; q < w; ++q) {
-          const int64_t ej = (int64_t)q * n + j;
-          if (col[ej] == (int32_t)i) {
-            const double b = -val[ej];
-            s = b > 0.0 && b >= theta * mo[j];
-            break;
-          }
-        }
-      }
-      if (s) msk |= (1ULL << k);
+      if (a > 0.0 && a >= theta * mo[i]) msk |= (1ULL << k);
     }
     mask[i] = msk;
   }
@@ -127,13 +123,22 @@ __global__ void k_assign(int64_t n, int w, const int32_t* col, const double* val
   }
 }
 
+// rows with agg < 0 (left out by a refresh) belong to no aggregate
 __global__ void k_count_members(int64_t n, const int32_t* agg, int32_t* cnt) {
-  GS(i, n) atomicAdd(&cnt[agg[i]], 1);
+  GS(i, n) if (agg[i] >= 0) atomicAdd(&cnt[agg[i]], 1);
 }
 __global__ void k_fill_members(int64_t n, const int32_t* agg, const int32_t* ptr, int32_t* cur, int32_t* idx) {
   GS(i, n) {
     const int32_t a = agg[i];
-    idx[ptr[a] + atomicAdd(&cur[a], 1)] = (int32_t)i;
+    if (a >= 0) idx[ptr[a] + atomicAdd(&cur[a], 1)] = (int32_t)i;
+  }
+}
+// refresh: rows whose cells carry no pressure leave their aggregates (a row
+// regaining pressure would need a new aggregation: flagged)
+__global__ void k_mask_agg(int64_t n, const int32_t* act, const uint8_t* ppe, int32_t* agg, int* err) {
+  GS(i, n) {
+    if (!ppe[act[i]]) agg[i] = -1;
+    else if (agg[i] < 0) atomicOr(err, 8);
   }
 }
 __global__ void k_sort_members(int64_t nc, const int32_t* ptr, int32_t* idx) {
@@ -153,19 +158,25 @@ __global__ void k_sort_members(int64_t nc, const int32_t* ptr, int32_t* idx) {
 // shared memory, bitonic-sort by key, reduce equal keys in a fixed order
 // (deterministic).  Pass 1 counts entries, pass 2 writes the ELL rows.
 // ---------------------------------------------------------------------------
-template <bool FILL>
-__global__ void __launch_bounds__(32) k_galerkin(int64_t nc, int64_t n, int w, const int32_t* col, const double* val,
-                                                 const int32_t* agg, const int32_t* mptr, const int32_t* midx,
-                                                 int32_t* rowlen, int wc, int32_t* ccol, double* cval, double* cdiag,
-                                                 int* err) {
-  __shared__ int32_t key[GAL_CAP];
-  __shared__ double v[GAL_CAP];
-  const int lane = threadIdx.x;
-  for (int64_t I = blockIdx.x; I < nc; I += gridDim.x) {
+// Two instances: CAP = GAL_SMALL with several warps per block (most rows;
+// high occupancy) takes rows of at most GAL_SMALL gathered entries, CAP =
+// GAL_CAP with one warp per block the rest (min_total = GAL_SMALL).
+template <bool FILL, int CAP, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) k_galerkin(int64_t nc, int64_t n, int w, const int32_t* col,
+                                                         const double* val, const int32_t* agg, const int32_t* mptr,
+                                                         const int32_t* midx, int32_t* rowlen, int wc, int32_t* ccol,
+                                                         double* cval, double* cdiag, int* err, int min_total) {
+  __shared__ int32_t key_s[WARPS * CAP];
+  __shared__ double v_s[WARPS * CAP];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int32_t* key = key_s + wid * CAP;
+  double* v = v_s + wid * CAP;
+  for (int64_t I = (int64_t)blockIdx.x * WARPS + wid; I < nc; I += (int64_t)gridDim.x * WARPS) {
     const int32_t lo = mptr[I], hi = mptr[I + 1];
     const int total = (hi - lo) * w;
-    if (total > GAL_CAP) {
-      if (lane == 0) { atomicOr(err, 2); if (!FILL) rowlen[I] = 0; }
+    if (total <= min_total) continue;
+    if (total > CAP) {
+      if (CAP >= GAL_CAP && lane == 0) { atomicOr(err, 2); if (!FILL) rowlen[I] = 0; }
       continue;
     }
     int P = 32;
@@ -240,144 +251,338 @@ __global__ void k_max_int(int64_t n, const int32_t* a, int* out) {
 }
 
 // ---------------------------------------------------------------------------
-// coarsest level: dense copy, connected parts, pins, Gauss-Jordan inverse
-// (one block; n <= AmgOptions::coarsest)
+// coarsest level: dense copy, connected parts, pins, Gauss-Jordan inverse.
+// Larger coarsest levels (n > SMEM_COARSEST) are inverted in place in global
+// memory by the whole GPU: one small pivot launch and one elimination launch
+// per column (FP64 arithmetic is scarce on this part, so the O(n^3) work is
+// spread over every SM instead of one block).
 // ---------------------------------------------------------------------------
-__global__ void k_coarsest(int n, int w, const int32_t* col, const double* val, double* M, double* Ainv,
-                           int32_t* lab, uint8_t* sing, int* ncomp_out, int* err) {
-  extern __shared__ double shd[];
-  double* fac = shd;                 // [n]
-  __shared__ int piv;
-  __shared__ double pmax;
-  const int n2 = 2 * n;
-  // augmented [D | I]
-  for (int e = threadIdx.x; e < n * n2; e += blockDim.x) M[e] = 0.0;
+__global__ void k_dense_fill(int n, int w, const int32_t* col, const double* val, double* M) {
+  GS(i, n) {
+    for (int k = 0; k < w; ++k) M[(int64_t)i * n + col[(int64_t)k * n + i]] += val[(int64_t)k * n + i];
+  }
+}
+// Connected parts of the symmetric pattern of M: the block builds a bit
+// matrix of the pattern and the row sums in shared memory, then one thread
+// runs a breadth-first search over 32-bit words.  Each singular part (zero
+// row sums) gets its first (lowest) row pinned.  'order' lists the rows
+// grouped by part, parts in order of discovery.
+static constexpr int DENSE_PARTS_MAX = 1024;
+static size_t dense_parts_smem(int n) {
+  const size_t nw = (size_t)(n + 31) / 32;
+  return 2 * (size_t)n * sizeof(double) + ((size_t)n * nw + nw + (size_t)n) * sizeof(uint32_t);
+}
+__global__ void __launch_bounds__(1024) k_dense_parts(int n, double* M, int32_t* lab, uint8_t* sing, int32_t* order,
+                                                      int* ncomp_out) {
+  extern __shared__ double psm[];
+  const int nw = (n + 31) / 32;
+  double* rs = psm;                                   // [n] row sums
+  double* dg = rs + n;                                // [n] |diagonal|
+  uint32_t* adj = (uint32_t*)(dg + n);                // [n][nw]
+  uint32_t* vis = adj + (size_t)n * nw;               // [nw]
+  int* queue = (int*)(vis + nw);                      // [n]
+  for (int e = threadIdx.x; e < n * nw; e += blockDim.x) adj[e] = 0u;
+  for (int e = threadIdx.x; e < nw; e += blockDim.x) vis[e] = 0u;
   __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e - i * n;
+    if (M[e] != 0.0) {
+      atomicOr(&adj[i * nw + (j >> 5)], 1u << (j & 31));
+      atomicOr(&adj[j * nw + (i >> 5)], 1u << (i & 31));
+    }
+  }
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    for (int k = 0; k < w; ++k) M[(int64_t)i * n2 + col[(int64_t)k * n + i]] += val[(int64_t)k * n + i];
-    M[(int64_t)i * n2 + n + i] = 1.0;
+    double a = 0.0;
+    for (int j = 0; j < n; ++j) a += M[(int64_t)i * n + j];
+    rs[i] = a;
+    dg[i] = fabs(M[(int64_t)i * n + i]);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    // connected parts by breadth-first search over the symmetric pattern
-    for (int i = 0; i < n; ++i) lab[i] = -1;
-    int nc = 0;
-    int* queue = (int*)(fac);       // reuse shared memory as a queue (n ints fit in n doubles)
+    int nc = 0, qt = 0;
     for (int s0 = 0; s0 < n; ++s0) {
-      if (lab[s0] >= 0) continue;
-      int qh = 0, qt = 0;
+      if ((vis[s0 >> 5] >> (s0 & 31)) & 1u) continue;
+      const int start = qt;
+      int qh = qt;
       queue[qt++] = s0;
-      lab[s0] = nc;
+      vis[s0 >> 5] |= 1u << (s0 & 31);
       while (qh < qt) {
         const int i = queue[qh++];
-        for (int j = 0; j < n; ++j)
-          if (lab[j] < 0 && (M[(int64_t)i * n2 + j] != 0.0 || M[(int64_t)j * n2 + i] != 0.0)) {
-            lab[j] = nc;
-            queue[qt++] = j;
+        lab[i] = nc;
+        for (int w = 0; w < nw; ++w) {
+          uint32_t c = adj[i * nw + w] & ~vis[w];
+          vis[w] |= c;
+          while (c) {
+            const int b = __ffs(c) - 1;
+            c &= c - 1u;
+            queue[qt++] = w * 32 + b;
           }
+        }
       }
+      double r = 0.0, sc = 0.0;
+      for (int q = start; q < qt; ++q) {
+        r += rs[queue[q]];
+        sc += dg[queue[q]];
+      }
+      const bool sg = fabs(r) <= 1e-9 * sc;
+      sing[nc] = sg ? 1 : 0;
+      if (sg)   // pin the first row of the part: p = 0 there
+        for (int j = 0; j < n; ++j) M[(int64_t)s0 * n + j] = (j == s0) ? 1.0 : 0.0;
       ++nc;
-    }
-    // singular parts: row sums vanish; pin the first unknown of each
-    for (int c = 0; c < nc; ++c) {
-      double rs = 0.0, sc = 0.0;
-      int first = -1;
-      for (int i = 0; i < n; ++i) {
-        if (lab[i] != c) continue;
-        if (first < 0) first = i;
-        for (int j = 0; j < n; ++j) rs += M[(int64_t)i * n2 + j];
-        sc += fabs(M[(int64_t)i * n2 + i]);
-      }
-      const bool sg = fabs(rs) <= 1e-9 * sc;
-      sing[c] = sg ? 1 : 0;
-      if (sg) {
-        for (int j = 0; j < n; ++j) M[(int64_t)first * n2 + j] = 0.0;
-        M[(int64_t)first * n2 + first] = 1.0;
-      }
     }
     *ncomp_out = nc;
   }
   __syncthreads();
-  // Gauss-Jordan with partial pivoting
+  for (int q = threadIdx.x; q < n; q += blockDim.x) order[q] = queue[q];
+}
+// column k: partial pivot (largest |M[i][k]|, i >= k, lowest index on ties),
+// row swap, scaling of the pivot row, elimination factors
+__global__ void __launch_bounds__(256) k_gj_pivot(int n, int k, double* M, double* fac, int32_t* perm, int* err) {
+  __shared__ double bv[256];
+  __shared__ int bi[256];
+  if (*err) return;
+  double best = -1.0;
+  int arg = n;
+  for (int i = k + threadIdx.x; i < n; i += blockDim.x) {
+    const double a = fabs(M[(int64_t)i * n + k]);
+    if (a > best) { best = a; arg = i; }
+  }
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = arg;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      const double b2 = bv[threadIdx.x + o];
+      const int i2 = bi[threadIdx.x + o];
+      if (b2 > bv[threadIdx.x] || (b2 == bv[threadIdx.x] && i2 < bi[threadIdx.x])) {
+        bv[threadIdx.x] = b2;
+        bi[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  const int p = bi[0];
+  if (!(bv[0] > 1e-300)) {
+    if (threadIdx.x == 0) atomicOr(err, 8);
+    return;
+  }
+  if (threadIdx.x == 0) perm[k] = p;
+  if (p != k)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const double t = M[(int64_t)k * n + j];
+      M[(int64_t)k * n + j] = M[(int64_t)p * n + j];
+      M[(int64_t)p * n + j] = t;
+    }
+  __syncthreads();
+  const double inv = 1.0 / M[(int64_t)k * n + k];
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    if (i == k) {
+      fac[i] = 0.0;
+    } else {
+      fac[i] = M[(int64_t)i * n + k];
+      M[(int64_t)i * n + k] = 0.0;
+    }
+  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x)
+    M[(int64_t)k * n + j] = (j == k ? 1.0 : M[(int64_t)k * n + j]) * inv;
+}
+// rows i != k: M[i][:] -= fac[i] * M[k][:]  (one block per row)
+__global__ void __launch_bounds__(128) k_gj_elim(int n, int k, double* M, const double* fac, const int* err) {
+  if (*err) return;
+  for (int i = blockIdx.x; i < n; i += gridDim.x) {
+    const double f = fac[i];
+    if (i == k || f == 0.0) continue;
+    double* Mi = M + (int64_t)i * n;
+    const double* Mk = M + (int64_t)k * n;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) Mi[j] -= f * Mk[j];
+  }
+}
+// undo the row swaps as column swaps, last first (one thread per row)
+__global__ void k_gj_unswap(int n, double* M, const int32_t* perm, const int* err) {
+  if (*err) return;
+  GS(i, n) {
+    double* Mi = M + (int64_t)i * n;
+    for (int k = n - 1; k >= 0; --k) {
+      const int p = perm[k];
+      if (p != k) { const double t = Mi[k]; Mi[k] = Mi[p]; Mi[p] = t; }
+    }
+  }
+}
+// M <- P M (LEFT) or M P (!LEFT), P v = v - (mean of v on each singular part)
+template <bool LEFT>
+__global__ void k_dense_fold(int n, double* M, const int32_t* lab, const uint8_t* sing, const int32_t* order,
+                             const int* ncomp, const int* err) {
+  if (*err) return;
+  const int ncs = *ncomp;
+  GS(t, n) {
+    int pos = 0;
+    for (int c = 0; c < ncs; ++c) {
+      int cnt = 0;
+      double sum = 0.0;
+      for (int q = pos; q < n && lab[order[q]] == c; ++q, ++cnt)
+        sum += LEFT ? M[(int64_t)order[q] * n + t] : M[(int64_t)t * n + order[q]];
+      if (sing[c]) {
+        const double m = sum / (double)cnt;
+        for (int q = pos; q < pos + cnt; ++q) {
+          if (LEFT) M[(int64_t)order[q] * n + t] -= m;
+          else M[(int64_t)t * n + order[q]] -= m;
+        }
+      }
+      pos += cnt;
+    }
+  }
+}
+
+// Small coarsest levels (n <= SMEM_COARSEST): the same pinned inverse, but
+// in place in shared memory (one block), which is an order of magnitude
+// faster than the global-memory version above.
+static constexpr int SMEM_COARSEST = 160;
+
+__global__ void __launch_bounds__(1024) k_coarsest_smem(int n, int w, const int32_t* col, const double* val,
+                                                        double* Ainv, int32_t* lab, uint8_t* sing,
+                                                        int* ncomp_out, int* err) {
+  extern __shared__ double smem[];
+  double* M = smem;                          // [n*n] in-place inverse
+  double* fac = M + n * n;                   // [n]
+  int* perm = (int*)(fac + n);               // [n] row swaps
+  int* lb = perm + n;                        // [n] labels
+  int* order = lb + n;                       // [n] rows grouped by part
+  __shared__ int piv, ncs;
+  __shared__ double pval;
+  __shared__ uint8_t sg[SMEM_COARSEST];
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) M[e] = 0.0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    for (int k = 0; k < w; ++k) M[i * n + col[(int64_t)k * n + i]] += val[(int64_t)k * n + i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // connected parts (breadth-first over the symmetric pattern), queue in 'order'
+    for (int i = 0; i < n; ++i) lb[i] = -1;
+    int nc = 0;
+    for (int s0 = 0; s0 < n; ++s0) {
+      if (lb[s0] >= 0) continue;
+      int qh = 0, qt = 0;
+      order[qt++] = s0;
+      lb[s0] = nc;
+      while (qh < qt) {
+        const int i = order[qh++];
+        for (int j = 0; j < n; ++j)
+          if (lb[j] < 0 && (M[i * n + j] != 0.0 || M[j * n + i] != 0.0)) {
+            lb[j] = nc;
+            order[qt++] = j;
+          }
+      }
+      ++nc;
+    }
+    for (int c = 0; c < nc; ++c) {
+      double rs = 0.0, sc = 0.0;
+      int first = -1;
+      for (int i = 0; i < n; ++i) {
+        if (lb[i] != c) continue;
+        if (first < 0) first = i;
+        for (int j = 0; j < n; ++j) rs += M[i * n + j];
+        sc += fabs(M[i * n + i]);
+      }
+      const bool s = fabs(rs) <= 1e-9 * sc;
+      sg[c] = s ? 1 : 0;
+      if (s) {
+        for (int j = 0; j < n; ++j) M[first * n + j] = 0.0;
+        M[first * n + first] = 1.0;
+      }
+    }
+    int pos = 0;
+    for (int c = 0; c < nc; ++c)
+      for (int i = 0; i < n; ++i)
+        if (lb[i] == c) order[pos++] = i;
+    ncs = nc;
+    *ncomp_out = nc;
+  }
+  __syncthreads();
+  // in-place Gauss-Jordan with partial (row) pivoting
   for (int k = 0; k < n; ++k) {
     if (threadIdx.x == 0) {
       int p = k;
-      double best = fabs(M[(int64_t)k * n2 + k]);
+      double best = fabs(M[k * n + k]);
       for (int i = k + 1; i < n; ++i) {
-        const double a = fabs(M[(int64_t)i * n2 + k]);
+        const double a = fabs(M[i * n + k]);
         if (a > best) { best = a; p = i; }
       }
       piv = p;
-      pmax = best;
+      perm[k] = p;
+      pval = best;
     }
     __syncthreads();
-    if (!(pmax > 1e-300)) {
+    if (!(pval > 1e-300)) {
       if (threadIdx.x == 0) atomicOr(err, 8);
       return;
     }
-    if (piv != k) {
-      for (int j = threadIdx.x; j < n2; j += blockDim.x) {
-        const double t = M[(int64_t)k * n2 + j];
-        M[(int64_t)k * n2 + j] = M[(int64_t)piv * n2 + j];
-        M[(int64_t)piv * n2 + j] = t;
+    if (piv != k)
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const double t = M[k * n + j];
+        M[k * n + j] = M[piv * n + j];
+        M[piv * n + j] = t;
       }
+    __syncthreads();
+    const double inv = 1.0 / M[k * n + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) M[k * n + j] = (j == k ? 1.0 : M[k * n + j]) * inv;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) fac[i] = (i == k) ? 0.0 : M[i * n + k];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != k) M[i * n + k] = 0.0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, j = e - i * n;
+      if (i != k) M[e] -= fac[i] * M[k * n + j];
     }
     __syncthreads();
-    const double inv = 1.0 / M[(int64_t)k * n2 + k];
-    __syncthreads();
-    for (int j = threadIdx.x; j < n2; j += blockDim.x) M[(int64_t)k * n2 + j] *= inv;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) fac[i] = M[(int64_t)i * n2 + k];
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * n2; e += blockDim.x) {
-      const int i = e / n2, j = e - i * n2;
-      if (i != k) M[e] -= fac[i] * M[(int64_t)k * n2 + j];
-    }
+  }
+  // undo the row swaps as column swaps, last first
+  for (int k = n - 1; k >= 0; --k) {
+    const int p = perm[k];
+    if (p != k)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const double t = M[i * n + k];
+        M[i * n + k] = M[i * n + p];
+        M[i * n + p] = t;
+      }
     __syncthreads();
   }
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const int i = e / n, j = e - i * n;
-    Ainv[e] = M[(int64_t)i * n2 + n + j];
-  }
-  __syncthreads();
-  // fold the projections onto zero-mean parts into the inverse:
-  // Ainv <- P Ainv P, P v = v - (mean of v on each singular part)
-  int* order = (int*)fac;           // rows grouped by part (n ints)
-  __shared__ int ncs;
-  if (threadIdx.x == 0) {
-    ncs = *ncomp_out;
-    int pos = 0;
-    for (int c = 0; c < ncs; ++c)
-      for (int i = 0; i < n; ++i)
-        if (lab[i] == c) order[pos++] = i;
-  }
-  __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {      // left: column j
+  // fold the projections onto zero-mean parts: M <- P M P
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
     int pos = 0;
     for (int c = 0; c < ncs; ++c) {
       int cnt = 0;
       double sum = 0.0;
-      for (int q = pos; q < n && lab[order[q]] == c; ++q, ++cnt) sum += Ainv[(int64_t)order[q] * n + j];
-      if (sing[c]) {
+      for (int q = pos; q < n && lb[order[q]] == c; ++q, ++cnt) sum += M[order[q] * n + j];
+      if (sg[c]) {
         const double m = sum / (double)cnt;
-        for (int q = pos; q < pos + cnt; ++q) Ainv[(int64_t)order[q] * n + j] -= m;
+        for (int q = pos; q < pos + cnt; ++q) M[order[q] * n + j] -= m;
       }
       pos += cnt;
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {      // right: row i
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
     int pos = 0;
     for (int c = 0; c < ncs; ++c) {
       int cnt = 0;
       double sum = 0.0;
-      for (int q = pos; q < n && lab[order[q]] == c; ++q, ++cnt) sum += Ainv[(int64_t)i * n + order[q]];
-      if (sing[c]) {
+      for (int q = pos; q < n && lb[order[q]] == c; ++q, ++cnt) sum += M[i * n + order[q]];
+      if (sg[c]) {
         const double m = sum / (double)cnt;
-        for (int q = pos; q < pos + cnt; ++q) Ainv[(int64_t)i * n + order[q]] -= m;
+        for (int q = pos; q < pos + cnt; ++q) M[i * n + order[q]] -= m;
       }
       pos += cnt;
     }
   }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Ainv[e] = M[e];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    lab[i] = lb[i];
+  }
+  for (int c = threadIdx.x; c < ncs; c += blockDim.x) sing[c] = sg[c];
 }
 
 // coarsest solve: y = Ainv b with the projections already folded into Ainv;
@@ -436,7 +641,10 @@ __global__ void k_restrict(int64_t nc, const int32_t* mptr, const int32_t* midx,
 }
 template <typename T>
 __global__ void k_prolong(int64_t n, const int32_t* agg, const T* yc, T scale, T* x) {
-  GS(i, n) x[i] += scale * yc[agg[i]];
+  GS(i, n) {
+    const int32_t a = agg[i];
+    if (a >= 0) x[i] += scale * yc[a];
+  }
 }
 template <typename A, typename B>
 __global__ void k_convert(int64_t n, const A* a, B* b) {
@@ -445,42 +653,52 @@ __global__ void k_convert(int64_t n, const A* a, B* b) {
 
 // label propagation down the hierarchy and per-component counts
 __global__ void k_pull_labels(int64_t n, const int32_t* agg, const int32_t* lab_c, int32_t* lab) {
-  GS(i, n) lab[i] = lab_c[agg[i]];
+  GS(i, n) lab[i] = agg[i] >= 0 ? lab_c[agg[i]] : -1;
 }
 __global__ void k_copy_i32(int64_t n, const int32_t* a, int32_t* b) {
   GS(i, n) b[i] = a[i];
 }
+// rows with a negative label (cells frozen since the hierarchy was built)
+// take no part in the projection
 __global__ void k_comp_count(int64_t n, const int32_t* lab, double* cnt) {
-  GS(i, n) atomicAdd(&cnt[lab[i]], 1.0);
+  GS(i, n) if (lab[i] >= 0) atomicAdd(&cnt[lab[i]], 1.0);
 }
 __global__ void k_comp_sum(int64_t n, const int32_t* lab, const double* v, double* s) {
-  GS(i, n) atomicAdd(&s[lab[i]], v[i]);
+  GS(i, n) if (lab[i] >= 0) atomicAdd(&s[lab[i]], v[i]);
 }
 __global__ void k_comp_sub(int64_t n, const int32_t* lab, const uint8_t* sing, const double* s, const double* cnt,
                            double* v) {
   GS(i, n) {
     const int32_t c = lab[i];
-    if (sing[c]) v[i] -= s[c] / cnt[c];
+    if (c >= 0 && sing[c]) v[i] -= s[c] / cnt[c];
   }
 }
-// single component: deterministic mean via block partials
-__global__ void k_sum_part(int64_t n, const double* v, double* part) {
+// single component: deterministic mean via block partials (lab, when given,
+// masks rows out; cnt_dev, when given, holds the row count)
+__global__ void k_sum_part(int64_t n, const double* v, const int32_t* lab, double* part) {
   __shared__ double sh[32];
   double a = 0.0;
-  GS(i, n) a += v[i];
+  GS(i, n) if (!lab || lab[i] >= 0) a += v[i];
   a = block_sum(a, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = a;
 }
-__global__ void k_mean_final(int nb, const double* part, double cnt, double* mean) {
+__global__ void k_mean_final(int nb, const double* part, double cnt, const double* cnt_dev, double* mean) {
   __shared__ double sh[32];
   double a = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) a += part[b];
   a = block_sum(a, sh);
-  if (threadIdx.x == 0) *mean = a / cnt;
+  if (threadIdx.x == 0) {
+    const double c = cnt_dev ? *cnt_dev : cnt;
+    *mean = c > 0.0 ? a / c : 0.0;
+  }
 }
-__global__ void k_sub_scalar(int64_t n, const double* mean, double* v) {
+__global__ void k_sub_scalar(int64_t n, const double* mean, const int32_t* lab, double* v) {
   const double m = *mean;
-  GS(i, n) v[i] -= m;
+  GS(i, n) if (!lab || lab[i] >= 0) v[i] -= m;
+}
+// refresh: rows whose cells no longer carry pressure leave the null-space labels
+__global__ void k_mask_labels(int64_t n, const int32_t* act, const uint8_t* ppe, int32_t* lab) {
+  GS(i, n) if (!ppe[act[i]]) lab[i] = -1;
 }
 
 // ---------------------------------------------------------------------------
@@ -492,6 +710,27 @@ static fvs_status read_int(cudaStream_t s, const int* d, int* h) {
   return FVS_OK;
 }
 
+// one Galerkin pass (count or fill) over all coarse rows
+static void galerkin_pass(cudaStream_t s, bool fill, int64_t nc, const Ell& A, const int32_t* agg,
+                          const int32_t* mptr, const int32_t* midx, int32_t* rowlen, int wc, int32_t* ccol,
+                          double* cval, double* cdiag, int* err) {
+  if (nc <= 0) return;
+  const int64_t n = A.n;
+  const int gs = (int)std::min<int64_t>((nc + 3) / 4, (int64_t)sm_count() * 16);
+  const int gb = (int)std::min<int64_t>(nc, (int64_t)sm_count() * 32);
+  if (fill) {
+    k_galerkin<true, GAL_SMALL, 4><<<gs, 128, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol,
+                                                      cval, cdiag, err, -1); FVS_COUNT_LAUNCH();
+    k_galerkin<true, GAL_CAP, 1><<<gb, 32, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol, cval,
+                                                   cdiag, err, GAL_SMALL); FVS_COUNT_LAUNCH();
+  } else {
+    k_galerkin<false, GAL_SMALL, 4><<<gs, 128, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol,
+                                                       cval, cdiag, err, -1); FVS_COUNT_LAUNCH();
+    k_galerkin<false, GAL_CAP, 1><<<gb, 32, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol,
+                                                    cval, cdiag, err, GAL_SMALL); FVS_COUNT_LAUNCH();
+  }
+}
+
 static double env_num(const char* name, double dflt) {
   const char* v = getenv(name);
   return (v && *v) ? atof(v) : dflt;
@@ -499,6 +738,8 @@ static double env_num(const char* name, double dflt) {
 
 fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
   ready = false;
+  masked = false;
+  ++version;
   lv.clear();
   opt.theta = env_num("FVS_AMG_THETA", opt.theta);
   opt.omega = env_num("FVS_AMG_OMEGA", opt.omega);
@@ -517,7 +758,19 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
     L0->A = &A;
     lv.push_back(std::move(L0));
   }
+  // phase timing for FVS_DEBUG (waits for the stream at each phase end)
+  const bool dbg = getenv("FVS_DEBUG") != nullptr;
+  double tph[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  auto t_last = std::chrono::steady_clock::now();
+  auto tick = [&](int k) {
+    if (!dbg) return;
+    cudaStreamSynchronize(s);
+    const auto now = std::chrono::steady_clock::now();
+    tph[k] += std::chrono::duration<double, std::milli>(now - t_last).count();
+    t_last = now;
+  };
   for (int l = 0;; ++l) {
+    tick(0);
     AmgLevel* L = lv[l].get();
     const Ell* cur = L->A;
     const int64_t n = cur->n;
@@ -531,36 +784,48 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
       k_maxoff<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mo, L->dinv, cur->diag); FVS_COUNT_LAUNCH();
       FVS_LAUNCH_CHECK();
     }
-    if (n <= opt.coarsest || l + 1 >= opt.max_levels || cur->w > 64) break;
-    // strength and aggregation
+    if (n <= opt.coarsest || l + 1 >= opt.max_levels) break;
+    // strength and aggregation; if the strong graph coarsens too little (small
+    // coarse levels of anisotropic problems), retry with every negative
+    // coupling counted as strong
     DBuf<uint64_t> mask;
     DBuf<uint8_t> st, st2;
-    FVS_TRY(mask.alloc(n)); FVS_TRY(st.alloc(n)); FVS_TRY(st2.alloc(n));
-    FVS_TRY(st.zero(s));
-    k_strong<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mo, opt.theta, mask); FVS_COUNT_LAUNCH();
-    FVS_LAUNCH_CHECK();
-    for (int round = 0;; ++round) {
-      FVS_TRY(cnt.zero(s));
-      k_mis_select<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, mask, st, st2); FVS_COUNT_LAUNCH();
-      k_mis_remove<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, mask, st2, st, cnt); FVS_COUNT_LAUNCH();
-      FVS_LAUNCH_CHECK();
-      int und = 0;
-      FVS_TRY(read_int(s, cnt, &und));
-      if (und == 0) break;
-      if (round == 63) {
-        set_error("AMG aggregation did not finish");
-        return FVS_ERR_NOT_CONVERGED;
-      }
-    }
     DBuf<int32_t> flag, rid;
+    FVS_TRY(mask.alloc(n)); FVS_TRY(st.alloc(n)); FVS_TRY(st2.alloc(n));
     FVS_TRY(flag.alloc(n + 1)); FVS_TRY(rid.alloc(n + 1));
-    FVS_TRY(flag.zero(s));
-    k_is_root<<<stride_grid(n, 256), 256, 0, s>>>(n, st, flag); FVS_COUNT_LAUNCH();
-    FVS_TRY(exclusive_scan(s, sw, n + 1, flag, rid));
     int nc = 0;
-    FVS_CUDA(cudaMemcpyAsync(&nc, rid.p + n, sizeof(int), cudaMemcpyDeviceToHost, s));
-    FVS_CUDA(cudaStreamSynchronize(s));
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      const double theta = attempt == 0 ? opt.theta : 0.0;
+      FVS_TRY(st.zero(s));
+      k_strong<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mo, theta, mask); FVS_COUNT_LAUNCH();
+      FVS_LAUNCH_CHECK();
+      tick(1);
+      for (int round = 0;; round += 2) {
+        // two independent-set rounds per check (rounds after completion change nothing)
+        FVS_TRY(cnt.zero(s));
+        for (int q = 0; q < 2; ++q) {
+          k_mis_select<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, mask, st, st2); FVS_COUNT_LAUNCH();
+          k_mis_remove<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, mask, st2, st,
+                                                             q == 1 ? cnt.p : cnt.p + 1); FVS_COUNT_LAUNCH();
+        }
+        FVS_LAUNCH_CHECK();
+        int und = 0;
+        FVS_TRY(read_int(s, cnt, &und));
+        if (und == 0) break;
+        if (round >= 62) {
+          set_error("AMG aggregation did not finish");
+          return FVS_ERR_NOT_CONVERGED;
+        }
+      }
+      FVS_TRY(flag.zero(s));
+      k_is_root<<<stride_grid(n, 256), 256, 0, s>>>(n, st, flag); FVS_COUNT_LAUNCH();
+      FVS_TRY(exclusive_scan(s, sw, n + 1, flag, rid));
+      FVS_CUDA(cudaMemcpyAsync(&nc, rid.p + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+      FVS_CUDA(cudaStreamSynchronize(s));
+      if ((double)nc <= 0.6 * (double)n) break;
+    }
     if (nc <= 0 || nc >= n || (double)nc > 0.85 * (double)n) break;  // stagnation: L is the coarsest
+    tick(2);
     FVS_TRY(L->agg.alloc(n));
     k_assign<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mask, st, rid, L->agg, err); FVS_COUNT_LAUNCH();
     DBuf<int32_t> mc;
@@ -576,9 +841,7 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
     FVS_LAUNCH_CHECK();
     DBuf<int32_t> rowlen;
     FVS_TRY(rowlen.alloc(nc));
-    const int gb = (int)std::min<int64_t>((int64_t)nc, (int64_t)sm_count() * 32);
-    k_galerkin<false><<<gb, 32, 0, s>>>(nc, n, cur->w, cur->col, cur->val, L->agg, L->mptr, L->midx, rowlen, 0,
-                                        nullptr, nullptr, nullptr, err); FVS_COUNT_LAUNCH();
+    galerkin_pass(s, false, nc, *cur, L->agg, L->mptr, L->midx, rowlen, 0, nullptr, nullptr, nullptr, err);
     FVS_TRY(cnt.zero(s));
     k_max_int<<<stride_grid(nc, 256), 256, 0, s>>>(nc, rowlen, cnt); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
@@ -589,14 +852,16 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
       set_error("AMG setup failed (flags 0x%x) at level %d", e, l);
       return FVS_ERR_NOT_CONVERGED;
     }
+    tick(3);
     std::unique_ptr<AmgLevel> C(new AmgLevel());
     FVS_TRY(C->own.alloc(nc, wc));
     FVS_TRY(C->own.diag.zero(s));
-    k_galerkin<true><<<gb, 32, 0, s>>>(nc, n, cur->w, cur->col, cur->val, L->agg, L->mptr, L->midx, rowlen, wc,
-                                       C->own.col, C->own.val, C->own.diag, err); FVS_COUNT_LAUNCH();
+    galerkin_pass(s, true, nc, *cur, L->agg, L->mptr, L->midx, rowlen, wc, C->own.col, C->own.val, C->own.diag,
+                  err);
     FVS_LAUNCH_CHECK();
     C->A = &C->own;
     lv.push_back(std::move(C));
+    tick(4);
   }
   {
     int e = 0;
@@ -606,12 +871,16 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
       return FVS_ERR_NOT_CONVERGED;
     }
   }
+  tick(0);
   FVS_TRY(coarsest_setup(s));
+  tick(5);
   if (opt.fp32) FVS_TRY(setup_fp32(s));
-  if (getenv("FVS_DEBUG")) {
+  tick(6);
+  if (dbg) {
     fprintf(stderr, "[fvs amg] levels %d:", (int)lv.size());
     for (auto& L : lv) fprintf(stderr, " %lld(w%d)", (long long)L->n, L->A->w);
-    fprintf(stderr, " coarsest %d parts %d\n", nc, ncomp);
+    fprintf(stderr, " coarsest %d parts %d | ms: misc %.2f strength %.2f mis %.2f members %.2f galerkin %.2f "
+            "coarsest %.2f fp32 %.2f\n", nc, ncomp, tph[0], tph[1], tph[2], tph[3], tph[4], tph[5], tph[6]);
   }
   ready = true;
   return FVS_OK;
@@ -621,20 +890,57 @@ fvs_status Amg::coarsest_setup(cudaStream_t s) {
   AmgLevel* L = lv.back().get();
   const Ell& A = *L->A;
   nc = (int)A.n;
-  if (nc > 4 * opt.coarsest) {
+  if (nc > 4 * opt.coarsest || nc > DENSE_PARTS_MAX) {
     set_error("AMG coarsest level too large (%d rows)", nc);
     return FVS_ERR_NOT_CONVERGED;
   }
-  DBuf<double> M;
   DBuf<int> err, ncd;
-  FVS_TRY(M.alloc((size_t)2 * nc * nc + 1));
   FVS_TRY(Ainv.alloc((size_t)nc * nc + 1));
   FVS_TRY(clab.alloc(nc + 1));
   FVS_TRY(csing.alloc(nc + 1));
   FVS_TRY(err.alloc(1)); FVS_TRY(ncd.alloc(1));
   FVS_TRY(err.zero(s));
   if (nc > 0) {
-    k_coarsest<<<1, 512, (size_t)nc * sizeof(double) + 64, s>>>(nc, A.w, A.col, A.val, M, Ainv, clab, csing, ncd, err); FVS_COUNT_LAUNCH();
+    if (nc <= SMEM_COARSEST) {
+      const size_t sh = (size_t)nc * nc * sizeof(double) + (size_t)nc * sizeof(double) + 3 * (size_t)nc * sizeof(int);
+      // the attribute is per function, shared by every thread: set it once to
+      // the largest size any launch uses (concurrent solvers launch smaller ones)
+      static bool attr_set[64] = {false};
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        const size_t shmax = (size_t)SMEM_COARSEST * SMEM_COARSEST * sizeof(double) +
+                             (size_t)SMEM_COARSEST * sizeof(double) + 3 * (size_t)SMEM_COARSEST * sizeof(int);
+        FVS_CUDA(cudaFuncSetAttribute(k_coarsest_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmax));
+        attr_set[dev] = true;
+      }
+      k_coarsest_smem<<<1, 1024, sh, s>>>(nc, A.w, A.col, A.val, Ainv, clab, csing, ncd, err); FVS_COUNT_LAUNCH();
+    } else {
+      DBuf<double> fac;
+      DBuf<int32_t> perm, order;
+      FVS_TRY(fac.alloc(nc)); FVS_TRY(perm.alloc(nc)); FVS_TRY(order.alloc(nc));
+      FVS_CUDA(cudaMemsetAsync(Ainv.p, 0, (size_t)nc * nc * sizeof(double), s));
+      k_dense_fill<<<stride_grid(nc, 128), 128, 0, s>>>(nc, A.w, A.col, A.val, Ainv); FVS_COUNT_LAUNCH();
+      static bool parts_attr[64] = {false};
+      int dev = 0;
+      cudaGetDevice(&dev);
+      if (dev >= 0 && dev < 64 && !parts_attr[dev]) {
+        FVS_CUDA(cudaFuncSetAttribute(k_dense_parts, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)dense_parts_smem(DENSE_PARTS_MAX)));
+        parts_attr[dev] = true;
+      }
+      k_dense_parts<<<1, 1024, dense_parts_smem(nc), s>>>(nc, Ainv, clab, csing, order, ncd); FVS_COUNT_LAUNCH();
+      const int eb = std::min(nc, 4 * sm_count());
+      for (int k = 0; k < nc; ++k) {
+        k_gj_pivot<<<1, 256, 0, s>>>(nc, k, Ainv, fac, perm, err); FVS_COUNT_LAUNCH();
+        k_gj_elim<<<eb, 128, 0, s>>>(nc, k, Ainv, fac, err); FVS_COUNT_LAUNCH();
+      }
+      k_gj_unswap<<<stride_grid(nc, 128), 128, 0, s>>>(nc, Ainv, perm, err); FVS_COUNT_LAUNCH();
+      k_dense_fold<true><<<stride_grid(nc, 128), 128, 0, s>>>(nc, Ainv, clab, csing, order, ncd, err);
+      FVS_COUNT_LAUNCH();
+      k_dense_fold<false><<<stride_grid(nc, 128), 128, 0, s>>>(nc, Ainv, clab, csing, order, ncd, err);
+      FVS_COUNT_LAUNCH();
+    }
     FVS_LAUNCH_CHECK();
   }
   int e = 0, ncomp_c = 0;
@@ -676,15 +982,88 @@ fvs_status Amg::coarsest_setup(cudaStream_t s) {
   return FVS_OK;
 }
 
+fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) {
+  if (!ready || lv.empty()) {
+    set_error("AMG refresh without a hierarchy");
+    return FVS_ERR_STATE;
+  }
+  const int64_t n0 = lv[0]->n;
+  if (lv[0]->A->n != n0) {
+    set_error("AMG refresh: operator has %lld rows, hierarchy %lld", (long long)lv[0]->A->n, (long long)n0);
+    return FVS_ERR_STATE;
+  }
+  ready = false;
+  ++version;
+  DBuf<int> err;
+  DBuf<double> mo;
+  FVS_TRY(err.alloc(1));
+  FVS_TRY(err.zero(s));
+  FVS_TRY(mo.alloc(n0 + 1));
+  if (lv.size() > 1 && n0 > 0) {
+    // level 0: same aggregates without the rows of cells that lost pressure
+    AmgLevel* L = lv[0].get();
+    const int64_t nc = lv[1]->n;
+    k_mask_agg<<<stride_grid(n0, 256), 256, 0, s>>>(n0, act, ppe, L->agg, err); FVS_COUNT_LAUNCH();
+    DBuf<int32_t> mc;
+    FVS_TRY(mc.alloc(nc + 1));
+    FVS_TRY(mc.zero(s));
+    k_count_members<<<stride_grid(n0, 256), 256, 0, s>>>(n0, L->agg, mc); FVS_COUNT_LAUNCH();
+    FVS_TRY(exclusive_scan(s, sw, nc + 1, mc, L->mptr));
+    FVS_TRY(mc.zero(s));
+    k_fill_members<<<stride_grid(n0, 256), 256, 0, s>>>(n0, L->agg, L->mptr, mc, L->midx); FVS_COUNT_LAUNCH();
+    k_sort_members<<<stride_grid(nc, 256), 256, 0, s>>>(nc, L->mptr, L->midx); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+  }
+  // Galerkin products level by level on the kept aggregates; the coarse rows
+  // can only lose entries, so the widths of the setup still hold (checked)
+  for (size_t l = 0; l < lv.size(); ++l) {
+    AmgLevel* L = lv[l].get();
+    const Ell* cur = L->A;
+    const int64_t n = L->n;
+    if (n > 0) {
+      k_maxoff<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mo, L->dinv, cur->diag);
+      FVS_COUNT_LAUNCH();
+    }
+    if (l + 1 == lv.size()) break;
+    AmgLevel* C = lv[l + 1].get();
+    const int64_t nc = C->n;
+    FVS_TRY(C->own.diag.zero(s));
+    galerkin_pass(s, true, nc, *cur, L->agg, L->mptr, L->midx, nullptr, C->own.w, C->own.col, C->own.val,
+                  C->own.diag, err);
+    FVS_LAUNCH_CHECK();
+  }
+  {
+    int e = 0;
+    FVS_TRY(read_int(s, err, &e));
+    if (e) {
+      set_error("AMG refresh needs a new aggregation (flags 0x%x)", e);
+      return FVS_ERR_NOT_CONVERGED;
+    }
+  }
+  FVS_TRY(coarsest_setup(s));
+  if (n0 > 0) {
+    k_mask_labels<<<stride_grid(n0, 256), 256, 0, s>>>(n0, act, ppe, fine_lab); FVS_COUNT_LAUNCH();
+    FVS_TRY(ccnt.zero(s));
+    k_comp_count<<<stride_grid(n0, 256), 256, 0, s>>>(n0, fine_lab, ccnt); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+  }
+  if (opt.fp32) FVS_TRY(setup_fp32(s));
+  masked = true;
+  ready = true;
+  return FVS_OK;
+}
+
 fvs_status Amg::project(cudaStream_t s, double* v) {
   const int64_t n = lv[0]->n;
   if (n == 0 || ncomp == 0) return FVS_OK;
   if (ncomp == 1) {
     if (!sing_host[0]) return FVS_OK;
     const int nb = std::min(1024, 2 * sm_count());
-    k_sum_part<<<nb, 256, 0, s>>>(n, v, cpart); FVS_COUNT_LAUNCH();
-    k_mean_final<<<1, 1024, 0, s>>>(nb, cpart, (double)n, cpart.p + 1024); FVS_COUNT_LAUNCH();
-    k_sub_scalar<<<stride_grid(n, 256), 256, 0, s>>>(n, cpart.p + 1024, v); FVS_COUNT_LAUNCH();
+    const int32_t* mask = masked ? fine_lab.p : nullptr;
+    k_sum_part<<<nb, 256, 0, s>>>(n, v, mask, cpart); FVS_COUNT_LAUNCH();
+    k_mean_final<<<1, 1024, 0, s>>>(nb, cpart, (double)n, masked ? ccnt.p : nullptr, cpart.p + 1024);
+    FVS_COUNT_LAUNCH();
+    k_sub_scalar<<<stride_grid(n, 256), 256, 0, s>>>(n, cpart.p + 1024, mask, v); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
     return FVS_OK;
   }

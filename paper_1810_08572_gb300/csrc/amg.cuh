@@ -32,7 +32,7 @@ struct AmgOptions {
   double omega = 0.85;     // Jacobi damping
   double coarse_scale = 1.5;  // over-correction of the piecewise-constant coarse correction
   int max_levels = 20;
-  int coarsest = 256;      // stop coarsening at or below this size
+  int coarsest = 160;      // stop coarsening at or below this size (shared-memory inverse)
   int npre = 1, npost = 1;
   bool fp32 = false;       // V-cycle in single precision
 };
@@ -53,8 +53,19 @@ struct Amg : Precond {
   ScanWork sw;
   bool ready = false;
 
+  bool masked = false;            // some fine rows carry label -1 (refreshed)
+
   fvs_status setup(cudaStream_t s, const Ell& A);
+  // The operator's values changed on the same rows (cells frozen since the
+  // setup became identity rows): take the new fine diagonal, drop the rows of
+  // cells without pressure (ppe[act[i]] == 0) from the null-space labels and
+  // keep the coarse levels.  The launches captured for apply() stay valid.
+  fvs_status refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe);
   fvs_status apply(cudaStream_t s, const double* r, double* z) override;
+  uint64_t version = 0;          // bumped by every setup
+  uint64_t signature() const override {
+    return version * 2654435761ULL + (opt.fp32 ? 1 : 0) + (masked ? 2 : 0);
+  }
   // subtract the component mean on every singular component (fine level)
   fvs_status project(cudaStream_t s, double* v);
   int levels() const { return (int)lv.size(); }

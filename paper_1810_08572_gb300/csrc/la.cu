@@ -1,5 +1,7 @@
 // Sparse linear algebra kernels and Krylov drivers (Section 2.5: the paper
 // uses AMG-preconditioned Krylov solvers; these are the GPU-native ones).
+#include <cstdlib>
+
 #include "la.cuh"
 
 namespace fvs {
@@ -125,6 +127,8 @@ fvs_status Reducer::init() {
   FVS_TRY(sc.zero(st));
   FVS_TRY(ticket.alloc(1));
   FVS_TRY(ticket.zero(st));
+  FVS_TRY(iter.alloc(1));
+  FVS_TRY(iter.zero(st));
   if (!host) FVS_CUDA(cudaMallocHost(&host, S_NSLOT * sizeof(double)));
   return FVS_OK;
 }
@@ -248,32 +252,35 @@ __device__ void finish2(double a, double b, double* part, unsigned int* ticket, 
         sc[S_RR] = x;
         sc[S_RHO_OLD] = sc[S_RHO];
         sc[S_RHO] = y;
+        sc[S_FIRST] = 0.0;
         break;
       case FIN_PQ: sc[S_PQ] = x; break;
-      case FIN_RR: sc[S_RR] = x; break;
+      case FIN_RR: sc[S_RR] = x; sc[S_FIRST] = 0.0; break;
       case FIN_RZ: sc[S_RZ_OLD] = sc[S_RZ]; sc[S_RZ] = x; break;
     }
     *ticket = 0u;
   }
 }
 
-// y = A x (+ dextra x); sums d.y (and y.y when yy)
-__global__ void k_spmv_dot(int64_t n, int w, const int32_t* __restrict__ col, const double* __restrict__ val,
-                           const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ dextra,
-                           const double* __restrict__ d, int yy, double* part, unsigned int* ticket, double* sc,
-                           int mode) {
+// y = A x (+ dextra x); sums d.y (and y.y when YY)
+template <int MODE, bool YY, bool DX>
+__global__ void __launch_bounds__(256, 8) k_spmv_dot(int64_t n, int w, const int32_t* __restrict__ col,
+                                                     const double* __restrict__ val, const double* __restrict__ x,
+                                                     double* __restrict__ y, const double* __restrict__ dextra,
+                                                     const double* __restrict__ d, double* part,
+                                                     unsigned int* ticket, double* sc) {
   double a = 0.0, b = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = dextra ? dextra[i] * x[i] : 0.0;
+    double acc = DX ? dextra[i] * x[i] : 0.0;
     for (int k = 0; k < w; ++k) {
       const int64_t e = (int64_t)k * n + i;
       acc = fma(val[e], x[col[e]], acc);
     }
     y[i] = acc;
     a = fma(d[i], acc, a);
-    if (yy) b = fma(acc, acc, b);
+    if (YY) b = fma(acc, acc, b);
   }
-  finish2(a, b, part, ticket, sc, mode);
+  finish2(a, b, part, ticket, sc, MODE);
 }
 
 // BiCGStab: x += alpha ph + omega sh ; r = s - omega t ; sums r.r and rh.r
@@ -320,6 +327,7 @@ __global__ void k_dot_rz(int64_t n, const double* __restrict__ r, const double* 
 // BiCGStab: p = r + beta (p - omega v), beta = (rho/rho_old)(alpha/omega)
 __global__ void k_bicg_p(int64_t n, const double* __restrict__ sc, const double* __restrict__ r,
                          const double* __restrict__ v, double* __restrict__ p, int first) {
+  first = first || sc[S_FIRST] != 0.0;
   const double beta = first ? 0.0 : sdiv(sc[S_RHO], sc[S_RHO_OLD]) * sdiv(sc[S_ALPHA], sc[S_OMEGA]);
   const double om = sc[S_OMEGA];
   GRID_STRIDE(i, n) p[i] = first ? r[i] : r[i] + beta * (p[i] - om * v[i]);
@@ -332,6 +340,7 @@ __global__ void k_bicg_s(int64_t n, const double* __restrict__ sc, const double*
 }
 __global__ void k_cg_p(int64_t n, const double* __restrict__ sc, const double* __restrict__ z,
                        double* __restrict__ p, int first) {
+  first = first || sc[S_FIRST] != 0.0;
   const double beta = first ? 0.0 : sdiv(sc[S_RZ], sc[S_RZ_OLD]);
   GRID_STRIDE(i, n) p[i] = first ? z[i] : z[i] + beta * p[i];
 }
@@ -341,15 +350,183 @@ static inline bool bad(double v) { return !(v == v) || v > 1e300 || v < -1e300; 
 static fvs_status spmv_dot(cudaStream_t s, Reducer& red, const Ell& A, const double* x, double* y,
                            const double* dextra, const double* d, bool yy, int mode) {
   ProfScope ps(&A, "spmv", (double)A.n * (12.0 * A.w + 24.0 + (dextra ? 8.0 : 0.0)), s);
-  k_spmv_dot<<<red.blocks, 256, 0, s>>>(A.n, A.w, A.col, A.val, x, y, dextra, d, yy ? 1 : 0, red.part,
-                                         red.ticket, red.sc, mode); FVS_COUNT_LAUNCH();
+#define FVS_SPMV_DOT(M_, Y_, D_) \
+  k_spmv_dot<M_, Y_, D_><<<red.blocks, 256, 0, s>>>(A.n, A.w, A.col, A.val, x, y, dextra, d, red.part, red.ticket, red.sc)
+  if (mode == FIN_RV) { if (dextra) FVS_SPMV_DOT(FIN_RV, false, true); else FVS_SPMV_DOT(FIN_RV, false, false); }
+  else if (mode == FIN_TSTT) { if (dextra) FVS_SPMV_DOT(FIN_TSTT, true, true); else FVS_SPMV_DOT(FIN_TSTT, true, false); }
+  else { if (dextra) FVS_SPMV_DOT(FIN_PQ, false, true); else FVS_SPMV_DOT(FIN_PQ, false, false); }
+#undef FVS_SPMV_DOT
+  (void)yy;
+  FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   return FVS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// CUDA-graph replay of one Krylov iteration (launch overhead dominates the
+// small levels of the V-cycle and small meshes).  The first iteration runs
+// eagerly; the next ones replay a captured graph while its key (operator,
+// vectors, preconditioner state) is unchanged.  Disabled while kernels are
+// being timed and by FVS_NO_GRAPHS.
+// ---------------------------------------------------------------------------
+bool graphs_enabled() {
+  static int cached = -1;
+  if (cached < 0) cached = getenv("FVS_NO_GRAPHS") ? 0 : 1;
+  return cached == 1 && !(g_prof && g_prof->on);
+}
+
+static uint64_t mixk(uint64_t h, uint64_t v) {
+  h ^= v + 0x9e3779b97f4a7c15ULL + (h << 6) + (h >> 2);
+  return h;
+}
+
+static uint64_t graph_key(const Ell& A, const double* dextra, const Precond& M, const double* b, const double* x,
+                          const KrylovWork& w, const Reducer& red) {
+  uint64_t h = 1469598103934665603ULL;
+  h = mixk(h, (uint64_t)(uintptr_t)A.val.p);
+  h = mixk(h, (uint64_t)(uintptr_t)A.col.p);
+  h = mixk(h, (uint64_t)A.n * 131 + (uint64_t)A.w);
+  h = mixk(h, (uint64_t)(uintptr_t)dextra);
+  h = mixk(h, M.signature());
+  h = mixk(h, (uint64_t)(uintptr_t)b);
+  h = mixk(h, (uint64_t)(uintptr_t)x);
+  h = mixk(h, (uint64_t)(uintptr_t)w.r.p);
+  h = mixk(h, (uint64_t)(uintptr_t)w.p.p);
+  h = mixk(h, (uint64_t)(uintptr_t)red.sc.p);
+  h = mixk(h, (uint64_t)(uintptr_t)red.part.p);
+  return h ? h : 1;
+}
+
+template <typename F>
+static fvs_status run_body(cudaStream_t s, IterGraph* g, uint64_t key, bool first, F& body) {
+  if (first || !g || g->disabled || !graphs_enabled() || s == nullptr) return body(first);
+  if (!g->exec || g->key != key) {
+    g->reset();
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      g->disabled = true;
+      return body(first);
+    }
+    const unsigned long long before = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+    fvs_status r = body(false);
+    g->kernels = __atomic_load_n(&g_launches, __ATOMIC_RELAXED) - before;
+    __atomic_sub_fetch(&g_launches, g->kernels, __ATOMIC_RELAXED);   // counted when replayed
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (r != FVS_OK || e != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      g->disabled = true;
+      return body(first);
+    }
+    e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      g->exec = nullptr;
+      g->disabled = true;
+      return body(first);
+    }
+    g->key = key;
+  }
+  FVS_CUDA(cudaGraphLaunch(g->exec, s));
+  __atomic_add_fetch(&g_launches, g->kernels, __ATOMIC_RELAXED);
+  return FVS_OK;
+}
+
+// Loop controllers: the last node of each iteration decides on the device
+// whether the conditional while-node runs the body again (no host round
+// trip per iteration).  Bounded by maxit; a NaN residual or a breakdown of
+// the BiCGStab recurrence also stops the loop (the host then restarts or
+// reports).
+__global__ void k_ctl_bicg(cudaGraphConditionalHandle h, double* sc, int* it, int maxit) {
+  const int n = ++(*it);
+  sc[S_ITER] = (double)n;
+  const double rr = sc[S_RR];
+  const bool go = n < maxit && rr > sc[S_TOL2] && rr == rr && rr < 1e300 && sc[S_TT] != 0.0 &&
+                  sc[S_RV] != 0.0 && sc[S_RHO] != 0.0;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+__global__ void k_ctl_cg(cudaGraphConditionalHandle h, double* sc, int* it, int maxit) {
+  const int n = ++(*it);
+  sc[S_ITER] = (double)n;
+  const double rr = sc[S_RR];
+  const bool go = n < maxit && rr > sc[S_TOL2] && rr == rr && rr < 1e300;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+__global__ void k_loop_init(double* sc, int* it, double tol2, int fresh) {
+  sc[S_FIRST] = fresh ? 1.0 : 0.0;
+  *it = 0;
+  sc[S_ITER] = 0.0;
+  sc[S_TOL2] = tol2;
+}
+
+// Runs up to maxit iterations of body() as one graph launch with a
+// conditional while-node; returns false (nothing launched) when the loop
+// graph cannot be used, so the caller iterates from the host instead.
+template <typename F>
+static bool run_loop(cudaStream_t s, IterGraph* g, uint64_t key, Reducer& red, double tol2, int maxit, bool bicg, bool fresh,
+                     F& body, fvs_status& st) {
+  st = FVS_OK;
+  if (!g || g->loop_disabled || !graphs_enabled() || s == nullptr || maxit <= 0) return false;
+  if (!g->loop || g->loop_key != key) {
+    if (g->loop) cudaGraphExecDestroy(g->loop);
+    g->loop = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphConditionalHandle h;
+    bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+    ok = ok && cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    cudaGraphNodeParams p = {};
+    cudaGraphNode_t node;
+    if (ok) {
+      p.type = cudaGraphNodeTypeConditional;
+      p.conditional.handle = h;
+      p.conditional.type = cudaGraphCondTypeWhile;
+      p.conditional.size = 1;
+      ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p) == cudaSuccess;
+    }
+    if (ok) {
+      cudaGraph_t bodyg = p.conditional.phGraph_out[0];
+      ok = cudaStreamBeginCaptureToGraph(s, bodyg, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+           cudaSuccess;
+      if (ok) {
+        const unsigned long long before = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+        fvs_status r = body(false);
+        if (bicg)
+          k_ctl_bicg<<<1, 1, 0, s>>>(h, red.sc.p, red.iter.p, maxit);
+        else
+          k_ctl_cg<<<1, 1, 0, s>>>(h, red.sc.p, red.iter.p, maxit);
+        g->loop_kernels = __atomic_load_n(&g_launches, __ATOMIC_RELAXED) - before + 1;
+        __atomic_sub_fetch(&g_launches, g->loop_kernels - 1, __ATOMIC_RELAXED);
+        cudaGraph_t out = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &out);
+        ok = r == FVS_OK && e == cudaSuccess;
+      }
+    }
+    if (ok) ok = cudaGraphInstantiate(&g->loop, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+      cudaGetLastError();
+      if (g->loop) cudaGraphExecDestroy(g->loop);
+      g->loop = nullptr;
+      g->loop_disabled = true;
+      return false;
+    }
+    g->loop_key = key;
+  }
+  k_loop_init<<<1, 1, 0, s>>>(red.sc.p, red.iter.p, tol2, fresh ? 1 : 0);
+  FVS_COUNT_LAUNCH();
+  const cudaError_t e = cudaGraphLaunch(g->loop, s);
+  if (e != cudaSuccess) {
+    set_error("cudaGraphLaunch: %s", cudaGetErrorString(e));
+    st = FVS_ERR_CUDA;
+  }
+  return true;
+}
+
 fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, const double* dextra,
                     Precond& M, const double* b, double* x, double rtol, int maxit, Projector* proj,
-                    SolveResult& res, double bnorm_floor) {
+                    SolveResult& res, double bnorm_floor, IterGraph* graph) {
   const int64_t n = A.n;
   res = SolveResult();
   if (n == 0) {
@@ -381,8 +558,8 @@ fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, c
   }
   // K x has zero sum on every singular part (zero column sums), so the
   // Krylov vectors stay in the range once r is projected
-  for (int it = 0; it < maxit; ++it) {
-    k_bicg_p<<<grid, 256, 0, s>>>(n, red.sc, w.r, w.v, w.p, it == 0); FVS_COUNT_LAUNCH();
+  auto body = [&](bool first) -> fvs_status {
+    k_bicg_p<<<grid, 256, 0, s>>>(n, red.sc, w.r, w.v, w.p, first ? 1 : 0); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
     FVS_TRY(M.apply(s, w.p, w.ph));
     FVS_TRY(spmv_dot(s, red, A, w.ph, w.v, dextra, w.rh, false, FIN_RV));
@@ -393,9 +570,29 @@ fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, c
     k_bicg_xr_dot<<<red.blocks, 256, 0, s>>>(n, red.sc, w.ph, w.sh, w.sv, w.t, w.rh, x, w.r, red.part,
                                               red.ticket); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
+    return FVS_OK;
+  };
+  const uint64_t key = graph_key(A, dextra, M, b, x, w, red) ^ 0x6b696367ULL;
+  // the first iteration of a recurrence runs from the host; the following
+  // ones run as one device-driven loop (or one graph replay per iteration)
+  bool fresh = true;
+  int it = 0;
+  const double tol2 = (rtol * bnorm) * (rtol * bnorm);
+  while (it < maxit) {
+    bool looped = false;
+    {
+      fvs_status st = FVS_OK;
+      looped = run_loop(s, graph, key, red, tol2, maxit - it, true, fresh, body, st);
+      FVS_TRY(st);
+    }
+    if (!looped) FVS_TRY(run_body(s, graph, key, fresh, body));
+    fresh = false;
     FVS_TRY(red.fetch(s));
+    const int done = looped ? (int)red.host[S_ITER] : 1;
+    if (looped) __atomic_add_fetch(&g_launches, graph->loop_kernels * (unsigned long long)done, __ATOMIC_RELAXED);
+    it += done;
     rn = sqrt(red.host[S_RR]);
-    res.iters = it + 1;
+    res.iters = it;
     res.relres = rn / bnorm;
     if (bad(rn)) return FVS_OK;
     if (res.relres <= rtol) {
@@ -408,8 +605,7 @@ fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, c
       if (proj) FVS_TRY(proj->apply(s, w.r));
       FVS_TRY(vcopy(s, n, w.r, w.rh));
       FVS_TRY(red.dot(s, n, w.rh, w.r, S_RHO));
-      it = -1 + it;   // keep counting iterations, restart the recurrence
-      k_bicg_p<<<grid, 256, 0, s>>>(n, red.sc, w.r, w.v, w.p, 1); FVS_COUNT_LAUNCH();
+      fresh = true;
     }
   }
   // recompute the true residual (the recursive one drifts)
@@ -426,7 +622,7 @@ fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, c
 // preconditioned CG (symmetric systems)
 // ---------------------------------------------------------------------------
 fvs_status pcg(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, Precond& M, const double* b,
-               double* x, double rtol, int maxit, Projector* proj, SolveResult& res) {
+               double* x, double rtol, int maxit, Projector* proj, SolveResult& res, IterGraph* graph) {
   const int64_t n = A.n;
   res = SolveResult();
   if (n == 0) {
@@ -452,18 +648,33 @@ fvs_status pcg(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, Precon
     res.converged = true;
     return FVS_OK;
   }
-  for (int it = 0; it < maxit; ++it) {
+  auto body = [&](bool first) -> fvs_status {
     FVS_TRY(M.apply(s, w.r, w.z));
     if (proj) FVS_TRY(proj->apply(s, w.z));
     k_dot_rz<<<red.blocks, 256, 0, s>>>(n, w.r, w.z, red.part, red.ticket, red.sc); FVS_COUNT_LAUNCH();
-    k_cg_p<<<grid, 256, 0, s>>>(n, red.sc, w.z, w.p, it == 0); FVS_COUNT_LAUNCH();
+    k_cg_p<<<grid, 256, 0, s>>>(n, red.sc, w.z, w.p, first ? 1 : 0); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
     FVS_TRY(spmv_dot(s, red, A, w.p, w.q, nullptr, w.p, false, FIN_PQ));
     k_cg_xr_dot<<<red.blocks, 256, 0, s>>>(n, red.sc, w.p, w.q, x, w.r, red.part, red.ticket); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
+    return FVS_OK;
+  };
+  const uint64_t key = graph_key(A, nullptr, M, b, x, w, red) ^ (proj ? 0x70636770ULL : 0x70636700ULL);
+  const double tol2 = (rtol * bnorm) * (rtol * bnorm);
+  for (int it = 0; it < maxit;) {
+    bool looped = false;
+    {
+      fvs_status st = FVS_OK;
+      looped = run_loop(s, graph, key, red, tol2, maxit - it, false, it == 0, body, st);
+      FVS_TRY(st);
+    }
+    if (!looped) FVS_TRY(run_body(s, graph, key, it == 0, body));
     FVS_TRY(red.fetch(s));
+    const int done = looped ? (int)red.host[S_ITER] : 1;
+    if (looped) __atomic_add_fetch(&g_launches, graph->loop_kernels * (unsigned long long)done, __ATOMIC_RELAXED);
+    it += done;
     const double rn = sqrt(red.host[S_RR]);
-    res.iters = it + 1;
+    res.iters = it;
     res.relres = rn / bnorm;
     if (bad(rn)) return FVS_OK;
     if (res.relres <= rtol) {

@@ -30,7 +30,7 @@ struct Ell {
 // Scalar slots of the Krylov drivers (device memory).
 enum Slot {
   S_RHO = 0, S_RHO_OLD, S_ALPHA, S_OMEGA, S_RV, S_TS, S_TT, S_RR, S_BB, S_RZ, S_RZ_OLD, S_PQ,
-  S_TMP0, S_TMP1, S_NSLOT
+  S_TMP0, S_TMP1, S_TOL2, S_ITER, S_FIRST, S_NSLOT
 };
 
 // Reduction scratch owned by a solver: block partials + scalar slots +
@@ -40,6 +40,7 @@ struct Reducer {
   DBuf<double> part;   // [2*blocks]
   DBuf<double> sc;     // [S_NSLOT]
   DBuf<unsigned int> ticket;   // last-block counter of the fused reductions
+  DBuf<int> iter;              // iteration counter of device-driven solve loops
   double* host = nullptr;  // pinned [S_NSLOT]
   fvs_status init();
   ~Reducer() { if (host) cudaFreeHost(host); }
@@ -63,13 +64,43 @@ fvs_status residual(cudaStream_t s, const Ell& A, const double* x, const double*
 struct Precond {
   virtual ~Precond() {}
   virtual fvs_status apply(cudaStream_t s, const double* r, double* z) = 0;
+  // identifies the state the launches depend on (a captured iteration is
+  // replayed only while it is unchanged)
+  virtual uint64_t signature() const = 0;
 };
+
+// One Krylov iteration captured as a CUDA graph and replayed while the
+// operator, vectors and preconditioner stay the same.
+struct IterGraph {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t key = 0;
+  unsigned long long kernels = 0;   // launches per replay (for the launch counter)
+  bool disabled = false;
+  // whole-solve loop: a conditional while-node whose body is one iteration
+  cudaGraphExec_t loop = nullptr;
+  uint64_t loop_key = 0;
+  unsigned long long loop_kernels = 0;
+  bool loop_disabled = false;
+  ~IterGraph() { reset(); }
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    key = 0;
+    if (loop) cudaGraphExecDestroy(loop);
+    loop = nullptr;
+    loop_key = 0;
+  }
+};
+bool graphs_enabled();
 
 // Jacobi: z = r / (diag + dextra)
 struct JacobiPrecond : Precond {
   const Ell* A = nullptr;
   const double* dextra = nullptr;
   fvs_status apply(cudaStream_t s, const double* r, double* z) override;
+  uint64_t signature() const override {
+    return (uint64_t)(uintptr_t)A->diag.p * 31u + (uint64_t)(uintptr_t)dextra * 17u + (uint64_t)A->n;
+  }
 };
 
 struct KrylovWork {
@@ -94,9 +125,10 @@ struct Projector {
 // The residual is measured against max(||b||, bnorm_floor).
 fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, const double* dextra,
                     Precond& M, const double* b, double* x, double rtol, int maxit,
-                    Projector* proj, SolveResult& res, double bnorm_floor = 0.0);
+                    Projector* proj, SolveResult& res, double bnorm_floor = 0.0, IterGraph* graph = nullptr);
 fvs_status pcg(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, Precond& M,
-               const double* b, double* x, double rtol, int maxit, Projector* proj, SolveResult& res);
+               const double* b, double* x, double rtol, int maxit, Projector* proj, SolveResult& res,
+               IterGraph* graph = nullptr);
 
 // small vector kernels
 fvs_status vcopy(cudaStream_t s, int64_t n, const double* a, double* b);

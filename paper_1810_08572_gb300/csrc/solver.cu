@@ -9,6 +9,7 @@
 //  5. energy with latent heat on all cells (Eq. 4, Eq. 18-20, Section 2.4.4)
 //  6. liquidus/solidus crossing times for the microstructure relations (Eq. 22-23)
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 
 #include "solver.cuh"
@@ -36,12 +37,20 @@ __device__ __forceinline__ double solid_fraction_slope(double T, double Ts, doub
 // ---------------------------------------------------------------------------
 // 1. tags and compaction
 // ---------------------------------------------------------------------------
+// counts: [1] cells whose tag changed, [2] LM cells outside the current
+// system numbering (melted), [3] numbered cells that are no longer LM, [4] LM cells
 __global__ void k_tag(int64_t Nc, const double* T, double Ts, uint8_t* lm, int32_t* flag, double* u, double* uold,
-                      int* changed) {
-  int ch = 0;
+                      int* counts, const int32_t* map, int numbered) {
+  int ch = 0, melted = 0, dead = 0, nlm = 0;
   GS(c, Nc) {
     const bool l = T[c] > Ts;
     ch += (lm[c] != (uint8_t)l) ? 1 : 0;
+    if (numbered) {
+      const bool in = map[c] >= 0;
+      melted += (l && !in) ? 1 : 0;
+      dead += (!l && in) ? 1 : 0;
+    }
+    nlm += l ? 1 : 0;
     lm[c] = l;
     flag[c] = l;
     if (!l) {
@@ -51,7 +60,10 @@ __global__ void k_tag(int64_t Nc, const double* T, double Ts, uint8_t* lm, int32
       }
     }
   }
-  if (ch) atomicAdd(changed, ch);
+  if (ch) atomicAdd(counts + 1, ch);
+  if (melted) atomicAdd(counts + 2, melted);
+  if (dead) atomicAdd(counts + 3, dead);
+  if (nlm) atomicAdd(counts + 4, nlm);
 }
 __global__ void k_compact(int64_t Nc, const uint8_t* lm, const int32_t* excl, int32_t* map, int32_t* act) {
   GS(c, Nc) {
@@ -109,10 +121,19 @@ __global__ void k_face_case(int64_t Nf, const int32_t* own, const int32_t* nei, 
 // 2. momentum predictor (Eq. 6)
 // ---------------------------------------------------------------------------
 __global__ void k_mom_matrix(int64_t nact, int64_t Nc, int W, const int32_t* act, const int32_t* map,
-                             const int32_t* Lcol, const double* Lval, const double* V, const double* fs, Mat m,
-                             double dt, int32_t* col, double* val, double* diag) {
+                             const uint8_t* lm, const int32_t* Lcol, const double* Lval, const double* V,
+                             const double* fs, Mat m, double dt, int32_t* col, double* val, double* diag) {
   GS(r, nact) {
     const int32_t c = act[r];
+    if (!lm[c]) {
+      // a numbered cell that has frozen since the numbering was made: u* = 0
+      for (int k = 0; k < W; ++k) {
+        col[(int64_t)k * nact + r] = (int32_t)r;
+        val[(int64_t)k * nact + r] = k == 0 ? 1.0 : 0.0;
+      }
+      diag[r] = 1.0;
+      continue;
+    }
     const double f = fs[c];
     const double D = m.C * f * f / ((1.0 - f) * (1.0 - f) * (1.0 - f) + m.eps);
     const double dterm = (m.rho / dt + D) * V[c];
@@ -128,7 +149,7 @@ __global__ void k_mom_matrix(int64_t nact, int64_t Nc, int W, const int32_t* act
           diag[r] = v;
           seen_diag = true;
         }
-      } else if (map[j] >= 0) {
+      } else if (map[j] >= 0 && lm[j]) {
         cc = map[j];
         v = -0.5 * m.mu * a;
       }
@@ -138,12 +159,20 @@ __global__ void k_mom_matrix(int64_t nact, int64_t Nc, int W, const int32_t* act
   }
 }
 
-__global__ void k_mom_rhs(int64_t nact, int64_t Nc, int W, const int32_t* act, const int32_t* cf, const int8_t* cfs,
-                          const int32_t* own, const int32_t* nei, const double* F, const double* Fold,
-                          const double* u, const double* uold, const int32_t* Lcol, const double* Lval,
-                          const double* V, const double* T, Mat m, double dt, double* rhs, double* x) {
+__global__ void k_mom_rhs(int64_t nact, int64_t Nc, int W, const int32_t* act, const uint8_t* lm, const int32_t* cf,
+                          const int8_t* cfs, const int32_t* own, const int32_t* nei, const double* F,
+                          const double* Fold, const double* u, const double* uold, const int32_t* Lcol,
+                          const double* Lval, const double* V, const double* T, Mat m, double dt, double* rhs,
+                          double* x) {
   GS(r, nact) {
     const int32_t c = act[r];
+    if (!lm[c]) {
+      for (int d = 0; d < 3; ++d) {
+        rhs[d * nact + r] = 0.0;
+        x[d * nact + r] = 0.0;
+      }
+      continue;
+    }
     double cn[3] = {0, 0, 0}, co[3] = {0, 0, 0};
     for (int s = 0; s < 6; ++s) {
       const int32_t f = cf[s * Nc + c];
@@ -173,10 +202,11 @@ __global__ void k_mom_rhs(int64_t nact, int64_t Nc, int W, const int32_t* act, c
   }
 }
 
-__global__ void k_scatter3(int64_t Nc, int64_t nact, const int32_t* map, const double* x, double* full) {
+__global__ void k_scatter3(int64_t Nc, int64_t nact, const int32_t* map, const uint8_t* lm, const double* x,
+                           double* full) {
   GS(c, Nc) {
     const int32_t r = map[c];
-    for (int d = 0; d < 3; ++d) full[d * Nc + c] = r >= 0 ? x[d * nact + r] : 0.0;
+    for (int d = 0; d < 3; ++d) full[d * Nc + c] = (r >= 0 && lm[c]) ? x[d * nact + r] : 0.0;
   }
 }
 
@@ -235,7 +265,7 @@ __global__ void k_ppe_matrix(PpeCtx x, int32_t* col, double* val, double* diag, 
         int32_t cc = (int32_t)r;
         double v = 0.0;
         if (k < nn) {
-          if (mj >= 0) { cc = mj; v = a; }
+          if (mj >= 0 && x.ppe[j]) { cc = mj; v = a; }
           else if (a != 0.0) atomicOr(err, 1);
           if (j == c) dg = v;
         }
@@ -579,7 +609,7 @@ fvs_status solver_alloc(fvs_solver s) {
   FVS_TRY(s->ebase.alloc(Nc)); FVS_TRY(s->erhs.alloc(Nc)); FVS_TRY(s->edx.alloc(Nc)); FVS_TRY(s->Tlin.alloc(Nc));
   FVS_TRY(s->lT.alloc(Nc));
   FVS_TRY(s->Tit.alloc(Nc)); FVS_TRY(s->fsit.alloc(Nc));
-  FVS_TRY(s->cnt.alloc(2));
+  FVS_TRY(s->cnt.alloc(8));
   FVS_TRY(s->red.init());
   FVS_TRY(s->ustar.zero(s->stream));
   FVS_TRY(s->fcase.zero(s->stream));
@@ -662,10 +692,31 @@ fvs_status solver_set_state(fvs_solver s, const double* T, const double* u, int 
   s->nstep = 0;
   s->have_step = false;
   s->k_valid = false;
+  s->numbered = false;
+  s->force_full = false;
+  s->amg_ok = false;
   return FVS_OK;
 }
 
 // tags, compaction and face cases for the current temperature
+// a new system numbering: the LM cells in mesh order
+static fvs_status renumber_lm(fvs_solver s) {
+  fvs_mesh m = s->mesh;
+  cudaStream_t st = s->stream;
+  const int64_t Nc = m->Nc;
+  FVS_TRY(exclusive_scan(st, s->sw, Nc + 1, s->flag, s->excl));
+  k_compact<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->lm, s->excl, s->map, s->act); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  int32_t na = 0;
+  FVS_CUDA(cudaMemcpyAsync(&na, s->excl.p + Nc, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  FVS_CUDA(cudaStreamSynchronize(st));
+  s->nact = na;
+  s->numbered = true;
+  s->renumbered = true;
+  s->k_valid = false;
+  return FVS_OK;
+}
+
 static fvs_status classify(fvs_solver s) {
   fvs_mesh m = s->mesh;
   cudaStream_t st = s->stream;
@@ -673,10 +724,26 @@ static fvs_status classify(fvs_solver s) {
   const Mat mt = mat_of(s->props);
   FVS_TRY(s->flag.zero(st));
   FVS_TRY(s->cnt.zero(st));
-  k_tag<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, mt.Ts, s->lm, s->flag, s->u, s->uold, s->cnt.p + 1);
+  k_tag<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, mt.Ts, s->lm, s->flag, s->u, s->uold, s->cnt.p,
+                                               s->map, s->numbered ? 1 : 0);
   FVS_COUNT_LAUNCH();
-  FVS_TRY(exclusive_scan(st, s->sw, Nc + 1, s->flag, s->excl));
-  k_compact<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->lm, s->excl, s->map, s->act); FVS_COUNT_LAUNCH();
+  int tc[5];
+  FVS_CUDA(cudaMemcpyAsync(tc, s->cnt.p, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  FVS_CUDA(cudaStreamSynchronize(st));
+  s->nlm = tc[4];
+  // The system numbering (LM cells when it was made) is kept while cells only
+  // freeze and the frozen share stays small: frozen rows become identity
+  // rows, so the AMG hierarchy built for that numbering keeps serving as the
+  // preconditioner (refreshed on its fine level).  A melted cell, a larger
+  // frozen share, or the rebuild policy renumbers.
+  const char* rf = getenv("FVS_REFRESH_FRACTION");   // frozen share kept on one numbering
+  const double frac = (rf && *rf) ? atof(rf) : 0.01;
+  const int64_t dead_cap = std::max<int64_t>(64, (int64_t)(frac * (double)s->nact));
+  const bool renumber = !s->numbered || tc[2] > 0 || tc[3] > dead_cap || s->force_full;
+  s->renumbered = false;
+  if (renumber) FVS_TRY(renumber_lm(s));
+  if (tc[1] != 0) s->k_valid = false;
+  FVS_TRY(s->cnt.zero(st));
   FVS_TRY(s->flow.zero(st));
   k_faces_open<<<stride_grid(Nf, 256), 256, 0, st>>>(Nf, m->own, m->nei, s->lm, s->F, s->Fold, s->flow); FVS_COUNT_LAUNCH();
   k_ppe_cells<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->lm, s->flow, s->ppe); FVS_COUNT_LAUNCH();
@@ -685,16 +752,10 @@ static fvs_status classify(fvs_solver s) {
   FVS_LAUNCH_CHECK();
   k_count_u8<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->ppe, s->cnt); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
-  int32_t na = 0;
   int hc[2];
-  FVS_CUDA(cudaMemcpyAsync(&na, s->excl.p + Nc, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   FVS_CUDA(cudaMemcpyAsync(hc, s->cnt.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   FVS_CUDA(cudaStreamSynchronize(st));
-  s->nact = na;
   s->nppe = hc[0];
-  // the pressure system depends on the tags only: keep it (and its AMG
-  // hierarchy) while no cell changed phase
-  if (hc[1] != 0) s->k_valid = false;
   return FVS_OK;
 }
 
@@ -730,7 +791,29 @@ static fvs_status assemble_pressure(fvs_solver s) {
   }
   // AMG hierarchy for the new active set (Section 2.5); on failure the
   // solve falls back to single-grid Jacobi BiCGStab
+  // Same numbering and a usable hierarchy: refresh its fine level only
+  // (new diagonal, rows of frozen cells left out of the null-space
+  // projection); otherwise build the hierarchy anew.
+  if (!s->renumbered && s->amg_ok && !s->force_full && s->nact > 0) {
+    const fvs_status r = s->amg.refresh(st, s->act, s->ppe);
+    if (r == FVS_OK) {
+      s->amg_full = false;
+      return FVS_OK;
+    }
+    if (r != FVS_ERR_NOT_CONVERGED) return r;
+    // the kept aggregation no longer fits: number the LM cells anew
+    FVS_TRY(renumber_lm(s));
+    return assemble_pressure(s);
+  }
+  if (!s->renumbered && s->nact > 0 && s->props.p_solver == FVS_PSOLVER_AMG) {
+    // a full setup always starts from a numbering without frozen rows
+    FVS_TRY(renumber_lm(s));
+    return assemble_pressure(s);
+  }
   s->amg_ok = false;
+  s->amg_full = true;
+  s->force_full = false;
+  s->steps_since_setup = 0;
   if (s->props.p_solver == FVS_PSOLVER_AMG && s->nact > 0) {
     s->amg.opt.fp32 = s->props.precision == FVS_PREC_MIXED;
     fvs_status r = s->amg.setup(st, s->K);
@@ -750,11 +833,26 @@ static fvs_status solve_pressure(fvs_solver s, double rtol, SolveResult& res, in
   cudaStream_t st = s->stream;
   fallback = 0;
   const int maxit = s->props.max_krylov_iters;
+  // on a refreshed hierarchy a slow solve means it has gone stale (e.g. a
+  // liquid pocket split by freezing cells): stop early and let the caller
+  // rebuild it rather than fall back to single-grid Jacobi
+  const bool refreshed = s->amg_ok && !s->amg_full && s->p_its_ref > 0;
+  if (refreshed) {
+    const int cap = std::min(maxit, std::max(s->p_its_ref * 2, s->p_its_ref + 12));
+    if (s->mesh->orthogonal)
+      FVS_TRY(pcg(st, s->red, s->kw, s->K, s->amg, s->prhs, s->px, rtol, cap, &s->aproj, res, &s->g_p));
+    else
+      FVS_TRY(bicgstab(st, s->red, s->kw, s->K, nullptr, s->amg, s->prhs, s->px, rtol, cap, &s->aproj, res, 0.0,
+                       &s->g_p));
+    if (res.converged) FVS_TRY(s->amg.project(st, s->px));
+    return FVS_OK;
+  }
   if (s->amg_ok) {
     if (s->mesh->orthogonal)
-      FVS_TRY(pcg(st, s->red, s->kw, s->K, s->amg, s->prhs, s->px, rtol, maxit, &s->aproj, res));
+      FVS_TRY(pcg(st, s->red, s->kw, s->K, s->amg, s->prhs, s->px, rtol, maxit, &s->aproj, res, &s->g_p));
     else
-      FVS_TRY(bicgstab(st, s->red, s->kw, s->K, nullptr, s->amg, s->prhs, s->px, rtol, maxit, &s->aproj, res));
+      FVS_TRY(bicgstab(st, s->red, s->kw, s->K, nullptr, s->amg, s->prhs, s->px, rtol, maxit, &s->aproj, res, 0.0,
+                       &s->g_p));
     if (res.converged) {
       FVS_TRY(s->amg.project(st, s->px));
       return FVS_OK;
@@ -789,17 +887,18 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
 
   // 1. tags, compaction, face cases
   FVS_TRY(classify(s));
-  const int64_t na = s->nact;
-  S.n_active = na;
+  int64_t na = s->nact;
+  S.n_active = s->nlm;
 
   // 2. momentum predictor
   FVS_TRY(s->M.alloc(na, m->W));
   FVS_TRY(s->mrhs.alloc(3 * na + 1));
   FVS_TRY(s->mx.alloc(3 * na + 1));
   if (na > 0) {
-    k_mom_matrix<<<stride_grid(na, 256), 256, 0, st>>>(na, Nc, m->W, s->act, s->map, m->Lu.col, m->Lu.val, m->V,
-                                                       s->fs, mt, dt, s->M.col, s->M.val, s->M.diag); FVS_COUNT_LAUNCH();
-    k_mom_rhs<<<stride_grid(na, 256), 256, 0, st>>>(na, Nc, m->W, s->act, m->cf, m->cfs, m->own, m->nei, s->F,
+    k_mom_matrix<<<stride_grid(na, 256), 256, 0, st>>>(na, Nc, m->W, s->act, s->map, s->lm, m->Lu.col, m->Lu.val,
+                                                       m->V, s->fs, mt, dt, s->M.col, s->M.val, s->M.diag);
+    FVS_COUNT_LAUNCH();
+    k_mom_rhs<<<stride_grid(na, 256), 256, 0, st>>>(na, Nc, m->W, s->act, s->lm, m->cf, m->cfs, m->own, m->nei, s->F,
                                                     s->Fold, s->u, s->uold, m->Lu.col, m->Lu.val, m->V, s->T, mt, dt,
                                                     s->mrhs, s->mx); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
@@ -816,7 +915,7 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
     for (int d = 0; d < 3; ++d) {
       SolveResult r;
       FVS_TRY(bicgstab(st, s->red, s->kw, s->M, nullptr, J, s->mrhs.p + d * na, s->mx.p + d * na,
-                       s->props.mom_rtol, s->props.max_krylov_iters, nullptr, r, bmax));
+                       s->props.mom_rtol, s->props.max_krylov_iters, nullptr, r, bmax, &s->g_m[d]));
       S.mom_its += r.iters;
       if (!r.converged) {
         status = FVS_ERR_NOT_CONVERGED;
@@ -824,14 +923,18 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
       }
     }
   }
-  k_scatter3<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, na, s->map, s->mx, s->ustar); FVS_COUNT_LAUNCH();
+  k_scatter3<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, na, s->map, s->lm, s->mx, s->ustar); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
 
   // 3. pressure system
   if (!s->k_valid) {
+    const auto t0 = std::chrono::steady_clock::now();
     FVS_TRY(assemble_pressure(s));
+    FVS_CUDA(cudaStreamSynchronize(st));
+    S.setup_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     s->k_valid = true;
-    S.p_rebuilt = 1;
+    S.p_rebuilt = s->amg_full ? 1 : 2;
+    na = s->nact;   // a failed refresh renumbers
   }
   FVS_TRY(s->prhs.alloc(na + 1));
   FVS_TRY(s->px.alloc(na + 1));
@@ -842,6 +945,35 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
     SolveResult r;
     int fb = 0;
     FVS_TRY(solve_pressure(s, s->props.p_rtol, r, fb));
+    // a refreshed hierarchy that has gone stale: rebuild it for the next step
+    // when the solve was slow, at once (and solve again) when it failed
+    if (!s->amg_full && s->amg_ok && r.converged &&
+        r.iters > std::max(s->p_its_ref * 3 / 2, s->p_its_ref + 6))
+      s->force_full = true;
+    if (!s->amg_full && s->amg_ok && !r.converged) {
+      const auto t0 = std::chrono::steady_clock::now();
+      FVS_TRY(renumber_lm(s));
+      s->force_full = true;
+      FVS_TRY(assemble_pressure(s));
+      FVS_CUDA(cudaStreamSynchronize(st));
+      S.setup_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      S.p_rebuilt = 1;
+      const int64_t nb = s->nact;
+      FVS_TRY(s->prhs.alloc(nb + 1));
+      FVS_TRY(s->px.alloc(nb + 1));
+      k_ppe_rhs<<<stride_grid(nb, 256), 256, 0, st>>>(nb, Nc, Nf, s->act, s->ppe, m->cf, m->cfs, s->fcase, m->own,
+                                                      m->nei, m->A, m->nrm, s->ustar, dt, s->p, s->prhs, s->px);
+      FVS_COUNT_LAUNCH();
+      FVS_LAUNCH_CHECK();
+      const int first_its = r.iters;
+      FVS_TRY(solve_pressure(s, s->props.p_rtol, r, fb));
+      if (s->amg_full) s->p_its_ref = r.iters;
+      r.iters += first_its;
+    } else if (s->amg_full) {
+      s->p_its_ref = r.iters;
+    }
+    // periodic renumbering and rebuild after a run of refreshes
+    if (S.p_rebuilt == 2 && ++s->steps_since_setup >= 25) s->force_full = true;
     S.p_its = r.iters;
     S.p_relres = r.relres;
     S.fallback = fb;
@@ -886,7 +1018,7 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
       FVS_LAUNCH_CHECK();
       SolveResult r;
       FVS_TRY(bicgstab(st, s->red, s->kw, s->Ke, s->edx, J, s->erhs, s->Tlin, rtol_m,
-                       s->props.max_krylov_iters, nullptr, r));
+                       s->props.max_krylov_iters, nullptr, r, 0.0, &s->g_e));
       S.e_lin_its += r.iters;
       if (!r.converged) {
         status = FVS_ERR_NOT_CONVERGED;

@@ -18,6 +18,13 @@ struct fvs_solver_s {
   bool have_props = false;
   bool have_step = false;     // tags / compact systems of a step exist
   bool k_valid = false;       // pressure system and AMG match the current tags
+  bool numbered = false;      // map/act hold a system numbering
+  bool renumbered = false;    // this step made a new numbering
+  bool force_full = false;    // next step renumbers and rebuilds the hierarchy
+  bool amg_full = false;      // the hierarchy was built (not refreshed) this step
+  int steps_since_setup = 0;
+  int p_its_ref = 0;          // pressure iterations right after the last full setup
+  int64_t nlm = 0;            // liquid + mushy cells
   fvs_props props{};
   std::vector<fvs_patch_bc> bc;
   double time = 0.0;
@@ -63,6 +70,7 @@ struct fvs_solver_s {
   int ncomp = 0;
   fvs_step_stats last{};
   fvs::Prof prof;
+  fvs::IterGraph g_p, g_e, g_m[3];   // captured Krylov iterations
 };
 
 namespace fvs {

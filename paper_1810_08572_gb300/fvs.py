@@ -61,7 +61,7 @@ class fvs_step_stats(C.Structure):
     _fields_ = [("n_active", C.c_int64), ("n_ppe", C.c_int64), ("mom_its", C.c_int32), ("p_its", C.c_int32),
                 ("e_its", C.c_int32), ("e_lin_its", C.c_int32), ("p_relres", C.c_double),
                 ("fallback", C.c_int32), ("n_components", C.c_int32), ("amg_levels", C.c_int32),
-                ("status", C.c_int32), ("p_rebuilt", C.c_int32)]
+                ("status", C.c_int32), ("p_rebuilt", C.c_int32), ("setup_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -39,7 +39,7 @@ def test_struct_layouts_match_header(lib):
     # doubles are 8-aligned, so the int32 members pad as in C
     assert C.sizeof(lib.fvs_patch_bc) == 16
     assert C.sizeof(lib.fvs_material) == 14 * 8
-    assert C.sizeof(lib.fvs_step_stats) == 2 * 8 + 4 * 4 + 8 + 5 * 4 + 4
+    assert C.sizeof(lib.fvs_step_stats) == 2 * 8 + 4 * 4 + 8 + 5 * 4 + 4 + 8
     assert C.sizeof(lib.fvs_mesh_info) == 4 * 8 + 4 * 4 + 8
 
 

@@ -127,6 +127,22 @@ def test_pressure_solve_matches_oracle(fvs):
     assert rel(p.cpu().numpy(), o.p) < 1e-10
 
 
+def test_large_coarsest_level(fvs, monkeypatch):
+    """A coarsest AMG level far above the shared-memory size (several hundred rows
+    here) is inverted in global memory by the whole GPU; one step still
+    matches the oracle."""
+    monkeypatch.setenv("FVS_AMG_COARSEST", "1000")
+    m = box_mesh(24, 24, 6, cases.CAVITY, jitter=0.2, jitter_seed=71, permute_seed=72)
+    T0 = frozen_corner_field(m, seed=7)
+    rng = np.random.default_rng(8)
+    u0 = rng.normal(scale=2e-3, size=(len(T0), 3))
+    o, M, S = make_pair(fvs, m, cases.props(**TIGHT), T0, u0)
+    o.step(1e-3)
+    st = S.step(1e-3)
+    assert st["amg_levels"] >= 2 and st["fallback"] == 0 and st["p_its"] < 200, st
+    compare(o, S, 1e-10)
+
+
 def test_two_hundred_steps_cavity(fvs):
     """The 32x32x4 configuration for its 200 steps: temperature within 1e-6 K."""
     c = cases.config_small()
@@ -209,3 +225,47 @@ def test_uq_batch_matches_oracle(fvs):
         done = np.isfinite(q["t_f"])
         ref = [q[name][done].mean() for name in ("t_f", "cooling_rate", "sdas", "yield_strength")]
         np.testing.assert_allclose(qoi[i], ref, rtol=1e-8)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_refreshed_hierarchy_while_cells_freeze(fvs, monkeypatch, precision):
+    """Cells that freeze keep the system numbering: their rows turn into
+    identity rows and the AMG hierarchy is re-formed on its old aggregates
+    (p_rebuilt == 2) instead of aggregated anew.  Fifty steps of a cavity
+    cooled on every wall, freezing from about step 8, match the oracle."""
+    monkeypatch.setenv("FVS_REFRESH_FRACTION", "1.0")
+    m = box_mesh(16, 16, 4, (0.02, 0.02, 0.005), jitter=0.2, jitter_seed=61, permute_seed=62)
+    props = cases.props(walls=cases.all_walls(700.0), T_init=920.0, **dict(TIGHT, precision=precision))
+    o, M, S = make_pair(fvs, m, props)
+    kinds = []
+    for _ in range(50):
+        o.step(2e-3)
+        st = S.step(2e-3)
+        assert st["p_relres"] <= 1e-12
+        kinds.append(st["p_rebuilt"])
+    assert kinds.count(2) >= 5, kinds
+    assert np.abs(S.query("T") - o.T).max() <= 1e-8
+    compare(o, S, 1e-9, fields=("U", "P", "FLUX"))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replayed_iterations_on_a_stream(fvs, precision):
+    """On a non-default stream the Krylov iterations are captured once and
+    replayed as CUDA graphs; results still match the oracle."""
+    import torch
+    m = box_mesh(20, 20, 4, cases.CAVITY, jitter=0.2, jitter_seed=51, permute_seed=52)
+    T0 = frozen_corner_field(m, seed=5)
+    rng = np.random.default_rng(7)
+    u0 = rng.normal(scale=2e-3, size=(len(T0), 3))
+    props = cases.props(**dict(TIGHT, precision=precision))
+    st = torch.cuda.Stream()
+    M = fvs.Mesh(m, stream=st)
+    S = fvs.Solver(M, props, stream=st)
+    S.set_state(T0, u0)
+    o = Oracle(m, props)
+    set_state(o, T0, u0)
+    for _ in range(3):
+        o.step(1e-3)
+        S.step(1e-3)
+    torch.cuda.synchronize()
+    compare(o, S, 1e-10)
