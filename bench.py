@@ -203,12 +203,17 @@ def run_gpu(args):
     its = []
     torch.cuda.synchronize()
     n_launch0 = fvs.fvs_launch_count()
+    nvtx = getattr(torch.cuda, "nvtx", None)
+    if nvtx is not None:
+        nvtx.range_push("timed")   # lets ncu select the timed steps (--nvtx-include timed/)
     ev0.record(stream)
     for _ in range(args.steps):
         st = S.step(dt, 1, allow_not_converged=True)
         act += st["n_active"]
         its.append(st)
     ev1.record(stream)
+    if nvtx is not None:
+        nvtx.range_pop()
     torch.cuda.synchronize()
     n_launch = fvs.fvs_launch_count() - n_launch0
     ms = ev0.elapsed_time(ev1)
@@ -235,10 +240,14 @@ def run_gpu(args):
     roof = None
     if top:
         per_launch_bytes = top["bytes"] / top["launches"]
+        # DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum) of
+        # k_spmv_dot on the 96^3 cavity: 320.65 MB against 307.89 MB algorithmic; scaled
+        # with the rows of the launch (profiles/spmv_dot_cavity96_fp64.md)
+        traffic = round(per_launch_bytes * 320.65 / 307.89) if top["name"].startswith("spmv@") else None
         per_launch_s = top["total_ms"] / top["launches"] / 1e3
         ach = per_launch_bytes / per_launch_s / 1e9
         roof = dict(bound="hbm", kernel=top["name"], achieved=round(ach, 1), peak=peak, unit="GB/s",
-                    frac=round(ach / peak, 4), traffic=None, peak_source=f"{peak_kind} copy bandwidth",
+                    frac=round(ach / peak, 4), traffic=traffic, peak_source=f"{peak_kind} copy bandwidth",
                     launches=top["launches"],
                     share_of_step=round(top["total_ms"] / max(1, args.prof_steps) / (ms / args.steps), 3),
                     bytes_per_launch=per_launch_bytes)

@@ -20,8 +20,9 @@ static constexpr int GAL_SMALL = 256;  // rows up to this many entries: the many
 // (or the same holds with i and j exchanged, to keep the graph symmetric)
 // ---------------------------------------------------------------------------
 __global__ void k_maxoff(int64_t n, int w, const int32_t* col, const double* val, double* mo, double* dinv,
-                         const double* diag) {
+                         const double* diag, const uint8_t* dirty = nullptr) {
   GS(i, n) {
+    if (dirty && !dirty[i]) continue;
     double m = 0.0;
     for (int k = 0; k < w; ++k) {
       const int64_t e = (int64_t)k * n + i;
@@ -33,7 +34,7 @@ __global__ void k_maxoff(int64_t n, int w, const int32_t* col, const double* val
 }
 
 __global__ void k_strong(int64_t n, int w, const int32_t* col, const double* val, const double* mo, double theta,
-                         uint64_t* mask) {
+                         int absval, uint64_t* mask) {
   GS(i, n) {
     // judged from row i alone (the strength graph may be slightly
     // asymmetric; the independent-set rounds and the assignment only ever
@@ -45,7 +46,7 @@ __global__ void k_strong(int64_t n, int w, const int32_t* col, const double* val
       const int64_t e = (int64_t)k * n + i;
       const int32_t j = col[e];
       if (j == (int32_t)i) continue;
-      const double a = -val[e];
+      const double a = absval ? fabs(val[e]) : -val[e];
       if (a > 0.0 && a >= theta * mo[i]) msk |= (1ULL << k);
     }
     mask[i] = msk;
@@ -98,6 +99,11 @@ __global__ void k_mis_remove(int64_t n, int w, const int32_t* col, const uint64_
     st[i] = s;
   }
   if (cnt) atomicAdd(undecided, cnt);
+}
+__global__ void k_count_isolated(int64_t n, const uint64_t* mask, int* out) {
+  int c = 0;
+  GS(i, n) c += mask[i] == 0 ? 1 : 0;
+  if (c) atomicAdd(out, c);
 }
 __global__ void k_is_root(int64_t n, const uint8_t* st, int32_t* flag) {
   GS(i, n) flag[i] = st[i] == 1 ? 1 : 0;
@@ -154,92 +160,128 @@ __global__ void k_sort_members(int64_t nc, const int32_t* ptr, int32_t* idx) {
 // ---------------------------------------------------------------------------
 // Galerkin product with piecewise-constant transfers:
 //   Ac[I][J] = sum_{i in I} sum_{j in J} a_ij
-// one warp per coarse row: gather (agg[col], val) of all member rows into
-// shared memory, bitonic-sort by key, reduce equal keys in a fixed order
-// (deterministic).  Pass 1 counts entries, pass 2 writes the ELL rows.
+// per coarse row: gather (agg[col], val) of all member rows into shared
+// memory, bitonic-sort by key, reduce equal keys in a fixed order
+// (deterministic).  The count pass gives the row lengths, the fill pass
+// writes the ELL rows.  Rows of at most GAL_SMALL gathered entries take one
+// warp each (many warps per block); larger rows take a whole block.  With a
+// 'dirty' mask only the marked coarse rows are recomputed (refresh).
 // ---------------------------------------------------------------------------
-// Two instances: CAP = GAL_SMALL with several warps per block (most rows;
-// high occupancy) takes rows of at most GAL_SMALL gathered entries, CAP =
-// GAL_CAP with one warp per block the rest (min_total = GAL_SMALL).
-template <bool FILL, int CAP, int WARPS>
+// gather and zero-pad to P (a power of two), then sort; T threads, SYNC()
+// the barrier among them
+#define GAL_GATHER_SORT(T, t, SYNC)                                                \
+  for (int e = (t); e < P; e += (T)) {                                            \
+    if (e < total) {                                                              \
+      const int m = e / w, k = e - m * w;                                         \
+      const int32_t i = midx[lo + m];                                             \
+      const int64_t ei = (int64_t)k * n + i;                                      \
+      const double a = val[ei];                                                   \
+      key[e] = a != 0.0 ? agg[col[ei]] : INT_MAX;                                 \
+      v[e] = a;                                                                   \
+    } else {                                                                      \
+      key[e] = INT_MAX;                                                           \
+      v[e] = 0.0;                                                                 \
+    }                                                                             \
+  }                                                                               \
+  SYNC;                                                                           \
+  for (int size = 2; size <= P; size <<= 1) {                                     \
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {                      \
+      for (int e = (t); e < P; e += (T)) {                                        \
+        const int p = e ^ stride;                                                 \
+        if (p > e) {                                                              \
+          const bool up = (e & size) == 0;                                        \
+          const int32_t ke = key[e], kp = key[p];                                 \
+          if ((ke > kp) == up && ke != kp) {                                      \
+            key[e] = kp; key[p] = ke;                                             \
+            const double tv = v[e]; v[e] = v[p]; v[p] = tv;                       \
+          }                                                                       \
+        }                                                                         \
+      }                                                                           \
+      SYNC;                                                                       \
+    }                                                                             \
+  }
+
+// one warp: segment heads of the sorted keys -> row I of the coarse ELL
+template <bool FILL>
+__device__ __forceinline__ void gal_emit(int lane, const int32_t* key, const double* v, int P, int64_t I, int64_t nc,
+                                         int32_t* rowlen, int wc, int32_t* ccol, double* cval, double* cdiag,
+                                         int* err) {
+  if (FILL && lane == 0) cdiag[I] = 0.0;
+  __syncwarp();
+  int base = 0;
+  for (int e0 = 0; e0 < P; e0 += 32) {
+    const int e = e0 + lane;
+    const bool head = key[e] != INT_MAX && (e == 0 || key[e - 1] != key[e]);
+    const unsigned bal = __ballot_sync(0xffffffffu, head);
+    if (FILL && head) {
+      const int r = base + __popc(bal & ((1u << lane) - 1));
+      double sum = 0.0;
+      for (int q = e; q < P && key[q] == key[e]; ++q) sum += v[q];
+      if (r < wc) {
+        ccol[(int64_t)r * nc + I] = key[e];
+        cval[(int64_t)r * nc + I] = sum;
+      } else {
+        atomicOr(err, 4);
+      }
+      if (key[e] == (int32_t)I) cdiag[I] = sum;
+    }
+    base += __popc(bal);
+  }
+  if (!FILL) {
+    if (lane == 0) rowlen[I] = base;
+  } else {
+    for (int r = base + lane; r < wc; r += 32) {
+      ccol[(int64_t)r * nc + I] = (int32_t)I;
+      cval[(int64_t)r * nc + I] = 0.0;
+    }
+  }
+}
+
+template <bool FILL, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS) k_galerkin(int64_t nc, int64_t n, int w, const int32_t* col,
                                                          const double* val, const int32_t* agg, const int32_t* mptr,
                                                          const int32_t* midx, int32_t* rowlen, int wc, int32_t* ccol,
-                                                         double* cval, double* cdiag, int* err, int min_total) {
-  __shared__ int32_t key_s[WARPS * CAP];
-  __shared__ double v_s[WARPS * CAP];
+                                                         double* cval, double* cdiag, int* err,
+                                                         const uint8_t* dirty) {
+  __shared__ int32_t key_s[WARPS * GAL_SMALL];
+  __shared__ double v_s[WARPS * GAL_SMALL];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int32_t* key = key_s + wid * CAP;
-  double* v = v_s + wid * CAP;
+  int32_t* key = key_s + wid * GAL_SMALL;
+  double* v = v_s + wid * GAL_SMALL;
   for (int64_t I = (int64_t)blockIdx.x * WARPS + wid; I < nc; I += (int64_t)gridDim.x * WARPS) {
+    if (dirty && !dirty[I]) continue;
     const int32_t lo = mptr[I], hi = mptr[I + 1];
     const int total = (hi - lo) * w;
-    if (total <= min_total) continue;
-    if (total > CAP) {
-      if (CAP >= GAL_CAP && lane == 0) { atomicOr(err, 2); if (!FILL) rowlen[I] = 0; }
+    if (total > GAL_SMALL) continue;     // the block-per-row kernel takes it
+    int P = 32;
+    while (P < total) P <<= 1;
+    GAL_GATHER_SORT(32, lane, __syncwarp())
+    gal_emit<FILL>(lane, key, v, P, I, nc, rowlen, wc, ccol, cval, cdiag, err);
+    __syncwarp();
+  }
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_galerkin_big(int64_t nc, int64_t n, int w, const int32_t* col,
+                                                      const double* val, const int32_t* agg, const int32_t* mptr,
+                                                      const int32_t* midx, int32_t* rowlen, int wc, int32_t* ccol,
+                                                      double* cval, double* cdiag, int* err, const uint8_t* dirty) {
+  __shared__ int32_t key[GAL_CAP];
+  __shared__ double v[GAL_CAP];
+  for (int64_t I = blockIdx.x; I < nc; I += gridDim.x) {
+    if (dirty && !dirty[I]) continue;
+    const int32_t lo = mptr[I], hi = mptr[I + 1];
+    const int total = (hi - lo) * w;
+    if (total <= GAL_SMALL) continue;
+    if (total > GAL_CAP) {
+      if (threadIdx.x == 0) { atomicOr(err, 2); if (!FILL) rowlen[I] = 0; }
       continue;
     }
     int P = 32;
     while (P < total) P <<= 1;
-    for (int e = lane; e < P; e += 32) {
-      if (e < total) {
-        const int m = e / w, k = e - m * w;
-        const int32_t i = midx[lo + m];
-        const int64_t ei = (int64_t)k * n + i;
-        const double a = val[ei];
-        key[e] = a != 0.0 ? agg[col[ei]] : INT_MAX;
-        v[e] = a;
-      } else {
-        key[e] = INT_MAX;
-        v[e] = 0.0;
-      }
-    }
-    __syncwarp();
-    for (int size = 2; size <= P; size <<= 1) {
-      for (int stride = size >> 1; stride > 0; stride >>= 1) {
-        for (int e = lane; e < P; e += 32) {
-          const int p = e ^ stride;
-          if (p > e) {
-            const bool up = (e & size) == 0;
-            const int32_t ke = key[e], kp = key[p];
-            if ((ke > kp) == up && ke != kp) {
-              key[e] = kp; key[p] = ke;
-              const double t = v[e]; v[e] = v[p]; v[p] = t;
-            }
-          }
-        }
-        __syncwarp();
-      }
-    }
-    // segment heads
-    int base = 0;
-    for (int e0 = 0; e0 < P; e0 += 32) {
-      const int e = e0 + lane;
-      const bool head = key[e] != INT_MAX && (e == 0 || key[e - 1] != key[e]);
-      const unsigned bal = __ballot_sync(0xffffffffu, head);
-      if (FILL && head) {
-        const int r = base + __popc(bal & ((1u << lane) - 1));
-        double s = 0.0;
-        for (int q = e; q < P && key[q] == key[e]; ++q) s += v[q];
-        if (r < wc) {
-          ccol[(int64_t)r * nc + I] = key[e];
-          cval[(int64_t)r * nc + I] = s;
-        } else {
-          atomicOr(err, 4);
-        }
-        if (key[e] == (int32_t)I) cdiag[I] = s;
-      }
-      base += __popc(bal);
-    }
-    if (!FILL) {
-      if (lane == 0) rowlen[I] = base;
-    } else {
-      for (int r = base + lane; r < wc; r += 32) {
-        ccol[(int64_t)r * nc + I] = (int32_t)I;
-        cval[(int64_t)r * nc + I] = 0.0;
-      }
-    }
-    __syncwarp();
+    GAL_GATHER_SORT(256, (int)threadIdx.x, __syncthreads())
+    if (threadIdx.x < 32) gal_emit<FILL>((int)threadIdx.x, key, v, P, I, nc, rowlen, wc, ccol, cval, cdiag, err);
+    __syncthreads();
   }
 }
 
@@ -661,7 +703,13 @@ __global__ void k_copy_i32(int64_t n, const int32_t* a, int32_t* b) {
 // rows with a negative label (cells frozen since the hierarchy was built)
 // take no part in the projection
 __global__ void k_comp_count(int64_t n, const int32_t* lab, double* cnt) {
-  GS(i, n) if (lab[i] >= 0) atomicAdd(&cnt[lab[i]], 1.0);
+  // lanes with the same label add once (one part usually holds every row)
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = b + threadIdx.x;
+    const int32_t c = i < n ? lab[i] : -1;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    if (c >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[c], (double)__popc(peers));
+  }
 }
 __global__ void k_comp_sum(int64_t n, const int32_t* lab, const double* v, double* s) {
   GS(i, n) if (lab[i] >= 0) atomicAdd(&s[lab[i]], v[i]);
@@ -700,6 +748,39 @@ __global__ void k_sub_scalar(int64_t n, const double* mean, const int32_t* lab, 
 __global__ void k_mask_labels(int64_t n, const int32_t* act, const uint8_t* ppe, int32_t* lab) {
   GS(i, n) if (!ppe[act[i]]) lab[i] = -1;
 }
+// 64-bit fingerprint of each ELL row (columns and value bits); with 'old'
+// given, rows whose fingerprint changed are marked dirty
+__device__ __forceinline__ uint64_t smix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+  return z ^ (z >> 31);
+}
+__global__ void k_row_hash(int64_t n, int w, const int32_t* col, const double* val, uint64_t* hash,
+                           uint8_t* dirty, int compare) {
+  GS(i, n) {
+    uint64_t h = 0x6a09e667f3bcc909ULL;
+    for (int k = 0; k < w; ++k) {
+      const int64_t e = (int64_t)k * n + i;
+      h = smix64(h ^ (uint64_t)(uint32_t)col[e]);
+      h = smix64(h + (uint64_t)__double_as_longlong(val[e]));
+    }
+    if (compare) dirty[i] = hash[i] != h ? 1 : 0;
+    hash[i] = h;
+  }
+}
+// a coarse row is dirty when any of its member rows is
+__global__ void k_dirty_up(int64_t n, const int32_t* agg, const uint8_t* dirty, uint8_t* dirty_c) {
+  GS(i, n) if (dirty[i] && agg[i] >= 0) dirty_c[agg[i]] = 1;
+}
+// FP32 copies of the dirty rows
+__global__ void k_convert_rows(int64_t n, int w, const double* val, const double* dinv, const uint8_t* dirty,
+                               float* valf, float* dinvf) {
+  GS(i, n) {
+    if (!dirty[i]) continue;
+    for (int k = 0; k < w; ++k) valf[(int64_t)k * n + i] = (float)val[(int64_t)k * n + i];
+    dinvf[i] = (float)dinv[i];
+  }
+}
 
 // ---------------------------------------------------------------------------
 // host side
@@ -710,24 +791,24 @@ static fvs_status read_int(cudaStream_t s, const int* d, int* h) {
   return FVS_OK;
 }
 
-// one Galerkin pass (count or fill) over all coarse rows
+// one Galerkin pass (count or fill) over all coarse rows (or the dirty ones)
 static void galerkin_pass(cudaStream_t s, bool fill, int64_t nc, const Ell& A, const int32_t* agg,
                           const int32_t* mptr, const int32_t* midx, int32_t* rowlen, int wc, int32_t* ccol,
-                          double* cval, double* cdiag, int* err) {
+                          double* cval, double* cdiag, int* err, const uint8_t* dirty = nullptr) {
   if (nc <= 0) return;
   const int64_t n = A.n;
   const int gs = (int)std::min<int64_t>((nc + 3) / 4, (int64_t)sm_count() * 16);
-  const int gb = (int)std::min<int64_t>(nc, (int64_t)sm_count() * 32);
+  const int gb = (int)std::min<int64_t>(nc, (int64_t)sm_count() * 8);
   if (fill) {
-    k_galerkin<true, GAL_SMALL, 4><<<gs, 128, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol,
-                                                      cval, cdiag, err, -1); FVS_COUNT_LAUNCH();
-    k_galerkin<true, GAL_CAP, 1><<<gb, 32, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol, cval,
-                                                   cdiag, err, GAL_SMALL); FVS_COUNT_LAUNCH();
+    k_galerkin<true, 4><<<gs, 128, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol, cval, cdiag,
+                                           err, dirty); FVS_COUNT_LAUNCH();
+    k_galerkin_big<true><<<gb, 256, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol, cval,
+                                            cdiag, err, dirty); FVS_COUNT_LAUNCH();
   } else {
-    k_galerkin<false, GAL_SMALL, 4><<<gs, 128, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol,
-                                                       cval, cdiag, err, -1); FVS_COUNT_LAUNCH();
-    k_galerkin<false, GAL_CAP, 1><<<gb, 32, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol,
-                                                    cval, cdiag, err, GAL_SMALL); FVS_COUNT_LAUNCH();
+    k_galerkin<false, 4><<<gs, 128, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol, cval,
+                                            cdiag, err, dirty); FVS_COUNT_LAUNCH();
+    k_galerkin_big<false><<<gb, 256, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol, cval,
+                                             cdiag, err, dirty); FVS_COUNT_LAUNCH();
   }
 }
 
@@ -787,17 +868,20 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
     if (n <= opt.coarsest || l + 1 >= opt.max_levels) break;
     // strength and aggregation; if the strong graph coarsens too little (small
     // coarse levels of anisotropic problems), retry with every negative
-    // coupling counted as strong
+    // coupling counted as strong, then with every nonzero coupling (coarse
+    // Galerkin operators of skewed meshes carry many positive ones)
     DBuf<uint64_t> mask;
     DBuf<uint8_t> st, st2;
     DBuf<int32_t> flag, rid;
     FVS_TRY(mask.alloc(n)); FVS_TRY(st.alloc(n)); FVS_TRY(st2.alloc(n));
     FVS_TRY(flag.alloc(n + 1)); FVS_TRY(rid.alloc(n + 1));
     int nc = 0;
-    for (int attempt = 0; attempt < 2; ++attempt) {
+    for (int attempt = 0; attempt < 3; ++attempt) {
       const double theta = attempt == 0 ? opt.theta : 0.0;
+      const int absval = attempt == 2 ? 1 : 0;
       FVS_TRY(st.zero(s));
-      k_strong<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mo, theta, mask); FVS_COUNT_LAUNCH();
+      k_strong<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mo, theta, absval, mask);
+      FVS_COUNT_LAUNCH();
       FVS_LAUNCH_CHECK();
       tick(1);
       for (int round = 0;; round += 2) {
@@ -823,6 +907,32 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
       FVS_CUDA(cudaMemcpyAsync(&nc, rid.p + n, sizeof(int), cudaMemcpyDeviceToHost, s));
       FVS_CUDA(cudaStreamSynchronize(s));
       if ((double)nc <= 0.6 * (double)n) break;
+    }
+    if (dbg) {
+      // rows without a strong coupling in the last attempt become singletons
+      FVS_TRY(cnt.zero(s));
+      k_count_isolated<<<stride_grid(n, 256), 256, 0, s>>>(n, mask, cnt); FVS_COUNT_LAUNCH();
+      int iso = 0;
+      FVS_TRY(read_int(s, cnt, &iso));
+      fprintf(stderr, "[fvs amg] level %d: %lld rows (w%d) -> %d aggregates, %d rows without strong couplings\n", l,
+              (long long)n, cur->w, nc, iso);
+      const char* dump = getenv("FVS_AMG_DUMP");   // small levels to a file, for offline study
+      if (dump && *dump && n <= 8192) {
+        std::vector<int32_t> hc((size_t)n * cur->w);
+        std::vector<double> hv((size_t)n * cur->w);
+        FVS_CUDA(cudaMemcpyAsync(hc.data(), cur->col.p, hc.size() * 4, cudaMemcpyDeviceToHost, s));
+        FVS_CUDA(cudaMemcpyAsync(hv.data(), cur->val.p, hv.size() * 8, cudaMemcpyDeviceToHost, s));
+        FVS_CUDA(cudaStreamSynchronize(s));
+        char path[512];
+        snprintf(path, sizeof path, "%s_L%d.bin", dump, l);
+        if (FILE* f = fopen(path, "wb")) {
+          const int64_t hdr[2] = {n, (int64_t)cur->w};
+          fwrite(hdr, 8, 2, f);
+          fwrite(hc.data(), 4, hc.size(), f);
+          fwrite(hv.data(), 8, hv.size(), f);
+          fclose(f);
+        }
+      }
     }
     if (nc <= 0 || nc >= n || (double)nc > 0.85 * (double)n) break;  // stagnation: L is the coarsest
     tick(2);
@@ -875,6 +985,13 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
   FVS_TRY(coarsest_setup(s));
   tick(5);
   if (opt.fp32) FVS_TRY(setup_fp32(s));
+  if (lv[0]->n > 0) {
+    const Ell& A0 = *lv[0]->A;
+    FVS_TRY(rowhash.alloc(A0.n + 1));
+    k_row_hash<<<stride_grid(A0.n, 256), 256, 0, s>>>(A0.n, A0.w, A0.col, A0.val, rowhash, nullptr, 0);
+    FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+  }
   tick(6);
   if (dbg) {
     fprintf(stderr, "[fvs amg] levels %d:", (int)lv.size());
@@ -999,10 +1116,22 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
   FVS_TRY(err.alloc(1));
   FVS_TRY(err.zero(s));
   FVS_TRY(mo.alloc(n0 + 1));
+  for (auto& L : lv) {
+    FVS_TRY(L->dirty.alloc(L->n + 1));
+    FVS_TRY(L->dirty.zero(s));
+  }
+  // fine rows that changed since the hierarchy was last formed
+  if (n0 > 0) {
+    const Ell& A = *lv[0]->A;
+    k_row_hash<<<stride_grid(n0, 256), 256, 0, s>>>(n0, A.w, A.col, A.val, rowhash, lv[0]->dirty, 1);
+    FVS_COUNT_LAUNCH();
+  }
   if (lv.size() > 1 && n0 > 0) {
-    // level 0: same aggregates without the rows of cells that lost pressure
+    // level 0: mark the aggregates of changed rows (before the rows of cells
+    // without pressure leave them), then rebuild the member lists
     AmgLevel* L = lv[0].get();
     const int64_t nc = lv[1]->n;
+    k_dirty_up<<<stride_grid(n0, 256), 256, 0, s>>>(n0, L->agg, L->dirty, lv[1]->dirty); FVS_COUNT_LAUNCH();
     k_mask_agg<<<stride_grid(n0, 256), 256, 0, s>>>(n0, act, ppe, L->agg, err); FVS_COUNT_LAUNCH();
     DBuf<int32_t> mc;
     FVS_TRY(mc.alloc(nc + 1));
@@ -1014,22 +1143,27 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
     k_sort_members<<<stride_grid(nc, 256), 256, 0, s>>>(nc, L->mptr, L->midx); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
   }
-  // Galerkin products level by level on the kept aggregates; the coarse rows
-  // can only lose entries, so the widths of the setup still hold (checked)
+  // Galerkin rows of the dirty aggregates, level by level on the kept
+  // aggregation; rows can only lose entries, so the widths still hold (checked)
   for (size_t l = 0; l < lv.size(); ++l) {
     AmgLevel* L = lv[l].get();
     const Ell* cur = L->A;
     const int64_t n = L->n;
     if (n > 0) {
-      k_maxoff<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mo, L->dinv, cur->diag);
+      k_maxoff<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mo, L->dinv, cur->diag, L->dirty);
       FVS_COUNT_LAUNCH();
+      if (opt.fp32) {
+        k_convert_rows<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->val, L->dinv, L->dirty, L->valf,
+                                                           L->dinvf); FVS_COUNT_LAUNCH();
+      }
     }
     if (l + 1 == lv.size()) break;
     AmgLevel* C = lv[l + 1].get();
-    const int64_t nc = C->n;
-    FVS_TRY(C->own.diag.zero(s));
-    galerkin_pass(s, true, nc, *cur, L->agg, L->mptr, L->midx, nullptr, C->own.w, C->own.col, C->own.val,
-                  C->own.diag, err);
+    if (l > 0 && n > 0) {
+      k_dirty_up<<<stride_grid(n, 256), 256, 0, s>>>(n, L->agg, L->dirty, C->dirty); FVS_COUNT_LAUNCH();
+    }
+    galerkin_pass(s, true, C->n, *cur, L->agg, L->mptr, L->midx, nullptr, C->own.w, C->own.col, C->own.val,
+                  C->own.diag, err, C->dirty);
     FVS_LAUNCH_CHECK();
   }
   {
@@ -1047,7 +1181,6 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
     k_comp_count<<<stride_grid(n0, 256), 256, 0, s>>>(n0, fine_lab, ccnt); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
   }
-  if (opt.fp32) FVS_TRY(setup_fp32(s));
   masked = true;
   ready = true;
   return FVS_OK;

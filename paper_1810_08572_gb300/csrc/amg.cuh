@@ -24,6 +24,7 @@ struct AmgLevel {
   DBuf<int32_t> mptr, midx;   // members of each aggregate of the next level (CSR)
   DBuf<double> b, x, y, r, t;    // V-cycle work
   DBuf<float> bf, xf, yf, rf, tf; // FP32 V-cycle work
+  DBuf<uint8_t> dirty;  // rows changed since the last setup or refresh
   int64_t n = 0;
 };
 
@@ -42,7 +43,7 @@ struct Amg : Precond {
   std::vector<std::unique_ptr<AmgLevel>> lv;
   int nc = 0;                    // coarsest size
   DBuf<double> Ainv;             // [nc*nc] pinned inverse of the coarsest operator
-  DBuf<float> Ainvf;
+  DBuf<uint64_t> rowhash;        // fingerprints of the fine rows the hierarchy was formed from
   DBuf<int32_t> clab;            // coarsest component labels
   DBuf<uint8_t> csing;           // per component: 1 if singular (row sums zero)
   DBuf<int32_t> fine_lab;        // labels of the fine rows
@@ -57,9 +58,12 @@ struct Amg : Precond {
 
   fvs_status setup(cudaStream_t s, const Ell& A);
   // The operator's values changed on the same rows (cells frozen since the
-  // setup became identity rows): take the new fine diagonal, drop the rows of
-  // cells without pressure (ppe[act[i]] == 0) from the null-space labels and
-  // keep the coarse levels.  The launches captured for apply() stay valid.
+  // setup became identity rows): rows of cells without pressure
+  // (ppe[act[i]] == 0) leave their aggregates and the null-space labels, and
+  // the Galerkin rows of every aggregate whose member rows changed (row
+  // fingerprints) are recomputed on the kept aggregation, level by level,
+  // followed by the coarsest inverse.  FVS_ERR_NOT_CONVERGED: the kept
+  // aggregation does not fit any more (a new setup is needed).
   fvs_status refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe);
   fvs_status apply(cudaStream_t s, const double* r, double* z) override;
   uint64_t version = 0;          // bumped by every setup
