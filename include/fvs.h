@@ -221,9 +221,15 @@ fvs_status fvs_query_fields(fvs_solver solver, fvs_field field, double* dst,
  *   dt        time step (s); each sample starts at rest at its melt
  *             temperature and runs until a step starts with every cell solid,
  *             or for max_steps steps
- *   mode      0: plain solves (the only mode available)
- *   n_streams concurrent samples, each on its own CUDA stream and solver
- *             (0 = 8)
+ *   mode      FVS_UQ_LOCKSTEP (0): all samples advance together, every
+ *             field stored [row][sample], one launch per phase for all
+ *             samples, shared operators and AMG aggregation, per-sample
+ *             pressure rows and coarse values (needs a coarsest AMG level of
+ *             at most 160 rows on the all-liquid pressure operator, else
+ *             FVS_ERR_NOT_CONVERGED);
+ *             FVS_UQ_STREAMS (1): independent solves, each on its own CUDA
+ *             stream and solver
+ *   n_streams mode 1: concurrent samples (0 = 8); ignored by mode 0
  *   qoi_out   host double [n_samples*4]: per sample the mean over the
  *             solidified cells of local solidification time t_f (s), cooling
  *             rate (K/s), SDAS (um) and yield strength (MPa); NaN if no cell
@@ -232,6 +238,7 @@ fvs_status fvs_query_fields(fvs_solver solver, fvs_field field, double* dst,
  * Blocks until all samples are done.  Fails with FVS_ERR_ARG if a sample's
  * liquidus falls to the solidus.
  * ------------------------------------------------------------------------ */
+enum { FVS_UQ_LOCKSTEP = 0, FVS_UQ_STREAMS = 1 };
 fvs_status fvs_uq_batch(fvs_mesh mesh, const fvs_props* base, int64_t n_samples, const double* inputs,
                         double dt, int32_t max_steps, int32_t mode, int32_t n_streams, double* qoi_out,
                         int64_t* steps_out);

@@ -483,7 +483,10 @@ static constexpr int SMEM_COARSEST = 160;
 
 __global__ void __launch_bounds__(1024) k_coarsest_smem(int n, int w, const int32_t* col, const double* val,
                                                         double* Ainv, int32_t* lab, uint8_t* sing,
-                                                        int* ncomp_out, int* err) {
+                                                        int* ncomp_out, int* err, int vs) {
+  // one block per sample s = blockIdx.x; values and outputs of sample s sit
+  // at stride vs (vs = 1, one block: a single system)
+  const int smp = blockIdx.x;
   extern __shared__ double smem[];
   double* M = smem;                          // [n*n] in-place inverse
   double* fac = M + n * n;                   // [n]
@@ -496,7 +499,7 @@ __global__ void __launch_bounds__(1024) k_coarsest_smem(int n, int w, const int3
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) M[e] = 0.0;
   __syncthreads();
   for (int i = threadIdx.x; i < n; i += blockDim.x)
-    for (int k = 0; k < w; ++k) M[i * n + col[(int64_t)k * n + i]] += val[(int64_t)k * n + i];
+    for (int k = 0; k < w; ++k) M[i * n + col[(int64_t)k * n + i]] += val[((int64_t)k * n + i) * vs + smp];
   __syncthreads();
   if (threadIdx.x == 0) {
     // connected parts (breadth-first over the symmetric pattern), queue in 'order'
@@ -538,7 +541,7 @@ __global__ void __launch_bounds__(1024) k_coarsest_smem(int n, int w, const int3
       for (int i = 0; i < n; ++i)
         if (lb[i] == c) order[pos++] = i;
     ncs = nc;
-    *ncomp_out = nc;
+    ncomp_out[smp] = nc;
   }
   __syncthreads();
   // in-place Gauss-Jordan with partial (row) pivoting
@@ -620,11 +623,11 @@ __global__ void __launch_bounds__(1024) k_coarsest_smem(int n, int w, const int3
     }
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Ainv[e] = M[e];
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) Ainv[(int64_t)e * vs + smp] = M[e];
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    lab[i] = lb[i];
+    lab[(int64_t)i * vs + smp] = lb[i];
   }
-  for (int c = threadIdx.x; c < ncs; c += blockDim.x) sing[c] = sg[c];
+  for (int c = threadIdx.x; c < ncs; c += blockDim.x) sing[(int64_t)c * vs + smp] = sg[c];
 }
 
 // coarsest solve: y = Ainv b with the projections already folded into Ainv;
@@ -1031,7 +1034,8 @@ fvs_status Amg::coarsest_setup(cudaStream_t s) {
         FVS_CUDA(cudaFuncSetAttribute(k_coarsest_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmax));
         attr_set[dev] = true;
       }
-      k_coarsest_smem<<<1, 1024, sh, s>>>(nc, A.w, A.col, A.val, Ainv, clab, csing, ncd, err); FVS_COUNT_LAUNCH();
+      k_coarsest_smem<<<1, 1024, sh, s>>>(nc, A.w, A.col, A.val, Ainv, clab, csing, ncd, err, 1);
+      FVS_COUNT_LAUNCH();
     } else {
       DBuf<double> fac;
       DBuf<int32_t> perm, order;
@@ -1284,6 +1288,31 @@ fvs_status Amg::setup_fp32(cudaStream_t s) {
       k_convert<double, float><<<stride_grid(n, 256), 256, 0, s>>>(n, L->dinv.p, L->dinvf.p); FVS_COUNT_LAUNCH();
     }
   }
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
+int amg_smem_coarsest() { return SMEM_COARSEST; }
+
+fvs_status amg_coarsest_batched(cudaStream_t s, int n, int w, const int32_t* col, const double* val, int Sp,
+                                double* Ainv, int32_t* lab, uint8_t* sing, int* ncomp, int* err) {
+  if (n <= 0) return FVS_OK;
+  if (n > SMEM_COARSEST) {
+    set_error("batched coarsest level has %d rows (at most %d)", n, SMEM_COARSEST);
+    return FVS_ERR_NOT_CONVERGED;
+  }
+  static bool attr_set[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+    const size_t shmax = (size_t)SMEM_COARSEST * SMEM_COARSEST * sizeof(double) +
+                         (size_t)SMEM_COARSEST * sizeof(double) + 3 * (size_t)SMEM_COARSEST * sizeof(int);
+    FVS_CUDA(cudaFuncSetAttribute(k_coarsest_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shmax));
+    attr_set[dev] = true;
+  }
+  const size_t sh = (size_t)n * n * sizeof(double) + (size_t)n * sizeof(double) + 3 * (size_t)n * sizeof(int);
+  k_coarsest_smem<<<Sp, 1024, sh, s>>>(n, w, col, val, Ainv, lab, sing, ncomp, err, Sp);
+  FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   return FVS_OK;
 }

@@ -86,4 +86,12 @@ struct AmgProjector : Projector {
   fvs_status apply(cudaStream_t s, double* v) override { return amg->project(s, v); }
 };
 
+// Pinned dense inverses of Sp coarsest systems at once (one block each):
+// values of system s at val[(k*n + i)*Sp + s]; outputs Ainv[(i*n + j)*Sp + s],
+// part labels lab[i*Sp + s], singular flags sing[c*Sp + s], part counts
+// ncomp[s].  n must not exceed amg_smem_coarsest().
+int amg_smem_coarsest();
+fvs_status amg_coarsest_batched(cudaStream_t s, int n, int w, const int32_t* col, const double* val, int Sp,
+                                double* Ainv, int32_t* lab, uint8_t* sing, int* ncomp, int* err);
+
 }  // namespace fvs

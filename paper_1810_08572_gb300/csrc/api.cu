@@ -5,6 +5,7 @@
 
 #include <new>
 
+#include "batch.cuh"
 #include "solver.cuh"
 
 namespace fvs {
@@ -339,8 +340,8 @@ FVS_API fvs_status fvs_uq_batch(fvs_mesh mesh, const fvs_props* base, int64_t n_
     set_error("fvs_uq_batch: bad argument");
     return FVS_ERR_ARG;
   }
-  if (mode != 0) {
-    set_error("fvs_uq_batch: mode %d is not available (0 = plain solves)", mode);
+  if (mode != FVS_UQ_LOCKSTEP && mode != FVS_UQ_STREAMS) {
+    set_error("fvs_uq_batch: mode %d is not available (0 lockstep batch, 1 independent solves)", mode);
     return FVS_ERR_ARG;
   }
   for (int64_t i = 0; i < n_samples; ++i) {
@@ -350,5 +351,6 @@ FVS_API fvs_status fvs_uq_batch(fvs_mesh mesh, const fvs_props* base, int64_t n_
       return FVS_ERR_ARG;
     }
   }
+  if (mode == FVS_UQ_LOCKSTEP) return batch_run(mesh, base, n_samples, inputs, dt, max_steps, qoi_out, steps_out);
   return uq_batch(mesh, base, n_samples, inputs, dt, max_steps, n_streams, qoi_out, steps_out);
 }

@@ -207,14 +207,19 @@ class Mesh:
             pass
 
 
-def uq_batch(mesh, props, inputs, dt, max_steps, n_streams=0):
-    """Plain batched UQ solves: inputs [S, 3] (T_melt, T_wall, C0) -> (qoi [S, 4], steps [S])."""
+UQ_LOCKSTEP, UQ_STREAMS = 0, 1
+
+
+def uq_batch(mesh, props, inputs, dt, max_steps, n_streams=0, mode=UQ_LOCKSTEP):
+    """Plain batched UQ solves: inputs [S, 3] (T_melt, T_wall, C0) -> (qoi [S, 4], steps [S]).
+    mode UQ_LOCKSTEP advances all samples together (one launch per phase);
+    UQ_STREAMS runs independent solves on n_streams CUDA streams."""
     inputs = np.ascontiguousarray(inputs, dtype=np.float64)
     n = len(inputs)
     qoi = np.empty((n, 4), dtype=np.float64)
     steps = np.empty(n, dtype=np.int64)
     pr = make_props(props)
-    check(fvs_uq_batch(mesh.h, C.byref(pr), n, _ptr(inputs), float(dt), int(max_steps), 0, int(n_streams),
+    check(fvs_uq_batch(mesh.h, C.byref(pr), n, _ptr(inputs), float(dt), int(max_steps), int(mode), int(n_streams),
                        _ptr(qoi), _ptr(steps)), "fvs_uq_batch")
     return qoi, steps
 

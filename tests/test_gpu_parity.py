@@ -202,29 +202,96 @@ def test_mixed_precision_matches_fp64(fvs):
         assert rel(runs[1][k], ref[k]) <= 1e-6, (k, rel(runs[1][k], ref[k]))
 
 
-def test_uq_batch_matches_oracle(fvs):
+def oracle_uq(m, props, inputs, dt, max_steps):
+    """Per-sample oracle runs to full solidification: (qoi means, steps)."""
+    out, nsteps = [], []
+    for Tm, Tw, C0 in inputs:
+        mat = dict(props["material"], T_liq=913.0 - 5.0 * (C0 - 4.0))
+        o = Oracle(m, cases.props(material=mat, walls=cases.all_walls(Tw), T_init=Tm, **TIGHT))
+        k = 0
+        while k < max_steps:
+            st = o.step(dt)
+            k += 1
+            if st["n_active"] == 0:
+                break
+        q = o.qoi()
+        done = np.isfinite(q["t_f"])
+        out.append([q[name][done].mean() for name in ("t_f", "cooling_rate", "sdas", "yield_strength")])
+        nsteps.append(k)
+    return np.array(out), np.array(nsteps)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_uq_batch_matches_oracle(fvs, mode):
     """fvs_uq_batch: each sample is a plain solve with its own melt and wall
     temperatures and liquidus; per-sample means of t_f, cooling rate, SDAS and
-    yield equal the oracle's runs of the same samples to full solidification."""
+    yield equal the oracle's runs of the same samples to full solidification.
+    Mode 0 advances the samples in lockstep (one launch per phase), mode 1
+    runs independent solves on streams."""
     m = box_mesh(8, 8, 2, (0.01, 0.01, 0.0025))
     inputs = np.array([[930.0, 700.0, 4.0], [955.0, 680.0, 3.2], [942.0, 735.0, 4.8]])
     props = cases.props(**TIGHT)
     M = fvs.Mesh(m)
-    qoi, steps = fvs.uq_batch(M, props, inputs, 2e-3, 400, n_streams=2)
-    for i, (Tm, Tw, C0) in enumerate(inputs):
-        mat = dict(props["material"], T_liq=913.0 - 5.0 * (C0 - 4.0))
-        o = Oracle(m, cases.props(material=mat, walls=cases.all_walls(Tw), T_init=Tm, **TIGHT))
-        k = 0
-        while k < 400:
-            st = o.step(2e-3)
-            k += 1
-            if st["n_active"] == 0:
-                break
-        assert steps[i] == k
-        q = o.qoi()
-        done = np.isfinite(q["t_f"])
-        ref = [q[name][done].mean() for name in ("t_f", "cooling_rate", "sdas", "yield_strength")]
-        np.testing.assert_allclose(qoi[i], ref, rtol=1e-8)
+    qoi, steps = fvs.uq_batch(M, props, inputs, 2e-3, 400, n_streams=2, mode=mode)
+    ref, ref_steps = oracle_uq(m, props, inputs, 2e-3, 400)
+    assert np.array_equal(steps, ref_steps)
+    np.testing.assert_allclose(qoi, ref, rtol=1e-8)
+
+
+def test_lockstep_batch_multilevel_matches_oracle(fvs):
+    """Lockstep batch on a mesh whose pressure hierarchy has several levels
+    (per-sample Galerkin values on the shared aggregation, per-sample
+    coarsest inverses) against the oracle, sample by sample, to full
+    solidification."""
+    m = box_mesh(16, 16, 4, (0.02, 0.02, 0.005))
+    inputs = np.array([[930.0, 700.0, 4.0], [948.0, 690.0, 3.4]])
+    props = cases.props(**TIGHT)
+    M = fvs.Mesh(m)
+    qoi, steps = fvs.uq_batch(M, props, inputs, 2e-3, 300, mode=0)
+    ref, ref_steps = oracle_uq(m, props, inputs, 2e-3, 300)
+    assert np.array_equal(steps, ref_steps)
+    np.testing.assert_allclose(qoi, ref, rtol=1e-8)
+
+
+def test_lockstep_batch_mixed_precision_matches_oracle(fvs):
+    """Lockstep batch with the FP32 V-cycle inside the FP64 Krylov method:
+    at the same (tight) outer tolerance the per-sample QoIs equal the
+    oracle's."""
+    m = box_mesh(16, 16, 4, (0.02, 0.02, 0.005))
+    inputs = np.array([[930.0, 700.0, 4.0], [948.0, 690.0, 3.4]])
+    props = cases.props(**dict(TIGHT, precision=1))
+    M = fvs.Mesh(m)
+    qoi, steps = fvs.uq_batch(M, props, inputs, 2e-3, 300, mode=0)
+    ref, ref_steps = oracle_uq(m, cases.props(**TIGHT), inputs, 2e-3, 300)
+    assert np.array_equal(steps, ref_steps)
+    np.testing.assert_allclose(qoi, ref, rtol=1e-8)
+
+
+def test_lockstep_batch_skewed_mesh_matches_oracle(fvs):
+    """Jittered (non-orthogonal) hexes: BiCGStab pressure solves, vertex
+    cross terms and smeared coefficients in the per-sample pressure rows.
+    Forty steps (the outer shell solidified) against the oracle."""
+    m = box_mesh(16, 16, 4, (0.02, 0.02, 0.005), jitter=0.15, jitter_seed=81, permute_seed=82)
+    inputs = np.array([[930.0, 700.0, 4.0], [948.0, 690.0, 3.4]])
+    props = cases.props(**TIGHT)
+    M = fvs.Mesh(m)
+    qoi, steps = fvs.uq_batch(M, props, inputs, 2e-3, 40, mode=0)
+    ref, ref_steps = oracle_uq(m, props, inputs, 2e-3, 40)
+    assert np.array_equal(steps, ref_steps) and (steps == 40).all()
+    np.testing.assert_allclose(qoi, ref, rtol=1e-8)
+
+
+def test_lockstep_batch_many_samples_matches_independent_solves(fvs):
+    """Forty samples (two tiles of 32, the second one partly padding):
+    lockstep and independent solves give the same QoIs and step counts."""
+    m = box_mesh(8, 8, 2, (0.01, 0.01, 0.0025))
+    inputs = cases.uq_inputs(40, seed=7)
+    props = cases.props(**TIGHT)
+    M = fvs.Mesh(m)
+    q0, s0 = fvs.uq_batch(M, props, inputs, 2e-3, 400, mode=0)
+    q1, s1 = fvs.uq_batch(M, props, inputs, 2e-3, 400, n_streams=4, mode=1)
+    assert np.array_equal(s0, s1)
+    np.testing.assert_allclose(q0, q1, rtol=1e-9)
 
 
 @pytest.mark.parametrize("precision", [0, 1])
