@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--uq-n", type=int, default=32, help="cells per axis of the UQ cavity")
     ap.add_argument("--uq-samples", type=int, default=32)
     ap.add_argument("--uq-streams", type=int, default=16)
+    ap.add_argument("--no-uq-streams", action="store_true", help="skip the independent-solves UQ baseline")
     ap.add_argument("--uq-dt", type=float, default=2e-3)
     return ap.parse_args()
 
@@ -301,9 +302,20 @@ def run_uq(fvs, args):
     props = bench_props("mixed")
     X = cases.uq_inputs(args.uq_samples, seed=2018)
     t0 = time.perf_counter()
-    Y, steps = fvs.uq_batch(M, props, X, args.uq_dt, 20000, n_streams=args.uq_streams)
+    Y, steps = fvs.uq_batch(M, props, X, args.uq_dt, 20000, mode=fvs.UQ_LOCKSTEP)
     sec = time.perf_counter() - t0
     plain = args.uq_samples / sec
+    # the same samples as independent solves (one solver per CUDA stream), FP64 V-cycle:
+    # the baseline the lockstep batch and its mixed precision are measured against
+    streams = None
+    if not args.no_uq_streams:
+        t0 = time.perf_counter()
+        Y1, steps1 = fvs.uq_batch(M, bench_props("fp64"), X, args.uq_dt, 20000, n_streams=args.uq_streams,
+                                  mode=fvs.UQ_STREAMS)
+        streams = dict(samples_per_s=round(args.uq_samples / (time.perf_counter() - t0), 3),
+                       streams=args.uq_streams, precision="fp64",
+                       max_rel_qoi_diff=float(np.nanmax(np.abs(Y1 - Y) / np.abs(Y1))),
+                       steps_equal=bool(np.array_equal(steps1, steps)))
     S = fvs.Surrogate(3, 128, 4, 4, seed=1)
     S.set_scaling(X.mean(0), X.std(0), Y.mean(0), Y.std(0))
     S.train(X, Y, 2000, 1e-3)
@@ -314,9 +326,10 @@ def run_uq(fvs, args):
     sur = len(Xmc) / (time.perf_counter() - t1)
     return dict(plain_samples_per_s=round(plain, 3), surrogate_samples_per_s=round(sur, 1), unit="samples/s",
                 samples=args.uq_samples, mesh=f"cavity {n}^3, all walls at the sampled temperature",
-                dt=args.uq_dt, mean_steps=float(np.mean(steps)), streams=args.uq_streams,
+                dt=args.uq_dt, mean_steps=float(np.mean(steps)), mode="lockstep (one launch per phase for all "
+                "samples), mixed precision", independent_solves=streams,
                 qoi_mean_plain=[float(v) for v in Y.mean(0)], qoi_mean_surrogate_1e6=[float(v) for v in Ymc.mean(0)],
-                note="plain: fvs_uq_batch to full solidification (mixed precision); surrogate: BF16 MLP "
+                note="plain: fvs_uq_batch to full solidification; surrogate: BF16 MLP "
                      "trained on those solves, inference on 1e6 inputs (host in/out)")
 
 

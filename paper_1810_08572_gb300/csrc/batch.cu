@@ -950,9 +950,102 @@ static fvs_status krylov_finish(Batch& B, const Op& op, const double* b, const d
   return FVS_OK;
 }
 
+// Device-driven loop: one graph launch runs iterations of body() under a
+// conditional while-node until no sample is active, a sample needs a
+// restart, or maxit is reached.  counts[3] returns the iterations done.
+__global__ void kb_ctl(cudaGraphConditionalHandle h, int* counts, int maxit) {
+  const int n = ++counts[3];
+  const bool go = n < maxit && counts[0] > 0 && counts[1] == 0;
+  cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+__global__ void kb_ctl_init(int* counts) { counts[3] = 0; }
+
+template <class Body>
+static fvs_status bloop(Batch& B, BatchGraph& g, uint64_t key, Body& body, int maxit, bool& used) {
+  used = false;
+  cudaStream_t s = B.stream;
+  if (g.disabled || !graphs_enabled() || maxit <= 0) return FVS_OK;
+  if (!g.exec || g.key != key) {
+    g.reset();
+    cudaGraph_t graph = nullptr;
+    cudaGraphConditionalHandle h;
+    bool ok = cudaGraphCreate(&graph, 0) == cudaSuccess;
+    ok = ok && cudaGraphConditionalHandleCreate(&h, graph, 1, cudaGraphCondAssignDefault) == cudaSuccess;
+    cudaGraphNodeParams p = {};
+    cudaGraphNode_t node;
+    if (ok) {
+      p.type = cudaGraphNodeTypeConditional;
+      p.conditional.handle = h;
+      p.conditional.type = cudaGraphCondTypeWhile;
+      p.conditional.size = 1;
+      ok = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &p) == cudaSuccess;
+    }
+    if (ok) {
+      ok = cudaStreamBeginCaptureToGraph(s, p.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+      if (ok) {
+        const unsigned long long before = __atomic_load_n(&g_launches, __ATOMIC_RELAXED);
+        const fvs_status r = body();
+        kb_ctl<<<1, 1, 0, s>>>(h, B.kcount, maxit);
+        g.kernels = __atomic_load_n(&g_launches, __ATOMIC_RELAXED) - before + 1;
+        __atomic_sub_fetch(&g_launches, g.kernels - 1, __ATOMIC_RELAXED);
+        cudaGraph_t out = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s, &out);
+        ok = r == FVS_OK && e == cudaSuccess;
+      }
+    }
+    if (ok) ok = cudaGraphInstantiate(&g.exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+      cudaGetLastError();
+      g.reset();
+      g.disabled = true;
+      return FVS_OK;
+    }
+    g.key = key;
+    g.maxit = maxit;
+  }
+  if (g.maxit != maxit) return FVS_OK;   // the iteration cap is part of the graph
+  kb_ctl_init<<<1, 1, 0, s>>>(B.kcount); FVS_COUNT_LAUNCH();
+  FVS_CUDA(cudaGraphLaunch(g.exec, s));
+  used = true;
+  return FVS_OK;
+}
+
+static uint64_t hkey(std::initializer_list<const void*> ptrs, uint64_t extra) {
+  uint64_t h = 0x84222325cbf29ce4ULL ^ extra;
+  for (const void* q : ptrs) h = (h ^ (uint64_t)(uintptr_t)q) * 0x100000001b3ULL;
+  return h;
+}
+
+// runs iterations until no sample is active (graph loop when available);
+// restart() handles samples whose recurrence broke down
+template <class Body, class Restart>
+static fvs_status bdrive(Batch& B, BatchGraph* g, uint64_t key, Body& body, Restart& restart, int maxit,
+                         int& active, int& it) {
+  it = 0;
+  while (active > 0 && it < maxit) {
+    bool used = false;
+    if (g) FVS_TRY(bloop(B, *g, key, body, maxit, used));
+    int h[4];
+    if (used) {
+      FVS_TRY(read_counts(B, h, 4));
+      __atomic_add_fetch(&g_launches, g->kernels * (unsigned long long)h[3], __ATOMIC_RELAXED);
+      it += h[3];
+    } else {
+      FVS_TRY(body());
+      FVS_TRY(read_counts(B, h, 2));
+      ++it;
+    }
+    active = h[0];
+    if (active > 0 && h[1] > 0) FVS_TRY(restart());
+  }
+  return FVS_OK;
+}
+
 template <class Op, class Prec, class Proj>
 static fvs_status bbicgstab(Batch& B, const Op& op, Prec& prec, Proj& proj, const double* b, double* x,
-                            const KrylovArgs& a, int& iters, int& failed) {
+                            const KrylovArgs& a, int& iters, int& failed, BatchGraph* graph = nullptr) {
   const int64_t n = op.n;
   const int Sp = B.Sp;
   const size_t len = (size_t)n * Sp;
@@ -972,8 +1065,8 @@ static fvs_status bbicgstab(Batch& B, const Op& op, Prec& prec, Proj& proj, cons
   FVS_TRY(krylov_start(B, op, b, x, a, proj.active(), active));
   FVS_TRY(bdot2(B, n, w.rh, w.r, nullptr, nullptr, B_RHO, -1));
   const dim3 g = bgrid(n, B.tiles);
-  int it = 0;
-  while (active > 0 && it < a.maxit) {
+  auto body = [&]() -> fvs_status {
+    FVS_CUDA(cudaMemsetAsync(B.kcount.p, 0, 3 * sizeof(int), st));
     kb_bicg_p<<<g, bblock(), 0, st>>>(n, Sp, B.sc, B.kact, w.r, w.v, w.p); FVS_COUNT_LAUNCH();
     FVS_TRY(prec(w.p, w.ph));
     FVS_TRY(bapply(B, op, w.ph, nullptr, w.v, 0));
@@ -984,30 +1077,31 @@ static fvs_status bbicgstab(Batch& B, const Op& op, Prec& prec, Proj& proj, cons
     FVS_TRY(bdot2(B, n, w.t, w.sv, w.t, w.t, B_TS, B_TT));
     kb_bicg_xr<<<g, bblock(), 0, st>>>(n, Sp, B.sc, B.kact, w.ph, w.sh, w.sv, w.t, x, w.r); FVS_COUNT_LAUNCH();
     FVS_TRY(bdot2(B, n, w.r, w.r, w.rh, w.r, B_RR, B_RZ));
-    FVS_CUDA(cudaMemsetAsync(B.kcount.p, 0, 4 * sizeof(int), st));
     kb_bicg_next<<<B.tiles, 32, 0, st>>>(Sp, B.sc, B.kact, B.krestart, B.kcount); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
-    int h[4];
-    FVS_TRY(read_counts(B, h, 2));
-    ++it;
-    active = h[0];
-    if (active > 0 && h[1] > 0) {
-      // restart the samples whose shadow residual broke down
-      FVS_TRY(bapply(B, op, x, b, w.t, 1));
-      FVS_TRY(proj(w.t));
-      kb_restart<<<g, bblock(), 0, st>>>(n, Sp, B.krestart, w.t, w.r, w.rh); FVS_COUNT_LAUNCH();
-      FVS_TRY(bdot2(B, n, w.rh, w.r, nullptr, nullptr, B_RZ, -1));
-      kb_restart_scalars<<<B.tiles, 32, 0, st>>>(Sp, B.sc, B.krestart); FVS_COUNT_LAUNCH();
-      FVS_LAUNCH_CHECK();
-    }
-  }
+    return FVS_OK;
+  };
+  // restart the samples whose shadow residual broke down
+  auto restart = [&]() -> fvs_status {
+    FVS_TRY(bapply(B, op, x, b, w.t, 1));
+    FVS_TRY(proj(w.t));
+    kb_restart<<<g, bblock(), 0, st>>>(n, Sp, B.krestart, w.t, w.r, w.rh); FVS_COUNT_LAUNCH();
+    FVS_TRY(bdot2(B, n, w.rh, w.r, nullptr, nullptr, B_RZ, -1));
+    kb_restart_scalars<<<B.tiles, 32, 0, st>>>(Sp, B.sc, B.krestart); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+    return FVS_OK;
+  };
+  const uint64_t key = hkey({b, x, w.r.p, w.rh.p, w.p.p, w.ph.p, w.v.p, w.sv.p, w.sh.p, w.t.p, B.sc.p, B.kact.p},
+                            B.batch_version * 0x9e3779b97f4a7c15ULL + 1);
+  int it = 0;
+  FVS_TRY(bdrive(B, graph, key, body, restart, a.maxit, active, it));
   iters = it;
   return krylov_finish(B, op, b, x, proj, a, failed);
 }
 
 template <class Op, class Prec, class Proj>
 static fvs_status bpcg(Batch& B, const Op& op, Prec& prec, Proj& proj, const double* b, double* x,
-                       const KrylovArgs& a, int& iters, int& failed) {
+                       const KrylovArgs& a, int& iters, int& failed, BatchGraph* graph = nullptr) {
   const int64_t n = op.n;
   const int Sp = B.Sp;
   const size_t len = (size_t)n * Sp;
@@ -1025,8 +1119,8 @@ static fvs_status bpcg(Batch& B, const Op& op, Prec& prec, Proj& proj, const dou
   int active = 0;
   FVS_TRY(krylov_start(B, op, b, x, a, proj.active(), active));
   const dim3 g = bgrid(n, B.tiles);
-  int it = 0;
-  while (active > 0 && it < a.maxit) {
+  auto body = [&]() -> fvs_status {
+    FVS_CUDA(cudaMemsetAsync(B.kcount.p, 0, 3 * sizeof(int), st));
     FVS_TRY(prec(w.r, w.z));
     FVS_TRY(proj(w.z));
     FVS_TRY(bdot2(B, n, w.r, w.z, nullptr, nullptr, B_RZ, -1));
@@ -1035,14 +1129,15 @@ static fvs_status bpcg(Batch& B, const Op& op, Prec& prec, Proj& proj, const dou
     FVS_TRY(bdot2(B, n, w.p, w.q, nullptr, nullptr, B_PQ, -1));
     kb_cg_xr<<<g, bblock(), 0, st>>>(n, Sp, B.sc, B.kact, w.p, w.q, x, w.r); FVS_COUNT_LAUNCH();
     FVS_TRY(bdot2(B, n, w.r, w.r, nullptr, nullptr, B_RR, -1));
-    FVS_CUDA(cudaMemsetAsync(B.kcount.p, 0, 4 * sizeof(int), st));
     kb_cg_next<<<B.tiles, 32, 0, st>>>(Sp, B.sc, B.kact, B.kcount); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
-    int h[4];
-    FVS_TRY(read_counts(B, h, 1));
-    ++it;
-    active = h[0];
-  }
+    return FVS_OK;
+  };
+  auto restart = [&]() -> fvs_status { return FVS_OK; };
+  const uint64_t key = hkey({b, x, w.r.p, w.z.p, w.p.p, w.q.p, B.sc.p, B.kact.p},
+                            B.batch_version * 0x9e3779b97f4a7c15ULL + 2);
+  int it = 0;
+  FVS_TRY(bdrive(B, graph, key, body, restart, a.maxit, active, it));
   iters = it;
   return krylov_finish(B, op, b, x, proj, a, failed);
 }
@@ -1680,7 +1775,7 @@ static fvs_status batch_step(Batch& B, double dt, int& failures, int (&its)[4]) 
     a.maxit = B.props.max_krylov_iters;
     for (int d = 0; d < 3; ++d) {
       int it = 0, fail = 0;
-      FVS_TRY(bbicgstab(B, op, J, np, B.mrhs.p + d * cs, B.mx.p + d * cs, a, it, fail));
+      FVS_TRY(bbicgstab(B, op, J, np, B.mrhs.p + d * cs, B.mx.p + d * cs, a, it, fail, &B.gmom[d]));
       failures += fail;
       its[0] += it;
     }
@@ -1704,6 +1799,7 @@ static fvs_status batch_step(Batch& B, double dt, int& failures, int (&its)[4]) 
     B.ocap = std::max<int64_t>(nmod, 2 * B.ocap);
     FVS_TRY(B.mval.alloc((size_t)B.ocap * m->W + 1));
     if (B.fp32) FVS_TRY(B.mvalf.alloc((size_t)B.ocap * m->W + 1));
+    ++B.batch_version;   // captured solve loops hold the old row buffers
   }
   FVS_TRY(B.ocount.zero(st));
   FVS_TRY(B.err.zero(st));
@@ -1739,8 +1835,8 @@ static fvs_status batch_step(Batch& B, double dt, int& failures, int (&its)[4]) 
     a.take = B.run;
     a.maxit = B.props.max_krylov_iters;
     int it = 0, fail = 0;
-    if (m->orthogonal) FVS_TRY(bpcg(B, op, M, P, B.prhs, B.px, a, it, fail));
-    else FVS_TRY(bbicgstab(B, op, M, P, B.prhs, B.px, a, it, fail));
+    if (m->orthogonal) FVS_TRY(bpcg(B, op, M, P, B.prhs, B.px, a, it, fail, &B.gp));
+    else FVS_TRY(bbicgstab(B, op, M, P, B.prhs, B.px, a, it, fail, &B.gp));
     failures += fail;
     its[1] = it;
     FVS_TRY(bproject(B, B.px));
@@ -1778,7 +1874,7 @@ static fvs_status batch_step(Batch& B, double dt, int& failures, int (&its)[4]) 
       kb_energy_lin<<<gc, blk, 0, st>>>(Nc, Sp, m->V, mt, B.Tliq, dt, B.Tnew, B.fsnew, B.fs, B.ebase, B.kevd, B.edx,
                                         B.erhs, B.Tlin, B.jd); FVS_COUNT_LAUNCH();
       int it2 = 0, fail = 0;
-      FVS_TRY(bbicgstab(B, op, J, np, B.erhs, B.Tlin, a, it2, fail));
+      FVS_TRY(bbicgstab(B, op, J, np, B.erhs, B.Tlin, a, it2, fail, &B.ge));
       failures += fail;
       its[3] += it2;
       its[2] = it;

@@ -46,6 +46,21 @@ struct BLevel {
   DBuf<int32_t> lab;              // null-space labels [i*Sp + s] (levels used for label pull-down)
 };
 
+// a device-driven Krylov loop captured as a graph (conditional while-node)
+struct BatchGraph {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t key = 0;
+  int maxit = 0;
+  unsigned long long kernels = 0;   // launches per iteration (launch counter)
+  bool disabled = false;
+  ~BatchGraph() { reset(); }
+  void reset() {
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    key = 0;
+  }
+};
+
 struct BatchWork {               // Krylov work vectors [n*Sp]
   DBuf<double> r, rh, p, ph, v, sv, sh, t, z, q;
   fvs_status ensure(size_t len);
@@ -123,6 +138,8 @@ struct Batch {
   DBuf<int> err;
   double* host = nullptr;         // pinned [B_NSLOT * Sp + 64]
   double* phase_ms = nullptr;     // phase times (debug)
+  uint64_t batch_version = 0;     // bumped when operator or hierarchy buffers move
+  BatchGraph gmom[3], gp, ge;     // captured solve loops
   BatchWork kw;
 
   ~Batch();
