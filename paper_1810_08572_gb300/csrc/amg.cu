@@ -227,9 +227,8 @@ __device__ __forceinline__ void gal_emit(int lane, const int32_t* key, const dou
     }
     base += __popc(bal);
   }
-  if (!FILL) {
-    if (lane == 0) rowlen[I] = base;
-  } else {
+  if (lane == 0 && rowlen) rowlen[I] = FILL ? min(base, wc) : base;
+  if (FILL) {
     for (int r = base + lane; r < wc; r += 32) {
       ccol[(int64_t)r * nc + I] = (int32_t)I;
       cval[(int64_t)r * nc + I] = 0.0;
@@ -654,10 +653,11 @@ __global__ void k_jac0(int64_t n, T omega, const T* dinv, const T* b, T* x) {
 template <typename T>
 __global__ void k_jac(int64_t n, int w, const int32_t* __restrict__ col, const T* __restrict__ val, T omega,
                       const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
-                      T* __restrict__ y) {
+                      T* __restrict__ y, const int32_t* __restrict__ rlen) {
   GS(i, n) {
     T acc = 0;
-    for (int k = 0; k < w; ++k) {
+    const int len = rlen ? rlen[i] : w;   // stored entries first, padding after
+    for (int k = 0; k < len; ++k) {
       const int64_t e = (int64_t)k * n + i;
       acc = fma(val[e], x[col[e]], acc);
     }
@@ -666,10 +666,12 @@ __global__ void k_jac(int64_t n, int w, const int32_t* __restrict__ col, const T
 }
 template <typename T>
 __global__ void k_resid(int64_t n, int w, const int32_t* __restrict__ col, const T* __restrict__ val,
-                        const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r) {
+                        const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r,
+                        const int32_t* __restrict__ rlen) {
   GS(i, n) {
     T acc = 0;
-    for (int k = 0; k < w; ++k) {
+    const int len = rlen ? rlen[i] : w;
+    for (int k = 0; k < len; ++k) {
       const int64_t e = (int64_t)k * n + i;
       acc = fma(val[e], x[col[e]], acc);
     }
@@ -823,6 +825,7 @@ static double env_num(const char* name, double dflt) {
 fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
   ready = false;
   masked = false;
+  refreshes = 0;
   ++version;
   lv.clear();
   opt.theta = env_num("FVS_AMG_THETA", opt.theta);
@@ -952,8 +955,9 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
     k_fill_members<<<stride_grid(n, 256), 256, 0, s>>>(n, L->agg, L->mptr, mc, L->midx); FVS_COUNT_LAUNCH();
     k_sort_members<<<stride_grid(nc, 256), 256, 0, s>>>(nc, L->mptr, L->midx); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
-    DBuf<int32_t> rowlen;
-    FVS_TRY(rowlen.alloc(nc));
+    std::unique_ptr<AmgLevel> C(new AmgLevel());
+    DBuf<int32_t>& rowlen = C->rlen;   // kept: the V-cycle walks only the stored entries of each row
+    FVS_TRY(rowlen.alloc(nc + 1));
     galerkin_pass(s, false, nc, *cur, L->agg, L->mptr, L->midx, rowlen, 0, nullptr, nullptr, nullptr, err);
     FVS_TRY(cnt.zero(s));
     k_max_int<<<stride_grid(nc, 256), 256, 0, s>>>(nc, rowlen, cnt); FVS_COUNT_LAUNCH();
@@ -966,7 +970,6 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
       return FVS_ERR_NOT_CONVERGED;
     }
     tick(3);
-    std::unique_ptr<AmgLevel> C(new AmgLevel());
     FVS_TRY(C->own.alloc(nc, wc));
     FVS_TRY(C->own.diag.zero(s));
     galerkin_pass(s, true, nc, *cur, L->agg, L->mptr, L->midx, rowlen, wc, C->own.col, C->own.val, C->own.diag,
@@ -1166,7 +1169,7 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
     if (l > 0 && n > 0) {
       k_dirty_up<<<stride_grid(n, 256), 256, 0, s>>>(n, L->agg, L->dirty, C->dirty); FVS_COUNT_LAUNCH();
     }
-    galerkin_pass(s, true, C->n, *cur, L->agg, L->mptr, L->midx, nullptr, C->own.w, C->own.col, C->own.val,
+    galerkin_pass(s, true, C->n, *cur, L->agg, L->mptr, L->midx, C->rlen, C->own.w, C->own.col, C->own.val,
                   C->own.diag, err, C->dirty);
     FVS_LAUNCH_CHECK();
   }
@@ -1178,7 +1181,11 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
       return FVS_ERR_NOT_CONVERGED;
     }
   }
-  FVS_TRY(coarsest_setup(s));
+  // the coarsest inverse (a dense O(n^3) factorisation) is redone on every
+  // few refreshes only; in between the V-cycle's coarsest solve uses the
+  // previous one (the coarse rows above it are exact Galerkin products)
+  const int every = std::max(1, (int)env_num("FVS_AMG_COARSEST_EVERY", 4));
+  if (++refreshes % every == 0) FVS_TRY(coarsest_setup(s));
   if (n0 > 0) {
     k_mask_labels<<<stride_grid(n0, 256), 256, 0, s>>>(n0, act, ppe, fine_lab); FVS_COUNT_LAUNCH();
     FVS_TRY(ccnt.zero(s));
@@ -1233,6 +1240,7 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
   T* cy = f32 ? (T*)C->yf.p : (T*)C->y.p;
   const double vb = (double)sizeof(T);
   const double jac_bytes = (double)n * ((4.0 + vb) * A.w + 4.0 * vb);
+  const int32_t* rl = L->rlen.n ? L->rlen.p : nullptr;   // coarse levels: stored row lengths
   const int g = stride_grid(n, 256);
   {
     ProfScope ps(L->A, f32 ? "jacobi0_f32" : "jacobi0", 3.0 * vb * (double)n, s);
@@ -1240,12 +1248,12 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
   }
   for (int k = 1; k < opt.npre; ++k) {
     ProfScope ps(L->A, f32 ? "jacobi_f32" : "jacobi", jac_bytes, s);
-    k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xa, xb); FVS_COUNT_LAUNCH();
+    k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xa, xb, rl); FVS_COUNT_LAUNCH();
     T* t = xa; xa = xb; xb = t;
   }
   {
     ProfScope ps(L->A, f32 ? "residual_f32" : "residual_vc", (double)n * ((4.0 + vb) * A.w + 3.0 * vb), s);
-    k_resid<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, xa, b, r); FVS_COUNT_LAUNCH();
+    k_resid<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, xa, b, r, rl); FVS_COUNT_LAUNCH();
   }
   k_restrict<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cb); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
@@ -1254,7 +1262,7 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
   for (int k = 0; k < opt.npost; ++k) {
     T* out = (k == opt.npost - 1) ? y : xb;
     ProfScope ps(L->A, f32 ? "jacobi_f32" : "jacobi", jac_bytes, s);
-    k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xa, out); FVS_COUNT_LAUNCH();
+    k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xa, out, rl); FVS_COUNT_LAUNCH();
     xb = xa;
     xa = out;
   }

@@ -20,6 +20,7 @@ struct AmgLevel {
   DBuf<double> dinv;    // 1 / diagonal
   DBuf<float> dinvf;
   DBuf<float> valf;     // FP32 copy of the operator values (mixed precision)
+  DBuf<int32_t> rlen;   // coarse levels: stored entries per row (the rest of the row is padding)
   DBuf<int32_t> agg;    // row -> aggregate (row of the next level)
   DBuf<int32_t> mptr, midx;   // members of each aggregate of the next level (CSR)
   DBuf<double> b, x, y, r, t;    // V-cycle work
@@ -55,6 +56,7 @@ struct Amg : Precond {
   bool ready = false;
 
   bool masked = false;            // some fine rows carry label -1 (refreshed)
+  int refreshes = 0;              // refreshes since the setup
 
   fvs_status setup(cudaStream_t s, const Ell& A);
   // The operator's values changed on the same rows (cells frozen since the

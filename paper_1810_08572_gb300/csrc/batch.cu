@@ -167,9 +167,11 @@ struct OpCoarseT {
   int w;
   const int32_t* col;
   const V* val;
+  const int32_t* rlen;   // stored entries per row (padding after), shared by all samples
   __device__ __forceinline__ V row(int64_t i, int s, int Sp, const V* x) const {
     V acc = 0;
-    for (int k = 0; k < w; ++k) {
+    const int len = rlen ? rlen[i] : w;
+    for (int k = 0; k < len; ++k) {
       const int64_t q = (int64_t)k * n + i;
       acc = fma(val[q * Sp + s], x[(int64_t)col[q] * Sp + s], acc);
     }
@@ -666,6 +668,7 @@ fvs_status batch_amg_setup(Batch& B) {
     BL.n = A->n;
     BL.w = A->A->w;
     BL.col = A->A->col.p;
+    BL.rlen = A->rlen.n ? A->rlen.p : nullptr;
     if (l + 1 < L) {
       BL.agg = A->agg.p;
       BL.mptr = A->mptr.p;
@@ -831,7 +834,7 @@ static fvs_status level_apply(Batch& B, int l, const double* x, const double* b,
                               const double* dinv, double omega) {
   if (l == 0) return bapply(B, ppe_op(B), x, b, y, mode, dinv, omega);
   BLevel& L = *B.lv[l];
-  return bapply(B, OpCoarse{L.n, L.w, L.col, L.val.p}, x, b, y, mode, dinv, omega);
+  return bapply(B, OpCoarse{L.n, L.w, L.col, L.val.p, L.rlen}, x, b, y, mode, dinv, omega);
 }
 static fvs_status level_applyf(Batch& B, int l, const float* x, const float* b, float* y, int mode,
                                const float* dinv, float omega) {
@@ -841,7 +844,7 @@ static fvs_status level_applyf(Batch& B, int l, const float* x, const float* b, 
                    omega);
   }
   BLevel& L = *B.lv[l];
-  return bapplyf(B, OpCoarseT<float>{L.n, L.w, L.col, L.valf.p}, x, b, y, mode, dinv, omega);
+  return bapplyf(B, OpCoarseT<float>{L.n, L.w, L.col, L.valf.p, L.rlen}, x, b, y, mode, dinv, omega);
 }
 
 // one V-cycle on level l: y = M^-1 b (damped Jacobi, piecewise-constant

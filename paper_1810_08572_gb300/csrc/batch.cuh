@@ -33,6 +33,7 @@ struct BLevel {
   int64_t n = 0;
   int w = 0;
   const int32_t* col = nullptr;   // shared pattern [k*n + i] (level 0: the pressure base operator's)
+  const int32_t* rlen = nullptr;  // levels >= 1: stored entries per row
   DBuf<double> val;               // levels >= 1: per-sample values [(k*n + i)*Sp + s]
   DBuf<int32_t> dslot;            // levels >= 1: slot of the diagonal in each row (-1 none)
   DBuf<double> dinv;              // [i*Sp + s]
