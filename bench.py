@@ -366,7 +366,8 @@ def run_reference(args):
         return
     cpu = cpu_oracle(args.cpu_n, max(1, args.steps // 10 or 1) if args.steps > 0 else 1)
     line = dict(impl="reference", metric=METRIC, value=round(cpu["value"], 2), unit="active cell-steps/s",
-                n_gpus=args.gpus, steps=args.steps, warmup=args.warmup, higher_is_better=True,
+                n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=round(1e3 * args.cpu_n ** 3 / cpu["value"], 3), higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload=f"cavity {args.n}^3 jittered+permuted, dt 1e-3 s, p_rtol 1e-8, "
                                      f"{args.precision}", cpu_sample_cells=args.cpu_n ** 3),
