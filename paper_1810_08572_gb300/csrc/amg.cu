@@ -1118,6 +1118,16 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
   }
   ready = false;
   ++version;
+  const bool dbg = getenv("FVS_DEBUG") != nullptr;
+  double tph[4] = {0, 0, 0, 0};
+  auto t_last = std::chrono::steady_clock::now();
+  auto tick = [&](int k) {
+    if (!dbg) return;
+    cudaStreamSynchronize(s);
+    const auto now = std::chrono::steady_clock::now();
+    tph[k] += std::chrono::duration<double, std::milli>(now - t_last).count();
+    t_last = now;
+  };
   DBuf<int> err;
   DBuf<double> mo;
   FVS_TRY(err.alloc(1));
@@ -1150,6 +1160,7 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
     k_sort_members<<<stride_grid(nc, 256), 256, 0, s>>>(nc, L->mptr, L->midx); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
   }
+  tick(0);
   // Galerkin rows of the dirty aggregates, level by level on the kept
   // aggregation; rows can only lose entries, so the widths still hold (checked)
   for (size_t l = 0; l < lv.size(); ++l) {
@@ -1184,14 +1195,20 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
   // the coarsest inverse (a dense O(n^3) factorisation) is redone on every
   // few refreshes only; in between the V-cycle's coarsest solve uses the
   // previous one (the coarse rows above it are exact Galerkin products)
+  tick(1);
   const int every = std::max(1, (int)env_num("FVS_AMG_COARSEST_EVERY", 4));
   if (++refreshes % every == 0) FVS_TRY(coarsest_setup(s));
+  tick(2);
   if (n0 > 0) {
     k_mask_labels<<<stride_grid(n0, 256), 256, 0, s>>>(n0, act, ppe, fine_lab); FVS_COUNT_LAUNCH();
     FVS_TRY(ccnt.zero(s));
     k_comp_count<<<stride_grid(n0, 256), 256, 0, s>>>(n0, fine_lab, ccnt); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
   }
+  tick(3);
+  if (dbg)
+    fprintf(stderr, "[fvs amg] refresh ms: fingerprints+members %.2f galerkin %.2f coarsest %.2f labels+fp32 %.2f\n",
+            tph[0], tph[1], tph[2], tph[3]);
   masked = true;
   ready = true;
   return FVS_OK;

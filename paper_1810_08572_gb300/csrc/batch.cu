@@ -14,10 +14,18 @@ namespace fvs {
 
 // rows of this thread (blockDim = (32, 8)); the sample is blockIdx.y*32 + threadIdx.x
 #define BROW(i, n) \
-  for (int64_t i = (int64_t)blockIdx.x * 8 + threadIdx.y; i < (n); i += (int64_t)gridDim.x * 8)
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.y + threadIdx.y; i < (n); i += (int64_t)gridDim.x * blockDim.y)
 #define BSAMPLE const int s = blockIdx.y * 32 + threadIdx.x
 
 static inline dim3 bblock() { return dim3(32, 8, 1); }
+// launch shape of the operator kernels (chosen by the tuner at set-up)
+static inline dim3 sblock(const BShape* sh) { return dim3(32, sh ? sh->rows : 8, 1); }
+static inline dim3 sgrid(int64_t n, int tiles, const BShape* sh) {
+  const int rows = sh ? sh->rows : 8, per_sm = sh ? sh->per_sm : 16;
+  const int64_t rb = (n + rows - 1) / rows;
+  const int64_t cap = std::max<int64_t>(1, (int64_t)sm_count() * per_sm / tiles);
+  return dim3((unsigned)std::max<int64_t>(1, std::min(rb, cap)), (unsigned)tiles, 1);
+}
 // elementwise grids: about 16 blocks per SM in total
 static inline dim3 bgrid(int64_t n, int tiles) {
   int64_t rb = (n + 7) / 8;
@@ -565,17 +573,54 @@ static fvs_status read_counts(Batch& B, int* h, int n) {
 }
 template <class Op>
 static fvs_status bapply(Batch& B, const Op& op, const double* x, const double* b, double* y, int mode,
-                         const double* dinv = nullptr, double omega = 0.0) {
-  kb_apply<Op, double><<<bgrid(op.n, B.tiles), bblock(), 0, B.stream>>>(op, B.Sp, x, b, y, mode, dinv, omega);
+                         const double* dinv = nullptr, double omega = 0.0, const BShape* sh = nullptr) {
+  kb_apply<Op, double><<<sgrid(op.n, B.tiles, sh), sblock(sh), 0, B.stream>>>(op, B.Sp, x, b, y, mode, dinv, omega);
   FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   return FVS_OK;
 }
 template <class Op>
 static fvs_status bapplyf(Batch& B, const Op& op, const float* x, const float* b, float* y, int mode,
-                          const float* dinv = nullptr, float omega = 0.0f) {
-  kb_apply<Op, float><<<bgrid(op.n, B.tiles), bblock(), 0, B.stream>>>(op, B.Sp, x, b, y, mode, dinv, omega);
+                          const float* dinv = nullptr, float omega = 0.0f, const BShape* sh = nullptr) {
+  kb_apply<Op, float><<<sgrid(op.n, B.tiles, sh), sblock(sh), 0, B.stream>>>(op, B.Sp, x, b, y, mode, dinv, omega);
   FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch-shape autotuner: rows per block (the block is 32 samples x rows) and
+// blocks per SM, timed with CUDA events on the live operator and buffers
+// (the operator kernels only write their output, so repeated launches are
+// harmless); the fastest shape is kept for that operator
+// ---------------------------------------------------------------------------
+template <class Op, typename V>
+static fvs_status tune_apply(Batch& B, const Op& op, const V* x, const V* b, V* y, const V* dinv, BShape& out) {
+  out = BShape();
+  if (getenv("FVS_NO_TUNE") || op.n <= 0) return FVS_OK;
+  cudaEvent_t e0, e1;
+  FVS_CUDA(cudaEventCreate(&e0));
+  FVS_CUDA(cudaEventCreate(&e1));
+  float best = 1e30f;
+  for (int rows : {4, 8, 16, 32}) {
+    for (int per_sm : {8, 16, 32}) {
+      if (32 * rows * per_sm > 2048 * 4) continue;   // well past full occupancy
+      BShape sh{rows, per_sm};
+      kb_apply<Op, V><<<sgrid(op.n, B.tiles, &sh), sblock(&sh), 0, B.stream>>>(op, B.Sp, x, b, y, 2, dinv, (V)0.5);
+      if (cudaGetLastError() != cudaSuccess) continue;   // shape not launchable (registers): skip it
+      cudaEventRecord(e0, B.stream);
+      for (int r = 0; r < 3; ++r)
+        kb_apply<Op, V><<<sgrid(op.n, B.tiles, &sh), sblock(&sh), 0, B.stream>>>(op, B.Sp, x, b, y, 2, dinv,
+                                                                                 (V)0.5);
+      cudaEventRecord(e1, B.stream);
+      const cudaError_t e = cudaEventSynchronize(e1);
+      float ms = 0.0f;
+      if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+      if (e == cudaSuccess && ms < best) { best = ms; out = sh; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   FVS_LAUNCH_CHECK();
   return FVS_OK;
 }
@@ -749,6 +794,34 @@ fvs_status batch_amg_setup(Batch& B) {
   FVS_TRY(B.ccount.alloc((size_t)nc * Sp + 1));
   FVS_TRY(B.ccnt.alloc((size_t)BATCH_NCM * Sp + 1));
   FVS_TRY(B.csum.alloc((size_t)BATCH_NCM * Sp + 1));
+  // launch shapes of every level's operator, on the buffers of that level
+  // (the fine rows all read their shared base row for the timing)
+  FVS_CUDA(cudaMemsetAsync(B.ovr.p, 0xFF, (size_t)Nc * Sp * sizeof(int32_t), st));
+  for (int l = 0; l + 1 < L || (L == 1 && l == 0); ++l) {
+    BLevel& F = *B.lv[l];
+    const size_t nS = (size_t)F.n * Sp;
+    if (l >= 1) FVS_CUDA(cudaMemsetAsync(F.val.p, 0, (size_t)F.n * F.w * Sp * sizeof(double), st));
+    if (B.fp32) {
+      if (l >= 1) FVS_CUDA(cudaMemsetAsync(F.valf.p, 0, (size_t)F.n * F.w * Sp * sizeof(float), st));
+      for (DBuf<float>* b : {&F.bf, &F.xf, &F.yf, &F.dinvf}) FVS_CUDA(cudaMemsetAsync(b->p, 0, nS * sizeof(float), st));
+      if (l == 0)
+        FVS_TRY(tune_apply(B, OpPpe0T<float>{Nc, W, B.K0.col.p, B.K0f.p, B.ovr.p, B.mvalf.p}, F.xf.p, F.bf.p, F.yf.p,
+                           F.dinvf.p, F.shape));
+      else
+        FVS_TRY(tune_apply(B, OpCoarseT<float>{F.n, F.w, F.col, F.valf.p, F.rlen}, F.xf.p, F.bf.p, F.yf.p, F.dinvf.p,
+                           F.shape));
+    } else {
+      for (DBuf<double>* b : {&F.b, &F.x, &F.y, &F.dinv}) FVS_CUDA(cudaMemsetAsync(b->p, 0, nS * sizeof(double), st));
+      if (l == 0)
+        FVS_TRY(tune_apply(B, OpPpe0{Nc, W, B.K0.col.p, B.K0.val.p, B.ovr.p, B.mval.p}, F.x.p, F.b.p, F.y.p, F.dinv.p,
+                           F.shape));
+      else
+        FVS_TRY(tune_apply(B, OpCoarse{F.n, F.w, F.col, F.val.p, F.rlen}, F.x.p, F.b.p, F.y.p, F.dinv.p, F.shape));
+    }
+    if (getenv("FVS_DEBUG"))
+      fprintf(stderr, "[fvs batch] level %d (%lld rows): operator shape %d rows x %d per SM\n", l, (long long)F.n,
+              F.shape.rows, F.shape.per_sm);
+  }
   FVS_CUDA(cudaStreamSynchronize(st));
   B.amg_ok = true;
   return FVS_OK;
@@ -832,19 +905,19 @@ static OpPpe0 ppe_op(Batch& B) {
 
 static fvs_status level_apply(Batch& B, int l, const double* x, const double* b, double* y, int mode,
                               const double* dinv, double omega) {
-  if (l == 0) return bapply(B, ppe_op(B), x, b, y, mode, dinv, omega);
   BLevel& L = *B.lv[l];
-  return bapply(B, OpCoarse{L.n, L.w, L.col, L.val.p, L.rlen}, x, b, y, mode, dinv, omega);
+  if (l == 0) return bapply(B, ppe_op(B), x, b, y, mode, dinv, omega, &L.shape);
+  return bapply(B, OpCoarse{L.n, L.w, L.col, L.val.p, L.rlen}, x, b, y, mode, dinv, omega, &L.shape);
 }
 static fvs_status level_applyf(Batch& B, int l, const float* x, const float* b, float* y, int mode,
                                const float* dinv, float omega) {
+  BLevel& L = *B.lv[l];
   if (l == 0) {
     fvs_mesh m = B.mesh;
     return bapplyf(B, OpPpe0T<float>{m->Nc, m->W, B.K0.col.p, B.K0f.p, B.ovr.p, B.mvalf.p}, x, b, y, mode, dinv,
-                   omega);
+                   omega, &L.shape);
   }
-  BLevel& L = *B.lv[l];
-  return bapplyf(B, OpCoarseT<float>{L.n, L.w, L.col, L.valf.p, L.rlen}, x, b, y, mode, dinv, omega);
+  return bapplyf(B, OpCoarseT<float>{L.n, L.w, L.col, L.valf.p, L.rlen}, x, b, y, mode, dinv, omega, &L.shape);
 }
 
 // one V-cycle on level l: y = M^-1 b (damped Jacobi, piecewise-constant
@@ -918,6 +991,7 @@ struct KrylovArgs {
   const double* floor = nullptr;    // per-sample floor of the right-side norm
   const uint8_t* take = nullptr;    // samples taking part (null: all)
   int maxit = 1000;
+  const BShape* shape = nullptr;    // tuned launch shape of the operator
 };
 
 template <class Op>
@@ -941,7 +1015,7 @@ template <class Op, class Proj>
 static fvs_status krylov_finish(Batch& B, const Op& op, const double* b, const double* x, Proj& proj,
                                 const KrylovArgs& a, int& failed) {
   BatchWork& w = B.kw;
-  FVS_TRY(bapply(B, op, x, b, w.t, 1));
+  FVS_TRY(bapply(B, op, x, b, w.t, 1, nullptr, 0.0, a.shape));
   FVS_TRY(proj(w.t));
   FVS_TRY(bdot2(B, op.n, w.t, w.t, nullptr, nullptr, B_RR, -1));
   FVS_CUDA(cudaMemsetAsync(B.kcount.p, 0, 4 * sizeof(int), B.stream));
@@ -1057,7 +1131,7 @@ static fvs_status bbicgstab(Batch& B, const Op& op, Prec& prec, Proj& proj, cons
   cudaStream_t st = B.stream;
   iters = 0;
   failed = 0;
-  FVS_TRY(bapply(B, op, x, b, w.r, 1));
+  FVS_TRY(bapply(B, op, x, b, w.r, 1, nullptr, 0.0, a.shape));
   FVS_TRY(proj(w.r));
   FVS_TRY(bcopy(B, len, w.r, w.rh));
   if (proj.active()) {
@@ -1072,11 +1146,11 @@ static fvs_status bbicgstab(Batch& B, const Op& op, Prec& prec, Proj& proj, cons
     FVS_CUDA(cudaMemsetAsync(B.kcount.p, 0, 3 * sizeof(int), st));
     kb_bicg_p<<<g, bblock(), 0, st>>>(n, Sp, B.sc, B.kact, w.r, w.v, w.p); FVS_COUNT_LAUNCH();
     FVS_TRY(prec(w.p, w.ph));
-    FVS_TRY(bapply(B, op, w.ph, nullptr, w.v, 0));
+    FVS_TRY(bapply(B, op, w.ph, nullptr, w.v, 0, nullptr, 0.0, a.shape));
     FVS_TRY(bdot2(B, n, w.rh, w.v, nullptr, nullptr, B_RV, -1));
     kb_bicg_s<<<g, bblock(), 0, st>>>(n, Sp, B.sc, B.kact, w.r, w.v, w.sv); FVS_COUNT_LAUNCH();
     FVS_TRY(prec(w.sv, w.sh));
-    FVS_TRY(bapply(B, op, w.sh, nullptr, w.t, 0));
+    FVS_TRY(bapply(B, op, w.sh, nullptr, w.t, 0, nullptr, 0.0, a.shape));
     FVS_TRY(bdot2(B, n, w.t, w.sv, w.t, w.t, B_TS, B_TT));
     kb_bicg_xr<<<g, bblock(), 0, st>>>(n, Sp, B.sc, B.kact, w.ph, w.sh, w.sv, w.t, x, w.r); FVS_COUNT_LAUNCH();
     FVS_TRY(bdot2(B, n, w.r, w.r, w.rh, w.r, B_RR, B_RZ));
@@ -1086,7 +1160,7 @@ static fvs_status bbicgstab(Batch& B, const Op& op, Prec& prec, Proj& proj, cons
   };
   // restart the samples whose shadow residual broke down
   auto restart = [&]() -> fvs_status {
-    FVS_TRY(bapply(B, op, x, b, w.t, 1));
+    FVS_TRY(bapply(B, op, x, b, w.t, 1, nullptr, 0.0, a.shape));
     FVS_TRY(proj(w.t));
     kb_restart<<<g, bblock(), 0, st>>>(n, Sp, B.krestart, w.t, w.r, w.rh); FVS_COUNT_LAUNCH();
     FVS_TRY(bdot2(B, n, w.rh, w.r, nullptr, nullptr, B_RZ, -1));
@@ -1113,7 +1187,7 @@ static fvs_status bpcg(Batch& B, const Op& op, Prec& prec, Proj& proj, const dou
   cudaStream_t st = B.stream;
   iters = 0;
   failed = 0;
-  FVS_TRY(bapply(B, op, x, b, w.r, 1));
+  FVS_TRY(bapply(B, op, x, b, w.r, 1, nullptr, 0.0, a.shape));
   FVS_TRY(proj(w.r));
   if (proj.active()) {
     FVS_TRY(bcopy(B, len, b, w.q));
@@ -1128,7 +1202,7 @@ static fvs_status bpcg(Batch& B, const Op& op, Prec& prec, Proj& proj, const dou
     FVS_TRY(proj(w.z));
     FVS_TRY(bdot2(B, n, w.r, w.z, nullptr, nullptr, B_RZ, -1));
     kb_cg_p<<<g, bblock(), 0, st>>>(n, Sp, B.sc, B.kact, w.z, w.p); FVS_COUNT_LAUNCH();
-    FVS_TRY(bapply(B, op, w.p, nullptr, w.q, 0));
+    FVS_TRY(bapply(B, op, w.p, nullptr, w.q, 0, nullptr, 0.0, a.shape));
     FVS_TRY(bdot2(B, n, w.p, w.q, nullptr, nullptr, B_PQ, -1));
     kb_cg_xr<<<g, bblock(), 0, st>>>(n, Sp, B.sc, B.kact, w.p, w.q, x, w.r); FVS_COUNT_LAUNCH();
     FVS_TRY(bdot2(B, n, w.r, w.r, nullptr, nullptr, B_RR, -1));
@@ -1302,16 +1376,6 @@ struct BPpe {
   const int32_t* nS;
   double rho;
 };
-__device__ __forceinline__ int b_find(const int32_t* nb, int64_t Nc, int nn, int64_t c, int32_t j) {
-  int lo = 0, hi = nn - 1;
-  while (lo <= hi) {
-    const int mid = (lo + hi) >> 1;
-    const int32_t v = nb[(int64_t)mid * Nc + c];
-    if (v == j) return mid;
-    if (v < j) lo = mid + 1; else hi = mid - 1;
-  }
-  return -1;
-}
 __device__ __forceinline__ bool b_modified(const BPpe& x, int64_t c, int s) {
   for (int t = 0; t < 6; ++t) {
     const uint8_t fc = x.fcase[(int64_t)x.cf[t * x.Nc + c] * x.Sp + s];
@@ -1327,14 +1391,15 @@ __global__ void kb_ppe_count(BPpe x, int* count) {
   }
   if (cnt) atomicAdd(count, cnt);
 }
-__device__ __forceinline__ void b_vertex(const BPpe& x, int64_t c, int s, int nn, int32_t v, double coef,
+// nbl: the row's sorted neighbour list, copied to thread-local memory once
+__device__ __forceinline__ void b_vertex(const BPpe& x, const int32_t* nbl, int s, int nn, int32_t v, double coef,
                                          double* acc) {
   const int32_t lo = x.vc_ptr[v], hi = x.vc_ptr[v + 1];
   const double share = coef / (double)(hi - lo);
   for (int32_t e = lo; e < hi; ++e) {
     const int32_t j = x.vc_idx[e];
     if (!x.ppe[(int64_t)j * x.Sp + s]) continue;
-    const int p = b_find(x.nb, x.Nc, nn, c, j);
+    const int p = find_sorted(nbl, 1, nn, j);
     if (p >= 0) acc[p] += share;
   }
 }
@@ -1354,21 +1419,25 @@ __global__ void kb_ppe_rows(BPpe x, int32_t* ovr, double* mval, double* dinv, in
     if (o >= cap) { atomicOr(err, 32); ovr[e] = -2; dinv[e] = 1.0; continue; }
     ovr[e] = o;
     const int nn = x.nnb[c];
-    for (int k = 0; k < nn; ++k) acc[k] = 0.0;
+    int32_t nbl[FVS_MAX_NB];
+    for (int k = 0; k < nn; ++k) {
+      acc[k] = 0.0;
+      nbl[k] = x.nb[(int64_t)k * x.Nc + c];
+    }
     for (int t = 0; t < 6; ++t) {
       const int32_t f = x.cf[t * x.Nc + c];
       const uint8_t fc = x.fcase[(int64_t)f * x.Sp + s];
       if (fc != 1 && fc != 2) continue;
       const double sg = (double)x.cfs[t * x.Nc + c];
       const int32_t ow = x.own[f], q = x.nei[f];
-      { const int pq = b_find(x.nb, x.Nc, nn, c, q); if (pq >= 0) acc[pq] += sg * x.cd[f]; else atomicOr(err, 8); }
-      { const int po = b_find(x.nb, x.Nc, nn, c, ow); if (po >= 0) acc[po] -= sg * x.cd[f]; else atomicOr(err, 8); }
+      { const int pq = find_sorted(nbl, 1, nn, q); if (pq >= 0) acc[pq] += sg * x.cd[f]; else atomicOr(err, 8); }
+      { const int po = find_sorted(nbl, 1, nn, ow); if (po >= 0) acc[po] -= sg * x.cd[f]; else atomicOr(err, 8); }
       const int32_t v1 = x.fv[f], v2 = x.fv[x.Nf + f], v3 = x.fv[2 * x.Nf + f], v4 = x.fv[3 * x.Nf + f];
       const double ce = sg * x.ce[f], cz = sg * x.cz[f];
-      b_vertex(x, c, s, nn, v3, ce, acc);
-      b_vertex(x, c, s, nn, v1, -ce, acc);
-      b_vertex(x, c, s, nn, v4, cz, acc);
-      b_vertex(x, c, s, nn, v2, -cz, acc);
+      b_vertex(x, nbl, s, nn, v3, ce, acc);
+      b_vertex(x, nbl, s, nn, v1, -ce, acc);
+      b_vertex(x, nbl, s, nn, v4, cz, acc);
+      b_vertex(x, nbl, s, nn, v2, -cz, acc);
       if (fc == 2) {
         auto frac = [&](int32_t v) {
           return (double)x.nS[(int64_t)v * x.Sp + s] / (double)(x.vc_ptr[v + 1] - x.vc_ptr[v]);
@@ -1381,7 +1450,7 @@ __global__ void kb_ppe_rows(BPpe x, int32_t* ovr, double* mval, double* dinv, in
         for (int k = 0; k < nf; ++k) {
           const int32_t j = x.fnb[(int64_t)k * x.Nf + f];
           if (!x.ppe[(int64_t)j * x.Sp + s]) continue;
-          const int p = b_find(x.nb, x.Nc, nn, c, j);
+          const int p = find_sorted(nbl, 1, nn, j);
           if (p >= 0) acc[p] += add; else atomicOr(err, 2);
         }
       }
@@ -1774,6 +1843,7 @@ static fvs_status batch_step(Batch& B, double dt, int& failures, int (&its)[4]) 
     KrylovArgs a;
     a.rtol = B.props.mom_rtol;
     a.floor = B.mfloor;
+    a.shape = &B.shp_mom;
     a.take = B.run;
     a.maxit = B.props.max_krylov_iters;
     for (int d = 0; d < 3; ++d) {
@@ -1836,6 +1906,7 @@ static fvs_status batch_step(Batch& B, double dt, int& failures, int (&its)[4]) 
     KrylovArgs a;
     a.rtol = B.props.p_rtol;
     a.take = B.run;
+    a.shape = &B.lv[0]->shape;
     a.maxit = B.props.max_krylov_iters;
     int it = 0, fail = 0;
     if (m->orthogonal) FVS_TRY(bpcg(B, op, M, P, B.prhs, B.px, a, it, fail, &B.gp));
@@ -1871,6 +1942,7 @@ static fvs_status batch_step(Batch& B, double dt, int& failures, int (&its)[4]) 
     KrylovArgs a;
     a.rtol_s = B.ertol;
     a.take = B.etake;
+    a.shape = &B.shp_energy;
     a.maxit = B.props.max_krylov_iters;
     int left = 1;
     for (int it = 1; it <= B.props.max_e_iters && left > 0; ++it) {
@@ -2008,6 +2080,20 @@ fvs_status batch_run(fvs_mesh mesh, const fvs_props* base, int64_t n, const doub
       FVS_COUNT_LAUNCH();
       FVS_LAUNCH_CHECK();
       FVS_TRY(batch_amg_setup(B));
+      {
+        // launch shapes of the shared momentum and energy operators (FP64,
+        // every row doing its full work)
+        FVS_TRY(B.kw.ensure(cs));
+        for (DBuf<double>* b : {&B.kw.r, &B.kw.p, &B.kw.v, &B.mdiag, &B.edx})
+          FVS_CUDA(cudaMemsetAsync(b->p, 0, cs * sizeof(double), st));
+        FVS_TRY(tune_apply(B, OpShared{Nc, W, mesh->Lu.col.p, B.moff.p, B.mdiag.p, nullptr}, B.kw.r.p, B.kw.p.p,
+                           B.kw.v.p, B.mdiag.p, B.shp_mom));
+        FVS_TRY(tune_apply(B, OpShared{Nc, W, B.LT.col.p, B.kev.p, B.edx.p, nullptr}, B.kw.r.p, B.kw.p.p, B.kw.v.p,
+                           B.edx.p, B.shp_energy));
+        if (getenv("FVS_DEBUG"))
+          fprintf(stderr, "[fvs batch] momentum shape %d x %d, energy shape %d x %d\n", B.shp_mom.rows,
+                  B.shp_mom.per_sm, B.shp_energy.rows, B.shp_energy.per_sm);
+      }
       // steps until every sample has taken the step that began fully solid
       std::vector<int> nlm(Sp);
       std::vector<uint8_t> runh = rn;

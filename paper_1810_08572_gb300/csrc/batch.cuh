@@ -28,6 +28,13 @@ enum BSlot {
   B_FIRST, B_T0, B_T1, B_T2, B_NSLOT
 };
 
+// launch shape of a batched operator kernel: blocks of 32 samples x rows,
+// at most per_sm blocks per SM (chosen by the autotuner)
+struct BShape {
+  int rows = 8;
+  int per_sm = 16;
+};
+
 // one level of the batched AMG hierarchy
 struct BLevel {
   int64_t n = 0;
@@ -45,6 +52,7 @@ struct BLevel {
   DBuf<float> valf, dinvf;        // FP32 copies (mixed precision)
   DBuf<float> bf, xf, rf, yf;
   DBuf<int32_t> lab;              // null-space labels [i*Sp + s] (levels used for label pull-down)
+  BShape shape;                   // tuned launch shape of this level's operator
 };
 
 // a device-driven Krylov loop captured as a graph (conditional while-node)
@@ -141,6 +149,7 @@ struct Batch {
   double* phase_ms = nullptr;     // phase times (debug)
   uint64_t batch_version = 0;     // bumped when operator or hierarchy buffers move
   BatchGraph gmom[3], gp, ge;     // captured solve loops
+  BShape shp_mom, shp_energy;     // tuned launch shapes of the shared operators
   BatchWork kw;
 
   ~Batch();

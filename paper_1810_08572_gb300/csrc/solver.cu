@@ -225,13 +225,15 @@ struct PpeCtx {
   int WF;
 };
 
-__device__ __forceinline__ void ppe_vertex(const PpeCtx& x, int64_t c, int nn, int32_t v, double coef, double* acc) {
+// nbl: the row's sorted neighbour list, copied to thread-local memory once
+__device__ __forceinline__ void ppe_vertex(const PpeCtx& x, const int32_t* nbl, int nn, int32_t v, double coef,
+                                           double* acc) {
   const int32_t lo = x.vc_ptr[v], hi = x.vc_ptr[v + 1];
   const double share = coef / (double)(hi - lo);
   for (int32_t e = lo; e < hi; ++e) {
     const int32_t j = x.vc_idx[e];
     if (!x.ppe[j]) continue;            // deleted column (solid or non-flowing)
-    const int p = find_sorted(x.nb + c, x.Nc, nn, j);
+    const int p = find_sorted(nbl, 1, nn, j);
     if (p >= 0) acc[p] += share;
   }
 }
@@ -276,21 +278,25 @@ __global__ void k_ppe_matrix(PpeCtx x, int32_t* col, double* val, double* diag, 
       continue;
     }
     // re-assembly from the faces (Section 2.4.2, step 3)
-    for (int k = 0; k < nn; ++k) acc[k] = 0.0;
+    int32_t nbl[FVS_MAX_NB];
+    for (int k = 0; k < nn; ++k) {
+      acc[k] = 0.0;
+      nbl[k] = x.nb[(int64_t)k * x.Nc + c];
+    }
     for (int s = 0; s < 6; ++s) {
       const int32_t f = x.cf[s * x.Nc + c];
       const uint8_t fc = x.fcase[f];
       if (fc != 1 && fc != 2) continue;
       const double sg = (double)x.cfs[s * x.Nc + c];
       const int32_t o = x.own[f], q = x.nei[f];
-      { const int pq = find_sorted(x.nb + c, x.Nc, nn, q); if (pq >= 0) acc[pq] += sg * x.cd[f]; else atomicOr(err, 8); }
-      { const int po = find_sorted(x.nb + c, x.Nc, nn, o); if (po >= 0) acc[po] -= sg * x.cd[f]; else atomicOr(err, 8); }
+      { const int pq = find_sorted(nbl, 1, nn, q); if (pq >= 0) acc[pq] += sg * x.cd[f]; else atomicOr(err, 8); }
+      { const int po = find_sorted(nbl, 1, nn, o); if (po >= 0) acc[po] -= sg * x.cd[f]; else atomicOr(err, 8); }
       const int32_t v1 = x.fv[f], v2 = x.fv[x.Nf + f], v3 = x.fv[2 * x.Nf + f], v4 = x.fv[3 * x.Nf + f];
       const double ce = sg * x.ce[f], cz = sg * x.cz[f];
-      ppe_vertex(x, c, nn, v3, ce, acc);
-      ppe_vertex(x, c, nn, v1, -ce, acc);
-      ppe_vertex(x, c, nn, v4, cz, acc);
-      ppe_vertex(x, c, nn, v2, -cz, acc);
+      ppe_vertex(x, nbl, nn, v3, ce, acc);
+      ppe_vertex(x, nbl, nn, v1, -ce, acc);
+      ppe_vertex(x, nbl, nn, v4, cz, acc);
+      ppe_vertex(x, nbl, nn, v2, -cz, acc);
       if (fc == 2) {
         // Eq. 16: the deleted neighbours' coefficients, spread equally over
         // the remaining members of N(f)
@@ -305,7 +311,7 @@ __global__ void k_ppe_matrix(PpeCtx x, int32_t* col, double* val, double* diag, 
         for (int k = 0; k < nf; ++k) {
           const int32_t j = x.fnb[(int64_t)k * x.Nf + f];
           if (!x.ppe[j]) continue;
-          const int p = find_sorted(x.nb + c, x.Nc, nn, j);
+          const int p = find_sorted(nbl, 1, nn, j);
           if (p >= 0) acc[p] += add; else atomicOr(err, 2);
         }
       }
@@ -774,12 +780,26 @@ static PpeCtx ppe_ctx(fvs_solver s) {
 static fvs_status assemble_pressure(fvs_solver s) {
   fvs_mesh m = s->mesh;
   cudaStream_t st = s->stream;
+  // phase times for FVS_DEBUG (waits for the stream at each mark)
+  const bool dbg = getenv("FVS_DEBUG") != nullptr;
+  if (dbg) cudaStreamSynchronize(st);
+  auto t_mark = std::chrono::steady_clock::now();
+  auto lap = [&]() {
+    cudaStreamSynchronize(st);
+    const auto now = std::chrono::steady_clock::now();
+    const double ms = std::chrono::duration<double, std::milli>(now - t_mark).count();
+    t_mark = now;
+    return ms;
+  };
   FVS_TRY(s->K.alloc(s->nact, m->W));
   DBuf<int> err;
   FVS_TRY(err.alloc(1));
   FVS_TRY(err.zero(st));
   if (s->nact > 0) {
-    k_ppe_matrix<<<stride_grid(s->nact, 128, 4), 128, 0, st>>>(ppe_ctx(s), s->K.col, s->K.val, s->K.diag, err); FVS_COUNT_LAUNCH();
+    // one thread per row: the re-assembled rows next to solid cells are
+    // latency-bound searches, so as many as possible run at once
+    k_ppe_matrix<<<(unsigned)((s->nact + 127) / 128), 128, 0, st>>>(ppe_ctx(s), s->K.col, s->K.val, s->K.diag, err);
+    FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
   }
   int h = 0;
@@ -794,10 +814,12 @@ static fvs_status assemble_pressure(fvs_solver s) {
   // Same numbering and a usable hierarchy: refresh its fine level only
   // (new diagonal, rows of frozen cells left out of the null-space
   // projection); otherwise build the hierarchy anew.
+  const double t_matrix = dbg ? lap() : 0.0;
   if (!s->renumbered && s->amg_ok && !s->force_full && s->nact > 0) {
     const fvs_status r = s->amg.refresh(st, s->act, s->ppe);
     if (r == FVS_OK) {
       s->amg_full = false;
+      if (dbg) fprintf(stderr, "[fvs step] pressure matrix %.2f ms, hierarchy refresh %.2f ms\n", t_matrix, lap());
       return FVS_OK;
     }
     if (r != FVS_ERR_NOT_CONVERGED) return r;
