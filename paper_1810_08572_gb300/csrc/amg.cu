@@ -649,18 +649,33 @@ template <typename T>
 __global__ void k_jac0(int64_t n, T omega, const T* dinv, const T* b, T* x) {
   GS(i, n) x[i] = omega * dinv[i] * b[i];
 }
+// (A x)_i.  Fine level (no row lengths): the plain loop over the full width.
+// Coarse levels: only the stored entries, in groups of eight loads (the
+// coarse rows are short and gather-latency-bound); same order of the sum.
+template <typename T>
+__device__ __forceinline__ T smoother_row(int64_t n, int w, const int32_t* __restrict__ col,
+                                          const T* __restrict__ val, const T* __restrict__ x,
+                                          const int32_t* __restrict__ rlen, int64_t i) {
+  if (!rlen) {
+    T acc = 0;
+    for (int k = 0; k < w; ++k) {
+      const int64_t e = (int64_t)k * n + i;
+      acc = fma(val[e], x[col[e]], acc);
+    }
+    return acc;
+  }
+  return row_dot8<T>(
+      rlen[i], [&](int k) { return col[(int64_t)k * n + i]; }, [&](int k) { return val[(int64_t)k * n + i]; },
+      [&](int32_t c) { return x[c]; }, (T)0);
+}
+
 // y = x + omega D^-1 (b - A x)
 template <typename T>
 __global__ void k_jac(int64_t n, int w, const int32_t* __restrict__ col, const T* __restrict__ val, T omega,
                       const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
                       T* __restrict__ y, const int32_t* __restrict__ rlen) {
   GS(i, n) {
-    T acc = 0;
-    const int len = rlen ? rlen[i] : w;   // stored entries first, padding after
-    for (int k = 0; k < len; ++k) {
-      const int64_t e = (int64_t)k * n + i;
-      acc = fma(val[e], x[col[e]], acc);
-    }
+    const T acc = smoother_row(n, w, col, val, x, rlen, i);
     y[i] = x[i] + omega * dinv[i] * (b[i] - acc);
   }
 }
@@ -669,12 +684,7 @@ __global__ void k_resid(int64_t n, int w, const int32_t* __restrict__ col, const
                         const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r,
                         const int32_t* __restrict__ rlen) {
   GS(i, n) {
-    T acc = 0;
-    const int len = rlen ? rlen[i] : w;
-    for (int k = 0; k < len; ++k) {
-      const int64_t e = (int64_t)k * n + i;
-      acc = fma(val[e], x[col[e]], acc);
-    }
+    const T acc = smoother_row(n, w, col, val, x, rlen, i);
     r[i] = b[i] - acc;
   }
 }
