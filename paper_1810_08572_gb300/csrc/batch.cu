@@ -1652,6 +1652,21 @@ __global__ void kb_energy_update(int64_t Nc, int Sp, BMat m, const double* Tliq,
     fsnext[e] = b_fs(T, m.Ts, Tl);
   }
 }
+// first iterate of the latent-heat loop: T^n extrapolated linearly in time
+// (samples that no longer run keep their state)
+__global__ void kb_energy_guess(int64_t Nc, int Sp, const double* T, const double* Told, const double* fs, double Ts,
+                                const double* Tliq, const uint8_t* run, double* Tm, double* fsm) {
+  BSAMPLE;
+  const bool r = run[s] != 0;
+  const double Tl = Tliq[s];
+  BROW(c, Nc) {
+    const int64_t e = c * Sp + s;
+    if (!r) { Tm[e] = T[e]; fsm[e] = fs[e]; continue; }
+    const double t = 2.0 * T[e] - Told[e];
+    Tm[e] = t;
+    fsm[e] = b_fs(t, Ts, Tl);
+  }
+}
 // latent-heat loop bookkeeping per sample: stop rule and the next pass's
 // inner tolerance; counts[0] samples still iterating
 __global__ void kb_energy_check(int Sp, const double* sc, uint8_t* take, uint8_t* conv, double* ertol, double e_tol_T,
@@ -1932,8 +1947,8 @@ static fvs_status batch_step(Batch& B, double dt, int& failures, int (&its)[4]) 
   // per-sample stop rule
   kb_energy_base<<<gc, blk, 0, st>>>(Nc, Sp, m->W, m->cf, m->cfs, m->own, m->nei, B.F, B.Fold, B.T, B.Told,
                                      B.LT.col, B.LT.val, B.lT1, B.Twall, m->V, mt, dt, B.ebase); FVS_COUNT_LAUNCH();
-  FVS_TRY(bcopy(B, cs, B.T, B.Tnew));
-  FVS_TRY(bcopy(B, cs, B.fs, B.fsnew));
+  kb_energy_guess<<<gc, blk, 0, st>>>(Nc, Sp, B.T, B.Told, B.fs, mt.Ts, B.Tliq, B.run, B.Tnew, B.fsnew);
+  FVS_COUNT_LAUNCH();
   kb_energy_start<<<B.tiles, 32, 0, st>>>(Sp, B.run, B.etake, B.econv, B.ertol, B.props.e_rtol); FVS_COUNT_LAUNCH();
   {
     OpShared op{Nc, m->W, B.LT.col.p, B.kev.p, B.edx.p, nullptr};

@@ -511,6 +511,17 @@ __global__ void k_count_u8(int64_t n, const uint8_t* a, int* out) {
   if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
 }
 
+// first iterate of the latent-heat loop: T^n extrapolated linearly in time
+// (the loop converges to the same discrete solution from any start, within
+// its stop rule; this start is closer)
+__global__ void k_energy_guess(int64_t Nc, const double* T, const double* Told, double Ts, double Tl, double* Tm,
+                               double* fsm) {
+  GS(c, Nc) {
+    const double t = 2.0 * T[c] - Told[c];
+    Tm[c] = t;
+    fsm[c] = solid_fraction(t, Ts, Tl);
+  }
+}
 __global__ void k_crossings(int64_t Nc, const double* Tn, const double* Tnew, double Ts, double Tl, double time,
                             double dt, double* tliq, double* tsol) {
   GS(c, Nc) {
@@ -1019,8 +1030,8 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
   // 5. energy: linearised latent heat, inner solve, enthalpy inversion
   k_energy_base<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, m->W, m->cf, m->cfs, m->own, m->nei, s->F, s->Fold, s->T,
                                                       s->Told, s->LT.col, s->LT.val, s->lT, m->V, mt, dt, s->ebase); FVS_COUNT_LAUNCH();
-  FVS_TRY(vcopy(st, Nc, s->T, s->Tnew));
-  FVS_TRY(vcopy(st, Nc, s->fs, s->fsnew));
+  k_energy_guess<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, s->Told, mt.Ts, mt.Tl, s->Tnew, s->fsnew);
+  FVS_COUNT_LAUNCH();
   {
     JacobiPrecond J;
     J.A = &s->Ke;
