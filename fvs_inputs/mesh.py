@@ -154,3 +154,14 @@ def box_mesh(nx, ny, nz, lengths=(0.1, 0.1, 0.0125), jitter=0.0, jitter_seed=0,
 def strip_mesh(n, length=0.1, width=1e-3):
     """A 1-D column of ``n`` cells along x (one cell in y and z)."""
     return box_mesh(n, 1, 1, lengths=(length, width, width))
+
+
+def zones_inner_box(mesh, lo, hi):
+    """Cell zones for a metal block inside a mold: 0 (metal) where the cell
+    centre lies inside the box [lo, hi], 1 (mold) elsewhere.  int32 [Nc]."""
+    X = np.asarray(mesh["nodes"], dtype=np.float64)
+    xc = X[np.asarray(mesh["cells"])].mean(axis=1)
+    lo = np.asarray(lo, dtype=np.float64)
+    hi = np.asarray(hi, dtype=np.float64)
+    inside = np.all((xc >= lo) & (xc <= hi), axis=1)
+    return np.where(inside, 0, 1).astype(np.int32)

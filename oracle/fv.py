@@ -75,6 +75,11 @@ class Geometry:
         c2 = np.where(self.interior[:, None], self.xc[np.maximum(self.neigh, 0)], self.xf)
         self.d = c2 - self.xc[self.owner]
         self.ndotd = np.einsum("fi,fi->f", self.n, self.d)
+        # distances from the owner / neighbour centre to the face centre
+        # (series resistance across a metal-mold interface)
+        self.d_own = np.linalg.norm(self.xf - self.xc[self.owner], axis=1)
+        self.d_nei = np.where(self.interior,
+                              np.linalg.norm(self.xf - self.xc[np.maximum(self.neigh, 0)], axis=1), 0.0)
         # local frame xi: C1C2, eta: V1V3, zeta: V2V4 (Eq. 12); rows of J
         self.J = np.stack([self.d, Vx[2] - Vx[0], Vx[3] - Vx[1]], axis=1)
         self.Jinv = np.linalg.inv(self.J)
@@ -162,9 +167,15 @@ def velocity_diffusion(g):
     return diffusion_operator(g, np.ones(g.Nf, bool), vP, vc, np.zeros(g.Nf))
 
 
-def temperature_diffusion(g, walls):
+def temperature_diffusion(g, walls, k_face=None, interface=None, G_int=None):
     """Fixed-temperature walls enter through their vertices and faces;
-    adiabatic walls carry no flux."""
+    adiabatic walls carry no flux.
+
+    With ``k_face`` the face flux is scaled by that face's conductivity (the
+    result is the conductive flux itself).  Faces flagged in ``interface``
+    (a metal cell against a mold cell) carry only the orthogonal flux
+    G_int (T_C2 - T_C1) through the series resistance of the two half cells
+    and the interface coefficient."""
     btype = np.full(g.Nf, -1)
     bval = np.zeros(g.Nf)
     for pid, (typ, T) in enumerate(walls):
@@ -184,7 +195,20 @@ def temperature_diffusion(g, walls):
     val = np.where(fixed, acc / np.maximum(cnt, 1), 0.0)
     vP, vc = vertex_operator(g, fixed, val)
     face_mask = g.interior | dir_face
-    return diffusion_operator(g, face_mask, vP, vc, bval)
+    if k_face is None:
+        return diffusion_operator(g, face_mask, vP, vc, bval)
+    Deta = g.E31 @ vP
+    Dzeta = g.E42 @ vP
+    N = g.normal_derivative_rows(g.Dxi, Deta, Dzeta)
+    k = g.Af * ((1.0 / g.ndotd + g.w[:, 0]) * np.where(g.interior, 0.0, bval)
+                + g.w[:, 1] * (g.E31 @ vc) + g.w[:, 2] * (g.E42 @ vc))
+    # conductive flux per face: k_f times the face gradient, or the series
+    # flux on interface faces (no cross terms there)
+    Nk = (sp.diags(np.where(interface, 0.0, k_face)) @ N
+          + sp.diags(np.where(interface, G_int, 0.0)) @ g.Dxi).tocsr()
+    kk = np.where(interface, 0.0, k_face * k)
+    M = g.Div @ sp.diags(face_mask.astype(np.float64))
+    return (M @ Nk).tocsr(), M @ kk
 
 
 # ----------------------------------------------------------------------------
@@ -267,12 +291,35 @@ class Oracle:
         self.walls = list(props["walls"])
         self.props = props
         self.Lu, _ = velocity_diffusion(g)
-        self.LT, self.lT = temperature_diffusion(g, self.walls)
+        m = self.m
+        # zones: 0 metal, 1 mold (conduction only: no flow, no latent heat);
+        # the mold material and the metal-mold interface coefficient h come
+        # from props["mold"] = dict(rho, cp, k, h, T_init)
+        zone = mesh.get("cell_zone")
+        self.metal = np.ones(g.Nc, bool) if zone is None else (np.asarray(zone) == 0)
+        mold = props.get("mold")
+        if mold is None:
+            self.metal[:] = True
+        self.mold = mold
+        rho_c = np.where(self.metal, m["rho"], mold["rho"] if mold else m["rho"])
+        cp_c = np.where(self.metal, m["cp"], mold["cp"] if mold else m["cp"])
+        k_c = np.where(self.metal, m["k"], mold["k"] if mold else m["k"])
+        self.rcp = rho_c * cp_c
+        self.rL = np.where(self.metal, m["rho"] * m["latent"], 0.0)
+        q = np.maximum(g.neigh, 0)
+        interface = g.interior & (self.metal[g.owner] != self.metal[q])
+        k_face = k_c[g.owner]
+        G = np.zeros(g.Nf)
+        if interface.any():
+            ko, kq = k_c[g.owner], k_c[q]
+            G = np.where(interface, g.Af / (g.d_own / ko + 1.0 / mold["h"] + g.d_nei / kq), 0.0)
+        self.interface = interface
+        # conductive operator (k inside): sum over faces of the face flux
+        self.LTk, self.lTk = temperature_diffusion(g, self.walls, k_face=k_face, interface=interface, G_int=G)
         self.Deta_p = (g.E31 @ g.Pavg).tocsr()
         self.Dzeta_p = (g.E42 @ g.Pavg).tocsr()
-        m = self.m
-        self.T = np.full(g.Nc, props["T_init"])
-        self.fs = solid_fraction(self.T, m["T_sol"], m["T_liq"])
+        self.T = np.where(self.metal, props["T_init"], mold["T_init"] if mold else props["T_init"])
+        self.fs = np.where(self.metal, solid_fraction(self.T, m["T_sol"], m["T_liq"]), 0.0)
         self.T_old = self.T.copy()
         self.u = np.zeros((g.Nc, 3))
         self.u_old = np.zeros((g.Nc, 3))
@@ -281,8 +328,8 @@ class Oracle:
         self.p = np.zeros(g.Nc)
         self.time = 0.0
         self.nstep = 0
-        self.t_liq = np.where(self.T <= m["T_liq"], 0.0, -1.0)
-        self.t_sol = np.where(self.T <= m["T_sol"], 0.0, -1.0)
+        self.t_liq = np.where(self.metal & (self.T <= m["T_liq"]), 0.0, -1.0)
+        self.t_sol = np.where(self.metal & (self.T <= m["T_sol"]), 0.0, -1.0)
         self.stats = {}
 
     # -- helpers ---------------------------------------------------------------
@@ -334,8 +381,8 @@ class Oracle:
         g, m = self.g, self.m
         rho, mu = m["rho"], m["mu"]
         T_n, fs_n = self.T, self.fs
-        # 1. tags from the previous temperature (Section 2.4)
-        lm = T_n > m["T_sol"]
+        # 1. tags from the previous temperature (Section 2.4); mold cells are never LM
+        lm = self.metal & (T_n > m["T_sol"])
         solid = ~lm
         u_n = self.u.copy(); u_n[solid] = 0.0
         u_o = self.u_old.copy(); u_o[solid] = 0.0
@@ -409,12 +456,12 @@ class Oracle:
     def energy_residual(self, T, dt, T_n, fs_n, T_o, F_n, F_o):
         """R(T) of the discrete energy equation (all terms moved to the left)."""
         g, m = self.g, self.m
-        rho, cp, k, L = m["rho"], m["cp"], m["k"], m["latent"]
+        rcp, rL = self.rcp, self.rL
         conv = 1.5 * self.conv(T_n, F_n) - 0.5 * self.conv(T_o, F_o)
-        fs = solid_fraction(T, m["T_sol"], m["T_liq"])
-        return (rho * cp * g.V / dt * (T - T_n) + rho * cp * conv
-                - 0.5 * k * (self.LT @ T + self.lT) - 0.5 * k * (self.LT @ T_n + self.lT)
-                - rho * L * g.V / dt * (fs - fs_n))
+        fs = np.where(self.metal, solid_fraction(T, m["T_sol"], m["T_liq"]), 0.0)
+        return (rcp * g.V / dt * (T - T_n) + rcp * conv
+                - 0.5 * (self.LTk @ T + self.lTk) - 0.5 * (self.LTk @ T_n + self.lTk)
+                - rL * g.V / dt * (fs - fs_n))
 
     def energy(self, dt, T_n, fs_n, T_o, F_n, F_o):
         """Section 2.4.4 iteration: S_p, S_c from the last iterate, solve,
@@ -422,26 +469,27 @@ class Oracle:
         passes without convergence the temperature is taken from the
         linearised enthalpy instead (same fixed point)."""
         g, m = self.g, self.m
-        rho, cp, k, L = m["rho"], m["cp"], m["k"], m["latent"]
+        cp, L = m["cp"], m["latent"]
+        rcp, rL, metal = self.rcp, self.rL, self.metal
         Ts, Tl = m["T_sol"], m["T_liq"]
         conv = 1.5 * self.conv(T_n, F_n) - 0.5 * self.conv(T_o, F_o)
-        base = (rho * cp * g.V / dt * T_n - rho * cp * conv
-                + 0.5 * k * (self.LT @ T_n + self.lT) + 0.5 * k * self.lT)
-        K = (-0.5 * k * self.LT).tocsr()
+        base = (rcp * g.V / dt * T_n - rcp * conv
+                + 0.5 * (self.LTk @ T_n + self.lTk) + 0.5 * self.lTk)
+        K = (-0.5 * self.LTk).tocsr()
         T, fs = T_n.copy(), fs_n.copy()
         tolT = self.props.get("oracle_tol_T", 1e-11)
         for it in range(1, 200):
-            dfs = solid_fraction_slope(T, Ts, Tl)
-            Sp = rho * L * g.V / dt * dfs
-            Sc = rho * L * g.V / dt * (fs - fs_n - dfs * T)
-            A = (K + sp.diags(rho * cp * g.V / dt - Sp)).tocsr()
+            dfs = np.where(metal, solid_fraction_slope(T, Ts, Tl), 0.0)
+            Sp = rL * g.V / dt * dfs
+            Sc = rL * g.V / dt * (fs - fs_n - dfs * T)
+            A = (K + sp.diags(rcp * g.V / dt - Sp)).tocsr()
             T_lin = solve(A, base + Sc)
             if it <= 20:
                 T_next = T_lin
             else:
                 H = cp * T_lin + L * (1.0 - fs - dfs * (T_lin - T))
-                T_next = temperature_from_enthalpy(H, cp, L, Ts, Tl)
-            fs_next = solid_fraction(T_next, Ts, Tl)
+                T_next = np.where(metal, temperature_from_enthalpy(H, cp, L, Ts, Tl), T_lin)
+            fs_next = np.where(metal, solid_fraction(T_next, Ts, Tl), 0.0)
             dT = np.max(np.abs(T_next - T))
             dF = np.max(np.abs(fs_next - fs))
             T, fs = T_next, fs_next
@@ -453,7 +501,7 @@ class Oracle:
         m = self.m
         for which, Tc in (("t_liq", m["T_liq"]), ("t_sol", m["T_sol"])):
             arr = getattr(self, which)
-            hit = (arr < 0) & (T_n > Tc) & (T_new <= Tc)
+            hit = self.metal & (arr < 0) & (T_n > Tc) & (T_new <= Tc)
             frac = (T_n - Tc) / np.where(hit, T_n - T_new, 1.0)
             arr[hit] = self.time + dt * frac[hit]
 
@@ -461,7 +509,7 @@ class Oracle:
         """Local solidification time, cooling rate, SDAS and yield strength
         per cell (NaN where the cell has not yet passed the solidus)."""
         m = self.m
-        done = (self.t_sol >= 0) & (self.t_liq >= 0)
+        done = self.metal & (self.t_sol >= 0) & (self.t_liq >= 0)
         tf = np.where(done, self.t_sol - self.t_liq, np.nan)
         with np.errstate(divide="ignore", invalid="ignore"):
             cr = (m["T_liq"] - m["T_sol"]) / tf

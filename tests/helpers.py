@@ -39,14 +39,16 @@ def set_state(o, T, u=None):
     """Put an oracle into a given state (temperature, optional velocity)."""
     from oracle.fv import solid_fraction
     m = o.m
+    metal = o.metal
     o.T = np.array(T, dtype=np.float64)
     o.T_old = o.T.copy()
-    o.fs = solid_fraction(o.T, m["T_sol"], m["T_liq"])
-    o.t_liq = np.where(o.T <= m["T_liq"], 0.0, -1.0)
-    o.t_sol = np.where(o.T <= m["T_sol"], 0.0, -1.0)
+    o.fs = np.where(metal, solid_fraction(o.T, m["T_sol"], m["T_liq"]), 0.0)
+    o.t_liq = np.where(metal & (o.T <= m["T_liq"]), 0.0, -1.0)
+    o.t_sol = np.where(metal & (o.T <= m["T_sol"]), 0.0, -1.0)
     if u is not None:
+        still = ~metal | (o.T <= m["T_sol"])
         o.u = np.array(u, dtype=np.float64)
         o.u_old = o.u.copy()
-        o.u[o.T <= m["T_sol"]] = 0.0
-        o.u_old[o.T <= m["T_sol"]] = 0.0
+        o.u[still] = 0.0
+        o.u_old[still] = 0.0
     return o

@@ -4,8 +4,9 @@ import os
 
 import numpy as np
 import pytest
+import scipy.sparse.linalg as spla
 
-from fvs_inputs import box_mesh, cases
+from fvs_inputs import box_mesh, cases, zones_inner_box
 from oracle.analytic import neumann_isothermal, stefan_linear
 from oracle.fv import Oracle, darcy_coefficient, sdas_um, solid_fraction, yield_strength_mpa
 from tests.helpers import mushy_field, set_state
@@ -110,21 +111,28 @@ def test_stefan_linear_solid_fraction():
     assert worst[2] < 0.8 and worst[0] / worst[2] > 5.0, worst
 
 
-def test_global_energy_balance():
+@pytest.mark.parametrize("with_mold", [False, True])
+def test_global_energy_balance(with_mold):
     """Summed over the cavity, the energy change of a step (sensible minus
     latent) equals dt times the mean of the wall heat flow at both time
-    levels: convective and interior diffusive fluxes telescope."""
+    levels: convective and interior diffusive fluxes telescope, including the
+    series flux through a metal-mold interface."""
     m = box_mesh(8, 8, 3, cases.CAVITY, jitter=0.15, jitter_seed=2)
-    o = Oracle(m, cases.props(oracle_tol_T=1e-12))
+    extra = {}
+    if with_mold:
+        m = dict(m, cell_zone=zones_inner_box(m, (0.02, 0.02, -1.0), (0.08, 0.08, 1.0)))
+        extra = dict(mold=dict(rho=7800.0, cp=500.0, k=30.0, h=2000.0, T_init=600.0))
+    o = Oracle(m, cases.props(oracle_tol_T=1e-12, **extra))
     rng = np.random.default_rng(4)
     set_state(o, mushy_field(m), u=rng.normal(scale=1e-3, size=(len(m["cells"]), 3)))
-    mat = o.m
+    if with_mold:
+        assert o.interface.sum() > 0 and (~o.metal).sum() > 0
     for _ in range(3):
         T0, fs0 = o.T.copy(), o.fs.copy()
-        q0 = mat["k"] * (o.LT @ T0 + o.lT).sum()
+        q0 = (o.LTk @ T0 + o.lTk).sum()
         o.step(1e-3)
-        q1 = mat["k"] * (o.LT @ o.T + o.lT).sum()
-        dE = (mat["rho"] * o.g.V * (mat["cp"] * (o.T - T0) - mat["latent"] * (o.fs - fs0))).sum()
+        q1 = (o.LTk @ o.T + o.lTk).sum()
+        dE = (o.g.V * (o.rcp * (o.T - T0) - o.rL * (o.fs - fs0))).sum()
         assert abs(dE - 1e-3 * 0.5 * (q0 + q1)) <= 1e-9 * abs(dE)
 
 
@@ -176,3 +184,26 @@ def test_crossing_times_linear_in_time():
     tf = 2.07 - 1.035
     assert q["t_f"][0] == pytest.approx(tf, rel=1e-12)
     assert q["cooling_rate"][0] == pytest.approx(80.0 / tf, rel=1e-12)
+
+
+@pytest.mark.parametrize("h", [500.0, 2000.0, 1e12])
+def test_metal_mold_interface_steady_conduction(h):
+    """Steady conduction through a metal slab and a mold slab held at two
+    temperatures: the conductive operator's steady solution is the
+    series-resistance profile q = (T1 - T2) / (a/k_metal + 1/h + a/k_mold),
+    linear in each slab with a jump of q/h at the interface, exact at the
+    cell centres (two-point fluxes are exact for linear profiles)."""
+    nx, Lx = 20, 0.04
+    m = box_mesh(nx, 1, 1, (Lx, 2e-3, 2e-3))
+    m = dict(m, cell_zone=zones_inner_box(m, (-1.0, -1.0, -1.0), (0.5 * Lx, 1.0, 1.0)))
+    mat = dict(cases.AL_ALLOY)
+    mold = dict(rho=7800.0, cp=500.0, k=30.0, h=h, T_init=500.0)
+    T1, T2 = 600.0, 400.0
+    o = Oracle(m, cases.props(material=mat, walls=cases.cavity_walls(T1, T2), mold=mold))
+    assert o.interface.sum() == 1
+    T = spla.spsolve(o.LTk.tocsc(), -o.lTk)
+    x = o.g.xc[:, 0]
+    a = 0.5 * Lx
+    q = (T1 - T2) / (a / mat["k"] + 1.0 / h + a / mold["k"])
+    exact = np.where(x < a, T1 - q * x / mat["k"], T2 + q * (Lx - x) / mold["k"])
+    assert np.abs(T - exact).max() <= 1e-9 * (T1 - T2)
