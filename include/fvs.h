@@ -86,6 +86,15 @@ fvs_status fvs_mesh_create(const double* nodes_xyz, int64_t n_nodes,
                            int reorder, void* stream, fvs_mesh* out);
 fvs_status fvs_mesh_destroy(fvs_mesh mesh);
 
+/* Cell zones for castings in a mold (Section 2.4.4: the energy equation runs
+ * on every cell; flow only in the metal).
+ *   zone   host int32 [n_cells] in the caller's cell order: 0 metal, 1 mold
+ * The zones take effect in solvers that are given a mold material
+ * (fvs_set_mold); otherwise every cell is metal.  Call before
+ * fvs_set_properties / fvs_set_mold of the solvers that use them.
+ * FVS_ERR_ARG for values other than 0 and 1. */
+fvs_status fvs_mesh_set_zones(fvs_mesh mesh, const int32_t* zone);
+
 typedef struct {
   int64_t n_cells, n_faces, n_nodes, n_interior_faces;
   int32_t max_cell_neighbours; /* width of the vertex-neighbour stencil       */
@@ -144,6 +153,18 @@ fvs_status fvs_solver_destroy(fvs_solver solver);
 /* Copies the settings and resets the state to the initial condition
  * (uniform T_init, u = 0, zero fluxes, time 0). */
 fvs_status fvs_set_properties(fvs_solver solver, const fvs_props* props);
+
+/* Mold material (zone-1 cells of fvs_mesh_set_zones): conduction only —
+ * never liquid/mushy, no latent heat, no flow — with density rho (kg/m3),
+ * heat capacity cp (J/kg K) and conductivity k (W/m K).  A face between a
+ * metal and a mold cell carries the orthogonal conductive flux
+ * A (T_2 - T_1) / (d_1/k_1 + 1/h + d_2/k_2), d_i the distance from cell
+ * centre i to the face centre and h (W/m2 K) the interface heat-transfer
+ * coefficient; faces inside a zone use that zone's k.  Resets the state as
+ * fvs_set_properties does, with the mold cells at T_init (K).  A later
+ * fvs_set_properties removes the mold again.  FVS_ERR_STATE before
+ * fvs_set_properties; FVS_ERR_ARG for non-positive rho, cp, k or h. */
+fvs_status fvs_set_mold(fvs_solver solver, double rho, double cp, double k, double h, double T_init);
 
 /* Overwrite the state with a given temperature field (and velocity, or NULL
  * for rest): T^n = T^{n-1} = T, fs = fs(T), u^n = u^{n-1} = u (zero in solid

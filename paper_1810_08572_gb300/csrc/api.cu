@@ -240,6 +240,24 @@ FVS_API fvs_status fvs_set_properties(fvs_solver s, const fvs_props* p) {
   return solver_set_properties(s, p);
 }
 
+FVS_API fvs_status fvs_mesh_set_zones(fvs_mesh mesh, const int32_t* zone) {
+  if (!mesh || !zone) {
+    set_error("fvs_mesh_set_zones: NULL argument");
+    return FVS_ERR_ARG;
+  }
+  AllocStream as(mesh->stream);
+  return mesh_set_zones(mesh, zone);
+}
+
+FVS_API fvs_status fvs_set_mold(fvs_solver s, double rho, double cp, double k, double h, double T_init) {
+  if (!s) {
+    set_error("fvs_set_mold: NULL solver");
+    return FVS_ERR_ARG;
+  }
+  AllocStream as(s->stream);
+  return solver_set_mold(s, rho, cp, k, h, T_init);
+}
+
 FVS_API fvs_status fvs_set_state(fvs_solver s, const double* T, const double* u, int on_device) {
   if (!s || !T) {
     set_error("fvs_set_state: NULL argument");

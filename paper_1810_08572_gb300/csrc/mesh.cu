@@ -274,7 +274,7 @@ __global__ void k_cell_centres(int64_t Nc, int64_t Nv, const double* Xn, const i
 __global__ void k_face_geometry(int64_t Nf, int64_t Nv, int64_t Nc, const double* Xn, const double* xc,
                                 const int32_t* fv, const int32_t* own, const int32_t* nei, double* A,
                                 double* nrm, double* cd, double* ce, double* cz, double* Jinv, double* xs,
-                                double* skew, int* err) {
+                                double* skew, double* dof, double* dnf, int* err) {
   GS(f, Nf) {
     double P[4][3];
     for (int k = 0; k < 4; ++k) {
@@ -311,6 +311,18 @@ __global__ void k_face_geometry(int64_t Nf, int64_t Nv, int64_t Nc, const double
     cz[f] = a * w[2];
     for (int k = 0; k < 9; ++k) Jinv[k * Nf + f] = Ji[k];
     xs[f] = (xf[0] * S[0] + xf[1] * S[1] + xf[2] * S[2]) / 3.0;
+    // distances from the owner / neighbour centre to the face centre
+    double a2 = 0.0, b2 = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      const double ea = xf[d] - xc[d * Nc + o];
+      a2 += ea * ea;
+      if (q >= 0) {
+        const double eb = xf[d] - xc[d * Nc + q];
+        b2 += eb * eb;
+      }
+    }
+    dof[f] = sqrt(a2);
+    dnf[f] = sqrt(b2);
     const double l1 = sqrt(e1[0] * e1[0] + e1[1] * e1[1] + e1[2] * e1[2]);
     const double l2 = sqrt(e2[0] * e2[0] + e2[1] * e2[1] + e2[2] * e2[2]);
     skew[f] = fmax(fabs(w[0]) * nd, fmax(fabs(w[1]) * l1, fabs(w[2]) * l2));
@@ -343,6 +355,8 @@ struct RowCtx {
   const int32_t* bc_type;
   const double* bc_T;
   const double* vfix;     // temperature: fixed vertex value or NaN if free
+  const double* kf;       // temperature: per-face conductivity factor (null: 1)
+  const double* gint;     // temperature: interface conductance (> 0 on metal-mold faces)
 };
 
 __device__ __forceinline__ void add_vertex(const RowCtx& x, int kind, int64_t c, int nn, int32_t v, double coef,
@@ -367,8 +381,17 @@ __device__ void assemble_base_row(const RowCtx& x, int kind, int64_t c, double* 
   const int pc = find_sorted(x.nb + c, x.Nc, nn, (int32_t)c);
   for (int s = 0; s < 6; ++s) {
     const int32_t f = x.cf[s * x.Nc + c];
-    const double sg = (double)x.cfs[s * x.Nc + c];
+    double sg = (double)x.cfs[s * x.Nc + c];
     const int32_t q = x.nei[f];
+    if (kind == 2 && x.gint && x.gint[f] > 0.0) {
+      // metal-mold interface: orthogonal flux through the series resistance
+      const int p2 = find_sorted(x.nb + c, x.Nc, nn, q);
+      const int p1 = find_sorted(x.nb + c, x.Nc, nn, x.own[f]);
+      if (p2 >= 0) acc[p2] += sg * x.gint[f];
+      if (p1 >= 0) acc[p1] -= sg * x.gint[f];
+      continue;
+    }
+    if (kind == 2 && x.kf) sg *= x.kf[f];   // conductive flux: k_f times the face gradient
     double phib = 0.0;
     if (q < 0) {
       if (kind == 1) continue;
@@ -437,11 +460,12 @@ static RowCtx row_ctx(fvs_mesh m) {
   x.cfs = m->cfs; x.vbnd = m->vbnd;
   x.cd = m->cd; x.ce = m->ce; x.cz = m->cz;
   x.bc_type = nullptr; x.bc_T = nullptr; x.vfix = nullptr;
+  x.kf = nullptr; x.gint = nullptr;
   return x;
 }
 
 fvs_status assemble_temperature_operator(fvs_mesh m, const int32_t* d_bc_type, const double* d_bc_T, Ell& LT,
-                                         double* lT, cudaStream_t s) {
+                                         double* lT, cudaStream_t s, const double* kf, const double* gint) {
   DBuf<double> vsum, vfix;
   DBuf<int32_t> vcnt;
   FVS_TRY(vsum.alloc(m->Nv)); FVS_TRY(vfix.alloc(m->Nv)); FVS_TRY(vcnt.alloc(m->Nv));
@@ -452,9 +476,41 @@ fvs_status assemble_temperature_operator(fvs_mesh m, const int32_t* d_bc_type, c
   FVS_TRY(LT.alloc(m->Nc, m->W));
   RowCtx x = row_ctx(m);
   x.bc_type = d_bc_type; x.bc_T = d_bc_T; x.vfix = vfix;
+  x.kf = kf; x.gint = gint;
   k_assemble_base<<<stride_grid(m->Nc, 128, 4), 128, 0, s>>>(x, 2, m->W, LT.col, LT.val, LT.diag, lT); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   FVS_CUDA(cudaStreamSynchronize(s));
+  return FVS_OK;
+}
+
+// zones in the mesh numbering from the caller's cell order; values other
+// than 0 (metal) and 1 (mold) are flagged
+__global__ void k_zone_in(int64_t Nc, const int32_t* cell_in, const int32_t* zin, uint8_t* zone, int* err) {
+  GS(c, Nc) {
+    const int32_t z = zin[cell_in[c]];
+    if (z != 0 && z != 1) atomicOr(err, 1);
+    zone[c] = z == 1 ? 1 : 0;
+  }
+}
+
+fvs_status mesh_set_zones(fvs_mesh m, const int32_t* zone_host) {
+  cudaStream_t s = m->stream;
+  const int64_t Nc = m->Nc;
+  DBuf<int32_t> zin;
+  DBuf<int> err;
+  FVS_TRY(zin.alloc(Nc + 1));
+  FVS_TRY(err.alloc(1));
+  FVS_TRY(err.zero(s));
+  FVS_CUDA(cudaMemcpyAsync(zin.p, zone_host, Nc * sizeof(int32_t), cudaMemcpyHostToDevice, s));
+  k_zone_in<<<stride_grid(Nc, 256), 256, 0, s>>>(Nc, m->cell_in, zin, m->zone, err); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  int h = 0;
+  FVS_CUDA(cudaMemcpyAsync(&h, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FVS_CUDA(cudaStreamSynchronize(s));
+  if (h) {
+    set_error("cell zones must be 0 (metal) or 1 (mold)");
+    return FVS_ERR_ARG;
+  }
   return FVS_OK;
 }
 
@@ -606,8 +662,12 @@ fvs_status mesh_build(fvs_mesh m, const double* nodes, int64_t Nv, const int32_t
   FVS_TRY(m->A.alloc(Nf)); FVS_TRY(m->nrm.alloc(3 * Nf)); FVS_TRY(m->cd.alloc(Nf)); FVS_TRY(m->ce.alloc(Nf));
   FVS_TRY(m->cz.alloc(Nf)); FVS_TRY(m->Jinv.alloc(9 * Nf)); FVS_TRY(m->V.alloc(Nc));
   k_cell_centres<<<stride_grid(Nc, 256), 256, 0, s>>>(Nc, Nv, Xn, cn, xc); FVS_COUNT_LAUNCH();
+  FVS_TRY(m->dof.alloc(Nf)); FVS_TRY(m->dnf.alloc(Nf));
+  FVS_TRY(m->zone.alloc(Nc));
+  FVS_TRY(m->zone.zero(s));   // every cell metal until fvs_mesh_set_zones says otherwise
   k_face_geometry<<<stride_grid(Nf, 128), 128, 0, s>>>(Nf, Nv, Nc, Xn, xc, m->fv, m->own, m->nei, m->A, m->nrm,
-                                                      m->cd, m->ce, m->cz, m->Jinv, xs, skew, err); FVS_COUNT_LAUNCH();
+                                                      m->cd, m->ce, m->cz, m->Jinv, xs, skew, m->dof, m->dnf, err);
+  FVS_COUNT_LAUNCH();
   k_volumes<<<stride_grid(Nc, 256), 256, 0, s>>>(Nc, m->cf, m->cfs, xs, m->V, err); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   FVS_TRY(check_err(err, s, "geometry"));

@@ -38,6 +38,8 @@ struct fvs_mesh_s {
   fvs::DBuf<double> nrm;     // [3*Nf] unit normal (owner -> neighbour)
   fvs::DBuf<double> cd, ce, cz;   // [Nf] A (1/(n.d) + w0), A w1, A w2 (Eq. 11-12)
   fvs::DBuf<double> Jinv;    // [9*Nf] inverse local Jacobian, row-major per face (slot-major)
+  fvs::DBuf<double> dof, dnf; // [Nf] owner / neighbour centre to face centre distances (0 on walls)
+  fvs::DBuf<uint8_t> zone;   // [Nc] 0 metal, 1 mold (all 0 unless set)
 
   // base operators over nb(c), unit coefficient (Eq. 10-12):
   // Lu: velocity diffusion, no-slip walls; Pb: pressure, all cells flowing
@@ -49,8 +51,15 @@ fvs_status mesh_build(fvs_mesh m, const double* nodes, int64_t Nv, const int32_t
                       const int32_t* faces, int64_t Nf, const int32_t* fcells, const int32_t* patch,
                       int reorder);
 
+// Cell zones (caller's cell order): 0 metal, 1 mold.
+fvs_status mesh_set_zones(fvs_mesh m, const int32_t* zone_host);
+
 // Assemble the unit temperature operator with wall data: L (same pattern as
 // Lu) and constant l (Dirichlet walls).  bc_type/bc_T indexed by patch.
+// With kf (per face) each face's flux is scaled by it (the conductive
+// operator); faces with gint > 0 (metal-mold interface) carry only
+// gint (T_C2 - T_C1).
 fvs_status assemble_temperature_operator(fvs_mesh m, const int32_t* d_bc_type, const double* d_bc_T,
-                                         Ell& LT, double* lT, cudaStream_t s);
+                                         Ell& LT, double* lT, cudaStream_t s, const double* kf = nullptr,
+                                         const double* gint = nullptr);
 }  // namespace fvs

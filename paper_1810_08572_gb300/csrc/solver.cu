@@ -40,10 +40,10 @@ __device__ __forceinline__ double solid_fraction_slope(double T, double Ts, doub
 // counts: [1] cells whose tag changed, [2] LM cells outside the current
 // system numbering (melted), [3] numbered cells that are no longer LM, [4] LM cells
 __global__ void k_tag(int64_t Nc, const double* T, double Ts, uint8_t* lm, int32_t* flag, double* u, double* uold,
-                      int* counts, const int32_t* map, int numbered) {
+                      int* counts, const int32_t* map, int numbered, const uint8_t* metal) {
   int ch = 0, melted = 0, dead = 0, nlm = 0;
   GS(c, Nc) {
-    const bool l = T[c] > Ts;
+    const bool l = metal[c] && T[c] > Ts;   // mold cells are never liquid/mushy
     ch += (lm[c] != (uint8_t)l) ? 1 : 0;
     if (numbered) {
       const bool in = map[c] >= 0;
@@ -450,10 +450,11 @@ __global__ void k_cell_correct(int64_t Nc, int64_t Nf, const uint8_t* lm, const 
 // ---------------------------------------------------------------------------
 // 5. energy with latent heat (Eq. 4, Eq. 18-20)
 // ---------------------------------------------------------------------------
+// Lval / lT: the conductive operator (conductivities inside); rcp = rho cp per cell
 __global__ void k_energy_base(int64_t Nc, int W, const int32_t* cf, const int8_t* cfs, const int32_t* own,
                               const int32_t* nei, const double* F, const double* Fold, const double* T,
                               const double* Told, const int32_t* Lcol, const double* Lval, const double* lT,
-                              const double* V, Mat m, double dt, double* base) {
+                              const double* V, const double* rcp, double dt, double* base) {
   GS(c, Nc) {
     double cn = 0.0, co = 0.0;
     for (int s = 0; s < 6; ++s) {
@@ -466,21 +467,21 @@ __global__ void k_energy_base(int64_t Nc, int W, const int32_t* cf, const int8_t
     }
     double lt = 0.0;
     for (int k = 0; k < W; ++k) lt += Lval[(int64_t)k * Nc + c] * T[Lcol[(int64_t)k * Nc + c]];
-    base[c] = m.rho * m.cp * V[c] / dt * T[c] - m.rho * m.cp * (1.5 * cn - 0.5 * co) + 0.5 * m.k * lt +
-              m.k * lT[c];
+    base[c] = rcp[c] * V[c] / dt * T[c] - rcp[c] * (1.5 * cn - 0.5 * co) + 0.5 * lt + lT[c];
   }
 }
 
 // source linearisation at the current iterate (Eq. 20): S_p, S_c
 __global__ void k_energy_lin(int64_t Nc, const double* V, Mat m, double dt, const double* Tm, const double* fsm,
-                             const double* fsn, const double* base, double* dextra, double* rhs, double* x) {
+                             const double* fsn, const double* base, double* dextra, double* rhs, double* x,
+                             const double* rcp, const double* rL, const uint8_t* metal) {
   GS(c, Nc) {
     const double t = Tm[c];
-    const double dfs = solid_fraction_slope(t, m.Ts, m.Tl);
-    const double a = m.rho * m.L * V[c] / dt;
+    const double dfs = metal[c] ? solid_fraction_slope(t, m.Ts, m.Tl) : 0.0;
+    const double a = rL[c] * V[c] / dt;
     const double Sp = a * dfs;
     const double Sc = a * (fsm[c] - fsn[c] - dfs * t);
-    dextra[c] = m.rho * m.cp * V[c] / dt - Sp;
+    dextra[c] = rcp[c] * V[c] / dt - Sp;
     rhs[c] = base[c] + Sc;
     x[c] = t;
   }
@@ -489,8 +490,13 @@ __global__ void k_energy_lin(int64_t Nc, const double* V, Mat m, double dt, cons
 // enthalpy-to-temperature inversion of the linearised update:
 // H = cp T_lin + L (1 - fs^m - dfs (T_lin - T^m)), T = H^-1(H), fs = fs(T)
 __global__ void k_energy_update(int64_t Nc, Mat m, const double* Tlin, const double* Tm, const double* fsm,
-                                double* Tnext, double* fsnext) {
+                                double* Tnext, double* fsnext, const uint8_t* metal) {
   GS(c, Nc) {
+    if (!metal[c]) {      // mold: no latent heat
+      Tnext[c] = Tlin[c];
+      fsnext[c] = 0.0;
+      continue;
+    }
     const double t = Tm[c];
     const double dfs = solid_fraction_slope(t, m.Ts, m.Tl);
     const double H = m.cp * Tlin[c] + m.L * (1.0 - fsm[c] - dfs * (Tlin[c] - t));
@@ -515,16 +521,17 @@ __global__ void k_count_u8(int64_t n, const uint8_t* a, int* out) {
 // (the loop converges to the same discrete solution from any start, within
 // its stop rule; this start is closer)
 __global__ void k_energy_guess(int64_t Nc, const double* T, const double* Told, double Ts, double Tl, double* Tm,
-                               double* fsm) {
+                               double* fsm, const uint8_t* metal) {
   GS(c, Nc) {
     const double t = 2.0 * T[c] - Told[c];
     Tm[c] = t;
-    fsm[c] = solid_fraction(t, Ts, Tl);
+    fsm[c] = metal[c] ? solid_fraction(t, Ts, Tl) : 0.0;
   }
 }
 __global__ void k_crossings(int64_t Nc, const double* Tn, const double* Tnew, double Ts, double Tl, double time,
-                            double dt, double* tliq, double* tsol) {
+                            double dt, double* tliq, double* tsol, const uint8_t* metal) {
   GS(c, Nc) {
+    if (!metal[c]) continue;
     const double a = Tn[c], b = Tnew[c];
     if (tliq[c] < 0.0 && a > Tl && b <= Tl) tliq[c] = time + dt * (a - Tl) / (a - b);
     if (tsol[c] < 0.0 && a > Ts && b <= Ts) tsol[c] = time + dt * (a - Ts) / (a - b);
@@ -536,22 +543,59 @@ __global__ void k_crossings(int64_t Nc, const double* Tn, const double* Tnew, do
 // ---------------------------------------------------------------------------
 __global__ void k_init_state(int64_t Nc, const int32_t* cell_in, const double* Tin, double Tuni, const double* uin,
                              Mat m, double* T, double* Told, double* fs, double* u, double* uold, double* p,
-                             double* tliq, double* tsol) {
+                             double* tliq, double* tsol, const uint8_t* metal, double T_mold) {
   GS(c, Nc) {
     const int32_t o = cell_in[c];
-    const double t = Tin ? Tin[o] : Tuni;
+    const bool me = metal[c] != 0;
+    const double t = Tin ? Tin[o] : (me ? Tuni : T_mold);
     T[c] = t;
     Told[c] = t;
-    fs[c] = solid_fraction(t, m.Ts, m.Tl);
-    const bool solid = !(t > m.Ts);
+    fs[c] = me ? solid_fraction(t, m.Ts, m.Tl) : 0.0;
+    const bool solid = !(me && t > m.Ts);
     for (int d = 0; d < 3; ++d) {
       const double v = (uin && !solid) ? uin[3 * (int64_t)o + d] : 0.0;
       u[d * Nc + c] = v;
       uold[d * Nc + c] = v;
     }
     p[c] = 0.0;
-    tliq[c] = t <= m.Tl ? 0.0 : -1.0;
-    tsol[c] = t <= m.Ts ? 0.0 : -1.0;
+    tliq[c] = me && t <= m.Tl ? 0.0 : -1.0;
+    tsol[c] = me && t <= m.Ts ? 0.0 : -1.0;
+  }
+}
+
+// materials per cell and conductance per face (metal and, with a mold
+// material, mold zones; Section 2.4.4 energy equation on all cells)
+struct MoldMat {
+  int on;
+  double rho_cp, k, rho_L;
+  double mold_rho_cp, mold_k, h;
+  MoldMat(int on_, double rho, double cp, double k_, double rhoL, double mrho, double mcp, double mk, double h_)
+      : on(on_), rho_cp(rho * cp), k(k_), rho_L(rhoL), mold_rho_cp(mrho * mcp), mold_k(mk), h(h_) {}
+};
+__global__ void k_cell_materials(int64_t Nc, const uint8_t* zone, MoldMat mm, uint8_t* metal, double* rcp,
+                                 double* rL) {
+  GS(c, Nc) {
+    const bool me = !mm.on || zone[c] == 0;
+    metal[c] = me ? 1 : 0;
+    rcp[c] = me ? mm.rho_cp : mm.mold_rho_cp;
+    rL[c] = me ? mm.rho_L : 0.0;
+  }
+}
+// kf: conductivity of the owner's zone; gint > 0 on a face between a metal
+// and a mold cell: A / (d_own/k_own + 1/h + d_nei/k_nei)
+__global__ void k_face_conductance(int64_t Nf, const int32_t* own, const int32_t* nei, const uint8_t* metal,
+                                   const double* A, const double* dof, const double* dnf, MoldMat mm, double* kf,
+                                   double* gint) {
+  GS(f, Nf) {
+    const int32_t o = own[f], q = nei[f];
+    const double ko = metal[o] ? mm.k : mm.mold_k;
+    kf[f] = ko;
+    double g = 0.0;
+    if (q >= 0 && metal[o] != metal[q]) {
+      const double kq = metal[q] ? mm.k : mm.mold_k;
+      g = A[f] / (dof[f] / ko + 1.0 / mm.h + dnf[f] / kq);
+    }
+    gint[f] = g;
   }
 }
 
@@ -634,7 +678,36 @@ fvs_status solver_alloc(fvs_solver s) {
   return FVS_OK;
 }
 
+static fvs_status apply_properties(fvs_solver s, const fvs_props* p);
+
 fvs_status solver_set_properties(fvs_solver s, const fvs_props* p) {
+  s->has_mold = false;   // new properties: every cell metal until fvs_set_mold
+  return apply_properties(s, p);
+}
+
+fvs_status solver_set_mold(fvs_solver s, double rho, double cp, double k, double h, double T_init) {
+  if (!s->have_props) {
+    set_error("fvs_set_properties must come first");
+    return FVS_ERR_STATE;
+  }
+  if (!(rho > 0 && cp > 0 && k > 0 && h > 0)) {
+    set_error("invalid mold data (rho, cp, k and h must be positive)");
+    return FVS_ERR_ARG;
+  }
+  s->has_mold = true;
+  s->mold_rho = rho;
+  s->mold_cp = cp;
+  s->mold_k = k;
+  s->mold_h = h;
+  s->mold_T = T_init;
+  std::vector<fvs_patch_bc> bc = s->bc;
+  fvs_props p = s->props;
+  p.bc = bc.data();
+  p.n_patches = (int32_t)bc.size();
+  return apply_properties(s, &p);
+}
+
+static fvs_status apply_properties(fvs_solver s, const fvs_props* p) {
   fvs_mesh m = s->mesh;
   if (p->n_patches < m->npatch || (p->n_patches > 0 && !p->bc)) {
     set_error("props give %d wall patches, the mesh uses %d", p->n_patches, m->npatch);
@@ -665,12 +738,24 @@ fvs_status solver_set_properties(fvs_solver s, const fvs_props* p) {
   FVS_TRY(s->bc_T.alloc(np));
   FVS_CUDA(cudaMemcpyAsync(s->bc_type.p, ht.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, s->stream));
   FVS_CUDA(cudaMemcpyAsync(s->bc_T.p, hT.data(), np * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-  FVS_TRY(assemble_temperature_operator(m, s->bc_type, s->bc_T, s->LT, s->lT, s->stream));
-  // Ke = -k/2 LT with the same pattern
+  // materials per cell (zones count only with a mold material) and the
+  // conductive operator: k_f times the face gradient, the series flux on
+  // metal-mold faces
+  FVS_TRY(s->metal.alloc(m->Nc)); FVS_TRY(s->rcp.alloc(m->Nc)); FVS_TRY(s->rL.alloc(m->Nc));
+  FVS_TRY(s->kface.alloc(m->Nf)); FVS_TRY(s->gint.alloc(m->Nf));
+  const MoldMat mm{s->has_mold ? 1 : 0, mt.rho, mt.cp, mt.k, mt.rho * mt.latent, s->mold_rho, s->mold_cp, s->mold_k,
+                   s->mold_h};
+  k_cell_materials<<<stride_grid(m->Nc, 256), 256, 0, s->stream>>>(m->Nc, m->zone, mm, s->metal, s->rcp, s->rL);
+  FVS_COUNT_LAUNCH();
+  k_face_conductance<<<stride_grid(m->Nf, 256), 256, 0, s->stream>>>(m->Nf, m->own, m->nei, s->metal, m->A, m->dof,
+                                                                     m->dnf, mm, s->kface, s->gint);
+  FVS_COUNT_LAUNCH();
+  FVS_TRY(assemble_temperature_operator(m, s->bc_type, s->bc_T, s->LT, s->lT, s->stream, s->kface, s->gint));
+  // Ke = -1/2 L (conductivities inside L) with the same pattern
   FVS_TRY(s->Ke.alloc(m->Nc, m->W));
   k_copy_i<<<stride_grid((int64_t)m->Nc * m->W, 256), 256, 0, s->stream>>>((int64_t)m->Nc * m->W, s->LT.col,
                                                                             s->Ke.col); FVS_COUNT_LAUNCH();
-  k_scale_ell<<<stride_grid(m->Nc, 256), 256, 0, s->stream>>>(m->Nc, m->W, -0.5 * mt.k, s->LT.val, s->LT.diag,
+  k_scale_ell<<<stride_grid(m->Nc, 256), 256, 0, s->stream>>>(m->Nc, m->W, -0.5, s->LT.val, s->LT.diag,
                                                              s->Ke.val, s->Ke.diag); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   s->have_props = true;
@@ -700,7 +785,9 @@ fvs_status solver_set_state(fvs_solver s, const double* T, const double* u, int 
   }
   const Mat mt = mat_of(s->props);
   k_init_state<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, m->cell_in, pT, s->props.T_init, pu, mt, s->T, s->Told,
-                                                     s->fs, s->u, s->uold, s->p, s->tliq, s->tsol); FVS_COUNT_LAUNCH();
+                                                     s->fs, s->u, s->uold, s->p, s->tliq, s->tsol, s->metal,
+                                                     s->mold_T);
+  FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   FVS_TRY(s->F.zero(st)); FVS_TRY(s->Fold.zero(st)); FVS_TRY(s->Fnew.zero(st));
   FVS_TRY(s->ustar.zero(st));
@@ -742,7 +829,7 @@ static fvs_status classify(fvs_solver s) {
   FVS_TRY(s->flag.zero(st));
   FVS_TRY(s->cnt.zero(st));
   k_tag<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, mt.Ts, s->lm, s->flag, s->u, s->uold, s->cnt.p,
-                                               s->map, s->numbered ? 1 : 0);
+                                               s->map, s->numbered ? 1 : 0, s->metal);
   FVS_COUNT_LAUNCH();
   int tc[5];
   FVS_CUDA(cudaMemcpyAsync(tc, s->cnt.p, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1029,8 +1116,8 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
 
   // 5. energy: linearised latent heat, inner solve, enthalpy inversion
   k_energy_base<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, m->W, m->cf, m->cfs, m->own, m->nei, s->F, s->Fold, s->T,
-                                                      s->Told, s->LT.col, s->LT.val, s->lT, m->V, mt, dt, s->ebase); FVS_COUNT_LAUNCH();
-  k_energy_guess<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, s->Told, mt.Ts, mt.Tl, s->Tnew, s->fsnew);
+                                                      s->Told, s->LT.col, s->LT.val, s->lT, m->V, s->rcp, dt, s->ebase); FVS_COUNT_LAUNCH();
+  k_energy_guess<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, s->Told, mt.Ts, mt.Tl, s->Tnew, s->fsnew, s->metal);
   FVS_COUNT_LAUNCH();
   {
     JacobiPrecond J;
@@ -1047,7 +1134,8 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
       // of the nonlinear change; the last passes reach e_rtol
       const double rtol_m = std::max(s->props.e_rtol, std::min(1e-4, 1e-5 * dT_prev));
       k_energy_lin<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, m->V, mt, dt, Tm, fsm, s->fs, s->ebase, s->edx,
-                                                          s->erhs, s->Tlin); FVS_COUNT_LAUNCH();
+                                                          s->erhs, s->Tlin, s->rcp, s->rL, s->metal);
+      FVS_COUNT_LAUNCH();
       FVS_LAUNCH_CHECK();
       SolveResult r;
       FVS_TRY(bicgstab(st, s->red, s->kw, s->Ke, s->edx, J, s->erhs, s->Tlin, rtol_m,
@@ -1058,7 +1146,8 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
         set_error("energy pass %d: relative residual %.3e after %d iterations", it, r.relres, r.iters);
       }
       // next iterate, then its change against the current one
-      k_energy_update<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, mt, s->Tlin, Tm, fsm, s->Tit, s->fsit); FVS_COUNT_LAUNCH();
+      k_energy_update<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, mt, s->Tlin, Tm, fsm, s->Tit, s->fsit, s->metal);
+      FVS_COUNT_LAUNCH();
       FVS_LAUNCH_CHECK();
       FVS_TRY(s->red.max_abs_diff2(st, Nc, s->Tit, Tm, s->fsit, fsm, S_TMP0, S_TMP1));
       dswap(s->Tit, Tm);
@@ -1078,7 +1167,9 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
   }
 
   // 6. crossing times, then rotate the time levels
-  k_crossings<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, s->Tnew, mt.Ts, mt.Tl, s->time, dt, s->tliq, s->tsol); FVS_COUNT_LAUNCH();
+  k_crossings<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, s->Tnew, mt.Ts, mt.Tl, s->time, dt, s->tliq, s->tsol,
+                                                    s->metal);
+  FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   dswap(s->Told, s->T);     // Told <- T^n
   dswap(s->T, s->Tnew);     // T <- T^{n+1}

@@ -27,6 +27,9 @@ struct fvs_solver_s {
   int64_t nlm = 0;            // liquid + mushy cells
   fvs_props props{};
   std::vector<fvs_patch_bc> bc;
+  // mold zone (conduction only) and the metal-mold interface coefficient
+  bool has_mold = false;
+  double mold_rho = 0.0, mold_cp = 0.0, mold_k = 0.0, mold_h = 0.0, mold_T = 0.0;
   double time = 0.0;
   int64_t nstep = 0;
 
@@ -39,6 +42,9 @@ struct fvs_solver_s {
   // wall data and the energy operator (-k/2 times the unit operator)
   fvs::DBuf<int32_t> bc_type;
   fvs::DBuf<double> bc_T;
+  fvs::DBuf<uint8_t> metal;        // [Nc] 1 metal, 0 mold
+  fvs::DBuf<double> rcp, rL;       // [Nc] rho cp and rho L (0 in the mold)
+  fvs::DBuf<double> kface, gint;   // [Nf] face conductivity, interface conductance
   fvs::Ell LT;            // unit temperature operator
   fvs::DBuf<double> lT;   // its constant part from fixed-temperature walls
   fvs::Ell Ke;            // -k/2 LT
@@ -76,6 +82,7 @@ struct fvs_solver_s {
 namespace fvs {
 fvs_status solver_alloc(fvs_solver s);
 fvs_status solver_set_properties(fvs_solver s, const fvs_props* p);
+fvs_status solver_set_mold(fvs_solver s, double rho, double cp, double k, double h, double T_init);
 fvs_status solver_set_state(fvs_solver s, const double* T, const double* u, int on_device);
 fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* st);
 fvs_status solver_pressure_solve(fvs_solver s, const double* rhs, double* p_out, double rtol, int* iters,

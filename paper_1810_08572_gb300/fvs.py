@@ -95,6 +95,8 @@ _SIGS = {
     "fvs_solver_create": ([_P, _P, C.POINTER(_P)], C.c_int),
     "fvs_solver_destroy": ([_P], C.c_int),
     "fvs_set_properties": ([_P, C.POINTER(fvs_props)], C.c_int),
+    "fvs_mesh_set_zones": ([_P, _P], C.c_int),
+    "fvs_set_mold": ([_P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double], C.c_int),
     "fvs_set_state": ([_P, _P, _P, C.c_int], C.c_int),
     "fvs_step": ([_P, C.c_double, C.c_int32, C.POINTER(fvs_step_stats)], C.c_int),
     "fvs_pressure_solve": ([_P, _P, _P, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double)], C.c_int),
@@ -188,6 +190,9 @@ class Mesh:
         self.info = info.as_dict()
         self.n_cells = info.n_cells
         self.n_faces = info.n_faces
+        if mesh.get("cell_zone") is not None:     # 0 metal, 1 mold
+            zone = np.ascontiguousarray(mesh["cell_zone"], dtype=np.int32)
+            check(fvs_mesh_set_zones(h, _ptr(zone)), "fvs_mesh_set_zones")
 
     def geometry(self, which):
         n = self.n_cells if which == 0 else self.n_faces
@@ -300,8 +305,14 @@ class Solver:
         self.set_properties(props)
 
     def set_properties(self, props):
+        """props as from fvs_inputs.cases.props; an optional props["mold"] =
+        dict(rho, cp, k, h, T_init) gives the mold zone its material."""
         self._props = make_props(props)
         check(fvs_set_properties(self.h, C.byref(self._props)), "fvs_set_properties")
+        mold = props.get("mold")
+        if mold is not None:
+            check(fvs_set_mold(self.h, float(mold["rho"]), float(mold["cp"]), float(mold["k"]), float(mold["h"]),
+                               float(mold["T_init"])), "fvs_set_mold")
 
     def set_state(self, T, u=None):
         """T [n_cells], u [n_cells, 3] (host numpy or device tensors, input numbering)."""

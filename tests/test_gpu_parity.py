@@ -7,7 +7,7 @@ the largest magnitude of each field.
 import numpy as np
 import pytest
 
-from fvs_inputs import box_mesh, cases
+from fvs_inputs import box_mesh, cases, zones_inner_box
 from oracle.fv import Oracle
 from tests.helpers import frozen_corner_field, set_state
 
@@ -141,6 +141,45 @@ def test_large_coarsest_level(fvs, monkeypatch):
     st = S.step(1e-3)
     assert st["amg_levels"] >= 2 and st["fallback"] == 0 and st["p_its"] < 200, st
     compare(o, S, 1e-10)
+
+
+MOLD = dict(rho=7800.0, cp=500.0, k=30.0, h=2000.0, T_init=500.0)
+
+
+def mold_case():
+    """Jittered cavity: a metal column through the middle, mold around it,
+    every outer wall (mold surface) held at 500 K."""
+    m = box_mesh(12, 12, 4, cases.CAVITY, jitter=0.2, jitter_seed=91, permute_seed=92)
+    m = dict(m, cell_zone=zones_inner_box(m, (0.025, 0.025, -1.0), (0.075, 0.075, 1.0)))
+    props = cases.props(walls=cases.all_walls(500.0), T_init=950.0, mold=MOLD, **TIGHT)
+    return m, props
+
+
+def test_mold_one_step(fvs):
+    """Metal in a mold (conduction-only cells, interface coefficient h): one
+    step equals the oracle's, fields within 1e-10."""
+    m, props = mold_case()
+    o, M, S = make_pair(fvs, m, props)
+    assert (~o.metal).sum() > 0 and o.interface.sum() > 0
+    o.step(1e-3)
+    S.step(1e-3)
+    compare(o, S, 1e-10)
+
+
+def test_mold_forty_steps(fvs):
+    """Forty steps of the metal column in its mold: temperature within 1e-8 K
+    of the oracle everywhere (metal and mold), velocity within 1e-8 relative,
+    no velocity in the mold."""
+    m, props = mold_case()
+    o, M, S = make_pair(fvs, m, props)
+    for _ in range(40):
+        o.step(2e-3)
+    S.step(2e-3, 40)
+    assert np.abs(S.query("T") - o.T).max() <= 1e-8
+    U = S.query("U")
+    assert rel(U, o.u) <= 1e-8
+    assert np.abs(U[~o.metal]).max() == 0.0
+    np.testing.assert_allclose(S.query("CROSS"), np.stack([o.t_liq, o.t_sol], 1), atol=1e-9)
 
 
 def test_two_hundred_steps_cavity(fvs):
