@@ -22,6 +22,10 @@ AL_ALLOY = dict(
     darcy_C=1e8, darcy_eps=1e-3,
 )
 
+# the same alloy with the smeared Gulliver-Scheil solid fraction: partition
+# coefficient and freezing temperature of an Al-Si-like alloy, smear width 2 K
+AL_SI_SCHEIL = dict(AL_ALLOY, fs_model=1, kp=0.13, T_f=933.0, T_eps=2.0)
+
 CAVITY = (0.1, 0.1, 0.0125)
 
 

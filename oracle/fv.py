@@ -24,8 +24,12 @@ Readings of points the paper leaves open (each is listed in the design doc too):
  * the energy equation uses the same Crank-Nicolson diffusion and
    Adams-Bashforth convection as the momentum predictor (Eq. 6), with the
    flux level matching each temperature level
- * the solid fraction is linear between solidus and liquidus; at the kinks
-   the derivative is taken from the mushy side
+ * the solid fraction is linear between solidus and liquidus, or (material
+   "fs_model" = 1) the Gulliver-Scheil law smeared near the solidus (Eq. 21,
+   with partition coefficient kp, freezing temperature T_f and smear width
+   T_eps); at each kink the derivative is taken from the side nearer the
+   mushy interior (the Scheil side at T_liq and at T_sol + T_eps, the smear
+   side at T_sol - T_eps); the tags stay T > T_sol in both laws
  * an LM cell none of whose faces carries flow is left out of the pressure
    system (its pressure is 0) and is treated like a solid cell when face
    gradients are smeared
@@ -212,15 +216,51 @@ def temperature_diffusion(g, walls, k_face=None, interface=None, G_int=None):
 
 
 # ----------------------------------------------------------------------------
-# Material laws (Eq. 3, Eq. 5 in its linear form, Eq. 22-23)
+# Material laws (Eq. 3, Eq. 5 in its linear form, Eq. 21, Eq. 22-23)
 # ----------------------------------------------------------------------------
-def solid_fraction(T, T_sol, T_liq):
-    return np.clip((T_liq - T) / (T_liq - T_sol), 0.0, 1.0)
+def scheil_law(m):
+    """(kp, T_f, T_eps) of the smeared Gulliver-Scheil law if the material
+    selects it (fs_model = 1), else None (linear solid fraction)."""
+    if int(m.get("fs_model", 0)) == 1:
+        return (float(m["kp"]), float(m["T_f"]), float(m["T_eps"]))
+    return None
 
 
-def solid_fraction_slope(T, T_sol, T_liq):
-    """dfs/dT, taken from the mushy side at the kinks."""
-    return np.where((T >= T_sol) & (T <= T_liq), -1.0 / (T_liq - T_sol), 0.0)
+def _scheil_core(T, T_liq, kp, T_f):
+    """Eq. 5 between the liquidus and the smear: 1 - r^(1/(kp-1)) with
+    r = (T - T_f)/(T_liq - T_f) (both differences negative), and its slope."""
+    e = 1.0 / (kp - 1.0)
+    r = (T - T_f) / (T_liq - T_f)
+    return 1.0 - r ** e, -e * r ** (e - 1.0) / (T_liq - T_f)
+
+
+def solid_fraction(T, T_sol, T_liq, scheil=None):
+    """fs(T): linear between T_sol and T_liq, or Eq. 21 when scheil =
+    (kp, T_f, T_eps) is given."""
+    T = np.asarray(T, dtype=np.float64)
+    if scheil is None:
+        return np.clip((T_liq - T) / (T_liq - T_sol), 0.0, 1.0)
+    kp, T_f, T_eps = scheil
+    T1, T2 = T_sol - T_eps, T_sol + T_eps
+    f_hat = _scheil_core(T2, T_liq, kp, T_f)[0]
+    Tc = np.clip(T, T2, T_liq)                      # keeps the power's base positive
+    f_sch = _scheil_core(Tc, T_liq, kp, T_f)[0]
+    f_smr = f_hat - (T - T2) * (1.0 - f_hat) / (2.0 * T_eps)
+    return np.where(T > T_liq, 0.0, np.where(T <= T1, 1.0, np.where(T < T2, f_smr, f_sch)))
+
+
+def solid_fraction_slope(T, T_sol, T_liq, scheil=None):
+    """dfs/dT, taken at each kink from the side nearer the mushy interior."""
+    T = np.asarray(T, dtype=np.float64)
+    if scheil is None:
+        return np.where((T >= T_sol) & (T <= T_liq), -1.0 / (T_liq - T_sol), 0.0)
+    kp, T_f, T_eps = scheil
+    T1, T2 = T_sol - T_eps, T_sol + T_eps
+    f_hat = _scheil_core(T2, T_liq, kp, T_f)[0]
+    Tc = np.clip(T, T2, T_liq)
+    d_sch = _scheil_core(Tc, T_liq, kp, T_f)[1]
+    d_smr = -(1.0 - f_hat) / (2.0 * T_eps)
+    return np.where((T > T_liq) | (T < T1), 0.0, np.where(T < T2, d_smr, d_sch))
 
 
 def darcy_coefficient(fs, C, eps):
@@ -319,7 +359,8 @@ class Oracle:
         self.Deta_p = (g.E31 @ g.Pavg).tocsr()
         self.Dzeta_p = (g.E42 @ g.Pavg).tocsr()
         self.T = np.where(self.metal, props["T_init"], mold["T_init"] if mold else props["T_init"])
-        self.fs = np.where(self.metal, solid_fraction(self.T, m["T_sol"], m["T_liq"]), 0.0)
+        self.scheil = scheil_law(m)
+        self.fs = self.fs_of(self.T)
         self.T_old = self.T.copy()
         self.u = np.zeros((g.Nc, 3))
         self.u_old = np.zeros((g.Nc, 3))
@@ -333,6 +374,11 @@ class Oracle:
         self.stats = {}
 
     # -- helpers ---------------------------------------------------------------
+    def fs_of(self, T):
+        """Solid fraction of every cell at temperatures T (0 in the mold)."""
+        m = self.m
+        return np.where(self.metal, solid_fraction(T, m["T_sol"], m["T_liq"], self.scheil), 0.0)
+
     def conv(self, phi, F):
         """Conv(phi, F)_c = sum_f sigma F_f (phi_C1 + phi_C2)/2 (walls carry F = 0)."""
         return self.g.Div @ (F * (self.g.Avg @ phi))
@@ -458,7 +504,7 @@ class Oracle:
         g, m = self.g, self.m
         rcp, rL = self.rcp, self.rL
         conv = 1.5 * self.conv(T_n, F_n) - 0.5 * self.conv(T_o, F_o)
-        fs = np.where(self.metal, solid_fraction(T, m["T_sol"], m["T_liq"]), 0.0)
+        fs = self.fs_of(T)
         return (rcp * g.V / dt * (T - T_n) + rcp * conv
                 - 0.5 * (self.LTk @ T + self.lTk) - 0.5 * (self.LTk @ T_n + self.lTk)
                 - rL * g.V / dt * (fs - fs_n))
@@ -479,7 +525,7 @@ class Oracle:
         T, fs = T_n.copy(), fs_n.copy()
         tolT = self.props.get("oracle_tol_T", 1e-11)
         for it in range(1, 200):
-            dfs = np.where(metal, solid_fraction_slope(T, Ts, Tl), 0.0)
+            dfs = np.where(metal, solid_fraction_slope(T, Ts, Tl, self.scheil), 0.0)
             Sp = rL * g.V / dt * dfs
             Sc = rL * g.V / dt * (fs - fs_n - dfs * T)
             A = (K + sp.diags(rcp * g.V / dt - Sp)).tocsr()
@@ -488,8 +534,8 @@ class Oracle:
                 T_next = T_lin
             else:
                 H = cp * T_lin + L * (1.0 - fs - dfs * (T_lin - T))
-                T_next = np.where(metal, temperature_from_enthalpy(H, cp, L, Ts, Tl), T_lin)
-            fs_next = np.where(metal, solid_fraction(T_next, Ts, Tl), 0.0)
+                T_next = np.where(metal, temperature_from_enthalpy(H, cp, L, Ts, Tl, self.scheil), T_lin)
+            fs_next = self.fs_of(T_next)
             dT = np.max(np.abs(T_next - T))
             dF = np.max(np.abs(fs_next - fs))
             T, fs = T_next, fs_next
@@ -523,10 +569,31 @@ class Oracle:
         return self
 
 
-def temperature_from_enthalpy(H, cp, L, T_sol, T_liq):
-    """Invert H(T) = cp T + L (1 - fs(T)) with linear fs: piecewise linear,
-    strictly increasing."""
-    H_sol = cp * T_sol
-    H_liq = cp * T_liq + L
-    T_mush = T_sol + (H - H_sol) / (H_liq - H_sol) * (T_liq - T_sol)
-    return np.where(H <= H_sol, H / cp, np.where(H >= H_liq, (H - L) / cp, T_mush))
+def temperature_from_enthalpy(H, cp, L, T_sol, T_liq, scheil=None):
+    """Invert H(T) = cp T + L (1 - fs(T)), strictly increasing in T.  Linear
+    fs: piecewise linear, inverted in closed form.  Eq. 21: closed form in
+    the solid, liquid and smear pieces; bisection on the Gulliver-Scheil
+    piece (200 halvings of [T_sol + T_eps, T_liq])."""
+    H = np.asarray(H, dtype=np.float64)
+    if scheil is None:
+        H_sol = cp * T_sol
+        H_liq = cp * T_liq + L
+        T_mush = T_sol + (H - H_sol) / (H_liq - H_sol) * (T_liq - T_sol)
+        return np.where(H <= H_sol, H / cp, np.where(H >= H_liq, (H - L) / cp, T_mush))
+    kp, T_f, T_eps = scheil
+    T1, T2 = T_sol - T_eps, T_sol + T_eps
+
+    def enthalpy(T):
+        return cp * T + L * (1.0 - solid_fraction(T, T_sol, T_liq, scheil))
+
+    H1, H2, H3 = cp * T1, float(enthalpy(T2)), cp * T_liq + L
+    lo = np.full(H.shape, T2)
+    hi = np.full(H.shape, T_liq)
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        below = enthalpy(mid) < H
+        lo = np.where(below, mid, lo)
+        hi = np.where(below, hi, mid)
+    T_sch = 0.5 * (lo + hi)
+    T_smr = T1 + (H - H1) / (H2 - H1) * (T2 - T1)
+    return np.where(H <= H1, H / cp, np.where(H >= H3, (H - L) / cp, np.where(H < H2, T_smr, T_sch)))

@@ -37,12 +37,11 @@ def small_jittered_mesh(nx=8, ny=8, nz=4, seed=7, permute=True):
 
 def set_state(o, T, u=None):
     """Put an oracle into a given state (temperature, optional velocity)."""
-    from oracle.fv import solid_fraction
     m = o.m
     metal = o.metal
     o.T = np.array(T, dtype=np.float64)
     o.T_old = o.T.copy()
-    o.fs = np.where(metal, solid_fraction(o.T, m["T_sol"], m["T_liq"]), 0.0)
+    o.fs = o.fs_of(o.T)
     o.t_liq = np.where(metal & (o.T <= m["T_liq"]), 0.0, -1.0)
     o.t_sol = np.where(metal & (o.T <= m["T_sol"]), 0.0, -1.0)
     if u is not None:

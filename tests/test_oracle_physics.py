@@ -111,17 +111,20 @@ def test_stefan_linear_solid_fraction():
     assert worst[2] < 0.8 and worst[0] / worst[2] > 5.0, worst
 
 
-@pytest.mark.parametrize("with_mold", [False, True])
-def test_global_energy_balance(with_mold):
+@pytest.mark.parametrize("with_mold,scheil", [(False, False), (True, False), (False, True)])
+def test_global_energy_balance(with_mold, scheil):
     """Summed over the cavity, the energy change of a step (sensible minus
     latent) equals dt times the mean of the wall heat flow at both time
     levels: convective and interior diffusive fluxes telescope, including the
-    series flux through a metal-mold interface."""
+    series flux through a metal-mold interface; the latent part follows the
+    solid-fraction law in use (linear or Eq. 21)."""
     m = box_mesh(8, 8, 3, cases.CAVITY, jitter=0.15, jitter_seed=2)
     extra = {}
     if with_mold:
         m = dict(m, cell_zone=zones_inner_box(m, (0.02, 0.02, -1.0), (0.08, 0.08, 1.0)))
         extra = dict(mold=dict(rho=7800.0, cp=500.0, k=30.0, h=2000.0, T_init=600.0))
+    if scheil:
+        extra["material"] = cases.AL_SI_SCHEIL
     o = Oracle(m, cases.props(oracle_tol_T=1e-12, **extra))
     rng = np.random.default_rng(4)
     set_state(o, mushy_field(m), u=rng.normal(scale=1e-3, size=(len(m["cells"]), 3)))
