@@ -112,13 +112,24 @@ fvs_status fvs_mesh_geometry(fvs_mesh mesh, int which, double* dst, int64_t dst_
 /* ------------------------------------------------------------------------
  * Material and run settings.
  *  Darcy drag D = darcy_C fs^2 / ((1 - fs)^3 + darcy_eps) (Eq. 3 with the
- *  dendrite spacing folded into darcy_C); solid fraction linear between
- *  T_sol and T_liq (Eq. 5 in its linear form); buoyancy -rho beta (T - T_ref) g.
+ *  dendrite spacing folded into darcy_C); buoyancy -rho beta (T - T_ref) g.
+ *  Solid fraction (fs_model): FVS_FS_LINEAR, linear between T_sol and T_liq
+ *  (Eq. 5 in its linear form; kp, T_f, T_eps unused), or FVS_FS_SCHEIL, the
+ *  Gulliver-Scheil law fs = 1 - ((T - T_f)/(T_liq - T_f))^(1/(kp - 1)) of
+ *  Eq. 5 smeared linearly across [T_sol - T_eps, T_sol + T_eps] (Eq. 21),
+ *  which needs 0 < kp < 1, T_eps > 0 and T_sol + T_eps < T_liq < T_f.  Cells
+ *  are liquid/mushy (flowing) while T > T_sol in both laws.  A zeroed
+ *  struct tail selects the linear law.
  * ------------------------------------------------------------------------ */
+enum { FVS_FS_LINEAR = 0, FVS_FS_SCHEIL = 1 };
 typedef struct {
   double rho, k, cp, latent, T_sol, T_liq, mu, beta, T_ref;
   double g[3];
   double darcy_C, darcy_eps;
+  int32_t fs_model;   /* FVS_FS_LINEAR or FVS_FS_SCHEIL                        */
+  double kp;          /* partition coefficient (Scheil)                        */
+  double T_f;         /* freezing temperature of the solvent, K (Scheil)       */
+  double T_eps;       /* half-width of the smear band, K (Scheil)              */
 } fvs_material;
 
 enum { FVS_BC_ADIABATIC = 0, FVS_BC_DIRICHLET = 1 };

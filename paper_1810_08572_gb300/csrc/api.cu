@@ -6,6 +6,7 @@
 #include <new>
 
 #include "batch.cuh"
+#include "fslaw.cuh"
 #include "solver.cuh"
 
 namespace fvs {
@@ -364,8 +365,9 @@ FVS_API fvs_status fvs_uq_batch(fvs_mesh mesh, const fvs_props* base, int64_t n_
   }
   for (int64_t i = 0; i < n_samples; ++i) {
     const double C0 = inputs[3 * i + 2];
-    if (!(base->mat.T_liq - 5.0 * (C0 - 4.0) > base->mat.T_sol)) {
-      set_error("fvs_uq_batch: sample %lld puts the liquidus below the solidus", (long long)i);
+    if (!fs_law_valid(base->mat, base->mat.T_liq - 5.0 * (C0 - 4.0))) {
+      set_error("fvs_uq_batch: sample %lld gives a liquidus that does not suit the solid-fraction law "
+                "(below the solidus, or outside T_sol + T_eps < T_liq < T_f for Scheil)", (long long)i);
       return FVS_ERR_ARG;
     }
   }

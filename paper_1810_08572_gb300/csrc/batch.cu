@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "batch.cuh"
+#include "fslaw.cuh"
 
 namespace fvs {
 
@@ -1224,13 +1225,12 @@ static fvs_status bpcg(Batch& B, const Op& op, Prec& prec, Proj& proj, const dou
 // ---------------------------------------------------------------------------
 struct BMat {
   double rho, k, cp, L, Ts, mu, beta, Tref, g0, g1, g2, C, eps;
+  FsLaw law;    // solid fraction; its liquidus is replaced by each sample's
 };
 
-__device__ __forceinline__ double b_fs(double T, double Ts, double Tl) {
-  return fmin(fmax((Tl - T) / (Tl - Ts), 0.0), 1.0);
-}
-__device__ __forceinline__ double b_dfs(double T, double Ts, double Tl) {
-  return (T >= Ts && T <= Tl) ? -1.0 / (Tl - Ts) : 0.0;
+__device__ __forceinline__ FsLaw b_law(FsLaw w, double Tl) {
+  w.Tl = Tl;
+  return w;
 }
 
 // 1. tags (Section 2.4): LM iff T > T_sol; solid cells lose their velocity
@@ -1614,11 +1614,11 @@ __global__ void kb_energy_lin(int64_t Nc, int Sp, const double* V, BMat m, const
                               const double* Tm, const double* fsm, const double* fsn, const double* base,
                               const double* kevd, double* dextra, double* rhs, double* x, double* jd) {
   BSAMPLE;
-  const double Tl = Tliq[s];
+  const FsLaw law = b_law(m.law, Tliq[s]);
   BROW(c, Nc) {
     const int64_t e = c * Sp + s;
     const double t = Tm[e];
-    const double dfs = b_dfs(t, m.Ts, Tl);
+    const double dfs = fs_slope(law, t);
     const double a = m.rho * m.L * V[c] / dt;
     const double Sp_ = a * dfs;
     const double Sc = a * (fsm[e] - fsn[e] - dfs * t);
@@ -1635,36 +1635,32 @@ __global__ void kb_energy_update(int64_t Nc, int Sp, BMat m, const double* Tliq,
                                  const double* Tlin, const double* Tm, const double* fsm, double* Tnext,
                                  double* fsnext) {
   BSAMPLE;
-  const double Tl = Tliq[s];
+  const FsLaw law = b_law(m.law, Tliq[s]);
   const bool go = take[s] != 0;
   BROW(c, Nc) {
     const int64_t e = c * Sp + s;
     if (!go) { Tnext[e] = Tm[e]; fsnext[e] = fsm[e]; continue; }
     const double t = Tm[e];
-    const double dfs = b_dfs(t, m.Ts, Tl);
+    const double dfs = fs_slope(law, t);
     const double H = m.cp * Tlin[e] + m.L * (1.0 - fsm[e] - dfs * (Tlin[e] - t));
-    const double Hs = m.cp * m.Ts, Hl = m.cp * Tl + m.L;
-    double T;
-    if (H <= Hs) T = H / m.cp;
-    else if (H >= Hl) T = (H - m.L) / m.cp;
-    else T = m.Ts + (H - Hs) / (Hl - Hs) * (Tl - m.Ts);
+    const double T = T_of_H(law, m.cp, m.L, H);
     Tnext[e] = T;
-    fsnext[e] = b_fs(T, m.Ts, Tl);
+    fsnext[e] = fs_of(law, T);
   }
 }
 // first iterate of the latent-heat loop: T^n extrapolated linearly in time
 // (samples that no longer run keep their state)
-__global__ void kb_energy_guess(int64_t Nc, int Sp, const double* T, const double* Told, const double* fs, double Ts,
-                                const double* Tliq, const uint8_t* run, double* Tm, double* fsm) {
+__global__ void kb_energy_guess(int64_t Nc, int Sp, const double* T, const double* Told, const double* fs,
+                                FsLaw law0, const double* Tliq, const uint8_t* run, double* Tm, double* fsm) {
   BSAMPLE;
   const bool r = run[s] != 0;
-  const double Tl = Tliq[s];
+  const FsLaw law = b_law(law0, Tliq[s]);
   BROW(c, Nc) {
     const int64_t e = c * Sp + s;
     if (!r) { Tm[e] = T[e]; fsm[e] = fs[e]; continue; }
     const double t = 2.0 * T[e] - Told[e];
     Tm[e] = t;
-    fsm[e] = b_fs(t, Ts, Tl);
+    fsm[e] = fs_of(law, t);
   }
 }
 // latent-heat loop bookkeeping per sample: stop rule and the next pass's
@@ -1745,16 +1741,16 @@ __global__ void kb_qoi_final(int nb, int Sp, const double* part, double* out) {
 }
 // initial state: T = melt temperature, at rest, no crossings yet; padding
 // samples are solid and never run
-__global__ void kb_init(int64_t Nc, int64_t Nf, int Sp, const double* Tmelt, const double* Tliq, double Ts,
+__global__ void kb_init(int64_t Nc, int64_t Nf, int Sp, const double* Tmelt, const double* Tliq, FsLaw law0,
                         const uint8_t* run, double* T, double* Told, double* fs, double* u, double* uold, double* p,
                         double* tliq, double* tsol, double* F, double* Fold) {
   BSAMPLE;
-  const double t0 = run[s] ? Tmelt[s] : Ts - 1.0;
+  const double t0 = run[s] ? Tmelt[s] : law0.Ts - 1.0;
   BROW(c, Nc) {
     const int64_t e = c * Sp + s;
     T[e] = t0;
     Told[e] = t0;
-    fs[e] = b_fs(t0, Ts, Tliq[s]);
+    fs[e] = fs_of(b_law(law0, Tliq[s]), t0);
     p[e] = 0.0;
     tliq[e] = -1.0;
     tsol[e] = -1.0;
@@ -1786,7 +1782,7 @@ __global__ void kb_shared_ops(int64_t Nc, int W, double mu, double k, const int3
 static BMat bmat_of(const fvs_props& p) {
   const fvs_material& m = p.mat;
   return BMat{m.rho, m.k, m.cp, m.latent, m.T_sol, m.mu, m.beta, m.T_ref, m.g[0], m.g[1], m.g[2], m.darcy_C,
-              m.darcy_eps};
+              m.darcy_eps, fs_law_of(m)};
 }
 
 struct JacobiB {
@@ -1947,7 +1943,7 @@ static fvs_status batch_step(Batch& B, double dt, int& failures, int (&its)[4]) 
   // per-sample stop rule
   kb_energy_base<<<gc, blk, 0, st>>>(Nc, Sp, m->W, m->cf, m->cfs, m->own, m->nei, B.F, B.Fold, B.T, B.Told,
                                      B.LT.col, B.LT.val, B.lT1, B.Twall, m->V, mt, dt, B.ebase); FVS_COUNT_LAUNCH();
-  kb_energy_guess<<<gc, blk, 0, st>>>(Nc, Sp, B.T, B.Told, B.fs, mt.Ts, B.Tliq, B.run, B.Tnew, B.fsnew);
+  kb_energy_guess<<<gc, blk, 0, st>>>(Nc, Sp, B.T, B.Told, B.fs, mt.law, B.Tliq, B.run, B.Tnew, B.fsnew);
   FVS_COUNT_LAUNCH();
   kb_energy_start<<<B.tiles, 32, 0, st>>>(Sp, B.run, B.etake, B.econv, B.ertol, B.props.e_rtol); FVS_COUNT_LAUNCH();
   {
@@ -2032,8 +2028,8 @@ fvs_status batch_run(fvs_mesh mesh, const fvs_props* base, int64_t n, const doub
           tm[s] = inputs[3 * s];
           tw[s] = inputs[3 * s + 1];
           tl[s] = base->mat.T_liq - 5.0 * (inputs[3 * s + 2] - 4.0);
-          if (!(tl[s] > base->mat.T_sol)) {
-            set_error("sample %d: liquidus %.3f K not above the solidus", s, tl[s]);
+          if (!fs_law_valid(base->mat, tl[s])) {
+            set_error("sample %d: liquidus %.3f K does not suit the solid-fraction law", s, tl[s]);
             return FVS_ERR_ARG;
           }
           rn[s] = 1;
@@ -2089,7 +2085,7 @@ fvs_status batch_run(fvs_mesh mesh, const fvs_props* base, int64_t n, const doub
       FVS_TRY(B.mval.alloc((size_t)B.ocap * W + 1));
       if (B.fp32) FVS_TRY(B.mvalf.alloc((size_t)B.ocap * W + 1));
       FVS_CUDA(cudaMallocHost((void**)&B.host, ((size_t)B_NSLOT * Sp + 64) * sizeof(double)));
-      kb_init<<<bgrid(std::max(Nc, Nf), B.tiles), bblock(), 0, st>>>(Nc, Nf, Sp, B.Tmelt, B.Tliq, base->mat.T_sol,
+      kb_init<<<bgrid(std::max(Nc, Nf), B.tiles), bblock(), 0, st>>>(Nc, Nf, Sp, B.Tmelt, B.Tliq, fs_law_of(base->mat),
                                                                       B.run, B.T, B.Told, B.fs, B.u, B.uold, B.p,
                                                                       B.tliq, B.tsol, B.F, B.Fold);
       FVS_COUNT_LAUNCH();

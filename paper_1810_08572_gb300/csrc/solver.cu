@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 
+#include "fslaw.cuh"
 #include "solver.cuh"
 
 namespace fvs {
@@ -20,18 +21,12 @@ namespace fvs {
 
 struct Mat {
   double rho, k, cp, L, Ts, Tl, mu, beta, Tref, g0, g1, g2, C, eps;
+  FsLaw law;    // solid fraction (linear or Eq. 21)
 };
 static Mat mat_of(const fvs_props& p) {
   const fvs_material& m = p.mat;
   return Mat{m.rho, m.k, m.cp, m.latent, m.T_sol, m.T_liq, m.mu, m.beta, m.T_ref, m.g[0], m.g[1], m.g[2],
-             m.darcy_C, m.darcy_eps};
-}
-
-__device__ __forceinline__ double solid_fraction(double T, double Ts, double Tl) {
-  return fmin(fmax((Tl - T) / (Tl - Ts), 0.0), 1.0);
-}
-__device__ __forceinline__ double solid_fraction_slope(double T, double Ts, double Tl) {
-  return (T >= Ts && T <= Tl) ? -1.0 / (Tl - Ts) : 0.0;
+             m.darcy_C, m.darcy_eps, fs_law_of(m)};
 }
 
 // ---------------------------------------------------------------------------
@@ -477,7 +472,7 @@ __global__ void k_energy_lin(int64_t Nc, const double* V, Mat m, double dt, cons
                              const double* rcp, const double* rL, const uint8_t* metal) {
   GS(c, Nc) {
     const double t = Tm[c];
-    const double dfs = metal[c] ? solid_fraction_slope(t, m.Ts, m.Tl) : 0.0;
+    const double dfs = metal[c] ? fs_slope(m.law, t) : 0.0;
     const double a = rL[c] * V[c] / dt;
     const double Sp = a * dfs;
     const double Sc = a * (fsm[c] - fsn[c] - dfs * t);
@@ -498,15 +493,11 @@ __global__ void k_energy_update(int64_t Nc, Mat m, const double* Tlin, const dou
       continue;
     }
     const double t = Tm[c];
-    const double dfs = solid_fraction_slope(t, m.Ts, m.Tl);
+    const double dfs = fs_slope(m.law, t);
     const double H = m.cp * Tlin[c] + m.L * (1.0 - fsm[c] - dfs * (Tlin[c] - t));
-    const double Hs = m.cp * m.Ts, Hl = m.cp * m.Tl + m.L;
-    double T;
-    if (H <= Hs) T = H / m.cp;
-    else if (H >= Hl) T = (H - m.L) / m.cp;
-    else T = m.Ts + (H - Hs) / (Hl - Hs) * (m.Tl - m.Ts);
+    const double T = T_of_H(m.law, m.cp, m.L, H);
     Tnext[c] = T;
-    fsnext[c] = solid_fraction(T, m.Ts, m.Tl);
+    fsnext[c] = fs_of(m.law, T);
   }
 }
 
@@ -520,12 +511,12 @@ __global__ void k_count_u8(int64_t n, const uint8_t* a, int* out) {
 // first iterate of the latent-heat loop: T^n extrapolated linearly in time
 // (the loop converges to the same discrete solution from any start, within
 // its stop rule; this start is closer)
-__global__ void k_energy_guess(int64_t Nc, const double* T, const double* Told, double Ts, double Tl, double* Tm,
+__global__ void k_energy_guess(int64_t Nc, const double* T, const double* Told, FsLaw law, double* Tm,
                                double* fsm, const uint8_t* metal) {
   GS(c, Nc) {
     const double t = 2.0 * T[c] - Told[c];
     Tm[c] = t;
-    fsm[c] = metal[c] ? solid_fraction(t, Ts, Tl) : 0.0;
+    fsm[c] = metal[c] ? fs_of(law, t) : 0.0;
   }
 }
 __global__ void k_crossings(int64_t Nc, const double* Tn, const double* Tnew, double Ts, double Tl, double time,
@@ -550,7 +541,7 @@ __global__ void k_init_state(int64_t Nc, const int32_t* cell_in, const double* T
     const double t = Tin ? Tin[o] : (me ? Tuni : T_mold);
     T[c] = t;
     Told[c] = t;
-    fs[c] = me ? solid_fraction(t, m.Ts, m.Tl) : 0.0;
+    fs[c] = me ? fs_of(m.law, t) : 0.0;
     const bool solid = !(me && t > m.Ts);
     for (int d = 0; d < 3; ++d) {
       const double v = (uin && !solid) ? uin[3 * (int64_t)o + d] : 0.0;
@@ -716,6 +707,11 @@ static fvs_status apply_properties(fvs_solver s, const fvs_props* p) {
   const fvs_material& mt = p->mat;
   if (!(mt.rho > 0 && mt.k > 0 && mt.cp > 0 && mt.T_liq > mt.T_sol && mt.mu >= 0 && mt.latent >= 0)) {
     set_error("invalid material data");
+    return FVS_ERR_ARG;
+  }
+  if (!fs_law_valid(mt, mt.T_liq)) {
+    set_error("invalid solid-fraction law (model %d; Scheil needs 0 < kp < 1, T_eps > 0, "
+              "T_sol + T_eps < T_liq < T_f)", (int)mt.fs_model);
     return FVS_ERR_ARG;
   }
   s->props = *p;
@@ -1117,7 +1113,7 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
   // 5. energy: linearised latent heat, inner solve, enthalpy inversion
   k_energy_base<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, m->W, m->cf, m->cfs, m->own, m->nei, s->F, s->Fold, s->T,
                                                       s->Told, s->LT.col, s->LT.val, s->lT, m->V, s->rcp, dt, s->ebase); FVS_COUNT_LAUNCH();
-  k_energy_guess<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, s->Told, mt.Ts, mt.Tl, s->Tnew, s->fsnew, s->metal);
+  k_energy_guess<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, s->Told, mt.law, s->Tnew, s->fsnew, s->metal);
   FVS_COUNT_LAUNCH();
   {
     JacobiPrecond J;

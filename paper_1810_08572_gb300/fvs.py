@@ -43,7 +43,8 @@ class fvs_material(C.Structure):
     _fields_ = [("rho", C.c_double), ("k", C.c_double), ("cp", C.c_double), ("latent", C.c_double),
                 ("T_sol", C.c_double), ("T_liq", C.c_double), ("mu", C.c_double), ("beta", C.c_double),
                 ("T_ref", C.c_double), ("g", C.c_double * 3), ("darcy_C", C.c_double),
-                ("darcy_eps", C.c_double)]
+                ("darcy_eps", C.c_double), ("fs_model", C.c_int32), ("kp", C.c_double), ("T_f", C.c_double),
+                ("T_eps", C.c_double)]
 
 
 class fvs_patch_bc(C.Structure):
@@ -160,7 +161,9 @@ def make_props(p):
     """fvs_props from the plain-dict settings of fvs_inputs.cases.props()."""
     m = p["material"]
     mat = fvs_material(m["rho"], m["k"], m["cp"], m["latent"], m["T_sol"], m["T_liq"], m["mu"], m["beta"],
-                       m["T_ref"], (C.c_double * 3)(*m["g"]), m["darcy_C"], m["darcy_eps"])
+                       m["T_ref"], (C.c_double * 3)(*m["g"]), m["darcy_C"], m["darcy_eps"],
+                       int(m.get("fs_model", 0)), float(m.get("kp", 0.0)), float(m.get("T_f", 0.0)),
+                       float(m.get("T_eps", 0.0)))
     walls = p["walls"]
     bcs = (fvs_patch_bc * max(1, len(walls)))(*[fvs_patch_bc(int(t), float(T)) for t, T in walls])
     props = fvs_props(mat, len(walls), C.cast(bcs, C.POINTER(fvs_patch_bc)), p["T_init"], p["p_rtol"],

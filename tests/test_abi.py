@@ -34,13 +34,35 @@ def test_version_and_error_without_device(lib):
     assert isinstance(lib.fvs_last_error(), str)
 
 
-def test_struct_layouts_match_header(lib):
+def test_struct_layouts_match_header(lib, root, tmp_path):
+    """Size and every member offset of the binding's ctypes structs equal
+    what a C compiler lays out from include/fvs.h."""
     import ctypes as C
-    # doubles are 8-aligned, so the int32 members pad as in C
-    assert C.sizeof(lib.fvs_patch_bc) == 16
-    assert C.sizeof(lib.fvs_material) == 14 * 8
-    assert C.sizeof(lib.fvs_step_stats) == 2 * 8 + 4 * 4 + 8 + 5 * 4 + 4 + 8
-    assert C.sizeof(lib.fvs_mesh_info) == 4 * 8 + 4 * 4 + 8
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = ["fvs_material", "fvs_patch_bc", "fvs_props", "fvs_step_stats", "fvs_mesh_info"]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fvs.h"', "int main(void) {"]
+    for name in structs:
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in getattr(lib, name)._fields_:
+            lines.append(f'  printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(root, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        a, b, v = line.split()
+        got[(a, b)] = int(v)
+    for name in structs:
+        T = getattr(lib, name)
+        assert got[(name, "size")] == C.sizeof(T), name
+        for field, _ in T._fields_:
+            assert got[(name, field)] == getattr(T, field).offset, (name, field)
 
 
 def test_null_arguments_are_rejected(lib):

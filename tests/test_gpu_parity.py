@@ -375,3 +375,59 @@ def test_graph_replayed_iterations_on_a_stream(fvs, precision):
         S.step(1e-3)
     torch.cuda.synchronize()
     compare(o, S, 1e-10)
+
+
+SCHEIL = cases.AL_SI_SCHEIL
+
+
+def test_scheil_one_step(fvs):
+    """Smeared Gulliver-Scheil solid fraction (Eq. 21) on a jittered,
+    permuted mesh whose cells span the liquid, Scheil, smear and solid
+    pieces: one step equals the oracle's within 1e-10, solid fraction too."""
+    m = box_mesh(10, 10, 4, cases.CAVITY, jitter=0.2, jitter_seed=61, permute_seed=62)
+    rng = np.random.default_rng(3)
+    T0 = 826.0 + 130.0 * m["cell_ijk"][:, 0] / 9.0 + rng.uniform(-6.0, 6.0, len(m["cells"]))
+    u0 = rng.normal(scale=1e-3, size=(len(T0), 3))
+    props = cases.props(material=SCHEIL, **TIGHT)
+    o, M, S = make_pair(fvs, m, props, T0, u0)
+    assert ((T0 > 831.0) & (T0 < 835.0)).any()
+    o.step(1e-3)
+    S.step(1e-3)
+    compare(o, S, 1e-10, fields=("T", "U", "P", "FLUX", "USTAR", "FS"))
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_scheil_forty_steps(fvs, precision):
+    """Forty steps of the Scheil alloy cooled through its freezing range on
+    every wall: temperature within 1e-8 K of the oracle, solid fraction within
+    1e-8, velocity within 1e-8 relative, crossing times equal; the FP32
+    V-cycle (precision 1) reaches the same solution at the same outer
+    tolerance."""
+    m = box_mesh(12, 12, 4, cases.CAVITY, jitter=0.2, jitter_seed=63, permute_seed=64)
+    rng = np.random.default_rng(5)
+    T0 = 836.0 + 110.0 * m["cell_ijk"][:, 0] / 11.0 + rng.uniform(-3.0, 3.0, len(m["cells"]))
+    props = cases.props(material=SCHEIL, walls=cases.all_walls(700.0), **dict(TIGHT, precision=precision))
+    o, M, S = make_pair(fvs, m, props, T0)
+    for _ in range(40):
+        o.step(2e-3)
+    S.step(2e-3, 40)
+    assert np.abs(S.query("T") - o.T).max() <= 1e-8
+    assert np.abs(S.query("FS") - o.fs).max() <= 1e-8
+    assert rel(S.query("U"), o.u) <= 1e-8
+    np.testing.assert_allclose(S.query("CROSS"), np.stack([o.t_liq, o.t_sol], 1), atol=1e-9)
+    assert (o.fs > 0.0).any() and ((o.fs > 0.0) & (o.fs < 1.0)).any() and (o.t_sol > 0.0).any()
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_scheil_uq_batch_matches_oracle(fvs, mode):
+    """fvs_uq_batch with the Scheil law and a liquidus per sample (the Scheil
+    curve moves with it): per-sample QoIs equal the oracle's runs to full
+    solidification, lockstep batch and independent solves."""
+    m = box_mesh(8, 8, 2, (0.01, 0.01, 0.0025))
+    inputs = np.array([[930.0, 700.0, 4.0], [952.0, 690.0, 3.3]])
+    props = cases.props(material=SCHEIL, **TIGHT)
+    M = fvs.Mesh(m)
+    qoi, steps = fvs.uq_batch(M, props, inputs, 2e-3, 400, n_streams=2, mode=mode)
+    ref, ref_steps = oracle_uq(m, props, inputs, 2e-3, 400)
+    assert np.array_equal(steps, ref_steps)
+    np.testing.assert_allclose(qoi, ref, rtol=1e-8)
