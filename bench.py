@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--cpu-n", type=int, default=20, help="cells per axis of the oracle sample")
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-uq", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision leg of an fp64 run")
     ap.add_argument("--prof-steps", type=int, default=3, help="steps with per-kernel event timing")
     ap.add_argument("--uq-n", type=int, default=32, help="cells per axis of the UQ cavity")
     ap.add_argument("--uq-samples", type=int, default=32)
@@ -224,6 +225,9 @@ def run_gpu(args):
     n_launch = fvs.fvs_launch_count() - n_launch0
     ms = ev0.elapsed_time(ev1)
     ck = clocks.stop()
+    ref_fields = None
+    if args.precision == "fp64" and not args.no_mixed and rank == 0:
+        ref_fields = {k: S.query(k) for k in ("T", "U", "P", "FS")}
     # per-kernel event timing right after the timed region, on the same
     # stream, for --prof-steps further steps (kernels run eagerly while timed)
     S.profile(True)
@@ -258,6 +262,10 @@ def run_gpu(args):
                     share_of_step=round(top["total_ms"] / max(1, args.prof_steps) / (ms / args.steps), 3),
                     bytes_per_launch=per_launch_bytes)
 
+    mixed = None
+    if ref_fields is not None:
+        mixed = run_mixed(fvs, c, args, stream, torch, ref_fields)
+
     e2e = None
     if not args.no_e2e and rank == 0:
         e2e = run_e2e(fvs, c, props, args, stream, torch)
@@ -280,7 +288,7 @@ def run_gpu(args):
                              f"{args.precision}", cells=args.n ** 3, dt=dt, p_rtol=1e-8,
                     precision=args.precision, l2="inputs larger than L2 (matrices ~1 GB)",
                     parallelism="replicas" if world > 1 else "single GPU"),
-        roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=ck, uq=uq,
+        roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=ck, uq=uq, mixed=mixed,
         gpu_launches=int(n_launch),
         kernel_profile=sorted(prof, key=lambda r: -r["total_ms"])[:8],
         step_stats=dict(p_its=[s["p_its"] for s in its], e_its=[s["e_its"] for s in its],
@@ -338,6 +346,44 @@ def run_uq(fvs, args):
                 qoi_mean_plain=[float(v) for v in Y.mean(0)], qoi_mean_surrogate_1e6=[float(v) for v in Ymc.mean(0)],
                 note="plain: fvs_uq_batch to full solidification; surrogate: BF16 MLP "
                      "trained on those solves, inference on 1e6 inputs (host in/out)")
+
+
+def run_mixed(fvs, c, args, stream, torch, ref):
+    """The same steps with the FP32 V-cycle inside the FP64 Krylov method:
+    throughput timed like the FP64 run (same warm-up and step count, CUDA
+    events on the solver stream) and the difference of each field from the
+    FP64 run after those steps."""
+    import numpy as np
+    mesh = fvs.Mesh(c["mesh"], stream=stream)
+    S = fvs.Solver(mesh, bench_props("mixed"), stream=stream)
+    dt = c["dt"]
+    for _ in range(args.warmup):
+        S.step(dt, 1, allow_not_converged=True)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    act, p_its = 0, []
+    ev0.record(stream)
+    for _ in range(args.steps):
+        st = S.step(dt, 1, allow_not_converged=True)
+        act += st["n_active"]
+        p_its.append(st["p_its"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    got = {k: S.query(k) for k in ref}
+    S.close()
+    mesh.close()
+
+    def rel(a, b):
+        return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+    return dict(value=round(act / (ms / 1e3), 1), unit="active cell-steps/s",
+                ms_per_step=round(ms / args.steps, 3), p_its=p_its,
+                err_vs_fp64=dict(T_max_abs_K=float(np.abs(got["T"] - ref["T"]).max()),
+                                 fs_max_abs=float(np.abs(got["FS"] - ref["FS"]).max()),
+                                 u_rel=rel(got["U"], ref["U"]), p_rel=rel(got["P"], ref["P"])),
+                note="FP32 V-cycle inside FP64 BiCGStab, same 1e-8 pressure residual; errors after "
+                     f"{args.warmup + args.steps} steps, max over cells, relative to the largest FP64 value")
 
 
 def run_e2e(fvs, c, props, args, stream, torch):

@@ -9,7 +9,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .mesh import box_mesh
+from .mesh import box_mesh, casting_mesh
 
 # wall types of a boundary patch
 BC_ADIABATIC = 0      # no heat flux, no-slip
@@ -75,3 +75,21 @@ def uq_inputs(n_samples, seed):
 def liquidus_of(C0):
     """Liquidus shifted linearly by -5 K per wt% about 913 K at 4 wt%."""
     return 913.0 - 5.0 * (np.asarray(C0) - 4.0)
+
+
+# steel mold shell of the casting-like workload, its initial temperature and
+# the metal-mold heat-transfer coefficient
+STEEL_MOLD = dict(rho=7800.0, cp=500.0, k=30.0, h=2000.0, T_init=500.0)
+
+
+def casting_props(precision=1, T_wall=500.0, **tol):
+    """Casting in its mold: melt at 950 K, mold at 500 K, the mold's outer
+    surface held at ``T_wall``; mixed precision by default."""
+    return props(walls=all_walls(T_wall), T_init=950.0, precision=precision, mold=dict(STEEL_MOLD), **tol)
+
+
+def config_casting(h=0.46e-3):
+    """Plate 0.2 x 0.1 x 0.02 m with three 5 mm ribs and a 20 mm riser in a
+    3 mm steel shell, voxels of side h (0.46 mm: about 4.4M metal and 2.1M
+    mold cells), dt 1e-3 s."""
+    return dict(mesh=casting_mesh(h), dt=1e-3, props=casting_props())

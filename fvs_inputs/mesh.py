@@ -165,3 +165,132 @@ def zones_inner_box(mesh, lo, hi):
     hi = np.asarray(hi, dtype=np.float64)
     inside = np.all((xc >= lo) & (xc <= hi), axis=1)
     return np.where(inside, 0, 1).astype(np.int32)
+
+
+def voxel_mesh(mask, h, origin=(0.0, 0.0, 0.0), zone=None):
+    """Hexahedral mesh of the True voxels of a boolean array ``mask``
+    [nx, ny, nz] with cubic voxels of side ``h`` whose corner (0, 0, 0) sits
+    at ``origin``.  Faces between two kept voxels are interior; a face
+    between a kept voxel and an empty one (or the array's edge) is a wall
+    whose patch is the direction of its outward normal (0..5 = -x, +x, -y, +y,
+    -z, +z).  ``zone`` (int array like ``mask``) gives each kept cell its
+    ``cell_zone``.  Same list conventions as ``box_mesh``."""
+    mask = np.asarray(mask, dtype=bool)
+    nx, ny, nz = mask.shape
+    NX, NY, NZ = nx + 1, ny + 1, nz + 1
+    # cells: ids in (i fastest, then j, then k) order of the kept voxels
+    flat = mask.transpose(2, 1, 0).ravel()                  # k-major, i fastest
+    cell_of = np.full(flat.shape, -1, dtype=np.int64)
+    cell_of[flat] = np.arange(int(flat.sum()))
+    cell_of = cell_of.reshape(nz, ny, nx).transpose(2, 1, 0)  # [i, j, k] -> cell id or -1
+    # nodes: corners of kept voxels
+    used = np.zeros((NX, NY, NZ), dtype=bool)
+    for di in (0, 1):
+        for dj in (0, 1):
+            for dk in (0, 1):
+                used[di:di + nx, dj:dj + ny, dk:dk + nz] |= mask
+    uflat = used.transpose(2, 1, 0).ravel()
+    node_of = np.full(uflat.shape, -1, dtype=np.int64)
+    node_of[uflat] = np.arange(int(uflat.sum()))
+    node_of = node_of.reshape(NZ, NY, NX).transpose(2, 1, 0)
+    ni, nj, nk = (a.transpose(2, 1, 0).ravel()[uflat] for a in
+                  np.meshgrid(np.arange(NX), np.arange(NY), np.arange(NZ), indexing="ij"))
+    o = np.asarray(origin, dtype=np.float64)
+    nodes = np.stack([o[0] + ni * h, o[1] + nj * h, o[2] + nk * h], axis=1)
+
+    ci, cj, ck = np.nonzero(mask.transpose(2, 1, 0))         # k, j, i order ...
+    ci, ck = ck, ci                                           # ... back to i, j, k
+    cells = np.stack([node_of[ci, cj, ck], node_of[ci + 1, cj, ck], node_of[ci + 1, cj + 1, ck],
+                      node_of[ci, cj + 1, ck], node_of[ci, cj, ck + 1], node_of[ci + 1, cj, ck + 1],
+                      node_of[ci + 1, cj + 1, ck + 1], node_of[ci, cj + 1, ck + 1]], axis=1)
+
+    pad = np.pad(cell_of, 1, constant_values=-1)              # pad[i+1, j+1, k+1] = cell_of[i, j, k]
+    faces, fcells, patch = [], [], []
+    for axis in range(3):
+        # face positions: index p along the axis (0..n), the others span the voxels
+        shape = [nx, ny, nz]
+        shape[axis] += 1
+        grids = np.meshgrid(*[np.arange(s) for s in shape], indexing="ij")
+        lo = [g + 1 for g in grids]
+        lo[axis] = grids[axis]                                # voxel below the face (pad coords)
+        hi = [g + 1 for g in grids]                           # voxel above the face
+        a = pad[lo[0], lo[1], lo[2]].ravel()
+        b = pad[hi[0], hi[1], hi[2]].ravel()
+        keep = (a >= 0) | (b >= 0)
+        fi, fj, fk = (g.ravel()[keep] for g in grids)
+        a, b = a[keep], b[keep]
+        if axis == 0:
+            quad = np.stack([node_of[fi, fj, fk], node_of[fi, fj + 1, fk], node_of[fi, fj + 1, fk + 1],
+                             node_of[fi, fj, fk + 1]], axis=1)
+        elif axis == 1:
+            quad = np.stack([node_of[fi, fj, fk], node_of[fi, fj, fk + 1], node_of[fi + 1, fj, fk + 1],
+                             node_of[fi + 1, fj, fk]], axis=1)
+        else:
+            quad = np.stack([node_of[fi, fj, fk], node_of[fi + 1, fj, fk], node_of[fi + 1, fj + 1, fk],
+                             node_of[fi, fj + 1, fk]], axis=1)
+        # owner below (normal along +axis); a face with only the voxel above
+        # is a wall owned by that voxel, with the corner cycle reversed
+        only_hi = a < 0
+        own = np.where(only_hi, b, a)
+        nei = np.where((a >= 0) & (b >= 0), b, -1)
+        quad = np.where(only_hi[:, None], quad[:, ::-1], quad)
+        pat = np.where(nei >= 0, -1, np.where(only_hi, 2 * axis, 2 * axis + 1))
+        faces.append(quad); fcells.append(np.stack([own, nei], 1)); patch.append(pat)
+
+    out = dict(
+        nodes=np.ascontiguousarray(nodes, dtype=np.float64),
+        cells=np.ascontiguousarray(cells, dtype=np.int32),
+        faces=np.ascontiguousarray(np.concatenate(faces), dtype=np.int32),
+        face_cells=np.ascontiguousarray(np.concatenate(fcells), dtype=np.int32),
+        patch=np.ascontiguousarray(np.concatenate(patch), dtype=np.int32),
+        cell_ijk=np.ascontiguousarray(np.stack([ci, cj, ck], axis=1), dtype=np.int32),
+        shape=(nx, ny, nz),
+        lengths=(nx * h, ny * h, nz * h),
+    )
+    if zone is not None:
+        out["cell_zone"] = np.ascontiguousarray(np.asarray(zone)[ci, cj, ck], dtype=np.int32)
+    return out
+
+
+def _dilate(mask, s):
+    """Grow a boolean voxel set by s voxels along every axis (cube element)."""
+    out = mask.copy()
+    for axis in range(3):
+        src = out.copy()
+        for d in range(1, s + 1):
+            sl_a = [slice(None)] * 3
+            sl_b = [slice(None)] * 3
+            sl_a[axis] = slice(d, None)
+            sl_b[axis] = slice(None, -d)
+            out[tuple(sl_a)] |= src[tuple(sl_b)]
+            out[tuple(sl_b)] |= src[tuple(sl_a)]
+    return out
+
+
+def casting_mesh(h, shell=0.003, plate=(0.2, 0.1, 0.02), rib_width=0.005, rib_height=0.01,
+                 rib_x=(0.05, 0.10, 0.15), riser=0.02, riser_x=0.18):
+    """Voxelised casting in a mold shell: a plate [0, Lx] x [0, Ly] x [0, Lz],
+    three ribs of width ``rib_width`` (along x) hanging ``rib_height`` below
+    it across the full y span at ``rib_x``, and a cubic riser of side
+    ``riser`` on its top face centred at (``riser_x``, Ly/2); all of it metal
+    (zone 0) inside a mold shell (zone 1) of every voxel within ``shell`` of
+    the metal (cube neighbourhood).  Voxel side ``h``; a voxel is metal when
+    its centre lies inside the metal.  The walls of the mesh are the outer
+    surface of the shell."""
+    Lx, Ly, Lz = plate
+    s = max(1, int(round(shell / h)))
+    x0, y0, z0 = -shell, -shell, -rib_height - shell
+    x1, y1, z1 = Lx + shell, Ly + shell, Lz + riser + shell
+    nx, ny, nz = (int(np.ceil((b - a) / h - 1e-9)) for a, b in ((x0, x1), (y0, y1), (z0, z1)))
+    xc = x0 + (np.arange(nx) + 0.5) * h
+    yc = y0 + (np.arange(ny) + 0.5) * h
+    zc = z0 + (np.arange(nz) + 0.5) * h
+    X, Y, Z = np.meshgrid(xc, yc, zc, indexing="ij")
+    metal = (X > 0) & (X < Lx) & (Y > 0) & (Y < Ly) & (Z > 0) & (Z < Lz)
+    for rx in rib_x:
+        metal |= (np.abs(X - rx) < 0.5 * rib_width) & (Y > 0) & (Y < Ly) & (Z > -rib_height) & (Z <= 0)
+    metal |= ((np.abs(X - riser_x) < 0.5 * riser) & (np.abs(Y - 0.5 * Ly) < 0.5 * riser)
+              & (Z >= Lz) & (Z < Lz + riser))
+    solid = _dilate(metal, s)
+    zone = np.where(metal, 0, 1)
+    return voxel_mesh(solid, h, origin=(x0, y0, z0), zone=zone)

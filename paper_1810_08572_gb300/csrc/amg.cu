@@ -12,7 +12,7 @@ namespace fvs {
 
 #define GS(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
-static constexpr int GAL_CAP = 2048;   // entries gathered per coarse row
+static constexpr int GAL_CAP = 4096;   // entries gathered per coarse row (48 KB of shared memory)
 static constexpr int GAL_SMALL = 256;  // rows up to this many entries: the many-warp kernel
 
 // ---------------------------------------------------------------------------
@@ -33,23 +33,30 @@ __global__ void k_maxoff(int64_t n, int w, const int32_t* col, const double* val
   }
 }
 
+// strength masks: word q of row i (stored at [q*n + i]) flags slots
+// 64q .. 64q + 63 of the row; slots beyond 64 * SMASK_WORDS are never strong
+// (wider rows only occur on small coarse levels)
+constexpr int SMASK_WORDS = 4;
+
 __global__ void k_strong(int64_t n, int w, const int32_t* col, const double* val, const double* mo, double theta,
                          int absval, uint64_t* mask) {
   GS(i, n) {
     // judged from row i alone (the strength graph may be slightly
     // asymmetric; the independent-set rounds and the assignment only ever
-    // look at a node's own mask, so that stays consistent).  Slots beyond 64
-    // are never strong.
-    uint64_t msk = 0;
-    const int wk = w < 64 ? w : 64;
-    for (int k = 0; k < wk; ++k) {
-      const int64_t e = (int64_t)k * n + i;
-      const int32_t j = col[e];
-      if (j == (int32_t)i) continue;
-      const double a = absval ? fabs(val[e]) : -val[e];
-      if (a > 0.0 && a >= theta * mo[i]) msk |= (1ULL << k);
+    // look at a node's own mask, so that stays consistent)
+    const int wk = w < 64 * SMASK_WORDS ? w : 64 * SMASK_WORDS;
+    for (int q = 0; q < SMASK_WORDS; ++q) {
+      uint64_t msk = 0;
+      const int k1 = min(wk, 64 * (q + 1));
+      for (int k = 64 * q; k < k1; ++k) {
+        const int64_t e = (int64_t)k * n + i;
+        const int32_t j = col[e];
+        if (j == (int32_t)i) continue;
+        const double a = absval ? fabs(val[e]) : -val[e];
+        if (a > 0.0 && a >= theta * mo[i]) msk |= (1ULL << (k - 64 * q));
+      }
+      mask[(int64_t)q * n + i] = msk;
     }
-    mask[i] = msk;
   }
 }
 
@@ -70,12 +77,14 @@ __global__ void k_mis_select(int64_t n, int w, const int32_t* col, const uint64_
     uint8_t s = st[i];
     if (s == 0) {
       bool top = true;
-      uint64_t m = mask[i];
-      while (m) {
-        const int k = __ffsll((long long)m) - 1;
-        m &= m - 1;
-        const int32_t j = col[(int64_t)k * n + i];
-        if (st[j] == 0 && beats(j, (int32_t)i)) { top = false; break; }
+      for (int q = 0; q < SMASK_WORDS && top; ++q) {
+        uint64_t m = mask[(int64_t)q * n + i];
+        while (m) {
+          const int k = 64 * q + __ffsll((long long)m) - 1;
+          m &= m - 1;
+          const int32_t j = col[(int64_t)k * n + i];
+          if (st[j] == 0 && beats(j, (int32_t)i)) { top = false; break; }
+        }
       }
       if (top) s = 1;
     }
@@ -88,11 +97,13 @@ __global__ void k_mis_remove(int64_t n, int w, const int32_t* col, const uint64_
   GS(i, n) {
     uint8_t s = st2[i];
     if (s == 0) {
-      uint64_t m = mask[i];
-      while (m) {
-        const int k = __ffsll((long long)m) - 1;
-        m &= m - 1;
-        if (st2[col[(int64_t)k * n + i]] == 1) { s = 2; break; }
+      for (int q = 0; q < SMASK_WORDS && s == 0; ++q) {
+        uint64_t m = mask[(int64_t)q * n + i];
+        while (m) {
+          const int k = 64 * q + __ffsll((long long)m) - 1;
+          m &= m - 1;
+          if (st2[col[(int64_t)k * n + i]] == 1) { s = 2; break; }
+        }
       }
       if (s == 0) ++cnt;
     }
@@ -102,7 +113,11 @@ __global__ void k_mis_remove(int64_t n, int w, const int32_t* col, const uint64_
 }
 __global__ void k_count_isolated(int64_t n, const uint64_t* mask, int* out) {
   int c = 0;
-  GS(i, n) c += mask[i] == 0 ? 1 : 0;
+  GS(i, n) {
+    uint64_t any = 0;
+    for (int q = 0; q < SMASK_WORDS; ++q) any |= mask[(int64_t)q * n + i];
+    c += any == 0 ? 1 : 0;
+  }
   if (c) atomicAdd(out, c);
 }
 __global__ void k_is_root(int64_t n, const uint8_t* st, int32_t* flag) {
@@ -110,23 +125,146 @@ __global__ void k_is_root(int64_t n, const uint8_t* st, int32_t* flag) {
 }
 // every non-root joins its strongest root neighbour (ties: lower index)
 __global__ void k_assign(int64_t n, int w, const int32_t* col, const double* val, const uint64_t* mask,
-                         const uint8_t* st, const int32_t* rid, int32_t* agg, int* err) {
+                         const uint8_t* st, const int32_t* rid, int32_t* agg, int* err, int lenient = 0) {
   GS(i, n) {
     if (st[i] == 1) { agg[i] = rid[i]; continue; }
     double best = -1e300;
     int32_t bj = -1;
-    uint64_t m = mask[i];
-    while (m) {
-      const int k = __ffsll((long long)m) - 1;
-      m &= m - 1;
-      const int64_t e = (int64_t)k * n + i;
-      const int32_t j = col[e];
-      if (st[j] != 1) continue;
-      const double a = -val[e];
-      if (a > best || (a == best && j < bj)) { best = a; bj = j; }
+    for (int q = 0; q < SMASK_WORDS; ++q) {
+      uint64_t m = mask[(int64_t)q * n + i];
+      while (m) {
+        const int k = 64 * q + __ffsll((long long)m) - 1;
+        m &= m - 1;
+        const int64_t e = (int64_t)k * n + i;
+        const int32_t j = col[e];
+        if (st[j] != 1) continue;
+        const double a = -val[e];
+        if (a > best || (a == best && j < bj)) { best = a; bj = j; }
+      }
     }
-    if (bj < 0) { atomicOr(err, 1); agg[i] = 0; } else agg[i] = rid[bj];
+    if (bj < 0) {
+      if (lenient) agg[i] = -1;          // distance-2 set: joins a neighbour's aggregate next
+      else { atomicOr(err, 1); agg[i] = 0; }
+    } else {
+      agg[i] = rid[bj];
+    }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Distance-2 independent set (used where the distance-1 set coarsens a level
+// by less than the accepted ratio: chains and star-like couplings of small
+// coarse levels).  A node becomes a root when its key is the largest among
+// the undecided nodes within two strong hops; nodes within two hops of a root
+// drop out.  Keys: hash of the index, then the index (0 = not undecided).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t mis2_key(int64_t i, uint8_t st) {
+  return st == 0 ? (((uint64_t)hash32((uint32_t)i) << 32) | (uint64_t)(i + 1)) : 0ULL;
+}
+// t1[i] = largest undecided key among i and its strong neighbours
+__global__ void k_mis2_max1(int64_t n, const int32_t* col, const uint64_t* mask, const uint8_t* st, uint64_t* t1) {
+  GS(i, n) {
+    uint64_t best = mis2_key(i, st[i]);
+    for (int q = 0; q < SMASK_WORDS; ++q) {
+      uint64_t m = mask[(int64_t)q * n + i];
+      while (m) {
+        const int k = 64 * q + __ffsll((long long)m) - 1;
+        m &= m - 1;
+        const int32_t j = col[(int64_t)k * n + i];
+        const uint64_t kj = mis2_key(j, st[j]);
+        best = kj > best ? kj : best;
+      }
+    }
+    t1[i] = best;
+  }
+}
+// second hop; an undecided node holding the largest key within two hops is a root
+__global__ void k_mis2_select(int64_t n, const int32_t* col, const uint64_t* mask, const uint8_t* st,
+                              const uint64_t* t1, uint8_t* st2) {
+  GS(i, n) {
+    uint8_t s = st[i];
+    if (s == 0) {
+      uint64_t best = t1[i];
+      for (int q = 0; q < SMASK_WORDS; ++q) {
+        uint64_t m = mask[(int64_t)q * n + i];
+        while (m) {
+          const int k = 64 * q + __ffsll((long long)m) - 1;
+          m &= m - 1;
+          const uint64_t tj = t1[col[(int64_t)k * n + i]];
+          best = tj > best ? tj : best;
+        }
+      }
+      if (best == mis2_key(i, 0)) s = 1;
+    }
+    st2[i] = s;
+  }
+}
+// r1[i] = 1 if i or a strong neighbour is a root
+__global__ void k_mis2_near(int64_t n, const int32_t* col, const uint64_t* mask, const uint8_t* st2, uint8_t* r1) {
+  GS(i, n) {
+    uint8_t r = st2[i] == 1 ? 1 : 0;
+    for (int q = 0; q < SMASK_WORDS && !r; ++q) {
+      uint64_t m = mask[(int64_t)q * n + i];
+      while (m) {
+        const int k = 64 * q + __ffsll((long long)m) - 1;
+        m &= m - 1;
+        if (st2[col[(int64_t)k * n + i]] == 1) { r = 1; break; }
+      }
+    }
+    r1[i] = r;
+  }
+}
+// undecided nodes with a root within two hops drop out
+__global__ void k_mis2_remove(int64_t n, const int32_t* col, const uint64_t* mask, const uint8_t* st2,
+                              const uint8_t* r1, uint8_t* st, int* undecided) {
+  int cnt = 0;
+  GS(i, n) {
+    uint8_t s = st2[i];
+    if (s == 0) {
+      bool near = r1[i] != 0;
+      for (int q = 0; q < SMASK_WORDS && !near; ++q) {
+        uint64_t m = mask[(int64_t)q * n + i];
+        while (m) {
+          const int k = 64 * q + __ffsll((long long)m) - 1;
+          m &= m - 1;
+          if (r1[col[(int64_t)k * n + i]]) { near = true; break; }
+        }
+      }
+      if (near) s = 2;
+      else ++cnt;
+    }
+    st[i] = s;
+  }
+  if (cnt) atomicAdd(undecided, cnt);
+}
+// nodes two hops from their root join the aggregate of their strongest
+// assigned strong neighbour (reads one snapshot, writes another)
+__global__ void k_assign_near(int64_t n, const int32_t* col, const double* val, const uint64_t* mask,
+                              const int32_t* agg_in, int32_t* agg_out, int* left) {
+  int cnt = 0;
+  GS(i, n) {
+    int32_t a = agg_in[i];
+    if (a < 0) {
+      double best = -1e300;
+      int32_t bj = -1;
+      for (int q = 0; q < SMASK_WORDS; ++q) {
+        uint64_t m = mask[(int64_t)q * n + i];
+        while (m) {
+          const int k = 64 * q + __ffsll((long long)m) - 1;
+          m &= m - 1;
+          const int64_t e = (int64_t)k * n + i;
+          const int32_t j = col[e];
+          if (agg_in[j] < 0) continue;
+          const double v = -val[e];
+          if (v > best || (v == best && j < bj)) { best = v; bj = j; }
+        }
+      }
+      if (bj >= 0) a = agg_in[bj];
+      else ++cnt;
+    }
+    agg_out[i] = a;
+  }
+  if (cnt) atomicAdd(left, cnt);
 }
 
 // rows with agg < 0 (left out by a refresh) belong to no aggregate
@@ -184,6 +322,10 @@ __global__ void k_sort_members(int64_t nc, const int32_t* ptr, int32_t* idx) {
     }                                                                             \
   }                                                                               \
   SYNC;                                                                           \
+  GAL_SORT(T, t, SYNC)
+
+// bitonic sort of key[0..P) (with v) by key; T threads, SYNC() the barrier
+#define GAL_SORT(T, t, SYNC)                                                      \
   for (int size = 2; size <= P; size <<= 1) {                                     \
     for (int stride = size >> 1; stride > 0; stride >>= 1) {                      \
       for (int e = (t); e < P; e += (T)) {                                        \
@@ -271,14 +413,56 @@ __global__ void __launch_bounds__(256) k_galerkin_big(int64_t nc, int64_t n, int
     if (dirty && !dirty[I]) continue;
     const int32_t lo = mptr[I], hi = mptr[I + 1];
     const int total = (hi - lo) * w;
-    if (total <= GAL_SMALL) continue;
+    if (total <= GAL_SMALL || total > GAL_CAP) continue;   // the warp / wide kernels take these
+    int P = 32;
+    while (P < total) P <<= 1;
+    GAL_GATHER_SORT(256, (int)threadIdx.x, __syncthreads())
+    if (threadIdx.x < 32) gal_emit<FILL>((int)threadIdx.x, key, v, P, I, nc, rowlen, wc, ccol, cval, cdiag, err);
+    __syncthreads();
+  }
+}
+
+// coarse rows whose members' padded rows exceed GAL_CAP entries (wide, short
+// rows of small coarse levels): gather only the stored entries of each member
+// row (rlen; null: every slot), members in order
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_galerkin_wide(int64_t nc, int64_t n, int w, const int32_t* col,
+                                                       const double* val, const int32_t* rlen_in,
+                                                       const int32_t* agg, const int32_t* mptr,
+                                                       const int32_t* midx, int32_t* rowlen, int wc, int32_t* ccol,
+                                                       double* cval, double* cdiag, int* err, const uint8_t* dirty) {
+  __shared__ int32_t key[GAL_CAP];
+  __shared__ double v[GAL_CAP];
+  for (int64_t I = blockIdx.x; I < nc; I += gridDim.x) {
+    if (dirty && !dirty[I]) continue;
+    const int32_t lo = mptr[I], hi = mptr[I + 1];
+    if ((hi - lo) * w <= GAL_CAP) continue;
+    int total = 0;
+    for (int32_t m = lo; m < hi; ++m) total += rlen_in ? rlen_in[midx[m]] : w;
     if (total > GAL_CAP) {
       if (threadIdx.x == 0) { atomicOr(err, 2); if (!FILL) rowlen[I] = 0; }
       continue;
     }
     int P = 32;
     while (P < total) P <<= 1;
-    GAL_GATHER_SORT(256, (int)threadIdx.x, __syncthreads())
+    int base = 0;
+    for (int32_t m = lo; m < hi; ++m) {
+      const int32_t i = midx[m];
+      const int len = rlen_in ? rlen_in[i] : w;
+      for (int k = threadIdx.x; k < len; k += blockDim.x) {
+        const int64_t ei = (int64_t)k * n + i;
+        const double a = val[ei];
+        key[base + k] = a != 0.0 ? agg[col[ei]] : INT_MAX;
+        v[base + k] = a;
+      }
+      base += len;
+    }
+    for (int e = total + threadIdx.x; e < P; e += blockDim.x) {
+      key[e] = INT_MAX;
+      v[e] = 0.0;
+    }
+    __syncthreads();
+    GAL_SORT(256, (int)threadIdx.x, __syncthreads())
     if (threadIdx.x < 32) gal_emit<FILL>((int)threadIdx.x, key, v, P, I, nc, rowlen, wc, ccol, cval, cdiag, err);
     __syncthreads();
   }
@@ -807,9 +991,9 @@ static fvs_status read_int(cudaStream_t s, const int* d, int* h) {
 }
 
 // one Galerkin pass (count or fill) over all coarse rows (or the dirty ones)
-static void galerkin_pass(cudaStream_t s, bool fill, int64_t nc, const Ell& A, const int32_t* agg,
-                          const int32_t* mptr, const int32_t* midx, int32_t* rowlen, int wc, int32_t* ccol,
-                          double* cval, double* cdiag, int* err, const uint8_t* dirty = nullptr) {
+static void galerkin_pass(cudaStream_t s, bool fill, int64_t nc, const Ell& A, const int32_t* rlen_in,
+                          const int32_t* agg, const int32_t* mptr, const int32_t* midx, int32_t* rowlen, int wc,
+                          int32_t* ccol, double* cval, double* cdiag, int* err, const uint8_t* dirty = nullptr) {
   if (nc <= 0) return;
   const int64_t n = A.n;
   const int gs = (int)std::min<int64_t>((nc + 3) / 4, (int64_t)sm_count() * 16);
@@ -819,11 +1003,15 @@ static void galerkin_pass(cudaStream_t s, bool fill, int64_t nc, const Ell& A, c
                                            err, dirty); FVS_COUNT_LAUNCH();
     k_galerkin_big<true><<<gb, 256, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol, cval,
                                             cdiag, err, dirty); FVS_COUNT_LAUNCH();
+    k_galerkin_wide<true><<<gb, 256, 0, s>>>(nc, n, A.w, A.col, A.val, rlen_in, agg, mptr, midx, rowlen, wc, ccol,
+                                             cval, cdiag, err, dirty); FVS_COUNT_LAUNCH();
   } else {
     k_galerkin<false, 4><<<gs, 128, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol, cval,
                                             cdiag, err, dirty); FVS_COUNT_LAUNCH();
     k_galerkin_big<false><<<gb, 256, 0, s>>>(nc, n, A.w, A.col, A.val, agg, mptr, midx, rowlen, wc, ccol, cval,
                                              cdiag, err, dirty); FVS_COUNT_LAUNCH();
+    k_galerkin_wide<false><<<gb, 256, 0, s>>>(nc, n, A.w, A.col, A.val, rlen_in, agg, mptr, midx, rowlen, wc, ccol,
+                                              cval, cdiag, err, dirty); FVS_COUNT_LAUNCH();
   }
 }
 
@@ -844,6 +1032,7 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
   opt.npre = (int)env_num("FVS_AMG_NPRE", opt.npre);
   opt.npost = (int)env_num("FVS_AMG_NPOST", opt.npost);
   opt.coarsest = (int)env_num("FVS_AMG_COARSEST", opt.coarsest);
+  opt.mis2_ratio = env_num("FVS_AMG_MIS2_RATIO", opt.mis2_ratio);
   if (opt.npre < 1) opt.npre = 1;
   if (opt.npost < 1) opt.npost = 1;
   DBuf<int> err, cnt;
@@ -889,24 +1078,41 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
     DBuf<uint64_t> mask;
     DBuf<uint8_t> st, st2;
     DBuf<int32_t> flag, rid;
-    FVS_TRY(mask.alloc(n)); FVS_TRY(st.alloc(n)); FVS_TRY(st2.alloc(n));
+    FVS_TRY(mask.alloc((size_t)SMASK_WORDS * n)); FVS_TRY(st.alloc(n)); FVS_TRY(st2.alloc(n));
     FVS_TRY(flag.alloc(n + 1)); FVS_TRY(rid.alloc(n + 1));
     int nc = 0;
-    for (int attempt = 0; attempt < 3; ++attempt) {
-      const double theta = attempt == 0 ? opt.theta : 0.0;
+    bool mis2 = false;
+    DBuf<uint64_t> t1;
+    DBuf<uint8_t> r1;
+    // attempts 0-2: distance-1 independent sets on ever wider strength
+    // graphs; attempt 3, only where those would stall the coarsening: the
+    // distance-2 set on the first graph
+    for (int attempt = 0; attempt < 4; ++attempt) {
+      if (attempt == 3 && (double)nc <= opt.mis2_ratio * (double)n) break;   // keep the distance-1 result
+      mis2 = attempt == 3;
+      const double theta = (attempt == 0 || mis2) ? opt.theta : 0.0;
       const int absval = attempt == 2 ? 1 : 0;
       FVS_TRY(st.zero(s));
       k_strong<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mo, theta, absval, mask);
       FVS_COUNT_LAUNCH();
       FVS_LAUNCH_CHECK();
       tick(1);
+      if (mis2) { FVS_TRY(t1.alloc(n)); FVS_TRY(r1.alloc(n)); }
       for (int round = 0;; round += 2) {
         // two independent-set rounds per check (rounds after completion change nothing)
         FVS_TRY(cnt.zero(s));
         for (int q = 0; q < 2; ++q) {
-          k_mis_select<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, mask, st, st2); FVS_COUNT_LAUNCH();
-          k_mis_remove<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, mask, st2, st,
-                                                             q == 1 ? cnt.p : cnt.p + 1); FVS_COUNT_LAUNCH();
+          int* cq = q == 1 ? cnt.p : cnt.p + 1;
+          if (mis2) {
+            k_mis2_max1<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->col, mask, st, t1); FVS_COUNT_LAUNCH();
+            k_mis2_select<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->col, mask, st, t1, st2); FVS_COUNT_LAUNCH();
+            k_mis2_near<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->col, mask, st2, r1); FVS_COUNT_LAUNCH();
+            k_mis2_remove<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->col, mask, st2, r1, st, cq); FVS_COUNT_LAUNCH();
+          } else {
+            k_mis_select<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, mask, st, st2); FVS_COUNT_LAUNCH();
+            k_mis_remove<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, mask, st2, st, cq);
+            FVS_COUNT_LAUNCH();
+          }
         }
         FVS_LAUNCH_CHECK();
         int und = 0;
@@ -930,8 +1136,8 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
       k_count_isolated<<<stride_grid(n, 256), 256, 0, s>>>(n, mask, cnt); FVS_COUNT_LAUNCH();
       int iso = 0;
       FVS_TRY(read_int(s, cnt, &iso));
-      fprintf(stderr, "[fvs amg] level %d: %lld rows (w%d) -> %d aggregates, %d rows without strong couplings\n", l,
-              (long long)n, cur->w, nc, iso);
+      fprintf(stderr, "[fvs amg] level %d: %lld rows (w%d) -> %d aggregates%s, %d rows without strong couplings\n",
+              l, (long long)n, cur->w, nc, mis2 ? " (distance-2 set)" : "", iso);
       const char* dump = getenv("FVS_AMG_DUMP");   // small levels to a file, for offline study
       if (dump && *dump && n <= 8192) {
         std::vector<int32_t> hc((size_t)n * cur->w);
@@ -953,7 +1159,28 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
     if (nc <= 0 || nc >= n || (double)nc > 0.85 * (double)n) break;  // stagnation: L is the coarsest
     tick(2);
     FVS_TRY(L->agg.alloc(n));
-    k_assign<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mask, st, rid, L->agg, err); FVS_COUNT_LAUNCH();
+    k_assign<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mask, st, rid, L->agg, err,
+                                                 mis2 ? 1 : 0);
+    FVS_COUNT_LAUNCH();
+    if (mis2) {
+      // nodes two hops from a root: up to three passes of joining an
+      // assigned neighbour's aggregate; any left over is a setup failure
+      DBuf<int32_t> agg2;
+      FVS_TRY(agg2.alloc(n));
+      int left = 0;
+      for (int pass = 0; pass < 3; ++pass) {
+        FVS_TRY(cnt.zero(s));
+        k_assign_near<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->col, cur->val, mask, L->agg, agg2, cnt);
+        FVS_COUNT_LAUNCH();
+        FVS_CUDA(cudaMemcpyAsync(L->agg.p, agg2.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+        FVS_TRY(read_int(s, cnt, &left));
+        if (left == 0) break;
+      }
+      if (left) {
+        set_error("AMG aggregation left %d rows without an aggregate at level %d", left, l);
+        return FVS_ERR_NOT_CONVERGED;
+      }
+    }
     DBuf<int32_t> mc;
     FVS_TRY(mc.alloc(nc + 1));
     FVS_TRY(mc.zero(s));
@@ -968,7 +1195,8 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
     std::unique_ptr<AmgLevel> C(new AmgLevel());
     DBuf<int32_t>& rowlen = C->rlen;   // kept: the V-cycle walks only the stored entries of each row
     FVS_TRY(rowlen.alloc(nc + 1));
-    galerkin_pass(s, false, nc, *cur, L->agg, L->mptr, L->midx, rowlen, 0, nullptr, nullptr, nullptr, err);
+    galerkin_pass(s, false, nc, *cur, L->rlen.p, L->agg, L->mptr, L->midx, rowlen, 0, nullptr, nullptr, nullptr,
+                  err);
     FVS_TRY(cnt.zero(s));
     k_max_int<<<stride_grid(nc, 256), 256, 0, s>>>(nc, rowlen, cnt); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
@@ -982,8 +1210,8 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
     tick(3);
     FVS_TRY(C->own.alloc(nc, wc));
     FVS_TRY(C->own.diag.zero(s));
-    galerkin_pass(s, true, nc, *cur, L->agg, L->mptr, L->midx, rowlen, wc, C->own.col, C->own.val, C->own.diag,
-                  err);
+    galerkin_pass(s, true, nc, *cur, L->rlen.p, L->agg, L->mptr, L->midx, rowlen, wc, C->own.col, C->own.val,
+                  C->own.diag, err);
     FVS_LAUNCH_CHECK();
     C->A = &C->own;
     lv.push_back(std::move(C));
@@ -1190,8 +1418,8 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
     if (l > 0 && n > 0) {
       k_dirty_up<<<stride_grid(n, 256), 256, 0, s>>>(n, L->agg, L->dirty, C->dirty); FVS_COUNT_LAUNCH();
     }
-    galerkin_pass(s, true, C->n, *cur, L->agg, L->mptr, L->midx, C->rlen, C->own.w, C->own.col, C->own.val,
-                  C->own.diag, err, C->dirty);
+    galerkin_pass(s, true, C->n, *cur, L->rlen.p, L->agg, L->mptr, L->midx, C->rlen, C->own.w, C->own.col,
+                  C->own.val, C->own.diag, err, C->dirty);
     FVS_LAUNCH_CHECK();
   }
   {

@@ -36,6 +36,7 @@ struct AmgOptions {
   int max_levels = 20;
   int coarsest = 160;      // stop coarsening at or below this size (shared-memory inverse)
   int npre = 1, npost = 1;
+  double mis2_ratio = 0.85; // distance-2 aggregation where distance-1 sets keep more than this share of rows
   bool fp32 = false;       // V-cycle in single precision
 };
 

@@ -124,3 +124,29 @@ def test_conduction_converges_on_distorted_slab(distort):
         assert min(order) > 1.9, (errs, order)
     else:
         assert errs[2] < 0.25 and errs[1] / errs[2] > 1.6 and errs[0] > errs[1], errs
+
+
+def test_voxel_casting_mesh():
+    """The voxelised casting in its mold shell: closed cell surfaces, every
+    cell a cube of the voxel size, walls facing outward, metal volume equal
+    to the voxel count of plate, ribs and riser, and the metal enclosed by
+    the shell (no wall face on a metal cell)."""
+    from fvs_inputs import casting_mesh
+    h = 0.005
+    m = casting_mesh(h)
+    g = geom(m)
+    s = g.Div @ g.Sf
+    assert np.all(np.abs(s).max(axis=1) <= 1e-14 * (np.abs(g.Div) @ g.Af))
+    np.testing.assert_allclose(g.V, h ** 3, rtol=1e-12)
+    assert np.abs(g.w).max() < 1e-9 * np.abs(1 / g.ndotd).min()
+    zone = m["cell_zone"]
+    # plate 40 x 20 x 4 voxels, three ribs 1 x 20 x 2, riser 4 x 4 x 4
+    assert (zone == 0).sum() == 40 * 20 * 4 + 3 * 1 * 20 * 2 + 4 * 4 * 4
+    wall = ~g.interior
+    assert np.all(zone[g.owner[wall]] == 1)
+    # outward normals on the walls: they point away from the owner's centre
+    X = np.asarray(m["nodes"])
+    xc = X[np.asarray(m["cells"])].mean(axis=1)
+    fc = X[np.asarray(m["faces"])].mean(axis=1)
+    out = np.einsum("fi,fi->f", g.n[wall], fc[wall] - xc[g.owner[wall]])
+    assert np.all(out > 0)

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 import scipy.sparse.linalg as spla
 
-from fvs_inputs import box_mesh, cases, zones_inner_box
+from fvs_inputs import box_mesh, cases, casting_mesh, zones_inner_box
 from oracle.analytic import neumann_isothermal, stefan_linear
 from oracle.fv import Oracle, darcy_coefficient, sdas_um, solid_fraction, yield_strength_mpa
 from tests.helpers import mushy_field, set_state
@@ -111,7 +111,7 @@ def test_stefan_linear_solid_fraction():
     assert worst[2] < 0.8 and worst[0] / worst[2] > 5.0, worst
 
 
-@pytest.mark.parametrize("with_mold,scheil", [(False, False), (True, False), (False, True)])
+@pytest.mark.parametrize("with_mold,scheil", [(False, False), (True, False), (False, True), ("casting", False)])
 def test_global_energy_balance(with_mold, scheil):
     """Summed over the cavity, the energy change of a step (sensible minus
     latent) equals dt times the mean of the wall heat flow at both time
@@ -120,7 +120,11 @@ def test_global_energy_balance(with_mold, scheil):
     solid-fraction law in use (linear or Eq. 21)."""
     m = box_mesh(8, 8, 3, cases.CAVITY, jitter=0.15, jitter_seed=2)
     extra = {}
-    if with_mold:
+    if with_mold == "casting":
+        # voxelised plate with ribs and riser in its steel shell
+        m = casting_mesh(0.005)
+        extra = dict(mold=dict(cases.STEEL_MOLD))
+    elif with_mold:
         m = dict(m, cell_zone=zones_inner_box(m, (0.02, 0.02, -1.0), (0.08, 0.08, 1.0)))
         extra = dict(mold=dict(rho=7800.0, cp=500.0, k=30.0, h=2000.0, T_init=600.0))
     if scheil:
