@@ -35,6 +35,12 @@ Readings of points the paper leaves open (each is listed in the design doc too):
    gradients are smeared
  * the pressure of each connected part of the pressure system is fixed by
    zero mean; the right side is projected to zero sum on each part
+ * grain growth (Eq. 24-26): S takes the sign of the invariant-size
+   approximation, S = 2 (C_l - C_0)/(C_s - C_l) <= 0, with the Scheil
+   interface contents C_l = C_0 (1 - fs)^(kp - 1), C_s = kp C_l (as printed,
+   with C_s - C_0 on top, S lies in (0, 2] and Eq. 25 has no real root);
+   a cell grows only while 0 < fs < 1; d(r^2)/dt = lambda_s^2 D_s is
+   integrated by the trapezoidal rule over each step, from r_0
 """
 from __future__ import annotations
 
@@ -263,6 +269,31 @@ def solid_fraction_slope(T, T_sol, T_liq, scheil=None):
     return np.where((T > T_liq) | (T < T1), 0.0, np.where(T < T2, d_smr, d_sch))
 
 
+def grain_supersaturation(fs, kp):
+    """Eq. 26 in the sign of the invariant-size approximation:
+    S = 2 (C_l - C_0)/(C_s - C_l) with C_l = C_0 (1 - fs)^(kp - 1) and
+    C_s = kp C_l, so that C_0 / C_l = (1 - fs)^(1 - kp) and C_0 cancels."""
+    fs = np.clip(np.asarray(fs, dtype=np.float64), 0.0, 1.0)
+    c0_over_cl = (1.0 - fs) ** (1.0 - kp)
+    return 2.0 * (1.0 - c0_over_cl) / (kp - 1.0)
+
+
+def grain_lambda(fs, kp):
+    """Eq. 25: lambda_s = -S/(2 sqrt(pi)) + sqrt(S^2/(4 pi) - S); zero
+    outside the mushy range (no liquid to grow into, or no solid yet)."""
+    fs = np.asarray(fs, dtype=np.float64)
+    S = grain_supersaturation(fs, kp)
+    lam = -S / (2.0 * np.sqrt(np.pi)) + np.sqrt(np.maximum(S * S / (4.0 * np.pi) - S, 0.0))
+    return np.where((fs > 0.0) & (fs < 1.0), lam, 0.0)
+
+
+def grain_update(r2, fs_a, fs_b, dt, kp, D_s):
+    """One step of Eq. 24 written for r^2: d(r^2)/dt = lambda_s^2 D_s, by the
+    trapezoidal rule between the solid fractions at both ends of the step."""
+    la, lb = grain_lambda(fs_a, kp), grain_lambda(fs_b, kp)
+    return r2 + dt * D_s * 0.5 * (la * la + lb * lb)
+
+
 def darcy_coefficient(fs, C, eps):
     return C * fs * fs / ((1.0 - fs) ** 3 + eps)
 
@@ -361,6 +392,9 @@ class Oracle:
         self.T = np.where(self.metal, props["T_init"], mold["T_init"] if mold else props["T_init"])
         self.scheil = scheil_law(m)
         self.fs = self.fs_of(self.T)
+        # grain growth (Eq. 24-26): props["grain"] = dict(kp, D_s, r0)
+        self.grain = props.get("grain")
+        self.reset_grain()
         self.T_old = self.T.copy()
         self.u = np.zeros((g.Nc, 3))
         self.u_old = np.zeros((g.Nc, 3))
@@ -374,6 +408,14 @@ class Oracle:
         self.stats = {}
 
     # -- helpers ---------------------------------------------------------------
+    def reset_grain(self):
+        r0 = self.grain["r0"] if self.grain else 0.0
+        self.r2 = np.where(self.metal, r0 * r0, 0.0)
+
+    def grain_radius(self):
+        """Grain radius per cell (m); 0 in the mold."""
+        return np.sqrt(self.r2)
+
     def fs_of(self, T):
         """Solid fraction of every cell at temperatures T (0 in the mold)."""
         m = self.m
@@ -483,8 +525,12 @@ class Oracle:
         # 5. energy with latent heat on all cells (Eq. 4, Eq. 18-20)
         T_new, fs_new, e_its = self.energy(dt, T_n, fs_n, self.T_old, F_n, F_o)
 
-        # 6. microstructure bookkeeping (Eq. 22-23 use the local cooling rate)
+        # 6. microstructure bookkeeping (Eq. 22-23 use the local cooling rate;
+        # Eq. 24-26 grow the grains of the cells that are mushy)
         self.update_crossings(T_n, T_new, dt)
+        if self.grain:
+            gr = self.grain
+            self.r2 = np.where(self.metal, grain_update(self.r2, fs_n, fs_new, dt, gr["kp"], gr["D_s"]), 0.0)
 
         self.stats.update(e_its=e_its, n_faces_case2=int((case == 2).sum()),
                           n_faces_case3=int((case == 3).sum()))

@@ -42,6 +42,7 @@ def set_state(o, T, u=None):
     o.T = np.array(T, dtype=np.float64)
     o.T_old = o.T.copy()
     o.fs = o.fs_of(o.T)
+    o.reset_grain()
     o.t_liq = np.where(metal & (o.T <= m["T_liq"]), 0.0, -1.0)
     o.t_sol = np.where(metal & (o.T <= m["T_sol"]), 0.0, -1.0)
     if u is not None:
