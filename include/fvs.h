@@ -177,6 +177,19 @@ fvs_status fvs_set_properties(fvs_solver solver, const fvs_props* props);
  * fvs_set_properties; FVS_ERR_ARG for non-positive rho, cp, k or h. */
 fvs_status fvs_set_mold(fvs_solver solver, double rho, double cp, double k, double h, double T_init);
 
+/* Grain growth (Eq. 24-26): while a metal cell is mushy (0 < fs < 1) its
+ * grain radius r grows by d(r^2)/dt = lambda_s^2 D_s, integrated by the
+ * trapezoidal rule between the solid fractions at both ends of each step.
+ * lambda_s = -S/(2 sqrt(pi)) + sqrt(S^2/(4 pi) - S) with the supersaturation
+ * S = 2 (C_l - C_0)/(C_s - C_l) of the Scheil interface contents
+ * C_l = C_0 (1 - fs)^(kp - 1), C_s = kp C_l (C_0 cancels; the sign is the one
+ * that keeps lambda_s real).  kp: partition coefficient (0 < kp < 1), D_s:
+ * solute diffusion coefficient in the liquid (m2/s, >= 0; 0 switches growth
+ * off), r0: initial radius (m, >= 0).  Resets every metal cell to r0 now and
+ * whenever the state is reset; stays set across fvs_set_properties.
+ * FVS_ERR_STATE before fvs_set_properties; FVS_ERR_ARG otherwise. */
+fvs_status fvs_set_grain_growth(fvs_solver solver, double kp, double D_s, double r0);
+
 /* Overwrite the state with a given temperature field (and velocity, or NULL
  * for rest): T^n = T^{n-1} = T, fs = fs(T), u^n = u^{n-1} = u (zero in solid
  * cells), fluxes and pressure zero, time 0, crossing times reset.
@@ -233,7 +246,9 @@ typedef enum {
                       [n_cells*4]; NaN where the cell has not solidified      */
   FVS_USTAR = 7,   /* predictor velocity u* of the last step [n_cells*3]      */
   FVS_CROSS = 8,   /* liquidus / solidus crossing times [n_cells*2], -1 unset */
-  FVS_FACE_CASE = 9 /* pressure face case 0 wall,1,2,3 as double [n_faces]   */
+  FVS_FACE_CASE = 9, /* pressure face case 0 wall,1,2,3 as double [n_faces]  */
+  FVS_GRAIN = 10   /* grain radius in m [n_cells] (fvs_set_grain_growth), 0 in
+                      the mold                                                */
 } fvs_field;
 
 /* Copy a field (double values, input numbering) into dst (dst_len doubles,

@@ -259,6 +259,15 @@ FVS_API fvs_status fvs_set_mold(fvs_solver s, double rho, double cp, double k, d
   return solver_set_mold(s, rho, cp, k, h, T_init);
 }
 
+FVS_API fvs_status fvs_set_grain_growth(fvs_solver s, double kp, double D_s, double r0) {
+  if (!s) {
+    set_error("fvs_set_grain_growth: NULL solver");
+    return FVS_ERR_ARG;
+  }
+  AllocStream as(s->stream);
+  return solver_set_grain(s, kp, D_s, r0);
+}
+
 FVS_API fvs_status fvs_set_state(fvs_solver s, const double* T, const double* u, int on_device) {
   if (!s || !T) {
     set_error("fvs_set_state: NULL argument");

@@ -56,6 +56,10 @@ __global__ void k_na_gather(int64_t n, int comps, const int32_t* to_in, const do
     for (int d = 0; d < comps; ++d) out[comps * o + d] = src[d * n + i];
   }
 }
+// out[to_in[i]] = sqrt(a[i]) (grain radius from its square)
+__global__ void k_na_sqrt(int64_t n, const int32_t* to_in, const double* a, double* out) {
+  GS(i, n) out[to_in[i]] = sqrt(a[i]);
+}
 // out[2*to_in[i]] = a[i], out[2*to_in[i]+1] = b[i]
 __global__ void k_na_pair(int64_t n, const int32_t* to_in, const double* a, const double* b, double* out) {
   GS(i, n) {
@@ -104,7 +108,7 @@ extern "C" __attribute__((visibility("default"))) fvs_status fvs_query_fields_no
   const int64_t Nc = m->Nc, Nf = m->Nf;
   int64_t need = 0;
   switch (field) {
-    case FVS_T: case FVS_FS: case FVS_P: case FVS_TAG: need = Nc; break;
+    case FVS_T: case FVS_FS: case FVS_P: case FVS_TAG: case FVS_GRAIN: need = Nc; break;
     case FVS_U: case FVS_USTAR: need = 3 * Nc; break;
     case FVS_QOI: need = 4 * Nc; break;
     case FVS_CROSS: need = 2 * Nc; break;
@@ -137,6 +141,7 @@ extern "C" __attribute__((visibility("default"))) fvs_status fvs_query_fields_no
     case FVS_FACE_CASE: k_na_u8<<<gf, 256, 0, st>>>(Nf, m->face_in, s->fcase, buf); break;
     case FVS_QOI: k_na_qoi<<<gc, 256, 0, st>>>(Nc, m->cell_in, s->tliq, s->tsol, Ts, Tl, buf); break;
     case FVS_CROSS: k_na_pair<<<gc, 256, 0, st>>>(Nc, m->cell_in, s->tliq, s->tsol, buf); break;
+    case FVS_GRAIN: k_na_sqrt<<<gc, 256, 0, st>>>(Nc, m->cell_in, s->r2, buf); break;
     default: break;
   }
   FVS_COUNT_LAUNCH();

@@ -529,6 +529,31 @@ __global__ void k_crossings(int64_t Nc, const double* Tn, const double* Tnew, do
   }
 }
 
+// grain growth (Eq. 24-26): lambda_s of the invariant-size approximation for
+// the Scheil interface contents (C_0 / C_l = (1 - fs)^(1 - kp)), zero outside
+// the mushy range
+__device__ __forceinline__ double grain_lambda(double fs, double kp) {
+  if (!(fs > 0.0 && fs < 1.0)) return 0.0;
+  const double S = 2.0 * (1.0 - pow(1.0 - fs, 1.0 - kp)) / (kp - 1.0);
+  const double pi = 3.14159265358979323846;
+  return -S / (2.0 * sqrt(pi)) + sqrt(fmax(S * S / (4.0 * pi) - S, 0.0));
+}
+// d(r^2)/dt = lambda_s^2 D_s, trapezoidal over the step
+__global__ void k_grain(int64_t Nc, const double* fsa, const double* fsb, const uint8_t* metal, double kp, double Ds,
+                        double dt, double* r2) {
+  GS(c, Nc) {
+    if (!metal[c]) continue;
+    const double la = grain_lambda(fsa[c], kp), lb = grain_lambda(fsb[c], kp);
+    r2[c] += dt * Ds * 0.5 * (la * la + lb * lb);
+  }
+}
+__global__ void k_grain_init(int64_t Nc, const uint8_t* metal, double r0, double* r2) {
+  GS(c, Nc) r2[c] = metal[c] ? r0 * r0 : 0.0;
+}
+__global__ void k_sqrt_out(int64_t n, const int32_t* to_in, const double* a, double* out) {
+  GS(c, n) out[to_in[c]] = sqrt(a[c]);
+}
+
 // ---------------------------------------------------------------------------
 // state set-up and queries
 // ---------------------------------------------------------------------------
@@ -698,6 +723,27 @@ fvs_status solver_set_mold(fvs_solver s, double rho, double cp, double k, double
   return apply_properties(s, &p);
 }
 
+fvs_status solver_set_grain(fvs_solver s, double kp, double D_s, double r0) {
+  if (!s->have_props) {
+    set_error("fvs_set_properties must come first");
+    return FVS_ERR_STATE;
+  }
+  if (!(kp > 0.0 && kp < 1.0 && D_s >= 0.0 && r0 >= 0.0)) {
+    set_error("invalid grain-growth data (0 < kp < 1, D_s >= 0, r0 >= 0)");
+    return FVS_ERR_ARG;
+  }
+  s->grain_on = D_s > 0.0;
+  s->grain_kp = kp;
+  s->grain_Ds = D_s;
+  s->grain_r0 = r0;
+  const int64_t Nc = s->mesh->Nc;
+  FVS_TRY(s->r2.alloc(Nc));
+  k_grain_init<<<stride_grid(Nc, 256), 256, 0, s->stream>>>(Nc, s->metal, r0, s->r2); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  FVS_CUDA(cudaStreamSynchronize(s->stream));
+  return FVS_OK;
+}
+
 static fvs_status apply_properties(fvs_solver s, const fvs_props* p) {
   fvs_mesh m = s->mesh;
   if (p->n_patches < m->npatch || (p->n_patches > 0 && !p->bc)) {
@@ -787,6 +833,9 @@ fvs_status solver_set_state(fvs_solver s, const double* T, const double* u, int 
   FVS_LAUNCH_CHECK();
   FVS_TRY(s->F.zero(st)); FVS_TRY(s->Fold.zero(st)); FVS_TRY(s->Fnew.zero(st));
   FVS_TRY(s->ustar.zero(st));
+  FVS_TRY(s->r2.alloc(Nc));
+  k_grain_init<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->metal, s->grain_r0, s->r2); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
   FVS_CUDA(cudaStreamSynchronize(st));
   s->time = 0.0;
   s->nstep = 0;
@@ -1166,6 +1215,11 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
   k_crossings<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, s->Tnew, mt.Ts, mt.Tl, s->time, dt, s->tliq, s->tsol,
                                                     s->metal);
   FVS_COUNT_LAUNCH();
+  if (s->grain_on) {
+    k_grain<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->fs, s->fsnew, s->metal, s->grain_kp, s->grain_Ds, dt,
+                                                  s->r2);
+    FVS_COUNT_LAUNCH();
+  }
   FVS_LAUNCH_CHECK();
   dswap(s->Told, s->T);     // Told <- T^n
   dswap(s->T, s->Tnew);     // T <- T^{n+1}
@@ -1219,7 +1273,7 @@ fvs_status solver_query(fvs_solver s, fvs_field f, double* dst, int64_t len, int
   const int64_t Nc = m->Nc, Nf = m->Nf;
   int64_t need = 0;
   switch (f) {
-    case FVS_T: case FVS_FS: case FVS_P: case FVS_TAG: need = Nc; break;
+    case FVS_T: case FVS_FS: case FVS_P: case FVS_TAG: case FVS_GRAIN: need = Nc; break;
     case FVS_U: case FVS_USTAR: need = 3 * Nc; break;
     case FVS_QOI: need = 4 * Nc; break;
     case FVS_CROSS: need = 2 * Nc; break;
@@ -1248,6 +1302,7 @@ fvs_status solver_query(fvs_solver s, fvs_field f, double* dst, int64_t len, int
     case FVS_TAG: k_gather_u8<<<gc, 256, 0, st>>>(Nc, m->cell_in, s->lm, out); break;
     case FVS_FACE_CASE: k_gather_u8<<<gf, 256, 0, st>>>(Nf, m->face_in, s->fcase, out); break;
     case FVS_QOI: k_qoi<<<gc, 256, 0, st>>>(Nc, m->cell_in, s->tliq, s->tsol, mt.Ts, mt.Tl, out); break;
+    case FVS_GRAIN: k_sqrt_out<<<gc, 256, 0, st>>>(Nc, m->cell_in, s->r2, out); break;
     case FVS_CROSS: {
       DBuf<double> both;
       FVS_TRY(both.alloc(2 * Nc));

@@ -30,6 +30,10 @@ struct fvs_solver_s {
   // mold zone (conduction only) and the metal-mold interface coefficient
   bool has_mold = false;
   double mold_rho = 0.0, mold_cp = 0.0, mold_k = 0.0, mold_h = 0.0, mold_T = 0.0;
+  // grain growth (Eq. 24-26): r^2 per cell
+  bool grain_on = false;
+  double grain_kp = 0.0, grain_Ds = 0.0, grain_r0 = 0.0;
+  fvs::DBuf<double> r2;
   double time = 0.0;
   int64_t nstep = 0;
 
@@ -83,6 +87,7 @@ namespace fvs {
 fvs_status solver_alloc(fvs_solver s);
 fvs_status solver_set_properties(fvs_solver s, const fvs_props* p);
 fvs_status solver_set_mold(fvs_solver s, double rho, double cp, double k, double h, double T_init);
+fvs_status solver_set_grain(fvs_solver s, double kp, double D_s, double r0);
 fvs_status solver_set_state(fvs_solver s, const double* T, const double* u, int on_device);
 fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* st);
 fvs_status solver_pressure_solve(fvs_solver s, const double* rhs, double* p_out, double rtol, int* iters,

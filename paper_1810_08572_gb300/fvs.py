@@ -30,7 +30,7 @@ STATUS = {0: "FVS_OK", 1: "FVS_ERR_ARG", 2: "FVS_ERR_MESH", 3: "FVS_ERR_CUDA", 4
 FVS_BC_ADIABATIC, FVS_BC_DIRICHLET = 0, 1
 FVS_PREC_FP64, FVS_PREC_MIXED = 0, 1
 FVS_PSOLVER_AMG, FVS_PSOLVER_JACOBI = 0, 1
-FIELDS = dict(T=0, FS=1, U=2, P=3, FLUX=4, TAG=5, QOI=6, USTAR=7, CROSS=8, FACE_CASE=9)
+FIELDS = dict(T=0, FS=1, U=2, P=3, FLUX=4, TAG=5, QOI=6, USTAR=7, CROSS=8, FACE_CASE=9, GRAIN=10)
 
 
 class FvsError(RuntimeError):
@@ -98,6 +98,7 @@ _SIGS = {
     "fvs_set_properties": ([_P, C.POINTER(fvs_props)], C.c_int),
     "fvs_mesh_set_zones": ([_P, _P], C.c_int),
     "fvs_set_mold": ([_P, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double], C.c_int),
+    "fvs_set_grain_growth": ([_P, C.c_double, C.c_double, C.c_double], C.c_int),
     "fvs_set_state": ([_P, _P, _P, C.c_int], C.c_int),
     "fvs_step": ([_P, C.c_double, C.c_int32, C.POINTER(fvs_step_stats)], C.c_int),
     "fvs_pressure_solve": ([_P, _P, _P, C.c_double, C.POINTER(C.c_int32), C.POINTER(C.c_double)], C.c_int),
@@ -316,6 +317,10 @@ class Solver:
         if mold is not None:
             check(fvs_set_mold(self.h, float(mold["rho"]), float(mold["cp"]), float(mold["k"]), float(mold["h"]),
                                float(mold["T_init"])), "fvs_set_mold")
+        grain = props.get("grain")
+        if grain is not None:
+            check(fvs_set_grain_growth(self.h, float(grain["kp"]), float(grain["D_s"]), float(grain["r0"])),
+                  "fvs_set_grain_growth")
 
     def set_state(self, T, u=None):
         """T [n_cells], u [n_cells, 3] (host numpy or device tensors, input numbering)."""
@@ -336,7 +341,7 @@ class Solver:
         """Field in input numbering: host numpy array, or into a device tensor ``out``."""
         f = FIELDS[name]
         nc, nf = self.mesh.n_cells, self.mesh.n_faces
-        n = {0: nc, 1: nc, 2: 3 * nc, 3: nc, 4: nf, 5: nc, 6: 4 * nc, 7: 3 * nc, 8: 2 * nc, 9: nf}[f]
+        n = {0: nc, 1: nc, 2: 3 * nc, 3: nc, 4: nf, 5: nc, 6: 4 * nc, 7: 3 * nc, 8: 2 * nc, 9: nf, 10: nc}[f]
         if out is None:
             a = np.empty(n, dtype=np.float64)
             check(fvs_query_fields(self.h, f, _ptr(a), n, 0), "fvs_query_fields")
