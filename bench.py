@@ -31,6 +31,15 @@ sys.path.insert(0, ROOT)
 
 METRIC = "active cell-steps/s at 1e-8 pressure residual (mixed vs FP64) + UQ samples/s"
 
+# CUDA kernel behind each timed class of the solver's kernel timing
+CUDA_NAME = {"residual_vc": "k_resid<double>", "jacobi": "k_jac<double>", "jacobi0": "k_jac0<double>",
+             "spmv": "k_spmv_dot", "residual": "k_residual"}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture)
+# per algorithmic byte of the same launches, applied to the bench launch:
+# k_spmv_dot on the 96^3 cavity, 320.65 MB against 307.89 MB
+# (profiles/spmv_dot_cavity96_fp64.md)
+DRAM_PER_ALGORITHMIC = {"spmv": 320.65 / 307.89}
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -244,23 +253,38 @@ def run_gpu(args):
         act = float(a.item())
     value = act / (ms / 1e3)
 
-    # roofline of the kernel class with the largest total time
+    # roofline of the kernel with the largest total time.  A V-cycle kernel
+    # is one CUDA kernel on every level of the hierarchy, so its fine-level
+    # and coarse-level classes are summed (the ncu launch list names the
+    # kernel, not the level); the per-level split is kept beside it.
     peak, peak_kind = load_peaks()
-    top = max(prof, key=lambda r: r["total_ms"]) if prof else None
+    fams = {}
+    for r in prof:
+        key = r["name"].replace("_coarse", "")
+        f = fams.setdefault(key, dict(name=key, launches=0, total_ms=0.0, bytes=0.0, levels={}))
+        f["launches"] += r["launches"]
+        f["total_ms"] += r["total_ms"]
+        f["bytes"] += r["bytes"]
+        f["levels"]["coarse" if "_coarse" in r["name"] else "fine"] = r
+    top = max(fams.values(), key=lambda f: f["total_ms"]) if fams else None
     roof = None
     if top:
+        base = top["name"].split("@")[0]
         per_launch_bytes = top["bytes"] / top["launches"]
-        # DRAM bytes per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum) of
-        # k_spmv_dot on the 96^3 cavity: 320.65 MB against 307.89 MB algorithmic; scaled
-        # with the rows of the launch (profiles/spmv_dot_cavity96_fp64.md)
-        traffic = round(per_launch_bytes * 320.65 / 307.89) if top["name"].startswith("spmv@") else None
         per_launch_s = top["total_ms"] / top["launches"] / 1e3
         ach = per_launch_bytes / per_launch_s / 1e9
-        roof = dict(bound="hbm", kernel=top["name"], achieved=round(ach, 1), peak=peak, unit="GB/s",
-                    frac=round(ach / peak, 4), traffic=traffic, peak_source=f"{peak_kind} copy bandwidth",
-                    launches=top["launches"],
+        ratio = DRAM_PER_ALGORITHMIC.get(base)
+        levels = {}
+        for lvl, r in sorted(top["levels"].items()):
+            a = r["bytes"] / (r["total_ms"] / 1e3) / 1e9
+            levels[lvl] = dict(launches=r["launches"], total_ms=round(r["total_ms"], 3), achieved=round(a, 1),
+                               frac=round(a / peak, 4))
+        roof = dict(bound="hbm", kernel=f"{CUDA_NAME.get(base, base)} ({top['name']}, all levels)",
+                    achieved=round(ach, 1), peak=peak, unit="GB/s", frac=round(ach / peak, 4),
+                    traffic=round(per_launch_bytes * ratio) if ratio else None,
+                    peak_source=f"{peak_kind} copy bandwidth", launches=top["launches"],
                     share_of_step=round(top["total_ms"] / max(1, args.prof_steps) / (ms / args.steps), 3),
-                    bytes_per_launch=per_launch_bytes)
+                    bytes_per_launch=per_launch_bytes, levels=levels)
 
     mixed = None
     if ref_fields is not None:
@@ -290,7 +314,7 @@ def run_gpu(args):
                     parallelism="replicas" if world > 1 else "single GPU"),
         roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=ck, uq=uq, mixed=mixed,
         gpu_launches=int(n_launch),
-        kernel_profile=sorted(prof, key=lambda r: -r["total_ms"])[:8],
+        kernel_profile=sorted(prof, key=lambda r: -r["total_ms"])[:12],
         step_stats=dict(p_its=[s["p_its"] for s in its], e_its=[s["e_its"] for s in its],
                         e_lin_its=[s["e_lin_its"] for s in its], mom_its=[s["mom_its"] for s in its],
                         p_relres=max(s["p_relres"] for s in its), fallback=sum(s["fallback"] for s in its),

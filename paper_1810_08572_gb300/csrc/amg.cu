@@ -468,6 +468,13 @@ __global__ void __launch_bounds__(256) k_galerkin_wide(int64_t nc, int64_t n, in
   }
 }
 
+__global__ void k_sum_i32(int64_t n, const int32_t* a, unsigned long long* out) {
+  unsigned long long t = 0;
+  GS(i, n) t += (unsigned long long)(a[i] > 0 ? a[i] : 0);
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0 && t) atomicAdd(out, t);
+}
+
 __global__ void k_max_int(int64_t n, const int32_t* a, int* out) {
   int m = 0;
   GS(i, n) m = max(m, (int)a[i]);
@@ -872,6 +879,75 @@ __global__ void k_resid(int64_t n, int w, const int32_t* __restrict__ col, const
     r[i] = b[i] - acc;
   }
 }
+// Coarse levels, CG lanes per row: lane q of a row sums the stored entries
+// q, q + CG, q + 2 CG, ... (four loads in flight), then the row's lanes add
+// their partial sums by shuffles.  The 32 / CG rows of a warp are
+// consecutive, so with slot-major storage every slot's values and columns of
+// those rows fill whole 32-byte sectors, rows of uneven length idle fewer
+// lanes than one thread per row does, and short serial chains keep the small
+// levels (latency-bound) from waiting on one gather after another.
+constexpr int CG = 4;
+template <typename T>
+__device__ __forceinline__ T coarse_part(int64_t n, const int32_t* __restrict__ col, const T* __restrict__ val,
+                                         const T* __restrict__ x, int len, int64_t i, int q) {
+  T acc = 0;
+  int k = q;
+  for (; k + 3 * CG < len; k += 4 * CG) {
+    const int64_t e0 = (int64_t)k * n + i, e1 = e0 + (int64_t)CG * n, e2 = e1 + (int64_t)CG * n,
+                  e3 = e2 + (int64_t)CG * n;
+    const int32_t c0 = col[e0], c1 = col[e1], c2 = col[e2], c3 = col[e3];
+    const T v0 = val[e0], v1 = val[e1], v2 = val[e2], v3 = val[e3];
+    const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+    acc = fma(v0, x0, acc);
+    acc = fma(v1, x1, acc);
+    acc = fma(v2, x2, acc);
+    acc = fma(v3, x3, acc);
+  }
+  for (; k < len; k += CG) {
+    const int64_t e = (int64_t)k * n + i;
+    acc = fma(val[e], x[col[e]], acc);
+  }
+  return acc;
+}
+template <typename T>
+__device__ __forceinline__ T lanes_sum(T v) {
+#pragma unroll
+  for (int o = 1; o < CG; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+// r = b - A x on a coarse level (warp-uniform loop over groups of rows)
+template <typename T>
+__global__ void k_resid_g(int64_t n, const int32_t* __restrict__ col, const T* __restrict__ val,
+                          const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r,
+                          const int32_t* __restrict__ rlen) {
+  const int lane = threadIdx.x & 31, q = lane & (CG - 1);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i0 = warp * (32 / CG); i0 < n; i0 += nw * (32 / CG)) {
+    const int64_t i = i0 + lane / CG;
+    const bool ok = i < n;
+    T acc = ok ? coarse_part(n, col, val, x, rlen[i], i, q) : (T)0;
+    acc = lanes_sum(acc);
+    if (ok && q == 0) r[i] = b[i] - acc;
+  }
+}
+// y = x + omega D^-1 (b - A x) on a coarse level
+template <typename T>
+__global__ void k_jac_g(int64_t n, const int32_t* __restrict__ col, const T* __restrict__ val, T omega,
+                        const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
+                        T* __restrict__ y, const int32_t* __restrict__ rlen) {
+  const int lane = threadIdx.x & 31, q = lane & (CG - 1);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i0 = warp * (32 / CG); i0 < n; i0 += nw * (32 / CG)) {
+    const int64_t i = i0 + lane / CG;
+    const bool ok = i < n;
+    T acc = ok ? coarse_part(n, col, val, x, rlen[i], i, q) : (T)0;
+    acc = lanes_sum(acc);
+    if (ok && q == 0) y[i] = x[i] + omega * dinv[i] * (b[i] - acc);
+  }
+}
+
 template <typename T>
 __global__ void k_restrict(int64_t nc, const int32_t* mptr, const int32_t* midx, const T* r, T* bc) {
   GS(I, nc) {
@@ -1018,6 +1094,29 @@ static void galerkin_pass(cudaStream_t s, bool fill, int64_t nc, const Ell& A, c
 static double env_num(const char* name, double dflt) {
   const char* v = getenv(name);
   return (v && *v) ? atof(v) : dflt;
+}
+
+// entries per level that one smoother or residual sweep reads: every slot on
+// the fine level, the stored entries of each row on the coarse levels (for
+// the algorithmic bytes of the kernel timing)
+fvs_status Amg::count_stored(cudaStream_t s) {
+  DBuf<unsigned long long> acc;
+  FVS_TRY(acc.alloc(1));
+  for (auto& up : lv) {
+    AmgLevel* L = up.get();
+    if (!L->rlen.n || L->n == 0) {
+      L->stored = (double)L->n * (double)(L->A ? L->A->w : 0);
+      continue;
+    }
+    FVS_CUDA(cudaMemsetAsync(acc.p, 0, sizeof(unsigned long long), s));
+    k_sum_i32<<<stride_grid(L->n, 256), 256, 0, s>>>(L->n, L->rlen, acc); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+    unsigned long long h = 0;
+    FVS_CUDA(cudaMemcpyAsync(&h, acc.p, sizeof(h), cudaMemcpyDeviceToHost, s));
+    FVS_CUDA(cudaStreamSynchronize(s));
+    L->stored = (double)h;
+  }
+  return FVS_OK;
 }
 
 fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
@@ -1243,6 +1342,7 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
     fprintf(stderr, " coarsest %d parts %d | ms: misc %.2f strength %.2f mis %.2f members %.2f galerkin %.2f "
             "coarsest %.2f fp32 %.2f\n", nc, ncomp, tph[0], tph[1], tph[2], tph[3], tph[4], tph[5], tph[6]);
   }
+  FVS_TRY(count_stored(s));
   ready = true;
   return FVS_OK;
 }
@@ -1448,6 +1548,7 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
     fprintf(stderr, "[fvs amg] refresh ms: fingerprints+members %.2f galerkin %.2f coarsest %.2f labels+fp32 %.2f\n",
             tph[0], tph[1], tph[2], tph[3]);
   masked = true;
+  FVS_TRY(count_stored(s));
   ready = true;
   return FVS_OK;
 }
@@ -1494,21 +1595,39 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
   T* cb = f32 ? (T*)C->bf.p : (T*)C->b.p;
   T* cy = f32 ? (T*)C->yf.p : (T*)C->y.p;
   const double vb = (double)sizeof(T);
-  const double jac_bytes = (double)n * ((4.0 + vb) * A.w + 4.0 * vb);
+  // kernel timing: every level is credited to the hierarchy's fine operator,
+  // coarse levels under their own class names; algorithmic bytes from the
+  // entries a sweep reads (value + column per entry) and its vectors
+  const void* pkey = lv[0]->A;
+  const bool cl = l > 0;
+  const double ent = L->stored > 0.0 ? L->stored : (double)n * A.w;
+  const double jac_bytes = (4.0 + vb) * ent + 4.0 * vb * (double)n;
+  const double res_bytes = (4.0 + vb) * ent + 3.0 * vb * (double)n;
   const int32_t* rl = L->rlen.n ? L->rlen.p : nullptr;   // coarse levels: stored row lengths
   const int g = stride_grid(n, 256);
+  const char* n_jac0 = f32 ? (cl ? "jacobi0_f32_coarse" : "jacobi0_f32") : (cl ? "jacobi0_coarse" : "jacobi0");
+  const char* n_jac = f32 ? (cl ? "jacobi_f32_coarse" : "jacobi_f32") : (cl ? "jacobi_coarse" : "jacobi");
+  const char* n_res = f32 ? (cl ? "residual_f32_coarse" : "residual_f32") : (cl ? "residual_vc_coarse" : "residual_vc");
   {
-    ProfScope ps(L->A, f32 ? "jacobi0_f32" : "jacobi0", 3.0 * vb * (double)n, s);
+    ProfScope ps(pkey, n_jac0, 3.0 * vb * (double)n, s);
     k_jac0<T><<<g, 256, 0, s>>>(n, (T)opt.omega, dinv, b, xa); FVS_COUNT_LAUNCH();
   }
+  const int gg = stride_grid(n * CG, 256);   // coarse levels: CG lanes per row
+  auto jac = [&](T* xin, T* xout) {
+    ProfScope ps(pkey, n_jac, jac_bytes, s);
+    if (rl) k_jac_g<T><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
+    else k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
+    FVS_COUNT_LAUNCH();
+  };
   for (int k = 1; k < opt.npre; ++k) {
-    ProfScope ps(L->A, f32 ? "jacobi_f32" : "jacobi", jac_bytes, s);
-    k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xa, xb, rl); FVS_COUNT_LAUNCH();
+    jac(xa, xb);
     T* t = xa; xa = xb; xb = t;
   }
   {
-    ProfScope ps(L->A, f32 ? "residual_f32" : "residual_vc", (double)n * ((4.0 + vb) * A.w + 3.0 * vb), s);
-    k_resid<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, xa, b, r, rl); FVS_COUNT_LAUNCH();
+    ProfScope ps(pkey, n_res, res_bytes, s);
+    if (rl) k_resid_g<T><<<gg, 256, 0, s>>>(n, A.col, val, xa, b, r, rl);
+    else k_resid<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, xa, b, r, rl);
+    FVS_COUNT_LAUNCH();
   }
   k_restrict<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cb); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
@@ -1516,8 +1635,7 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
   k_prolong<T><<<g, 256, 0, s>>>(n, L->agg, cy, (T)opt.coarse_scale, xa); FVS_COUNT_LAUNCH();
   for (int k = 0; k < opt.npost; ++k) {
     T* out = (k == opt.npost - 1) ? y : xb;
-    ProfScope ps(L->A, f32 ? "jacobi_f32" : "jacobi", jac_bytes, s);
-    k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xa, out, rl); FVS_COUNT_LAUNCH();
+    jac(xa, out);
     xb = xa;
     xa = out;
   }

@@ -27,6 +27,7 @@ struct AmgLevel {
   DBuf<float> bf, xf, yf, rf, tf; // FP32 V-cycle work
   DBuf<uint8_t> dirty;  // rows changed since the last setup or refresh
   int64_t n = 0;
+  double stored = 0.0;  // operator entries the V-cycle reads (coarse levels: sum of rlen)
 };
 
 struct AmgOptions {
@@ -60,6 +61,7 @@ struct Amg : Precond {
   int refreshes = 0;              // refreshes since the setup
 
   fvs_status setup(cudaStream_t s, const Ell& A);
+  fvs_status count_stored(cudaStream_t s);   // AmgLevel::stored of every level
   // The operator's values changed on the same rows (cells frozen since the
   // setup became identity rows): rows of cells without pressure
   // (ppe[act[i]] == 0) leave their aggregates and the null-space labels, and

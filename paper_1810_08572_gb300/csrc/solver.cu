@@ -23,6 +23,8 @@ struct Mat {
   double rho, k, cp, L, Ts, Tl, mu, beta, Tref, g0, g1, g2, C, eps;
   FsLaw law;    // solid fraction (linear or Eq. 21)
 };
+constexpr int SOLVER_COARSEST = 1000;   // coarsest AMG level of the single solver (dense inverse)
+
 static Mat mat_of(const fvs_props& p) {
   const fvs_material& m = p.mat;
   return Mat{m.rho, m.k, m.cp, m.latent, m.T_sol, m.T_liq, m.mu, m.beta, m.T_ref, m.g[0], m.g[1], m.g[2],
@@ -981,6 +983,10 @@ static fvs_status assemble_pressure(fvs_solver s) {
   s->steps_since_setup = 0;
   if (s->props.p_solver == FVS_PSOLVER_AMG && s->nact > 0) {
     s->amg.opt.fp32 = s->props.precision == FVS_PREC_MIXED;
+    // stop coarsening below a thousand rows: the dense inverse of that level
+    // is one matrix-vector product per V-cycle, cheaper than the several
+    // latency-bound launches per level that the small levels below it cost
+    s->amg.opt.coarsest = SOLVER_COARSEST;
     fvs_status r = s->amg.setup(st, s->K);
     if (r == FVS_OK) {
       s->amg_ok = true;
