@@ -31,14 +31,23 @@ sys.path.insert(0, ROOT)
 
 METRIC = "active cell-steps/s at 1e-8 pressure residual (mixed vs FP64) + UQ samples/s"
 
-# CUDA kernel behind each timed class of the solver's kernel timing
-CUDA_NAME = {"residual_vc": "k_resid<double>", "jacobi": "k_jac<double>", "jacobi0": "k_jac0<double>",
+# CUDA kernel behind each timed class of the solver's kernel timing (the
+# coarse AMG levels run their own sweep kernels; k_jac0 serves every level)
+CUDA_NAME = {"residual_vc": "k_resid<double>", "residual_vc_coarse": "k_resid_g<double>",
+             "jacobi": "k_jac<double>", "jacobi_coarse": "k_jac_g<double>",
+             "jacobi0": "k_jac0<double>", "jacobi0_coarse": "k_jac0<double>",
+             "residual_f32": "k_resid<float>", "residual_f32_coarse": "k_resid_g<float>",
+             "jacobi_f32": "k_jac<float>", "jacobi_f32_coarse": "k_jac_g<float>",
+             "jacobi0_f32": "k_jac0<float>", "jacobi0_f32_coarse": "k_jac0<float>",
              "spmv": "k_spmv_dot", "residual": "k_residual"}
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture)
-# per algorithmic byte of the same launches, applied to the bench launch:
-# k_spmv_dot on the 96^3 cavity, 320.65 MB against 307.89 MB
-# (profiles/spmv_dot_cavity96_fp64.md)
-DRAM_PER_ALGORITHMIC = {"spmv": 320.65 / 307.89}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum of one ncu
+# capture, cold cache) per algorithmic byte of the same launches on the 96^3
+# cavity, applied to the bench launch (summaries under profiles/):
+# k_spmv_dot 320.65 MB against 307.89 MB; k_resid (fine level) 304.36 MB
+# against 307.89 MB; k_resid_g, the five coarse levels of one V-cycle,
+# 207.34 MB against 165.24 MB
+DRAM_PER_ALGORITHMIC = {"k_spmv_dot": 320.65 / 307.89, "k_resid<double>": 304.36 / 307.89,
+                        "k_resid_g<double>": 207.34 / 165.24}
 
 
 def parse():
@@ -69,6 +78,17 @@ def parse():
 def workload(n):
     from fvs_inputs import cases
     return cases.config_jittered(n=n)
+
+
+def reduce_over_ranks(dist, ms, act, device):
+    """Whole-job figures of a replicated run: the slowest rank's time and the
+    active cell-steps of all ranks together."""
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    a = torch.tensor([float(act)], device=device, dtype=torch.float64)
+    dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(a.item())
 
 
 def bench_props(precision):
@@ -245,46 +265,35 @@ def run_gpu(args):
     prof = S.profile_read()
     S.profile(False)
     if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        a = torch.tensor([act], device="cuda", dtype=torch.float64)
-        dist.all_reduce(a)
-        act = float(a.item())
+        ms, act = reduce_over_ranks(dist, ms, act, "cuda")
     value = act / (ms / 1e3)
 
-    # roofline of the kernel with the largest total time.  A V-cycle kernel
-    # is one CUDA kernel on every level of the hierarchy, so its fine-level
-    # and coarse-level classes are summed (the ncu launch list names the
-    # kernel, not the level); the per-level split is kept beside it.
+    # roofline of the CUDA kernel with the largest total time (classes that
+    # run the same kernel -- several matrices, or every level for k_jac0 --
+    # are summed, as the ncu launch list sums launches of one kernel)
     peak, peak_kind = load_peaks()
-    fams = {}
+    groups = {}
     for r in prof:
-        key = r["name"].replace("_coarse", "")
-        f = fams.setdefault(key, dict(name=key, launches=0, total_ms=0.0, bytes=0.0, levels={}))
-        f["launches"] += r["launches"]
-        f["total_ms"] += r["total_ms"]
-        f["bytes"] += r["bytes"]
-        f["levels"]["coarse" if "_coarse" in r["name"] else "fine"] = r
-    top = max(fams.values(), key=lambda f: f["total_ms"]) if fams else None
+        cls = r["name"].split("@")[0]
+        kern = CUDA_NAME.get(cls, cls)
+        g = groups.setdefault(kern, dict(kernel=kern, launches=0, total_ms=0.0, bytes=0.0, classes=[]))
+        g["launches"] += r["launches"]
+        g["total_ms"] += r["total_ms"]
+        g["bytes"] += r["bytes"]
+        g["classes"].append(r["name"])
+    top = max(groups.values(), key=lambda g: g["total_ms"]) if groups else None
     roof = None
     if top:
-        base = top["name"].split("@")[0]
         per_launch_bytes = top["bytes"] / top["launches"]
         per_launch_s = top["total_ms"] / top["launches"] / 1e3
         ach = per_launch_bytes / per_launch_s / 1e9
-        ratio = DRAM_PER_ALGORITHMIC.get(base)
-        levels = {}
-        for lvl, r in sorted(top["levels"].items()):
-            a = r["bytes"] / (r["total_ms"] / 1e3) / 1e9
-            levels[lvl] = dict(launches=r["launches"], total_ms=round(r["total_ms"], 3), achieved=round(a, 1),
-                               frac=round(a / peak, 4))
-        roof = dict(bound="hbm", kernel=f"{CUDA_NAME.get(base, base)} ({top['name']}, all levels)",
+        ratio = DRAM_PER_ALGORITHMIC.get(top["kernel"])
+        roof = dict(bound="hbm", kernel=top["kernel"], classes=top["classes"],
                     achieved=round(ach, 1), peak=peak, unit="GB/s", frac=round(ach / peak, 4),
                     traffic=round(per_launch_bytes * ratio) if ratio else None,
                     peak_source=f"{peak_kind} copy bandwidth", launches=top["launches"],
                     share_of_step=round(top["total_ms"] / max(1, args.prof_steps) / (ms / args.steps), 3),
-                    bytes_per_launch=per_launch_bytes, levels=levels)
+                    bytes_per_launch=per_launch_bytes)
 
     mixed = None
     if ref_fields is not None:

@@ -195,9 +195,19 @@ __global__ void k_jacobi_apply(int64_t n, const double* __restrict__ diag, const
   }
 }
 
+// z = dinv r: the inverse diagonal is formed once per linear system by its
+// owner (an FP64 division per row per application costs more than the
+// memory traffic of this kernel on this part)
+__global__ void k_jacobi_mul(int64_t n, const double* __restrict__ dinv, const double* __restrict__ r,
+                             double* __restrict__ z) {
+  GRID_STRIDE(i, n) z[i] = dinv[i] * r[i];
+}
+
 fvs_status JacobiPrecond::apply(cudaStream_t s, const double* r, double* z) {
   if (A->n == 0) return FVS_OK;
-  k_jacobi_apply<<<stride_grid(A->n, 256), 256, 0, s>>>(A->n, A->diag, dextra, r, z); FVS_COUNT_LAUNCH();
+  if (dinv) k_jacobi_mul<<<stride_grid(A->n, 256), 256, 0, s>>>(A->n, dinv, r, z);
+  else k_jacobi_apply<<<stride_grid(A->n, 256), 256, 0, s>>>(A->n, A->diag, dextra, r, z);
+  FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   return FVS_OK;
 }

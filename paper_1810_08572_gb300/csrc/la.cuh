@@ -97,9 +97,11 @@ bool graphs_enabled();
 struct JacobiPrecond : Precond {
   const Ell* A = nullptr;
   const double* dextra = nullptr;
+  const double* dinv = nullptr;   // optional 1 / (diag + dextra), kept by the caller: z = dinv r
   fvs_status apply(cudaStream_t s, const double* r, double* z) override;
   uint64_t signature() const override {
-    return (uint64_t)(uintptr_t)A->diag.p * 31u + (uint64_t)(uintptr_t)dextra * 17u + (uint64_t)A->n;
+    return (uint64_t)(uintptr_t)A->diag.p * 31u + (uint64_t)(uintptr_t)dextra * 17u +
+           (uint64_t)(uintptr_t)dinv * 13u + (uint64_t)A->n;
   }
 };
 

@@ -471,17 +471,24 @@ __global__ void k_energy_base(int64_t Nc, int W, const int32_t* cf, const int8_t
 // source linearisation at the current iterate (Eq. 20): S_p, S_c
 __global__ void k_energy_lin(int64_t Nc, const double* V, Mat m, double dt, const double* Tm, const double* fsm,
                              const double* fsn, const double* base, double* dextra, double* rhs, double* x,
-                             const double* rcp, const double* rL, const uint8_t* metal) {
+                             const double* rcp, const double* rL, const uint8_t* metal, const double* kdiag,
+                             double* jinv) {
   GS(c, Nc) {
     const double t = Tm[c];
     const double dfs = metal[c] ? fs_slope(m.law, t) : 0.0;
     const double a = rL[c] * V[c] / dt;
     const double Sp = a * dfs;
     const double Sc = a * (fsm[c] - fsn[c] - dfs * t);
-    dextra[c] = rcp[c] * V[c] / dt - Sp;
+    const double dx = rcp[c] * V[c] / dt - Sp;
+    dextra[c] = dx;
+    jinv[c] = 1.0 / (kdiag[c] + dx);   // Jacobi preconditioner of the pass
     rhs[c] = base[c] + Sc;
     x[c] = t;
   }
+}
+
+__global__ void k_inverse(int64_t n, const double* a, double* inv) {
+  GS(i, n) inv[i] = 1.0 / a[i];
 }
 
 // enthalpy-to-temperature inversion of the linearised update:
@@ -1073,8 +1080,11 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
                                                     s->Fold, s->u, s->uold, m->Lu.col, m->Lu.val, m->V, s->T, mt, dt,
                                                     s->mrhs, s->mx); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
+    FVS_TRY(s->jinv_m.alloc(na));
+    k_inverse<<<stride_grid(na, 256), 256, 0, st>>>(na, s->M.diag, s->jinv_m); FVS_COUNT_LAUNCH();
     JacobiPrecond J;
     J.A = &s->M;
+    J.dinv = s->jinv_m;
     // the three components are judged against the largest right side (a
     // component with a near-zero right side would otherwise chase roundoff)
     double bmax = 0.0;
@@ -1171,9 +1181,11 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
   k_energy_guess<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->T, s->Told, mt.law, s->Tnew, s->fsnew, s->metal);
   FVS_COUNT_LAUNCH();
   {
+    FVS_TRY(s->jinv_e.alloc(Nc));
     JacobiPrecond J;
     J.A = &s->Ke;
     J.dextra = s->edx;
+    J.dinv = s->jinv_e;
     // Tnew / fsnew hold the iterate m; Tlin the linear solution
     DBuf<double>& Tm = s->Tnew;
     DBuf<double>& fsm = s->fsnew;
@@ -1185,7 +1197,8 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
       // of the nonlinear change; the last passes reach e_rtol
       const double rtol_m = std::max(s->props.e_rtol, std::min(1e-4, 1e-5 * dT_prev));
       k_energy_lin<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, m->V, mt, dt, Tm, fsm, s->fs, s->ebase, s->edx,
-                                                          s->erhs, s->Tlin, s->rcp, s->rL, s->metal);
+                                                          s->erhs, s->Tlin, s->rcp, s->rL, s->metal, s->Ke.diag,
+                                                          s->jinv_e);
       FVS_COUNT_LAUNCH();
       FVS_LAUNCH_CHECK();
       SolveResult r;

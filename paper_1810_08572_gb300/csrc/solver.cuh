@@ -34,6 +34,9 @@ struct fvs_solver_s {
   bool grain_on = false;
   double grain_kp = 0.0, grain_Ds = 0.0, grain_r0 = 0.0;
   fvs::DBuf<double> r2;
+  // inverse Jacobi diagonals of the energy system (per latent-heat pass) and
+  // of the momentum system (per step)
+  fvs::DBuf<double> jinv_e, jinv_m;
   double time = 0.0;
   int64_t nstep = 0;
 
