@@ -840,45 +840,38 @@ template <typename T>
 __global__ void k_jac0(int64_t n, T omega, const T* dinv, const T* b, T* x) {
   GS(i, n) x[i] = omega * dinv[i] * b[i];
 }
-// (A x)_i.  Fine level (no row lengths): the plain loop over the full width.
-// Coarse levels: only the stored entries, in groups of eight loads (the
-// coarse rows are short and gather-latency-bound); same order of the sum.
+// Fine level: (A x)_i over every slot of the row (one thread per row; the
+// coarse levels have their own kernels below)
 template <typename T>
-__device__ __forceinline__ T smoother_row(int64_t n, int w, const int32_t* __restrict__ col,
-                                          const T* __restrict__ val, const T* __restrict__ x,
-                                          const int32_t* __restrict__ rlen, int64_t i) {
-  if (!rlen) {
-    T acc = 0;
-    for (int k = 0; k < w; ++k) {
-      const int64_t e = (int64_t)k * n + i;
-      acc = fma(val[e], x[col[e]], acc);
-    }
-    return acc;
+__device__ __forceinline__ T fine_row(int64_t n, int w, const int32_t* __restrict__ col, const T* __restrict__ val,
+                                      const T* __restrict__ x, int64_t i) {
+  T acc = 0;
+  for (int k = 0; k < w; ++k) {
+    const int64_t e = (int64_t)k * n + i;
+    acc = fma(val[e], x[col[e]], acc);
   }
-  return row_dot8<T>(
-      rlen[i], [&](int k) { return col[(int64_t)k * n + i]; }, [&](int k) { return val[(int64_t)k * n + i]; },
-      [&](int32_t c) { return x[c]; }, (T)0);
+  return acc;
 }
 
 // y = x + omega D^-1 (b - A x)
 template <typename T>
 __global__ void k_jac(int64_t n, int w, const int32_t* __restrict__ col, const T* __restrict__ val, T omega,
                       const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
-                      T* __restrict__ y, const int32_t* __restrict__ rlen) {
+                      T* __restrict__ y) {
   GS(i, n) {
-    const T acc = smoother_row(n, w, col, val, x, rlen, i);
+    const T acc = fine_row(n, w, col, val, x, i);
     y[i] = x[i] + omega * dinv[i] * (b[i] - acc);
   }
 }
 template <typename T>
 __global__ void k_resid(int64_t n, int w, const int32_t* __restrict__ col, const T* __restrict__ val,
-                        const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r,
-                        const int32_t* __restrict__ rlen) {
+                        const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r) {
   GS(i, n) {
-    const T acc = smoother_row(n, w, col, val, x, rlen, i);
+    const T acc = fine_row(n, w, col, val, x, i);
     r[i] = b[i] - acc;
   }
 }
+
 // Coarse levels, CG lanes per row: lane q of a row sums the stored entries
 // q, q + CG, q + 2 CG, ... (four loads in flight), then the row's lanes add
 // their partial sums by shuffles.  The 32 / CG rows of a warp are
@@ -1616,7 +1609,7 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
   auto jac = [&](T* xin, T* xout) {
     ProfScope ps(pkey, n_jac, jac_bytes, s);
     if (rl) k_jac_g<T><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
-    else k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
+    else k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xin, xout);
     FVS_COUNT_LAUNCH();
   };
   for (int k = 1; k < opt.npre; ++k) {
@@ -1626,7 +1619,7 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
   {
     ProfScope ps(pkey, n_res, res_bytes, s);
     if (rl) k_resid_g<T><<<gg, 256, 0, s>>>(n, A.col, val, xa, b, r, rl);
-    else k_resid<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, xa, b, r, rl);
+    else k_resid<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, xa, b, r);
     FVS_COUNT_LAUNCH();
   }
   k_restrict<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cb); FVS_COUNT_LAUNCH();

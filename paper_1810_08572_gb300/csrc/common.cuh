@@ -174,30 +174,6 @@ __device__ __forceinline__ int find_sorted(const int32_t* a, int64_t s, int n, i
   return -1;
 }
 
-// acc + sum_{k < len} val(k) * x(col(k)) in order k = 0, 1, ...; groups of
-// eight entries issue all their index, value and gather loads before the
-// multiply-adds (gathers are latency-bound; the order of the sum is that of
-// the plain loop)
-template <typename V, typename Col, typename Val, typename X>
-__device__ __forceinline__ V row_dot8(int len, Col col, Val val, X xat, V acc) {
-  for (int k0 = 0; k0 < len; k0 += 8) {
-    int32_t c[8];
-    V v[8], xv[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int k = k0 + u < len ? k0 + u : len - 1;
-      c[u] = col(k);
-      v[u] = val(k);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) xv[u] = xat(c[u]);
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (k0 + u < len) acc = fma(v[u], xv[u], acc);
-  }
-  return acc;
-}
-
 // ---------------------------------------------------------------------------
 // Optional per-kernel timing with CUDA events on the launching stream.
 // A solver registers the matrices it wants tracked under a label; while a
