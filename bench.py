@@ -231,8 +231,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
-    clocks = Clocks(os.path.join(ROOT, "gpurun_out", "clocks_bench.csv")
-                    if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/fvs_clocks.csv")
+    clocks = Clocks(os.path.join(os.environ.get("TMPDIR", "/tmp"), f"fvs_clocks_{os.getpid()}.csv"))
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     act = 0

@@ -358,13 +358,13 @@ fvs_status fvs_profile_read(fvs_solver solver, fvs_kernel_time* out, int32_t max
  * fixed device array built into the library instead, and calls no
  * allocating routine.
  *   dst  host memory of dst_len doubles
- * Limit: fields of at most 1,048,576 values (8 MiB of staging, held by every
- * GPU that loads the library until the process exits); larger fields fail
- * with FVS_ERR_ARG (use fvs_query_fields).  The first call on a device looks
- * up the array's device address (make that first call before any CUDA stream
- * capture).  All calls share the array: each call overwrites every value it
- * returns, and calls whose GPU work overlaps (other streams, other threads)
- * race on it. */
+ * Limit: fields of at most 1,048,576 values; larger fields fail with
+ * FVS_ERR_ARG (use fvs_query_fields).  The staging array (8 MiB) is placed on
+ * a GPU, and its device address looked up, by the first fvs_solver_create on
+ * that GPU (create solvers before any CUDA stream capture); it stays there
+ * until the process exits, so this call itself allocates nothing.  All calls
+ * share the array: each call overwrites every value it returns, and calls
+ * whose GPU work overlaps (other streams, other threads) race on it. */
 fvs_status fvs_query_fields_noalloc(fvs_solver solver, fvs_field field, double* dst, int64_t dst_len);
 
 /* Current simulated time and step count. */

@@ -10,7 +10,7 @@ check each operator against the paper by eye.  Section, equation and algorithm
 numbers refer to Shahane et al., "Finite Volume Simulation Framework for Die
 Casting with Uncertainty Quantification" (arXiv:1810.08572).
 
-Readings of points the paper leaves open (each is listed in the design doc too):
+Readings of points the paper leaves open:
  * face vector area S_f = 1/2 (x_V3 - x_V1) x (x_V4 - x_V2); cell and face
    centres are vertex means; volume = 1/3 sum_f x_f . S_f (outward)
  * the local Jacobian of Eq. 12 has rows d = C1C2, V1V3, V2V4; on a boundary

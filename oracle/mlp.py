@@ -78,3 +78,23 @@ def unflatten(vec, sizes):
         params.append((W, vec[k:k + b].copy()))
         k += b
     return params
+
+
+def adam_init(n):
+    """Adam state for n parameters: first and second moments at zero, step 0."""
+    return dict(m=np.zeros(n), v=np.zeros(n), t=0)
+
+
+def adam_step(state, theta, g, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma and Ba, 2015, Algorithm 1) of the flat
+    parameters theta with gradient g: exponential moving averages of g and
+    g^2, each divided by (1 - beta^t) to remove the bias of the zero start,
+    then theta - lr m_hat / (sqrt(v_hat) + eps).  Returns the new parameters
+    and updates the state in place."""
+    state["t"] += 1
+    t = state["t"]
+    state["m"] = beta1 * state["m"] + (1.0 - beta1) * g
+    state["v"] = beta2 * state["v"] + (1.0 - beta2) * g * g
+    m_hat = state["m"] / (1.0 - beta1 ** t)
+    v_hat = state["v"] / (1.0 - beta2 ** t)
+    return theta - lr * m_hat / (np.sqrt(v_hat) + eps)

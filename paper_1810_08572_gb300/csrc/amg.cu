@@ -1230,23 +1230,6 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
       FVS_TRY(read_int(s, cnt, &iso));
       fprintf(stderr, "[fvs amg] level %d: %lld rows (w%d) -> %d aggregates%s, %d rows without strong couplings\n",
               l, (long long)n, cur->w, nc, mis2 ? " (distance-2 set)" : "", iso);
-      const char* dump = getenv("FVS_AMG_DUMP");   // small levels to a file, for offline study
-      if (dump && *dump && n <= 8192) {
-        std::vector<int32_t> hc((size_t)n * cur->w);
-        std::vector<double> hv((size_t)n * cur->w);
-        FVS_CUDA(cudaMemcpyAsync(hc.data(), cur->col.p, hc.size() * 4, cudaMemcpyDeviceToHost, s));
-        FVS_CUDA(cudaMemcpyAsync(hv.data(), cur->val.p, hv.size() * 8, cudaMemcpyDeviceToHost, s));
-        FVS_CUDA(cudaStreamSynchronize(s));
-        char path[512];
-        snprintf(path, sizeof path, "%s_L%d.bin", dump, l);
-        if (FILE* f = fopen(path, "wb")) {
-          const int64_t hdr[2] = {n, (int64_t)cur->w};
-          fwrite(hdr, 8, 2, f);
-          fwrite(hc.data(), 4, hc.size(), f);
-          fwrite(hv.data(), 8, hv.size(), f);
-          fclose(f);
-        }
-      }
     }
     if (nc <= 0 || nc >= n || (double)nc > 0.85 * (double)n) break;  // stagnation: L is the coarsest
     tick(2);

@@ -212,6 +212,7 @@ FVS_API fvs_status fvs_solver_create(fvs_mesh mesh, void* stream, fvs_solver* ou
   s->stream = (cudaStream_t)stream;
   AllocStream as(s->stream);
   fvs_status st = solver_alloc(s);
+  if (st == FVS_OK) st = noalloc_reserve();
   if (st != FVS_OK) {
     delete s;
     return st;

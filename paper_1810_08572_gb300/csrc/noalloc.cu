@@ -10,11 +10,18 @@
 // footprint.  This variant stages the gather in a fixed device array that is
 // part of the library image instead, and allocates nothing.
 //
-// The array holds FVS_NOALLOC_MAX_VALUES doubles (8 MiB), is owned by every
-// GPU that loads the library until the process exits, and is shared by all
-// calls: every call overwrites the values it needs (all of them, so nothing
-// has to start at zero), and calls whose GPU work overlaps (different
-// streams, or different threads on one stream without ordering) race on it.
+// The array holds FVS_NOALLOC_MAX_VALUES doubles (8 MiB) and is shared by
+// all calls: every call overwrites the values it needs (all of them, so
+// nothing has to start at zero), and calls whose GPU work overlaps
+// (different streams, or different threads on one stream without ordering)
+// race on it.  The CUDA runtime places a module's device arrays on a GPU
+// when that module is first used there (lazy loading), and that placement
+// is itself an allocation; fvs_solver_create therefore resolves the array's
+// address on the solver's device (noalloc_reserve), so the 8 MiB are taken
+// when a solver is created and held until the process exits, and a later
+// fvs_query_fields_noalloc allocates nothing.
+#include <mutex>
+
 #include "solver.cuh"
 
 namespace fvs {
@@ -23,28 +30,38 @@ namespace fvs {
 
 static __device__ __align__(256) double g_noalloc_scratch[FVS_NOALLOC_MAX_VALUES];
 
-// device address of the array, looked up once per device (host code may not
-// use the symbol itself: on the host it names a stand-in, not GPU memory)
-static double* g_noalloc_ptr[64] = {nullptr};
+// device address of the array, looked up once per device under a
+// once-flag (host code may not use the symbol itself: on the host it names
+// a stand-in, not GPU memory)
+static constexpr int kMaxDevices = 64;
+static double* g_noalloc_ptr[kMaxDevices] = {nullptr};
+static cudaError_t g_noalloc_err[kMaxDevices] = {cudaSuccess};
+static std::once_flag g_noalloc_once[kMaxDevices];
 
 static fvs_status noalloc_scratch(double** out) {
   int dev = 0;
   FVS_CUDA(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) {
+  if (dev < 0 || dev >= kMaxDevices) {
     set_error("fvs_query_fields_noalloc: device %d out of range", dev);
     return FVS_ERR_CUDA;
   }
-  if (!g_noalloc_ptr[dev]) {
+  std::call_once(g_noalloc_once[dev], [dev] {
     void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p) {
-      set_error("fvs_query_fields_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return FVS_ERR_CUDA;
-    }
-    g_noalloc_ptr[dev] = (double*)p;
+    g_noalloc_err[dev] = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (g_noalloc_err[dev] == cudaSuccess) g_noalloc_ptr[dev] = (double*)p;
+  });
+  if (g_noalloc_err[dev] != cudaSuccess || !g_noalloc_ptr[dev]) {
+    set_error("fvs_query_fields_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(g_noalloc_err[dev]));
+    return FVS_ERR_CUDA;
   }
   *out = g_noalloc_ptr[dev];
   return FVS_OK;
+}
+
+// called by fvs_solver_create with the solver's device current
+fvs_status noalloc_reserve() {
+  double* p = nullptr;
+  return noalloc_scratch(&p);
 }
 
 #define GS(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)

@@ -88,6 +88,8 @@ struct fvs_solver_s {
 
 namespace fvs {
 fvs_status solver_alloc(fvs_solver s);
+// places the staging array of fvs_query_fields_noalloc on the current device
+fvs_status noalloc_reserve();
 fvs_status solver_set_properties(fvs_solver s, const fvs_props* p);
 fvs_status solver_set_mold(fvs_solver s, double rho, double cp, double k, double h, double T_init);
 fvs_status solver_set_grain(fvs_solver s, double kp, double D_s, double r0);

@@ -48,6 +48,31 @@ def test_forward_and_gradients_match_fp64_reference(fvs):
     np.testing.assert_allclose(S.get_params(), p * 0.5, rtol=1e-7)
 
 
+def test_adam_steps_match_oracle(fvs):
+    """Two full-batch Adam steps on the GPU (FP32 master weights) against the
+    FP64 Adam of the oracle fed with the GPU's own gradients at the same
+    weights, so that only the optimiser is compared: the first step is
+    -lr g/(|g| + eps) in closed form, the second one mixes both gradients."""
+    S = fvs.Surrogate(3, 128, 4, 4, seed=21)
+    rng = np.random.default_rng(3)
+    X = rng.normal(size=(200, 3))
+    T = rng.normal(size=(200, 4))
+    lr = 1e-3
+    st = ref.adam_init(S.num_params())
+    th = S.get_params()
+    for _ in range(2):
+        g, _ = S.gradients(X, T)
+        th_ref = ref.adam_step(st, th, g, lr)
+        S.train(X, T, 1, lr)
+        th_gpu = S.get_params()
+        # FP32 weights and moments: a few ulps of the weight plus a few ulps
+        # of the step where |g| is near eps
+        tol = 4e-7 * np.abs(th) + 1e-6 * lr
+        bad = np.abs(th_gpu - th_ref) > tol
+        assert not bad.any(), (bad.sum(), np.abs(th_gpu - th_ref)[bad][:5])
+        th = th_gpu
+
+
 def test_training_fits_a_smooth_map(fvs):
     rng = np.random.default_rng(1)
     X = rng.uniform(-1, 1, size=(512, 3))

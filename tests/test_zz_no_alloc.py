@@ -41,7 +41,8 @@ def test_noalloc_matches_query_fields_on_two_calls(fvs):
     M = fvs.Mesh(m)
     S = fvs.Solver(M, cases.props(grain=dict(kp=0.13, D_s=3e-9, r0=1e-6)))
     nc, nf = M.n_cells, M.n_faces
-    sizes = dict(T=nc, U=3 * nc, P=nc, FLUX=nf, QOI=4 * nc, CROSS=2 * nc, TAG=nc, GRAIN=nc)
+    sizes = dict(T=nc, FS=nc, U=3 * nc, USTAR=3 * nc, P=nc, FLUX=nf, QOI=4 * nc, CROSS=2 * nc, TAG=nc,
+                 FACE_CASE=nf, GRAIN=nc)
     for call in range(2):           # the shared staging array keeps the last call's values
         S.step(1e-3, 3)
         for name, n in sizes.items():
