@@ -35,6 +35,20 @@ Readings of points the paper leaves open:
    gradients are smeared
  * the pressure of each connected part of the pressure system is fixed by
    zero mean; the right side is projected to zero sum on each part
+ * a convective wall (heat-transfer coefficient h to an ambient T_inf)
+   carries the orthogonal flux A (T_inf - T_C1)/(d_1/k_1 + 1/h) through the
+   half cell and the film, d_1 the distance from the cell centre to the face
+   centre; its vertices are free (cell means), as on adiabatic walls
+ * a temperature-dependent conductivity k(T) of the metal (Section 4 uses a
+   table; piecewise linear here, held constant outside it) is evaluated per
+   face at the start of each step, at the mean of the two owner temperatures
+   T^n (a fixed-temperature wall: the mean of the cell and wall values; a
+   convective wall or a metal-mold interface: the metal cell's T^n), and
+   used in both Crank-Nicolson halves
+ * with natural convection off (Section 4: the castings are simulated
+   without it) the momentum, pressure and correction steps are skipped:
+   velocity, flux and pressure stay zero and the energy equation is pure
+   conduction with latent heat
  * grain growth (Eq. 24-26): S takes the sign of the invariant-size
    approximation, S = 2 (C_l - C_0)/(C_s - C_l) <= 0, with the Scheil
    interface contents C_l = C_0 (1 - fs)^(kp - 1), C_s = kp C_l (as printed,
@@ -51,6 +65,7 @@ from scipy.sparse.csgraph import connected_components
 
 BC_ADIABATIC = 0
 BC_DIRICHLET = 1
+BC_CONVECTIVE = 2
 
 
 # ----------------------------------------------------------------------------
@@ -177,7 +192,21 @@ def velocity_diffusion(g):
     return diffusion_operator(g, np.ones(g.Nf, bool), vP, vc, np.zeros(g.Nf))
 
 
-def temperature_diffusion(g, walls, k_face=None, interface=None, G_int=None):
+def wall_data(g, walls):
+    """Per face: wall type (-1 interior), wall temperature (or ambient
+    temperature of a convective wall) and film coefficient h."""
+    btype = np.full(g.Nf, -1)
+    bval = np.zeros(g.Nf)
+    bh = np.zeros(g.Nf)
+    for pid, w in enumerate(walls):
+        m = g.patch == pid
+        btype[m] = w[0]
+        bval[m] = w[1]
+        bh[m] = w[2] if len(w) > 2 else 0.0
+    return btype, bval, bh
+
+
+def temperature_diffusion(g, walls, k_face=None, interface=None, G_int=None, G_conv=None):
     """Fixed-temperature walls enter through their vertices and faces;
     adiabatic walls carry no flux.
 
@@ -185,14 +214,13 @@ def temperature_diffusion(g, walls, k_face=None, interface=None, G_int=None):
     result is the conductive flux itself).  Faces flagged in ``interface``
     (a metal cell against a mold cell) carry only the orthogonal flux
     G_int (T_C2 - T_C1) through the series resistance of the two half cells
-    and the interface coefficient."""
-    btype = np.full(g.Nf, -1)
-    bval = np.zeros(g.Nf)
-    for pid, (typ, T) in enumerate(walls):
-        m = g.patch == pid
-        btype[m] = typ
-        bval[m] = T
+    and the interface coefficient; convective wall faces carry
+    G_conv (T_inf - T_C1) (no cross terms on either)."""
+    btype, bval, bh = wall_data(g, walls)
     dir_face = btype == BC_DIRICHLET
+    conv_face = btype == BC_CONVECTIVE
+    if conv_face.any() and k_face is None:
+        raise ValueError("convective walls need face conductivities")
     # a vertex on fixed-temperature walls takes the mean of the values of the
     # fixed-temperature wall faces that contain it (each face counted once)
     cnt = np.zeros(g.Nv)
@@ -204,19 +232,26 @@ def temperature_diffusion(g, walls, k_face=None, interface=None, G_int=None):
     fixed = cnt > 0
     val = np.where(fixed, acc / np.maximum(cnt, 1), 0.0)
     vP, vc = vertex_operator(g, fixed, val)
-    face_mask = g.interior | dir_face
+    face_mask = g.interior | dir_face | conv_face
+    bdir = np.where(dir_face, bval, 0.0)
     if k_face is None:
-        return diffusion_operator(g, face_mask, vP, vc, bval)
+        return diffusion_operator(g, g.interior | dir_face, vP, vc, bdir)
+    if interface is None:
+        interface = np.zeros(g.Nf, bool)
+    G_int = np.zeros(g.Nf) if G_int is None else G_int
+    G_conv = np.zeros(g.Nf) if G_conv is None else G_conv
     Deta = g.E31 @ vP
     Dzeta = g.E42 @ vP
     N = g.normal_derivative_rows(g.Dxi, Deta, Dzeta)
-    k = g.Af * ((1.0 / g.ndotd + g.w[:, 0]) * np.where(g.interior, 0.0, bval)
+    k = g.Af * ((1.0 / g.ndotd + g.w[:, 0]) * np.where(g.interior, 0.0, bdir)
                 + g.w[:, 1] * (g.E31 @ vc) + g.w[:, 2] * (g.E42 @ vc))
     # conductive flux per face: k_f times the face gradient, or the series
-    # flux on interface faces (no cross terms there)
-    Nk = (sp.diags(np.where(interface, 0.0, k_face)) @ N
-          + sp.diags(np.where(interface, G_int, 0.0)) @ g.Dxi).tocsr()
-    kk = np.where(interface, 0.0, k_face * k)
+    # flux on interface faces and convective walls (no cross terms there);
+    # the wall row of Dxi carries -T_C1
+    series = interface | conv_face
+    G = np.where(interface, G_int, np.where(conv_face, G_conv, 0.0))
+    Nk = (sp.diags(np.where(series, 0.0, k_face)) @ N + sp.diags(G) @ g.Dxi).tocsr()
+    kk = np.where(series, np.where(conv_face, G_conv * bval, 0.0), k_face * k)
     M = g.Div @ sp.diags(face_mask.astype(np.float64))
     return (M @ Nk).tocsr(), M @ kk
 
@@ -374,22 +409,21 @@ class Oracle:
         self.mold = mold
         rho_c = np.where(self.metal, m["rho"], mold["rho"] if mold else m["rho"])
         cp_c = np.where(self.metal, m["cp"], mold["cp"] if mold else m["cp"])
-        k_c = np.where(self.metal, m["k"], mold["k"] if mold else m["k"])
         self.rcp = rho_c * cp_c
         self.rL = np.where(self.metal, m["rho"] * m["latent"], 0.0)
         q = np.maximum(g.neigh, 0)
-        interface = g.interior & (self.metal[g.owner] != self.metal[q])
-        k_face = k_c[g.owner]
-        G = np.zeros(g.Nf)
-        if interface.any():
-            ko, kq = k_c[g.owner], k_c[q]
-            G = np.where(interface, g.Af / (g.d_own / ko + 1.0 / mold["h"] + g.d_nei / kq), 0.0)
-        self.interface = interface
-        # conductive operator (k inside): sum over faces of the face flux
-        self.LTk, self.lTk = temperature_diffusion(g, self.walls, k_face=k_face, interface=interface, G_int=G)
+        self.interface = g.interior & (self.metal[g.owner] != self.metal[q])
+        # k(T) of the metal: props["k_table"] = [(T, k), ...], piecewise
+        # linear, constant outside; props["no_flow"]: natural convection off
+        kt = props.get("k_table")
+        self.k_table = None if not kt else (np.array([a for a, _ in kt], float), np.array([b for _, b in kt], float))
+        self.no_flow = bool(props.get("no_flow", False))
+        self.btype, self.bval, self.bh = wall_data(g, self.walls)
         self.Deta_p = (g.E31 @ g.Pavg).tocsr()
         self.Dzeta_p = (g.E42 @ g.Pavg).tocsr()
         self.T = np.where(self.metal, props["T_init"], mold["T_init"] if mold else props["T_init"])
+        # conductive operator (k inside): sum over faces of the face flux
+        self.LTk, self.lTk = self.conduction(self.T)
         self.scheil = scheil_law(m)
         self.fs = self.fs_of(self.T)
         # grain growth (Eq. 24-26): props["grain"] = dict(kp, D_s, r0)
@@ -408,6 +442,38 @@ class Oracle:
         self.stats = {}
 
     # -- helpers ---------------------------------------------------------------
+    def k_metal(self, T):
+        """Conductivity of the metal at temperatures T."""
+        if self.k_table is None:
+            return np.full(np.shape(T), float(self.m["k"]))
+        return np.interp(T, self.k_table[0], self.k_table[1])
+
+    def conduction(self, T):
+        """Conductive operator (L T + l = sum over faces of the conductive
+        flux) with the conductivities of the temperature field T (only read
+        with a k(T) table)."""
+        g, m, mold = self.g, self.m, self.mold
+        metal = self.metal
+        q = np.maximum(g.neigh, 0)
+        k_mold = mold["k"] if mold else m["k"]
+        if self.k_table is None:
+            k_own = np.where(metal[g.owner], m["k"], k_mold)
+            k_nei = np.where(metal[q], m["k"], k_mold)
+            k_face = k_own
+        else:
+            To = T[g.owner]
+            Tq = np.where(g.interior, T[q], np.where(self.btype == BC_DIRICHLET, self.bval, To))
+            k_own = np.where(metal[g.owner], self.k_metal(To), k_mold)
+            k_nei = np.where(metal[q], self.k_metal(T[q]), k_mold)
+            k_face = np.where(metal[g.owner], self.k_metal(0.5 * (To + Tq)), k_mold)
+        G_int = np.zeros(g.Nf)
+        if self.interface.any():
+            G_int = np.where(self.interface, g.Af / (g.d_own / k_own + 1.0 / mold["h"] + g.d_nei / k_nei), 0.0)
+        conv = self.btype == BC_CONVECTIVE
+        G_conv = np.where(conv, g.Af / (g.d_own / k_own + 1.0 / np.where(conv, self.bh, 1.0)), 0.0)
+        return temperature_diffusion(g, self.walls, k_face=k_face, interface=self.interface, G_int=G_int,
+                                     G_conv=G_conv)
+
     def reset_grain(self):
         r0 = self.grain["r0"] if self.grain else 0.0
         self.r2 = np.where(self.metal, r0 * r0, 0.0)
@@ -478,8 +544,51 @@ class Oracle:
         F_n = np.where(blocked, 0.0, self.F)
         F_o = np.where(blocked, 0.0, self.F_old)
 
-        # 2. momentum predictor on LM cells, Eq. 6 with Section 2.4.1 row deletion
         act = np.nonzero(lm)[0]
+        if self.no_flow:
+            # natural convection off: no flow at all
+            case, ppe = self.face_cases(lm)
+            u_star = np.zeros((g.Nc, 3))
+            u_new = np.zeros((g.Nc, 3))
+            F_new = np.zeros(g.Nf)
+            p = np.zeros(g.Nc)
+            b_full = np.zeros(g.Nc)
+            self.stats = dict(n_active=int(lm.sum()), n_ppe=0, ncomp=0, ppe_relres=0.0)
+        else:
+            u_star, u_new, F_new, p, case, ppe, b_full = self.flow_step(dt, lm, act, u_n, u_o, F_n, F_o, T_n, fs_n)
+
+        # 5. energy with latent heat on all cells (Eq. 4, Eq. 18-20), with the
+        # conductivities of T^n when k depends on T
+        if self.k_table is not None:
+            self.LTk, self.lTk = self.conduction(T_n)
+        T_new, fs_new, e_its = self.energy(dt, T_n, fs_n, self.T_old, F_n, F_o)
+
+        # 6. microstructure bookkeeping (Eq. 22-23 use the local cooling rate;
+        # Eq. 24-26 grow the grains of the cells that are mushy)
+        self.update_crossings(T_n, T_new, dt)
+        if self.grain:
+            gr = self.grain
+            self.r2 = np.where(self.metal, grain_update(self.r2, fs_n, fs_new, dt, gr["kp"], gr["D_s"]), 0.0)
+
+        self.stats.update(e_its=e_its, n_faces_case2=int((case == 2).sum()),
+                          n_faces_case3=int((case == 3).sum()))
+        self.T_old, self.T, self.fs = T_n, T_new, fs_new
+        self.u_old, self.u = u_n, u_new
+        self.F_old, self.F = F_n, F_new
+        self.p = p
+        self.u_star = u_star
+        self.case, self.ppe, self.lm = case, ppe, lm
+        self.b_ppe = b_full
+        self.time += dt
+        self.nstep += 1
+        return self.stats
+
+    def flow_step(self, dt, lm, act, u_n, u_o, F_n, F_o, T_n, fs_n):
+        """Steps 2-4 of Section 2.2: momentum predictor, pressure Poisson
+        equation and the flux / velocity correction on the LM cells."""
+        g, m = self.g, self.m
+        rho, mu = m["rho"], m["mu"]
+        # 2. momentum predictor on LM cells, Eq. 6 with Section 2.4.1 row deletion
         Lu = self.Lu[act][:, act]
         V = g.V[act]
         D = darcy_coefficient(fs_n[act], m["darcy_C"], m["darcy_eps"])
@@ -522,28 +631,7 @@ class Oracle:
         u_new = np.zeros((g.Nc, 3))
         u_new[act] = u_star[act] - dt / rho * grad_c[act]
 
-        # 5. energy with latent heat on all cells (Eq. 4, Eq. 18-20)
-        T_new, fs_new, e_its = self.energy(dt, T_n, fs_n, self.T_old, F_n, F_o)
-
-        # 6. microstructure bookkeeping (Eq. 22-23 use the local cooling rate;
-        # Eq. 24-26 grow the grains of the cells that are mushy)
-        self.update_crossings(T_n, T_new, dt)
-        if self.grain:
-            gr = self.grain
-            self.r2 = np.where(self.metal, grain_update(self.r2, fs_n, fs_new, dt, gr["kp"], gr["D_s"]), 0.0)
-
-        self.stats.update(e_its=e_its, n_faces_case2=int((case == 2).sum()),
-                          n_faces_case3=int((case == 3).sum()))
-        self.T_old, self.T, self.fs = T_n, T_new, fs_new
-        self.u_old, self.u = u_n, u_new
-        self.F_old, self.F = F_n, F_new
-        self.p = p
-        self.u_star = u_star
-        self.case, self.ppe, self.lm = case, ppe, lm
-        self.b_ppe = b_full
-        self.time += dt
-        self.nstep += 1
-        return self.stats
+        return u_star, u_new, F_new, p, case, ppe, b_full
 
     def energy_residual(self, T, dt, T_n, fs_n, T_o, F_n, F_o):
         """R(T) of the discrete energy equation (all terms moved to the left)."""

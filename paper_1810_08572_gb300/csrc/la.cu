@@ -562,6 +562,7 @@ fvs_status bicgstab(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, c
   if (bnorm == 0.0) bnorm = 1.0;
   double rn = sqrt(red.host[S_RR]);
   res.relres = rn / bnorm;
+  if (bad(rn) || bad(bnorm)) return FVS_OK;   // non-finite data: not converged, no iterations
   if (res.relres <= rtol) {
     res.converged = true;
     return FVS_OK;
@@ -654,6 +655,7 @@ fvs_status pcg(cudaStream_t s, Reducer& red, KrylovWork& w, const Ell& A, Precon
   double bnorm = sqrt(red.host[S_BB]);
   if (bnorm == 0.0) bnorm = 1.0;
   res.relres = sqrt(red.host[S_RR]) / bnorm;
+  if (bad(res.relres) || bad(bnorm)) return FVS_OK;   // non-finite data: not converged
   if (res.relres <= rtol) {
     res.converged = true;
     return FVS_OK;

@@ -159,14 +159,17 @@ __global__ void k_bias_grad(int M, int N, const bf16* delta, float* db) {
   for (int m = 0; m < M; ++m) s += __bfloat162float(delta[(int64_t)m * N + n]);
   db[n] = s;
 }
-// Adam on FP32 master weights; refresh the BF16 copy.  mask keeps padding at zero.
+// Adam on FP32 master weights; refresh the BF16 copy.  mask keeps padding at
+// zero.  omb1 = 1 - b1, omb2 = 1 - b2 and the bias corrections c1 = 1 - b1^t,
+// c2 = 1 - b2^t come from the host in double precision: formed in FP32,
+// 1 - b2^t loses about five digits to cancellation (b2^t is near 1).
 __global__ void k_adam(int64_t n, float* w, float* m, float* v, const float* g, const uint8_t* mask, float lr,
-                       float b1, float b2, float eps, float c1, float c2, bf16* wb) {
+                       float b1, float omb1, float b2, float omb2, float eps, float c1, float c2, bf16* wb) {
   GS(i, n) {
     if (!mask[i]) continue;
     const float gi = g[i];
-    const float mi = b1 * m[i] + (1.f - b1) * gi;
-    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    const float mi = b1 * m[i] + omb1 * gi;
+    const float vi = b2 * v[i] + omb2 * gi * gi;
     m[i] = mi;
     v[i] = vi;
     const float wi = w[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
@@ -547,13 +550,15 @@ FVS_API fvs_status fvs_surrogate_train(fvs_surrogate s, const double* X, const d
   FVS_TRY(upload_xt(s, X, T, n));
   FVS_TRY(sg_work(s, n + 16));
   FVS_TRY(zero_padding_rows(s, n));
-  const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+  const double b1 = 0.9, b2 = 0.999, eps = 1e-8;
   for (int e = 0; e < epochs; ++e) {
     FVS_TRY(sg_gradients(s, n, nullptr));
     ++s->step;
-    const float c1 = 1.f - powf(b1, (float)s->step), c2 = 1.f - powf(b2, (float)s->step);
+    const double c1 = 1.0 - pow(b1, (double)s->step), c2 = 1.0 - pow(b2, (double)s->step);
     k_adam<<<stride_grid(s->nparam, 256), 256, 0, s->stream>>>(s->nparam, s->w32.p, s->m.p, s->v.p, s->g.p,
-                                                              s->mask.p, (float)lr, b1, b2, eps, c1, c2, nullptr);
+                                                              s->mask.p, (float)lr, (float)b1, (float)(1.0 - b1),
+                                                              (float)b2, (float)(1.0 - b2), (float)eps, (float)c1,
+                                                              (float)c2, nullptr);
     FVS_COUNT_LAUNCH();
     k_to_bf16<<<stride_grid(s->nw, 256), 256, 0, s->stream>>>(s->nw, s->w32.p, s->wb.p);
     FVS_COUNT_LAUNCH();

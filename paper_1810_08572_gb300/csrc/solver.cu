@@ -1006,6 +1006,108 @@ static fvs_status assemble_pressure(fvs_solver s) {
   return FVS_OK;
 }
 
+// ---------------------------------------------------------------------------
+// connected parts of the pressure system (single-grid solve)
+// ---------------------------------------------------------------------------
+// par[i] <= i always holds (roots hook onto smaller roots), so a walk up the
+// parents ends at a root; the walk is bounded all the same
+__device__ __forceinline__ int32_t cc_root(const int32_t* par, int32_t i) {
+  for (int k = 0; k < (1 << 24); ++k) {
+    const int32_t q = par[i];
+    if (q == i || q < 0) return i;
+    i = q;
+  }
+  return i;
+}
+__global__ void k_cc_init(int64_t n, const int32_t* act, const uint8_t* ppe, int32_t* par) {
+  GS(i, n) par[i] = ppe[act[i]] ? (int32_t)i : -1;
+}
+// every stored coupling between two rows of the system joins their parts
+__global__ void k_cc_hook(int64_t n, int w, const int32_t* col, const double* val, int32_t* par, int* changed) {
+  GS(i, n) {
+    if (par[i] < 0) continue;
+    for (int k = 0; k < w; ++k) {
+      const int32_t j = col[(int64_t)k * n + i];
+      if (j == (int32_t)i || val[(int64_t)k * n + i] == 0.0 || par[j] < 0) continue;
+      const int32_t a = cc_root(par, (int32_t)i), b = cc_root(par, j);
+      if (a == b) continue;
+      atomicMin(&par[a > b ? a : b], a > b ? b : a);
+      *changed = 1;
+    }
+  }
+}
+__global__ void k_cc_compress(int64_t n, int32_t* par, int32_t* is_root) {
+  GS(i, n) {
+    const int32_t r = par[i] < 0 ? -1 : cc_root(par, (int32_t)i);
+    if (r >= 0) par[i] = r;
+    is_root[i] = (r == (int32_t)i) ? 1 : 0;
+  }
+}
+__global__ void k_cc_label(int64_t n, const int32_t* par, const int32_t* rid, int32_t* lab, double* cnt) {
+  GS(i, n) {
+    const int32_t r = par[i];
+    const int32_t c = r < 0 ? -1 : rid[r];
+    lab[i] = c;
+    if (c >= 0) atomicAdd(&cnt[c], 1.0);
+  }
+}
+__global__ void k_part_sum(int64_t n, const int32_t* lab, const double* v, double* sum) {
+  GS(i, n) if (lab[i] >= 0) atomicAdd(&sum[lab[i]], v[i]);
+}
+__global__ void k_part_sub(int64_t n, const int32_t* lab, const double* sum, const double* cnt, double* v) {
+  GS(i, n) {
+    const int32_t c = lab[i];
+    if (c >= 0) v[i] -= sum[c] / cnt[c];
+  }
+}
+
+fvs_status PartProjector::setup(cudaStream_t s, const Ell& K, const int32_t* act, const uint8_t* ppe,
+                                ScanWork& sw) {
+  const int64_t n = K.n;
+  ncomp = 0;
+  if (n == 0) return FVS_OK;
+  FVS_TRY(par.alloc(n + 1)); FVS_TRY(root_flag.alloc(n + 1)); FVS_TRY(root_id.alloc(n + 1));
+  FVS_TRY(lab.alloc(n + 1)); FVS_TRY(changed.alloc(1));
+  const int g = stride_grid(n, 256);
+  k_cc_init<<<g, 256, 0, s>>>(n, act, ppe, par); FVS_COUNT_LAUNCH();
+  int done = 0;
+  for (int it = 0; it < 200; ++it) {
+    FVS_TRY(changed.zero(s));
+    k_cc_hook<<<g, 256, 0, s>>>(n, K.w, K.col, K.val, par, changed); FVS_COUNT_LAUNCH();
+    k_cc_compress<<<g, 256, 0, s>>>(n, par, root_flag); FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+    int h = 1;
+    FVS_CUDA(cudaMemcpyAsync(&h, changed.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FVS_CUDA(cudaStreamSynchronize(s));
+    if (!h) {
+      done = 1;
+      break;
+    }
+  }
+  if (!done) {
+    set_error("pressure system parts: labels did not settle");
+    return FVS_ERR_NOT_CONVERGED;
+  }
+  FVS_TRY(exclusive_scan(s, sw, n, root_flag, root_id));
+  FVS_CUDA(cudaMemcpyAsync(&ncomp, sw.total.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  FVS_CUDA(cudaStreamSynchronize(s));
+  FVS_TRY(cnt.alloc(ncomp + 1)); FVS_TRY(sum.alloc(ncomp + 1));
+  FVS_TRY(cnt.zero(s));
+  k_cc_label<<<g, 256, 0, s>>>(n, par, root_id, lab, cnt); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
+fvs_status PartProjector::apply(cudaStream_t s, double* v) {
+  const int64_t n = lab.n ? (int64_t)lab.n - 1 : 0;
+  if (ncomp == 0 || n == 0) return FVS_OK;
+  FVS_TRY(sum.zero(s));
+  k_part_sum<<<stride_grid(n, 256), 256, 0, s>>>(n, lab, v, sum); FVS_COUNT_LAUNCH();
+  k_part_sub<<<stride_grid(n, 256), 256, 0, s>>>(n, lab, sum, cnt, v); FVS_COUNT_LAUNCH();
+  FVS_LAUNCH_CHECK();
+  return FVS_OK;
+}
+
 // solve K x = rhs (compact) with the configured method; fills stats
 static fvs_status solve_pressure(fvs_solver s, double rtol, SolveResult& res, int& fallback) {
   cudaStream_t st = s->stream;
@@ -1036,14 +1138,16 @@ static fvs_status solve_pressure(fvs_solver s, double rtol, SolveResult& res, in
       return FVS_OK;
     }
   }
-  // single-grid fallback (Section 2.5); the null space is handled by the
-  // AMG's component labels when they exist, else by a global mean
-  fallback = 1;
+  // single-grid Jacobi BiCGStab: the configured solver, or the fallback of
+  // a failed AMG solve (Section 2.5); the null space of every connected
+  // part (liquid pocket) is projected out with labels of its own
+  fallback = s->props.p_solver == FVS_PSOLVER_AMG ? 1 : 0;
   JacobiPrecond J;
   J.A = &s->K;
-  Projector* pj = s->amg_ok ? (Projector*)&s->aproj : nullptr;
-  FVS_TRY(bicgstab(st, s->red, s->kw, s->K, nullptr, J, s->prhs, s->px, rtol, maxit * 4, pj, res));
-  if (pj) FVS_TRY(s->amg.project(st, s->px));
+  FVS_TRY(s->pparts.setup(st, s->K, s->act, s->ppe, s->sw));
+  FVS_TRY(bicgstab(st, s->red, s->kw, s->K, nullptr, J, s->prhs, s->px, rtol, fallback ? maxit * 4 : maxit,
+                   &s->pparts, res));
+  FVS_TRY(s->pparts.apply(st, s->px));
   return FVS_OK;
 }
 
@@ -1253,7 +1357,7 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
   s->have_step = true;
 
   S.n_ppe = s->nppe;
-  S.n_components = s->amg_ok ? s->ncomp : -1;
+  S.n_components = s->amg_ok ? s->ncomp : (s->pparts.ncomp > 0 ? s->pparts.ncomp : -1);
   S.amg_levels = s->amg_ok ? s->amg_levels : 0;
   S.status = status;
   s->last = S;
@@ -1274,6 +1378,15 @@ fvs_status solver_pressure_solve(fvs_solver s, const double* rhs, double* p_out,
   if (s->nact > 0) {
     k_rhs_in<<<stride_grid(s->nact, 256), 256, 0, st>>>(s->nact, s->act, s->ppe, m->cell_in, rhs, s->prhs, s->px); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
+    // a NaN or infinity in the right side is the caller's error: refuse it
+    // before any iteration runs
+    FVS_TRY(s->red.dot(st, s->nact, s->prhs, s->prhs, S_TMP0));
+    FVS_TRY(s->red.fetch(st));
+    const double bb = s->red.host[S_TMP0];
+    if (!(bb == bb) || bb > 1.7e308) {
+      set_error("fvs_pressure_solve: the right side holds a non-finite value");
+      return FVS_ERR_ARG;
+    }
   }
   SolveResult r;
   int fb = 0;

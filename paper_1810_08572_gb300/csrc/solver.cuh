@@ -12,6 +12,24 @@ inline void dswap(fvs::DBuf<T>& a, fvs::DBuf<T>& b) {
   b.p = p; b.n = n;
 }
 
+namespace fvs {
+// Connected parts of the pressure system found on the GPU from the pattern
+// of its matrix, for the single-grid solve (Section 2.5: each liquid pocket
+// is a separate singular block): the right side and the result are
+// projected to zero mean on each part, as the AMG path does with the labels
+// of its coarsest level.
+struct PartProjector : Projector {
+  DBuf<int32_t> par, root_flag, root_id, lab;
+  DBuf<double> sum, cnt;
+  DBuf<int> changed;
+  int ncomp = 0;
+  // labels of the rows i with ppe[act[i]] (the others are identity rows and
+  // stay out of every part)
+  fvs_status setup(cudaStream_t s, const Ell& K, const int32_t* act, const uint8_t* ppe, ScanWork& sw);
+  fvs_status apply(cudaStream_t s, double* v) override;
+};
+}  // namespace fvs
+
 struct fvs_solver_s {
   fvs_mesh mesh = nullptr;
   cudaStream_t stream = nullptr;
@@ -78,6 +96,7 @@ struct fvs_solver_s {
   fvs::KrylovWork kw;
   fvs::Amg amg;
   fvs::AmgProjector aproj;
+  fvs::PartProjector pparts;      // parts of the system for the single-grid solve
   bool amg_ok = false;
   int amg_levels = 0;
   int ncomp = 0;
