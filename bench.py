@@ -72,6 +72,12 @@ def parse():
     ap.add_argument("--uq-max-steps", type=int, default=20000, help="step cap of every UQ sample")
     ap.add_argument("--uq-only", action="store_true", help="only the UQ section (for profiling the batch)")
     ap.add_argument("--uq-dt", type=float, default=2e-3)
+    ap.add_argument("--uq-heldout", type=int, default=16, help="held-out plain solves judging the surrogates")
+    ap.add_argument("--no-shrink", action="store_true", help="skip the active-fraction segments")
+    ap.add_argument("--shrink-steps", type=int, default=10, help="timed steps per active-fraction segment")
+    ap.add_argument("--uq-study", choices=["c4", "c5", "paper"], default=None,
+                    help="run one UQ study at its stated size instead of the step benchmark")
+    ap.add_argument("--study-steps", type=int, default=0, help="c4: timed steps (0: to full solidification)")
     return ap.parse_args()
 
 
@@ -100,7 +106,7 @@ def bench_props(precision):
 # ---------------------------------------------------------------------------
 # CPU oracle timing (the reference arm and the cpu_baseline key)
 # ---------------------------------------------------------------------------
-def _oracle_worker(n, steps, q):
+def _oracle_worker(n, steps, warmup, q):
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     os.environ.setdefault("OMP_NUM_THREADS", "1")
     import warnings
@@ -109,7 +115,8 @@ def _oracle_worker(n, steps, q):
     from oracle.fv import Oracle
     c = cases.config_jittered(n=n)
     o = Oracle(c["mesh"], bench_props("fp64"))
-    o.step(c["dt"])            # first step outside the timing (imports, caches)
+    for _ in range(max(1, warmup)):   # untimed steps (imports, caches, AB2 history)
+        o.step(c["dt"])
     t0 = time.perf_counter()
     act = 0
     for _ in range(steps):
@@ -119,13 +126,27 @@ def _oracle_worker(n, steps, q):
     q.put(dict(active_cell_steps=act, seconds=dt))
 
 
-def cpu_oracle(n, steps):
+def host_cpu():
+    """Core count and CPU model of this host (the oracle runs on one core)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return dict(nproc=os.cpu_count(), model=model, machine=os.uname().machine)
+
+
+def cpu_oracle(n, steps, warmup=1):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     env_keep = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
     for k in env_keep:
         os.environ[k] = "1"
-    p = ctx.Process(target=_oracle_worker, args=(n, steps, q))
+    p = ctx.Process(target=_oracle_worker, args=(n, steps, warmup, q))
     p.start()
     r = q.get(timeout=1800)
     p.join()
@@ -135,9 +156,10 @@ def cpu_oracle(n, steps):
         else:
             os.environ[k] = v
     value = r["active_cell_steps"] / r["seconds"]
-    return dict(value=value, unit="active cell-steps/s", cores=1, kind="oracle",
-                sample=f"{n}^3 jittered permuted cavity (same physics and dt), {steps} steps after one "
-                       f"untimed step, single-threaded scipy oracle, {r['seconds']:.1f} s")
+    return dict(value=value, unit="active cell-steps/s", cores=1, kind="oracle", host=host_cpu(),
+                seconds=round(r["seconds"], 2), steps=steps,
+                sample=f"{n}^3 jittered permuted cavity (same physics and dt), {steps} steps after {max(1, warmup)} "
+                       f"untimed, single-threaded scipy oracle, {r['seconds']:.1f} s")
 
 
 # ---------------------------------------------------------------------------
@@ -214,6 +236,9 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if args.uq_only:
         print(json.dumps(dict(uq=run_uq(fvs, args))), flush=True)
+        return
+    if args.uq_study:
+        run_study(fvs, args)
         return
     dist = None
     if world > 1:
@@ -294,9 +319,23 @@ def run_gpu(args):
                     share_of_step=round(top["total_ms"] / max(1, args.prof_steps) / (ms / args.steps), 3),
                     bytes_per_launch=per_launch_bytes)
 
+    # the FP64 roof next to the copy bandwidth: an ELL row does one FMA per
+    # 12 bytes (8-byte value, 4-byte column), so FP64 SpMV kernels meet both
+    fp64 = fvs.measure_fp64_fma()
+    if roof:
+        W = c_mesh_width(mesh)
+        fma_bytes = 12.0 + 20.0 / max(W, 1)          # bytes per FMA of a W-slot row (vectors once per row)
+        roof["fp64_fma_gflops_measured"] = round(fp64, 1)
+        roof["fp64_roof_gbs"] = round(fp64 / 2.0 * fma_bytes, 1)
+        roof["frac_of_fp64_roof"] = round(roof["achieved"] / (fp64 / 2.0 * fma_bytes), 4)
+
     mixed = None
     if ref_fields is not None:
         mixed = run_mixed(fvs, c, args, stream, torch, ref_fields)
+
+    shrink = None
+    if not args.no_shrink and rank == 0:
+        shrink = run_shrink(fvs, c, args, stream, torch)
 
     e2e = None
     if not args.no_e2e and rank == 0:
@@ -308,7 +347,7 @@ def run_gpu(args):
 
     cpu = None
     if not args.no_cpu and rank == 0 and world == 1:
-        cpu = cpu_oracle(args.cpu_n, args.cpu_steps)
+        cpu = cpu_oracle(args.cpu_n, args.cpu_steps, 1)
 
     nkern = sum(r["launches"] for r in prof)
     line = dict(
@@ -320,7 +359,7 @@ def run_gpu(args):
                              f"{args.precision}", cells=args.n ** 3, dt=dt, p_rtol=1e-8,
                     precision=args.precision, l2="inputs larger than L2 (matrices ~1 GB)",
                     parallelism="replicas" if world > 1 else "single GPU"),
-        roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=ck, uq=uq, mixed=mixed,
+        roofline=roof, cpu_baseline=cpu, e2e=e2e, clocks=ck, uq=uq, mixed=mixed, active_fraction_segments=shrink,
         gpu_launches=int(n_launch),
         kernel_profile=sorted(prof, key=lambda r: -r["total_ms"])[:12],
         step_stats=dict(p_its=[s["p_its"] for s in its], e_its=[s["e_its"] for s in its],
@@ -336,9 +375,100 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def c_mesh_width(mesh):
+    return int(mesh.info["max_cell_neighbours"])
+
+
+def run_shrink(fvs, c, args, stream, torch):
+    """The paper's claim that work shrinks as the casting freezes (Section
+    2.4), measured: segments that start from the 1-D conduction profile
+    T(x) = 700 + 250 erf(x/delta) K with delta chosen so that 100, 85, 70, 55
+    and 40 % of the cells are liquid or mushy; per segment and precision,
+    3 untimed and --shrink-steps timed steps."""
+    import numpy as np
+    from scipy.special import erf, erfinv
+    m = c["mesh"]
+    X = np.asarray(m["nodes"])[np.asarray(m["cells"])].mean(axis=1)
+    x = X[:, 0]
+    L = float(np.asarray(m["nodes"])[:, 0].max())
+    z = float(erfinv((833.0 - 700.0) / 250.0))      # erf(x/delta) at the solidus
+    out = []
+    mesh = fvs.Mesh(m, stream=stream)
+    for frac in (1.0, 0.85, 0.70, 0.55, 0.40):
+        T0 = np.full(len(x), 950.0) if frac >= 1.0 else 700.0 + 250.0 * erf(x / ((1.0 - frac) * L / z))
+        row = dict(target_active=frac, active_at_start=round(float((T0 > 833.0).mean()), 4))
+        for prec in ("fp64", "mixed"):
+            S = fvs.Solver(mesh, bench_props(prec), stream=stream)
+            S.set_state(T0)
+            for _ in range(3):
+                S.step(c["dt"], 1, allow_not_converged=True)
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            act, p_its = 0, []
+            ev0.record(stream)
+            for _ in range(args.shrink_steps):
+                st = S.step(c["dt"], 1, allow_not_converged=True)
+                act += st["n_active"]
+                p_its.append(st["p_its"])
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            row[prec] = dict(value=round(act / (ms / 1e3), 1), ms_per_step=round(ms / args.shrink_steps, 3),
+                             mean_active=round(act / args.shrink_steps), p_its=round(float(np.mean(p_its)), 1))
+            S.close()
+        out.append(row)
+    mesh.close()
+    return out
+
+
+UQ_FAMILIES = (0, 1, 1)        # melt ~ normal, wall and C0 ~ uniform (fvs_pce families)
+UQ_PARAMS = ((950.0, 10.0), (650.0, 750.0), (3.0, 5.0))
+
+
+def judge_surrogates(fvs, X, Y, Xte, Yte, mc_n=1000000, epochs=2000, pce_degree=2):
+    """MLP (BF16 tensor cores) and polynomial chaos (Eq. 27-28, least squares
+    on the same training solves) judged on held-out plain solves of the same
+    inputs (paired), then both on mc_n Monte Carlo inputs."""
+    import numpy as np
+    from fvs_inputs import cases
+    out = {}
+    S = fvs.Surrogate(3, 128, 4, 4, seed=1)
+    S.set_scaling(X.mean(0), X.std(0), Y.mean(0), Y.std(0))
+    t0 = time.perf_counter()
+    S.train(X, Y, epochs, 1e-3)
+    train_s = time.perf_counter() - t0
+    P = fvs.Pce(UQ_FAMILIES, UQ_PARAMS, pce_degree, 4)
+    P.fit(X, Y)
+    Xmc = cases.uq_inputs(mc_n, seed=4)
+    for name, model in (("mlp", S.predict), ("pce", P)):
+        Yp = model(Xte)
+        rel = np.abs(Yp - Yte) / np.abs(Yte)
+        model(Xmc[:4096])
+        t1 = time.perf_counter()
+        Ymc = model(Xmc)
+        rate = len(Xmc) / (time.perf_counter() - t1)
+        out[name] = dict(heldout_mean_rel_err=[round(float(v), 5) for v in rel.mean(0)],
+                         heldout_max_rel_err=[round(float(v), 5) for v in rel.max(0)],
+                         heldout_paired_mean_gap=[round(float(v), 5) for v in
+                                                  (Yp.mean(0) - Yte.mean(0)) / np.abs(Yte.mean(0))],
+                         mc_mean=[float(v) for v in Ymc.mean(0)], mc_var=[float(v) for v in Ymc.var(0)],
+                         samples_per_s=round(rate, 1))
+    out["mlp"]["train_s"] = round(train_s, 2)
+    _, var, total, first = P.sensitivity()
+    out["pce"].update(degree=pce_degree, terms=P.num_terms(), sobol_total=total.round(4).tolist(),
+                      sobol_first=first.round(4).tolist(), variance=var.tolist())
+    # plain Monte Carlo reference: every plain solve, mean +- standard error
+    Yall = np.concatenate([Y, Yte])
+    out["plain_mc"] = dict(n=len(Yall), mean=[float(v) for v in Yall.mean(0)],
+                           std_err=[float(v) for v in Yall.std(0, ddof=1) / np.sqrt(len(Yall))],
+                           var=[float(v) for v in Yall.var(0, ddof=1)])
+    return out
+
+
 def run_uq(fvs, args):
-    """UQ samples/s: plain batched solves to full solidification, then the
-    surrogate trained on them evaluated on 1e6 Monte Carlo inputs."""
+    """UQ samples/s: plain batched solves to full solidification (lockstep,
+    mixed precision), the same samples as independent FP64 and mixed solves,
+    and the two surrogates trained on them, judged on held-out solves."""
     import numpy as np
     from fvs_inputs import box_mesh, cases
     n = args.uq_n
@@ -350,34 +480,122 @@ def run_uq(fvs, args):
     Y, steps = fvs.uq_batch(M, props, X, args.uq_dt, args.uq_max_steps, mode=fvs.UQ_LOCKSTEP)
     sec = time.perf_counter() - t0
     plain = args.uq_samples / sec
-    # the same samples as independent solves (one solver per CUDA stream), FP64 V-cycle:
-    # the baseline the lockstep batch and its mixed precision are measured against
+    lock64 = None
     streams = None
     if not args.no_uq_streams:
+        # equal-precision comparison: lockstep FP64 against independent FP64
+        # solves on streams, then independent solves with the FP32 V-cycle
+        t0 = time.perf_counter()
+        Yl, _ = fvs.uq_batch(M, bench_props("fp64"), X, args.uq_dt, args.uq_max_steps, mode=fvs.UQ_LOCKSTEP)
+        lock64 = round(args.uq_samples / (time.perf_counter() - t0), 3)
         t0 = time.perf_counter()
         Y1, steps1 = fvs.uq_batch(M, bench_props("fp64"), X, args.uq_dt, args.uq_max_steps, n_streams=args.uq_streams,
                                   mode=fvs.UQ_STREAMS)
-        streams = dict(samples_per_s=round(args.uq_samples / (time.perf_counter() - t0), 3),
-                       streams=args.uq_streams, precision="fp64",
-                       max_rel_qoi_diff=float(np.nanmax(np.abs(Y1 - Y) / np.abs(Y1))),
+        s64 = args.uq_samples / (time.perf_counter() - t0)
+        t0 = time.perf_counter()
+        fvs.uq_batch(M, props, X, args.uq_dt, args.uq_max_steps, n_streams=args.uq_streams, mode=fvs.UQ_STREAMS)
+        s32 = args.uq_samples / (time.perf_counter() - t0)
+        streams = dict(fp64_samples_per_s=round(s64, 3), mixed_samples_per_s=round(s32, 3), streams=args.uq_streams,
+                       max_rel_qoi_diff_vs_lockstep=float(np.nanmax(np.abs(Y1 - Yl) / np.abs(Y1))),
                        steps_equal=bool(np.array_equal(steps1, steps)))
-    sur, Ymc = None, np.full((1, 4), np.nan)
-    if np.all(np.isfinite(Y)):     # step-capped runs leave samples without solidified cells
-        S = fvs.Surrogate(3, 128, 4, 4, seed=1)
-        S.set_scaling(X.mean(0), X.std(0), Y.mean(0), Y.std(0))
-        S.train(X, Y, 2000, 1e-3)
-        Xmc = cases.uq_inputs(1000000, seed=4)
-        S.predict(Xmc[:4096])
-        t1 = time.perf_counter()
-        Ymc = S.predict(Xmc)
-        sur = round(len(Xmc) / (time.perf_counter() - t1), 1)
-    return dict(plain_samples_per_s=round(plain, 3), surrogate_samples_per_s=sur, unit="samples/s",
-                samples=args.uq_samples, mesh=f"cavity {n}^3, all walls at the sampled temperature",
-                dt=args.uq_dt, mean_steps=float(np.mean(steps)), mode="lockstep (one launch per phase for all "
-                "samples), mixed precision", independent_solves=streams,
-                qoi_mean_plain=[float(v) for v in Y.mean(0)], qoi_mean_surrogate_1e6=[float(v) for v in Ymc.mean(0)],
-                note="plain: fvs_uq_batch to full solidification; surrogate: BF16 MLP "
-                     "trained on those solves, inference on 1e6 inputs (host in/out)")
+    sur = None
+    if args.uq_heldout > 0 and np.all(np.isfinite(Y)):
+        Xte = cases.uq_inputs(args.uq_heldout, seed=2019)
+        Yte, _ = fvs.uq_batch(M, props, Xte, args.uq_dt, args.uq_max_steps, mode=fvs.UQ_LOCKSTEP)
+        sur = judge_surrogates(fvs, X, Y, Xte, Yte)
+    return dict(plain_samples_per_s=round(plain, 3), unit="samples/s", samples=args.uq_samples,
+                mesh=f"cavity {n}^3, all walls at the sampled temperature", dt=args.uq_dt,
+                mean_steps=float(np.mean(steps)),
+                mode="lockstep (one launch per phase for all samples), mixed precision",
+                lockstep_fp64_samples_per_s=lock64, independent_solves=streams,
+                batching_gain_fp64=round(lock64 / streams["fp64_samples_per_s"], 3) if streams else None,
+                surrogates=sur,
+                note="plain: fvs_uq_batch to full solidification; surrogates trained on those solves, judged on "
+                     f"{args.uq_heldout} held-out plain solves (paired) and on 1e6 Monte Carlo inputs")
+
+
+def run_study(fvs, args):
+    """One UQ study at its stated size (not part of the step benchmark).
+    c4: 256 samples on the 64^3 cavity, lockstep, mixed precision, to full
+    solidification or for --study-steps timed steps (then extrapolated by
+    the step count of a 32^3 run of the same samples, stated).
+    c5: 512 training and 64 held-out plain solves of the 48^3 cavity; the
+    MLP and the polynomial chaos judged on the held-out ones (paired) and on
+    1e6 Monte Carlo inputs.
+    paper: the study of Section 5 (Al-Si, its input distributions,
+    convection off, grain growth, the four domain outputs) on the 64^3
+    cavity with 216 tensor collocation points (Table 2's level 6) and 60
+    Latin-hypercube test solves."""
+    import numpy as np
+    from fvs_inputs import box_mesh, cases
+    t_start = time.perf_counter()
+    out = dict(study=args.uq_study)
+    if args.uq_study == "c4":
+        m = box_mesh(64, 64, 64, cases.CAVITY)
+        M = fvs.Mesh(m)
+        X = cases.uq_inputs(256, seed=2018)
+        cap = args.study_steps if args.study_steps > 0 else args.uq_max_steps
+        t0 = time.perf_counter()
+        Y, steps = fvs.uq_batch(M, bench_props("mixed"), X, args.uq_dt, cap, mode=fvs.UQ_LOCKSTEP)
+        sec = time.perf_counter() - t0
+        out.update(samples=256, mesh="cavity 64^3", dt=args.uq_dt, seconds=round(sec, 2),
+                   steps_max=int(steps.max()), steps_mean=float(steps.mean()))
+        if args.study_steps > 0:
+            m32 = box_mesh(32, 32, 32, cases.CAVITY)
+            _, s32 = fvs.uq_batch(fvs.Mesh(m32), bench_props("mixed"), X, args.uq_dt, args.uq_max_steps,
+                                  mode=fvs.UQ_LOCKSTEP)
+            full = float(s32.max())
+            out.update(extrapolated=True, steps_to_solidify_32=full,
+                       samples_per_s=round(256 / (sec * full / cap), 4),
+                       note=f"{cap} timed steps of all 256 samples, scaled to the {full:.0f} steps the last sample "
+                            "of the same inputs needs on the 32^3 cavity")
+        else:
+            out.update(extrapolated=False, samples_per_s=round(256 / sec, 4), qoi_mean=Y.mean(0).tolist())
+    elif args.uq_study == "c5":
+        m = box_mesh(48, 48, 48, cases.CAVITY)
+        M = fvs.Mesh(m)
+        props = bench_props("mixed")
+        X = cases.uq_inputs(512, seed=1)
+        t0 = time.perf_counter()
+        Y, steps = fvs.uq_batch(M, props, X, args.uq_dt, args.uq_max_steps, mode=fvs.UQ_LOCKSTEP)
+        sec = time.perf_counter() - t0
+        Xte = cases.uq_inputs(64, seed=2)
+        Yte, _ = fvs.uq_batch(M, props, Xte, args.uq_dt, args.uq_max_steps, mode=fvs.UQ_LOCKSTEP)
+        out.update(train=512, heldout=64, mesh="cavity 48^3", plain_samples_per_s=round(512 / sec, 4),
+                   mean_steps=float(steps.mean()), surrogates=judge_surrogates(fvs, X, Y, Xte, Yte, pce_degree=3))
+    else:
+        m = box_mesh(64, 64, 64, cases.CAVITY)
+        M = fvs.Mesh(m)
+        props = bench_props("mixed")
+        props["material"] = dict(cases.AL_SI_PAPER)
+        props["no_flow"] = True
+        fam = (0, 0, 0)
+        par = ((1000.0, 10.0), (500.0, 5.0), (10.0, 0.2))
+        kw = dict(qoi_kind=fvs.QOI_EXTREMES, liquidus=(cases.AL_SI_T_F, cases.AL_SI_SLOPE),
+                  grain=dict(kp=cases.AL_SI_PAPER["kp"], D_s=3e-9, r0=1e-6))
+        res = {}
+        for level, deg in ((3, 2), (6, 4)):
+            P = fvs.Pce(fam, par, deg, 4)
+            Xc = P.nodes(level)
+            t0 = time.perf_counter()
+            Yc, st, _ = fvs.uq_run(M, props, Xc, args.uq_dt, args.uq_max_steps, mode=fvs.UQ_LOCKSTEP, **kw)
+            sec = time.perf_counter() - t0
+            P.fit(Xc, Yc)
+            res[level] = (P, len(Xc), sec, float(st.mean()))
+        Xt = cases.latin_hypercube_normal([p[0] for p in par], [p[1] for p in par], 60, seed=7)
+        Yt, _, _ = fvs.uq_run(M, props, Xt, args.uq_dt, args.uq_max_steps, mode=fvs.UQ_LOCKSTEP, **kw)
+        rows = []
+        for level, (P, npts, sec, mst) in res.items():
+            err = np.sqrt(np.mean((P(Xt) - Yt) ** 2, axis=0)) / np.abs(Yt.mean(0))
+            mean, var, total, first = P.sensitivity()
+            rows.append(dict(level=level, points=npts, plain_seconds=round(sec, 2), mean_steps=mst,
+                             rms_error_over_mean=[float(v) for v in err], sobol_total=total.round(4).tolist(),
+                             mean=mean.tolist(), std=np.sqrt(var).tolist()))
+        out.update(mesh="cavity 64^3, Al-Si (Scheil), convection off, grain growth", levels=rows,
+                   outputs=["total solidification time (s)", "max SDAS (um)", "min yield (MPa)", "max grain (m)"],
+                   inputs=["T_init ~ N(1000, 10) K", "T_wall ~ N(500, 5) K", "C0 ~ N(10, 0.2) wt%"])
+    out["wall_seconds"] = round(time.perf_counter() - t_start, 1)
+    print(json.dumps(out), flush=True)
 
 
 def run_mixed(fvs, c, args, stream, torch, ref):
@@ -446,16 +664,21 @@ def run_e2e(fvs, c, props, args, stream, torch):
 
 
 def run_reference(args):
+    """The oracle as it stands on the host cores: --warmup untimed and
+    --steps timed steps of a bounded sample (--cpu-n^3 cells) of the bench
+    workload; ms_per_step is per sample step."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    cpu = cpu_oracle(args.cpu_n, max(1, args.steps // 10 or 1) if args.steps > 0 else 1)
+    steps = max(1, args.steps)
+    cpu = cpu_oracle(args.cpu_n, steps, args.warmup)
     line = dict(impl="reference", metric=METRIC, value=round(cpu["value"], 2), unit="active cell-steps/s",
-                n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
-                ms_per_step=round(1e3 * args.cpu_n ** 3 / cpu["value"], 3), higher_is_better=True,
+                n_gpus=args.gpus, steps=steps, warmup=args.warmup,
+                ms_per_step=round(1e3 * cpu["seconds"] / steps, 3), higher_is_better=True,
                 scaling="weak", vs_baseline=None, dtype="f64", data="synthetic",
                 config=dict(workload=f"cavity {args.n}^3 jittered+permuted, dt 1e-3 s, p_rtol 1e-8, "
-                                     f"{args.precision}", cpu_sample_cells=args.cpu_n ** 3),
+                                     f"{args.precision}", cpu_sample_cells=args.cpu_n ** 3,
+                            sample="each step is one oracle step on the sample, not on the full mesh"),
                 cpu_baseline=cpu,
                 e2e=dict(value=round(cpu["value"], 2), unit="active cell-steps/s", h2d_bytes_per_step=0,
                          d2h_bytes_per_step=0))

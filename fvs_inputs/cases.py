@@ -26,6 +26,19 @@ AL_ALLOY = dict(
 # coefficient and freezing temperature of an Al-Si-like alloy, smear width 2 K
 AL_SI_SCHEIL = dict(AL_ALLOY, fs_model=1, kp=0.13, T_f=933.0, T_eps=2.0)
 
+# The Al-Si alloy of the paper's UQ study (Section 5): freezing point of Al
+# 660 C and eutectic (solidus) 577 C from the phase diagram; both lines
+# straight, with the eutectic at 12.6 wt% Si and the largest solubility of
+# Si in solid Al 1.65 wt% (textbook values of the Al-Si diagram, which the
+# paper reads off a figure), so the liquidus slope is -83/12.6 K per wt%
+# and kp, the ratio of the liquidus to the solidus slope, is 1.65/12.6.
+# Density, heat capacity, conductivity and latent heat stay those of the
+# cavity alloy; T_liq is the value at the mean composition of 10 wt%.
+AL_SI_T_F = 933.15
+AL_SI_SLOPE = (850.15 - 933.15) / 12.6
+AL_SI_PAPER = dict(AL_ALLOY, T_sol=850.15, T_liq=AL_SI_T_F + AL_SI_SLOPE * 10.0, T_ref=AL_SI_T_F + AL_SI_SLOPE * 10.0,
+                   fs_model=1, kp=1.65 / 12.6, T_f=AL_SI_T_F, T_eps=2.0)
+
 CAVITY = (0.1, 0.1, 0.0125)
 
 
@@ -70,6 +83,31 @@ def uq_inputs(n_samples, seed):
     T_wall = rng.uniform(650.0, 750.0, n_samples)
     C0 = rng.uniform(3.0, 5.0, n_samples)
     return np.stack([T_melt, T_wall, C0], axis=1)
+
+
+def paper_uq_inputs(n_samples, seed):
+    """The stochastic inputs of Section 5: initial melt temperature
+    ~ N(1000, 10) K, wall temperature ~ N(500, 5) K, solute C0 ~ N(10, 0.2)
+    wt%.  Returns [S, 3] in the order (T_melt, T_wall, C0)."""
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.normal(1000.0, 10.0, n_samples), rng.normal(500.0, 5.0, n_samples),
+                     rng.normal(10.0, 0.2, n_samples)], axis=1)
+
+
+def latin_hypercube_normal(means, sds, n, seed):
+    """n Latin-hypercube samples of independent normal inputs: one point in
+    each of n equal-probability strata of every marginal, the strata paired
+    across inputs by random permutations.  Returns [n, len(means)]."""
+    from scipy.stats import norm
+    rng = np.random.default_rng(seed)
+    d = len(means)
+    U = (np.stack([rng.permutation(n) for _ in range(d)], axis=1) + rng.uniform(size=(n, d))) / n
+    return np.asarray(means, dtype=np.float64) + np.asarray(sds, dtype=np.float64) * norm.ppf(U)
+
+
+def paper_liquidus_of(C0):
+    """Liquidus of the Al-Si line above: T_f + slope C0."""
+    return AL_SI_T_F + AL_SI_SLOPE * np.asarray(C0)
 
 
 def liquidus_of(C0):

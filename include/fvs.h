@@ -49,6 +49,7 @@ typedef enum {
 
 typedef struct fvs_mesh_s* fvs_mesh;
 typedef struct fvs_solver_s* fvs_solver;
+typedef struct fvs_surrogate_s* fvs_surrogate;   /* learned surrogate, see below */
 
 /* Message for the last non-OK status returned on this thread (never NULL). */
 const char* fvs_last_error(void);
@@ -132,10 +133,23 @@ typedef struct {
   double T_eps;       /* half-width of the smear band, K (Scheil)              */
 } fvs_material;
 
-enum { FVS_BC_ADIABATIC = 0, FVS_BC_DIRICHLET = 1 };
+/* Wall conditions of the energy equation (every wall is no-slip).
+ *  FVS_BC_ADIABATIC   no heat flux
+ *  FVS_BC_DIRICHLET   fixed wall temperature T; the wall's vertices take T
+ *                     in the cross-diffusion terms (Eq. 11-12)
+ *  FVS_BC_CONVECTIVE  heat-transfer coefficient h (W/m2 K) to an ambient
+ *                     temperature T: the face carries the orthogonal flux
+ *                     A (T - T_c)/(d/k_c + 1/h), d the distance from the cell
+ *                     centre to the face centre and k_c the cell's
+ *                     conductivity; the wall's vertices stay free (cell
+ *                     means), as on adiabatic walls.  The paper fixes the
+ *                     wall temperature (Section 4-5); this is the usual
+ *                     film condition of a cooled die. */
+enum { FVS_BC_ADIABATIC = 0, FVS_BC_DIRICHLET = 1, FVS_BC_CONVECTIVE = 2 };
 typedef struct {
-  int32_t type; /* FVS_BC_ADIABATIC or FVS_BC_DIRICHLET; every wall is no-slip */
-  double T;     /* wall temperature for FVS_BC_DIRICHLET                       */
+  int32_t type; /* FVS_BC_ADIABATIC, FVS_BC_DIRICHLET or FVS_BC_CONVECTIVE     */
+  double T;     /* wall temperature, or the ambient temperature (K)            */
+  double h;     /* FVS_BC_CONVECTIVE: heat-transfer coefficient (> 0)          */
 } fvs_patch_bc;
 
 enum { FVS_PREC_FP64 = 0, FVS_PREC_MIXED = 1 };
@@ -156,6 +170,22 @@ typedef struct {
   int32_t p_solver;             /* FVS_PSOLVER_AMG (AMG-preconditioned Krylov,
                                    falling back to Jacobi BiCGStab on failure as
                                    in Section 2.5) or FVS_PSOLVER_JACOBI         */
+  int32_t no_flow;              /* 1: natural convection off (Section 4 runs its
+                                   castings without it): no momentum, pressure
+                                   or correction step; u, fluxes and p stay 0
+                                   and the energy equation is conduction with
+                                   latent heat.  0: the full method            */
+  int32_t n_k;                  /* points of a piecewise-linear conductivity
+                                   k(T) of the metal (Section 4 uses a table;
+                                   0: the constant mat.k), at most 16          */
+  const double* k_T;            /* host [n_k] increasing temperatures (K)       */
+  const double* k_val;          /* host [n_k] conductivities (W/m K), held
+                                   constant outside the table.  Each step
+                                   evaluates k per face at T^n: at the mean of
+                                   the two cells, of the cell and a fixed wall
+                                   value, or at the metal cell on convective
+                                   walls and metal-mold faces; both
+                                   Crank-Nicolson halves use it                */
 } fvs_props;
 
 fvs_status fvs_solver_create(fvs_mesh mesh, void* stream, fvs_solver* out);
@@ -258,36 +288,87 @@ fvs_status fvs_query_fields(fvs_solver solver, fvs_field field, double* dst,
 
 /* ------------------------------------------------------------------------
  * Batched uncertainty quantification (Section 2.7: non-intrusive sampling of
- * the stochastic inputs, one plain solve per sample; Eq. 22-23 outputs).
+ * the stochastic inputs, one plain solve per sample; Section 5: melt
+ * temperature, wall temperature and solute content as the inputs).
  *   base      host: material and solver settings shared by all samples
- *             (its bc and T_init are replaced per sample)
+ *             (its bc and T_init are replaced per sample: every wall patch
+ *             is held at the sample's wall temperature)
  *   inputs    host double [n_samples*3], per sample: melt temperature (K),
- *             wall temperature applied to every wall patch (K), solute
- *             concentration C0 (wt%) which moves the liquidus to
- *             base T_liq - 5 (C0 - 4)
+ *             wall temperature (K), solute concentration C0 (wt%)
  *   dt        time step (s); each sample starts at rest at its melt
  *             temperature and runs until a step starts with every cell solid,
  *             or for max_steps steps
+ *   opt       host, nullable (NULL: the zero-initialised options)
+ *   qoi_out   host double [n_samples*4], per opt->qoi_kind:
+ *             FVS_QOI_MEANS: means over the solidified cells of the local
+ *               solidification time t_f (s), cooling rate (K/s), SDAS (um)
+ *               and yield strength (MPa) (Eq. 22-23); NaN if no cell
+ *               solidified
+ *             FVS_QOI_EXTREMES: the four outputs of Section 5, taken over
+ *               the whole domain: total solidification time (the latest
+ *               solidus crossing, s; NaN while a cell is still above the
+ *               solidus), maximum SDAS (um), minimum yield strength (MPa)
+ *               and maximum grain radius (m; 0 without grain growth)
+ *   steps_out host int64 [n_samples] steps taken, 0 for samples the surrogate
+ *             answered (nullable)
+ * Options:
  *   mode      FVS_UQ_LOCKSTEP (0): all samples advance together, every
  *             field stored [row][sample], one launch per phase for all
  *             samples, shared operators and AMG aggregation, per-sample
  *             pressure rows and coarse values (needs a coarsest AMG level of
  *             at most 160 rows on the all-liquid pressure operator, else
- *             FVS_ERR_NOT_CONVERGED);
+ *             FVS_ERR_NOT_CONVERGED; a k(T) table needs FVS_UQ_STREAMS);
  *             FVS_UQ_STREAMS (1): independent solves, each on its own CUDA
- *             stream and solver
- *   n_streams mode 1: concurrent samples (0 = 8); ignored by mode 0
- *   qoi_out   host double [n_samples*4]: per sample the mean over the
- *             solidified cells of local solidification time t_f (s), cooling
- *             rate (K/s), SDAS (um) and yield strength (MPa); NaN if no cell
- *             solidified
- *   steps_out host int64 [n_samples] steps taken (nullable)
- * Blocks until all samples are done.  Fails with FVS_ERR_ARG if a sample's
- * liquidus falls to the solidus.
+ *             stream and solver;
+ *             FVS_UQ_SURROGATE (2): the trained models answer every sample
+ *             inside the box [box_lo, box_hi] whose ensemble agrees (the
+ *             spread of the models' predictions, standard deviation over
+ *             models divided by the magnitude of their mean, at most
+ *             max_spread for every output; max_spread <= 0 skips the test);
+ *             the other samples fall back to plain solves in plain_mode.
+ *             The models must have been trained on this qoi_kind.
+ *   n_streams FVS_UQ_STREAMS: concurrent samples (0 = 8)
+ *   liquidus_T0, liquidus_slope
+ *             the sample's liquidus T_liq = liquidus_T0 + liquidus_slope C0
+ *             (a straight liquidus line; Section 5 reads it off the Al-Si
+ *             phase diagram, with liquidus_T0 the solvent's freezing point);
+ *             both 0: every sample keeps base->mat.T_liq.  FVS_ERR_ARG if a
+ *             sample's liquidus does not suit the solid-fraction law
+ *   grain_kp, grain_Ds, grain_r0
+ *             grain growth in every sample as fvs_set_grain_growth
+ *             (grain_Ds = 0: off)
+ *   models, n_models, box_lo, box_hi [3], max_spread, plain_mode
+ *             FVS_UQ_SURROGATE only (plain_mode LOCKSTEP or STREAMS)
+ *   used_plain host int32 [n_samples] out (nullable): 1 where the sample
+ *             was solved plainly
+ *   T_out, p_out [n_samples*n_cells], u_out [n_samples*n_cells*3]
+ *             host, nullable: each plainly solved sample's final
+ *             temperature, pressure and velocity (x,y,z per cell) in the
+ *             caller's cell order (rows of surrogate samples are untouched)
+ * Blocks until all samples are done.
  * ------------------------------------------------------------------------ */
-enum { FVS_UQ_LOCKSTEP = 0, FVS_UQ_STREAMS = 1 };
+enum { FVS_UQ_LOCKSTEP = 0, FVS_UQ_STREAMS = 1, FVS_UQ_SURROGATE = 2 };
+enum { FVS_QOI_MEANS = 0, FVS_QOI_EXTREMES = 1 };
+typedef struct {
+  int32_t mode;
+  int32_t n_streams;
+  int32_t qoi_kind;
+  double liquidus_T0;
+  double liquidus_slope;
+  double grain_kp, grain_Ds, grain_r0;
+  int32_t n_models;
+  const fvs_surrogate* models;
+  const double* box_lo;
+  const double* box_hi;
+  double max_spread;
+  int32_t plain_mode;
+  int32_t* used_plain;
+  double* T_out;
+  double* u_out;
+  double* p_out;
+} fvs_uq_options;
 fvs_status fvs_uq_batch(fvs_mesh mesh, const fvs_props* base, int64_t n_samples, const double* inputs,
-                        double dt, int32_t max_steps, int32_t mode, int32_t n_streams, double* qoi_out,
+                        double dt, int32_t max_steps, const fvs_uq_options* opt, double* qoi_out,
                         int64_t* steps_out);
 
 /* ------------------------------------------------------------------------
@@ -301,8 +382,6 @@ fvs_status fvs_uq_batch(fvs_mesh mesh, const fvs_props* base, int64_t n_samples,
  * doubles: for each layer its weight matrix [n_out x n_in] row-major, then
  * its bias [n_out].
  * ------------------------------------------------------------------------ */
-typedef struct fvs_surrogate_s* fvs_surrogate;
-
 /* n_in, n_hidden, n_out in 1..128, 1..16 hidden layers; weights drawn
  * uniform(-sqrt(6/fan_in), +sqrt(6/fan_in)) from a counter-based generator
  * keyed by seed, biases zero; scaling is the identity until set. */
@@ -328,6 +407,50 @@ fvs_status fvs_surrogate_train(fvs_surrogate s, const double* X, const double* T
                                double lr, double* final_loss);
 /* Y [n x n_out] = model(X [n x n_in]); both host or both device memory. */
 fvs_status fvs_surrogate_predict(fvs_surrogate s, const double* X, double* Y, int64_t n, int on_device);
+
+/* ------------------------------------------------------------------------
+ * Polynomial chaos surrogate (the paper's own: Section 2.7, Eq. 27-28, and
+ * the total Sobol indices of Section 5).  An output is expanded in products
+ * of orthonormal polynomials of the standardised inputs, truncated at a
+ * total degree: probabilists' Hermite He_n/sqrt(n!) of (x - mean)/sd for a
+ * normal input (the paper's inputs), Legendre sqrt(2n+1) P_n of
+ * (2x - lo - hi)/(hi - lo) for a uniform one.  Terms are ordered by total
+ * degree, then by their multi-indices with the last input varying fastest.
+ * The coefficients solve the Vandermonde system of Eq. 28 in the least-
+ * squares sense (normal equations, Cholesky, two refinement steps on the
+ * Vandermonde residual), on the GPU.
+ * ------------------------------------------------------------------------ */
+enum { FVS_PCE_NORMAL = 0, FVS_PCE_UNIFORM = 1 };
+typedef struct fvs_pce_s* fvs_pce;
+/* n_in inputs (1..8) with family[j] and parameters (p1, p2)[j] = (mean, sd)
+ * or (lo, hi), host arrays; total degree 0..24; n_out outputs (1..8). */
+fvs_status fvs_pce_create(int32_t n_in, const int32_t* family, const double* p1, const double* p2,
+                          int32_t degree, int32_t n_out, void* stream, fvs_pce* out);
+fvs_status fvs_pce_destroy(fvs_pce p);
+/* Number of expansion terms, or -1 for a NULL handle. */
+int64_t fvs_pce_num_terms(fvs_pce p);
+/* Multi-indices, host int32 [num_terms*n_in] (degree of input j in term k at
+ * k*n_in + j). */
+fvs_status fvs_pce_multi_indices(fvs_pce p, int32_t* alpha, int64_t len);
+/* Collocation points in the inputs' units (Section 2.7: roots of the basis
+ * polynomials): sparse = 0, the tensor product of level-point rules
+ * (level^n_in points; Section 5 uses levels 3 and 6, 27 and 216 points);
+ * sparse = 1, Smolyak's combination of the level-i rules with i points over
+ * max(n_in, level) <= |i| <= level + n_in - 1.  X (host [cap*n_in]) may be
+ * NULL to count the points into *n. */
+fvs_status fvs_pce_nodes(fvs_pce p, int32_t level, int32_t sparse, double* X, int64_t cap, int64_t* n);
+/* Fit to m runs: X host [m*n_in], Y host [m*n_out]; m >= num_terms.
+ * rms_resid (nullable) gets the root-mean-square residual of the fit.
+ * FVS_ERR_ARG when the points do not determine the coefficients. */
+fvs_status fvs_pce_fit(fvs_pce p, const double* X, const double* Y, int64_t m, double* rms_resid);
+/* Y [n*n_out] = expansion at X [n*n_in]; both host or both device. */
+fvs_status fvs_pce_eval(fvs_pce p, const double* X, double* Y, int64_t n, int on_device);
+/* Coefficients, host [num_terms*n_out] (term k, output q at k*n_out + q). */
+fvs_status fvs_pce_coefficients(fvs_pce p, double* c, int64_t len);
+/* From the coefficients: mean and variance per output (host [n_out]) and
+ * the total and first-order Sobol indices (host [n_out*n_in]); any pointer
+ * may be NULL. */
+fvs_status fvs_pce_sensitivity(fvs_pce p, double* mean, double* var, double* total, double* first);
 
 /* ------------------------------------------------------------------------
  * Kernel timing (not part of the method; for roofline measurement).
@@ -366,6 +489,13 @@ fvs_status fvs_profile_read(fvs_solver solver, fvs_kernel_time* out, int32_t max
  * share the array: each call overwrites every value it returns, and calls
  * whose GPU work overlaps (other streams, other threads) race on it. */
 fvs_status fvs_query_fields_noalloc(fvs_solver solver, fvs_field field, double* dst, int64_t dst_len);
+
+/* Measured FP64 fused-multiply-add rate of the current GPU (GFLOP/s, two
+ * flops per FMA): eight independent FMA chains per thread, 8 blocks of 256
+ * threads per SM, iters FMAs per chain, timed with CUDA events.  Not part
+ * of the method: the roof that FP64 sparse kernels meet next to the copy
+ * bandwidth. */
+fvs_status fvs_measure_fp64_fma(int64_t iters, double* gflops);
 
 /* Current simulated time and step count. */
 fvs_status fvs_get_time(fvs_solver solver, double* time, int64_t* steps);

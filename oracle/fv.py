@@ -697,6 +697,20 @@ class Oracle:
             ys = yield_strength_mpa(lam)
         return dict(t_f=tf, cooling_rate=cr, sdas=lam, yield_strength=ys)
 
+    def qoi_extremes(self):
+        """The four outputs of Section 5 over the whole domain: total
+        solidification time (the latest solidus crossing; NaN while a metal
+        cell is above the solidus), maximum SDAS, minimum yield strength and
+        maximum grain radius."""
+        q = self.qoi()
+        metal = self.metal
+        done = metal & (self.t_sol >= 0)
+        both = np.isfinite(q["sdas"]) & metal
+        t_total = self.t_sol[metal].max() if done.sum() == metal.sum() else np.nan
+        lam = q["sdas"][both].max() if both.any() else np.nan
+        ys = q["yield_strength"][both].min() if both.any() else np.nan
+        return np.array([t_total, lam, ys, self.grain_radius()[metal].max()])
+
     def run(self, dt, nsteps):
         for _ in range(nsteps):
             self.step(dt)

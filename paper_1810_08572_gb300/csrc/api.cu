@@ -363,24 +363,51 @@ FVS_API fvs_status fvs_get_time(fvs_solver s, double* time, int64_t* steps) {
 }
 
 FVS_API fvs_status fvs_uq_batch(fvs_mesh mesh, const fvs_props* base, int64_t n_samples, const double* inputs,
-                                double dt, int32_t max_steps, int32_t mode, int32_t n_streams, double* qoi_out,
+                                double dt, int32_t max_steps, const fvs_uq_options* opt_in, double* qoi_out,
                                 int64_t* steps_out) {
   if (!mesh || !base || !inputs || !qoi_out || n_samples <= 0 || !(dt > 0) || max_steps <= 0) {
     set_error("fvs_uq_batch: bad argument");
     return FVS_ERR_ARG;
   }
-  if (mode != FVS_UQ_LOCKSTEP && mode != FVS_UQ_STREAMS) {
-    set_error("fvs_uq_batch: mode %d is not available (0 lockstep batch, 1 independent solves)", mode);
+  fvs_uq_options opt{};
+  if (opt_in) opt = *opt_in;
+  const int mode = opt.mode;
+  if (mode != FVS_UQ_LOCKSTEP && mode != FVS_UQ_STREAMS && mode != FVS_UQ_SURROGATE) {
+    set_error("fvs_uq_batch: mode %d is not available (0 lockstep batch, 1 independent solves, 2 surrogate)", mode);
     return FVS_ERR_ARG;
   }
+  if (opt.qoi_kind != FVS_QOI_MEANS && opt.qoi_kind != FVS_QOI_EXTREMES) {
+    set_error("fvs_uq_batch: qoi_kind %d is not available", opt.qoi_kind);
+    return FVS_ERR_ARG;
+  }
+  if (opt.grain_Ds < 0.0 || (opt.grain_Ds > 0.0 && !(opt.grain_kp > 0.0 && opt.grain_kp < 1.0 && opt.grain_r0 >= 0.0))) {
+    set_error("fvs_uq_batch: invalid grain-growth data (0 < kp < 1, D_s >= 0, r0 >= 0)");
+    return FVS_ERR_ARG;
+  }
+  UqSpec spec;
+  spec.qoi_kind = opt.qoi_kind;
+  spec.grain_kp = opt.grain_kp;
+  spec.grain_Ds = opt.grain_Ds;
+  spec.grain_r0 = opt.grain_r0;
+  spec.T_out = opt.T_out;
+  spec.u_out = opt.u_out;
+  spec.p_out = opt.p_out;
+  spec.T_liq.resize(n_samples);
+  const bool shift = opt.liquidus_T0 != 0.0 || opt.liquidus_slope != 0.0;
   for (int64_t i = 0; i < n_samples; ++i) {
     const double C0 = inputs[3 * i + 2];
-    if (!fs_law_valid(base->mat, base->mat.T_liq - 5.0 * (C0 - 4.0))) {
-      set_error("fvs_uq_batch: sample %lld gives a liquidus that does not suit the solid-fraction law "
-                "(below the solidus, or outside T_sol + T_eps < T_liq < T_f for Scheil)", (long long)i);
+    spec.T_liq[i] = shift ? opt.liquidus_T0 + opt.liquidus_slope * C0 : base->mat.T_liq;
+    if (!fs_law_valid(base->mat, spec.T_liq[i])) {
+      set_error("fvs_uq_batch: sample %lld gives a liquidus of %.3f K that does not suit the solid-fraction law "
+                "(below the solidus, or outside T_sol + T_eps < T_liq < T_f for Scheil)", (long long)i,
+                spec.T_liq[i]);
       return FVS_ERR_ARG;
     }
   }
-  if (mode == FVS_UQ_LOCKSTEP) return batch_run(mesh, base, n_samples, inputs, dt, max_steps, qoi_out, steps_out);
-  return uq_batch(mesh, base, n_samples, inputs, dt, max_steps, n_streams, qoi_out, steps_out);
+  if (mode == FVS_UQ_SURROGATE)
+    return uq_surrogate(mesh, base, n_samples, inputs, dt, max_steps, opt, spec, qoi_out, steps_out);
+  if (opt.used_plain)
+    for (int64_t i = 0; i < n_samples; ++i) opt.used_plain[i] = 1;
+  if (mode == FVS_UQ_LOCKSTEP) return batch_run(mesh, base, n_samples, inputs, dt, max_steps, spec, qoi_out, steps_out);
+  return uq_batch(mesh, base, n_samples, inputs, dt, max_steps, opt.n_streams, spec, qoi_out, steps_out);
 }

@@ -10,6 +10,7 @@
 
 #include "batch.cuh"
 #include "fslaw.cuh"
+#include "solver.cuh"
 
 namespace fvs {
 
@@ -1700,6 +1701,86 @@ __global__ void kb_crossings(int64_t Nc, int Sp, const double* Tn, const double*
     if (tsol[e] < 0.0 && a > Ts && b <= Ts) tsol[e] = time + dt * (a - Ts) / (a - b);
   }
 }
+// grain growth (Eq. 24-26) per sample: d(r^2)/dt = lambda_s^2 D_s by the
+// trapezoidal rule between the solid fractions at both ends of the step
+__device__ __forceinline__ double b_grain_lambda(double fs, double kp) {
+  if (!(fs > 0.0 && fs < 1.0)) return 0.0;
+  const double S = 2.0 * (1.0 - pow(1.0 - fs, 1.0 - kp)) / (kp - 1.0);
+  const double pi = 3.14159265358979323846;
+  return -S / (2.0 * sqrt(pi)) + sqrt(fmax(S * S / (4.0 * pi) - S, 0.0));
+}
+__global__ void kb_grain(int64_t Nc, int Sp, const double* fsa, const double* fsb, const uint8_t* run, double kp,
+                         double Ds, double dt, double* r2) {
+  BSAMPLE;
+  if (!run[s]) return;
+  BROW(c, Nc) {
+    const int64_t e = c * Sp + s;
+    const double la = b_grain_lambda(fsa[e], kp), lb = b_grain_lambda(fsb[e], kp);
+    r2[e] += dt * Ds * 0.5 * (la * la + lb * lb);
+  }
+}
+__global__ void kb_fill(size_t n, double v, double* a) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) a[i] = v;
+}
+// the outputs of Section 5 per sample over the whole domain: latest solidus
+// crossing, largest SDAS, smallest yield strength, largest grain radius, and
+// the count of cells still above the solidus
+__global__ void kb_qoi_ext_part(int64_t Nc, int Sp, const double* tliq, const double* tsol, double Ts,
+                                const double* Tliq, const double* r2, double* part) {
+  __shared__ double sh[5][8][33];
+  BSAMPLE;
+  const double Tl = Tliq[s];
+  double a[5] = {-1.0, -1.0, 1e300, 0.0, 0.0};
+  BROW(c, Nc) {
+    const int64_t e = c * Sp + s;
+    if (tsol[e] < 0.0) {
+      a[4] += 1.0;
+    } else {
+      a[0] = fmax(a[0], tsol[e]);
+      if (tliq[e] >= 0.0) {
+        const double lam = 39.4 * pow((Tl - Ts) / (tsol[e] - tliq[e]), -0.317);   // Eq. 22
+        a[1] = fmax(a[1], lam);
+        a[2] = fmin(a[2], 59.0 / sqrt(lam) + 120.3);                            // Eq. 23
+      }
+    }
+    if (r2) a[3] = fmax(a[3], sqrt(r2[e]));
+  }
+  for (int k = 0; k < 5; ++k) sh[k][threadIdx.y][threadIdx.x] = a[k];
+  __syncthreads();
+  if (threadIdx.y == 0) {
+    double u[5] = {-1.0, -1.0, 1e300, 0.0, 0.0};
+    for (int y = 0; y < 8; ++y) {
+      u[0] = fmax(u[0], sh[0][y][threadIdx.x]);
+      u[1] = fmax(u[1], sh[1][y][threadIdx.x]);
+      u[2] = fmin(u[2], sh[2][y][threadIdx.x]);
+      u[3] = fmax(u[3], sh[3][y][threadIdx.x]);
+      u[4] += sh[4][y][threadIdx.x];
+    }
+    for (int k = 0; k < 5; ++k) part[((int64_t)k * Sp + s) * gridDim.x + blockIdx.x] = u[k];
+  }
+}
+__global__ void kb_qoi_ext_final(int nb, int Sp, const double* part, double* out) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= Sp) return;
+  double u[5] = {-1.0, -1.0, 1e300, 0.0, 0.0};
+  for (int b = 0; b < nb; ++b) {
+    u[0] = fmax(u[0], part[((int64_t)0 * Sp + s) * nb + b]);
+    u[1] = fmax(u[1], part[((int64_t)1 * Sp + s) * nb + b]);
+    u[2] = fmin(u[2], part[((int64_t)2 * Sp + s) * nb + b]);
+    u[3] = fmax(u[3], part[((int64_t)3 * Sp + s) * nb + b]);
+    u[4] += part[((int64_t)4 * Sp + s) * nb + b];
+  }
+  for (int k = 0; k < 5; ++k) out[k * Sp + s] = u[k];
+}
+// one sample's field in the caller's cell order: out[comps*to_in[c] + d] =
+// src[(d*Nc + c)*Sp + s]
+__global__ void kb_field_out(int64_t Nc, int Sp, int s, int comps, const int32_t* to_in, const double* src,
+                             double* out) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < Nc; c += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t o = to_in[c];
+    for (int d = 0; d < comps; ++d) out[comps * o + d] = src[((int64_t)d * Nc + c) * Sp + s];
+  }
+}
 // per-sample sums over solidified cells of t_f, cooling rate, SDAS, yield and the count
 __global__ void kb_qoi_part(int64_t Nc, int Sp, const double* tliq, const double* tsol, double Ts, const double* Tliq,
                             double* part) {
@@ -1839,6 +1920,8 @@ static fvs_status batch_step(Batch& B, double dt, int& failures, int (&its)[4]) 
   FVS_LAUNCH_CHECK();
 
   tick(0);
+  const bool flow_on = !B.props.no_flow;
+  if (flow_on) {
   // 2. momentum predictor, three components against the largest right side
   kb_mom_sys<<<gc, blk, 0, st>>>(Nc, Sp, m->W, m->Lu.col, m->Lu.val, m->V, B.fs, mt, dt, B.lm, m->cf, m->cfs,
                                  m->own, m->nei, B.F, B.Fold, B.u, B.uold, B.T, B.mdiag, B.jd, B.mrhs, B.mx);
@@ -1937,6 +2020,7 @@ static fvs_status batch_step(Batch& B, double dt, int& failures, int (&its)[4]) 
   kb_cell_correct<<<gc, blk, 0, st>>>(Nc, Nf, Sp, B.lm, m->cf, B.fcase, B.gradf, B.ustar, dt, mt.rho, B.run, B.u,
                                       B.unew); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
+  }   // flow_on: with natural convection off u, F and p stay zero
 
   tick(5);
   // 5. energy: linearised latent heat, inner solve, enthalpy inversion,
@@ -1984,20 +2068,30 @@ static fvs_status batch_step(Batch& B, double dt, int& failures, int (&its)[4]) 
   // 6. crossing times, then rotate the time levels
   kb_crossings<<<gc, blk, 0, st>>>(Nc, Sp, B.T, B.Tnew, mt.Ts, B.Tliq, B.run, B.time, dt, B.tliq, B.tsol);
   FVS_COUNT_LAUNCH();
+  if (B.grain_Ds > 0.0) {
+    kb_grain<<<gc, blk, 0, st>>>(Nc, Sp, B.fs, B.fsnew, B.run, B.grain_kp, B.grain_Ds, dt, B.r2);
+    FVS_COUNT_LAUNCH();
+  }
   FVS_LAUNCH_CHECK();
   dswap_b(B.Told, B.T);
   dswap_b(B.T, B.Tnew);
   dswap_b(B.fs, B.fsnew);
-  dswap_b(B.uold, B.u);
-  dswap_b(B.u, B.unew);
-  dswap_b(B.Fold, B.F);
-  dswap_b(B.F, B.Fnew);
+  if (flow_on) {
+    dswap_b(B.uold, B.u);
+    dswap_b(B.u, B.unew);
+    dswap_b(B.Fold, B.F);
+    dswap_b(B.F, B.Fnew);
+  }
   B.time += dt;
   return FVS_OK;
 }
 
 fvs_status batch_run(fvs_mesh mesh, const fvs_props* base, int64_t n, const double* inputs, double dt,
-                     int max_steps, double* qoi, int64_t* steps) {
+                     int max_steps, const UqSpec& spec, double* qoi, int64_t* steps) {
+  if (base->n_k > 0) {
+    set_error("the lockstep batch shares one conductivity operator; a k(T) table needs FVS_UQ_STREAMS");
+    return FVS_ERR_ARG;
+  }
   Batch B;
   B.mesh = mesh;
   FVS_CUDA(cudaStreamSynchronize(mesh->stream));
@@ -2017,6 +2111,10 @@ fvs_status batch_run(fvs_mesh mesh, const fvs_props* base, int64_t n, const doub
       B.Sp = (int)((n + 31) / 32 * 32);
       B.tiles = B.Sp / 32;
       B.props = *base;
+      B.props.bc = nullptr;
+      B.props.k_T = B.props.k_val = nullptr;
+      B.grain_kp = spec.grain_kp;
+      B.grain_Ds = spec.grain_Ds;
       B.aopt = AmgOptions();
       B.fp32 = base->precision == FVS_PREC_MIXED;
       const int Sp = B.Sp;
@@ -2027,7 +2125,7 @@ fvs_status batch_run(fvs_mesh mesh, const fvs_props* base, int64_t n, const doub
         if (s < n) {
           tm[s] = inputs[3 * s];
           tw[s] = inputs[3 * s + 1];
-          tl[s] = base->mat.T_liq - 5.0 * (inputs[3 * s + 2] - 4.0);
+          tl[s] = spec.T_liq[s];
           if (!fs_law_valid(base->mat, tl[s])) {
             set_error("sample %d: liquidus %.3f K does not suit the solid-fraction law", s, tl[s]);
             return FVS_ERR_ARG;
@@ -2090,7 +2188,14 @@ fvs_status batch_run(fvs_mesh mesh, const fvs_props* base, int64_t n, const doub
                                                                       B.tliq, B.tsol, B.F, B.Fold);
       FVS_COUNT_LAUNCH();
       FVS_LAUNCH_CHECK();
-      FVS_TRY(batch_amg_setup(B));
+      if (spec.grain_Ds > 0.0) {
+        FVS_TRY(B.r2.alloc(cs + 1));
+        kb_fill<<<stride_grid((int64_t)cs, 256), 256, 0, st>>>(cs, spec.grain_r0 * spec.grain_r0, B.r2);
+        FVS_COUNT_LAUNCH();
+        FVS_LAUNCH_CHECK();
+      }
+      // natural convection off: no pressure system, so no hierarchy
+      if (!base->no_flow) FVS_TRY(batch_amg_setup(B));
       {
         // launch shapes of the shared momentum and energy operators (FP64,
         // every row doing its full work)
@@ -2135,22 +2240,59 @@ fvs_status batch_run(fvs_mesh mesh, const fvs_props* base, int64_t n, const doub
                 "pressure solve %.1f correction %.1f energy %.1f\n", phase[0], phase[1], phase[2], phase[3],
                 phase[4], phase[5], phase[6]);
       B.phase_ms = nullptr;
-      // per-sample means over the solidified cells (Eq. 22-23)
+      // per-sample means over the solidified cells (Eq. 22-23), or the
+      // domain extremes of Section 5
       const int nb = red_blocks(Nc, B.tiles);
+      const bool ext = spec.qoi_kind == FVS_QOI_EXTREMES;
       DBuf<double> out;
       FVS_TRY(out.alloc((size_t)5 * Sp));
-      kb_qoi_part<<<dim3(nb, B.tiles), bblock(), 0, st>>>(Nc, Sp, B.tliq, B.tsol, base->mat.T_sol, B.Tliq, B.part);
-      FVS_COUNT_LAUNCH();
-      kb_qoi_final<<<B.tiles, 32, 0, st>>>(nb, Sp, B.part, out); FVS_COUNT_LAUNCH();
+      if (ext) {
+        kb_qoi_ext_part<<<dim3(nb, B.tiles), bblock(), 0, st>>>(Nc, Sp, B.tliq, B.tsol, base->mat.T_sol, B.Tliq,
+                                                                 spec.grain_Ds > 0.0 ? B.r2.p : nullptr, B.part);
+        FVS_COUNT_LAUNCH();
+        kb_qoi_ext_final<<<B.tiles, 32, 0, st>>>(nb, Sp, B.part, out); FVS_COUNT_LAUNCH();
+      } else {
+        kb_qoi_part<<<dim3(nb, B.tiles), bblock(), 0, st>>>(Nc, Sp, B.tliq, B.tsol, base->mat.T_sol, B.Tliq, B.part);
+        FVS_COUNT_LAUNCH();
+        kb_qoi_final<<<B.tiles, 32, 0, st>>>(nb, Sp, B.part, out); FVS_COUNT_LAUNCH();
+      }
       FVS_LAUNCH_CHECK();
       std::vector<double> h((size_t)5 * Sp);
       FVS_CUDA(cudaMemcpyAsync(h.data(), out.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
       FVS_CUDA(cudaStreamSynchronize(st));
       const double nan = std::nan("");
       for (int64_t i = 0; i < n; ++i) {
-        const double cnt = h[(size_t)4 * Sp + i];
-        for (int q = 0; q < 4; ++q) qoi[4 * i + q] = cnt > 0 ? h[(size_t)q * Sp + i] / cnt : nan;
+        if (ext) {
+          const bool all_solid = h[(size_t)4 * Sp + i] == 0.0;
+          const double tmax = h[i], lmax = h[(size_t)Sp + i];
+          qoi[4 * i + 0] = all_solid && tmax >= 0.0 ? tmax : nan;
+          qoi[4 * i + 1] = lmax >= 0.0 ? lmax : nan;
+          qoi[4 * i + 2] = lmax >= 0.0 ? h[(size_t)2 * Sp + i] : nan;
+          qoi[4 * i + 3] = h[(size_t)3 * Sp + i];
+        } else {
+          const double cnt = h[(size_t)4 * Sp + i];
+          for (int q = 0; q < 4; ++q) qoi[4 * i + q] = cnt > 0 ? h[(size_t)q * Sp + i] / cnt : nan;
+        }
         if (steps) steps[i] = B.steps[i];
+      }
+      // final fields of every sample in the caller's cell order
+      if (spec.T_out || spec.p_out || spec.u_out) {
+        DBuf<double> buf;
+        FVS_TRY(buf.alloc((size_t)3 * Nc + 1));
+        const int g = stride_grid(Nc, 256);
+        struct Out { double* dst; const double* src; int comps; };
+        const Out outs[3] = {{spec.T_out, B.T.p, 1}, {spec.p_out, B.p.p, 1}, {spec.u_out, B.u.p, 3}};
+        for (const Out& o : outs) {
+          if (!o.dst) continue;
+          for (int64_t i = 0; i < n; ++i) {
+            kb_field_out<<<g, 256, 0, st>>>(Nc, Sp, (int)i, o.comps, mesh->cell_in, o.src, buf.p);
+            FVS_COUNT_LAUNCH();
+            FVS_LAUNCH_CHECK();
+            FVS_CUDA(cudaMemcpyAsync(o.dst + i * o.comps * Nc, buf.p, (size_t)o.comps * Nc * sizeof(double),
+                                     cudaMemcpyDeviceToHost, st));
+          }
+        }
+        FVS_CUDA(cudaStreamSynchronize(st));
       }
       if (total_fails > 0) {
         set_error("lockstep batch: %lld sample solves stayed above their tolerance", (long long)total_fails);

@@ -86,6 +86,9 @@ struct Batch {
 
   // per-sample inputs
   DBuf<double> Tliq, Twall, Tmelt;   // [Sp]
+  // grain growth (Eq. 24-26): r^2 [Nc*Sp] when D_s > 0
+  double grain_kp = 0.0, grain_Ds = 0.0;
+  DBuf<double> r2;
   DBuf<uint8_t> run;              // 1 while the sample is being advanced
   std::vector<int64_t> steps;     // steps taken per sample
 
@@ -155,7 +158,8 @@ struct Batch {
   ~Batch();
 };
 
+struct UqSpec;
 fvs_status batch_run(fvs_mesh mesh, const fvs_props* base, int64_t n, const double* inputs, double dt,
-                     int max_steps, double* qoi, int64_t* steps);
+                     int max_steps, const UqSpec& spec, double* qoi, int64_t* steps);
 
 }  // namespace fvs

@@ -344,7 +344,9 @@ __global__ void k_volumes(int64_t Nc, const int32_t* cf, const int8_t* cfs, cons
 // kind 0: velocity (walls and wall vertices carry 0)
 // kind 1: pressure with every cell flowing (walls carry no flux)
 // kind 2: temperature (fixed-temperature walls and their vertices carry the
-//         wall value; adiabatic walls carry no flux)
+//         wall value; adiabatic walls carry no flux; faces with gint > 0 carry
+//         the orthogonal series flux only: metal-mold interfaces, and
+//         convective walls, whose gint includes the film coefficient)
 // ---------------------------------------------------------------------------
 struct RowCtx {
   int64_t Nc, Nf;
@@ -356,7 +358,7 @@ struct RowCtx {
   const double* bc_T;
   const double* vfix;     // temperature: fixed vertex value or NaN if free
   const double* kf;       // temperature: per-face conductivity factor (null: 1)
-  const double* gint;     // temperature: interface conductance (> 0 on metal-mold faces)
+  const double* gint;     // temperature: series conductance (> 0 on metal-mold faces and convective walls)
 };
 
 __device__ __forceinline__ void add_vertex(const RowCtx& x, int kind, int64_t c, int nn, int32_t v, double coef,
@@ -384,6 +386,12 @@ __device__ void assemble_base_row(const RowCtx& x, int kind, int64_t c, double* 
     double sg = (double)x.cfs[s * x.Nc + c];
     const int32_t q = x.nei[f];
     if (kind == 2 && x.gint && x.gint[f] > 0.0) {
+      if (q < 0) {
+        // convective wall: gint (T_amb - T_c), c the owner, no cross terms
+        if (pc >= 0) acc[pc] -= sg * x.gint[f];
+        cst += sg * x.gint[f] * x.bc_T[x.patch[f]];
+        continue;
+      }
       // metal-mold interface: orthogonal flux through the series resistance
       const int p2 = find_sorted(x.nb + c, x.Nc, nn, q);
       const int p1 = find_sorted(x.nb + c, x.Nc, nn, x.own[f]);

@@ -447,6 +447,19 @@ FVS_API fvs_status fvs_surrogate_create(int32_t n_in, int32_t n_hidden, int32_t 
   return FVS_OK;
 }
 
+namespace fvs {
+// input and output widths of a model (the UQ surrogate mode checks them)
+fvs_status surrogate_dims(fvs_surrogate s, int* nin, int* nout) {
+  if (!s) {
+    set_error("NULL surrogate");
+    return FVS_ERR_ARG;
+  }
+  *nin = s->nin;
+  *nout = s->nout;
+  return FVS_OK;
+}
+}  // namespace fvs
+
 FVS_API fvs_status fvs_surrogate_destroy(fvs_surrogate s) {
   if (!s) return FVS_ERR_ARG;
   cudaStream_t st = s->stream;

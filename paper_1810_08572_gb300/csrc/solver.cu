@@ -597,6 +597,19 @@ struct MoldMat {
   MoldMat(int on_, double rho, double cp, double k_, double rhoL, double mrho, double mcp, double mk, double h_)
       : on(on_), rho_cp(rho * cp), k(k_), rho_L(rhoL), mold_rho_cp(mrho * mcp), mold_k(mk), h(h_) {}
 };
+// piecewise-linear k(T) of the metal, constant outside the table (n = 0:
+// the constant k of the material)
+struct KTable {
+  int n = 0;
+  double T[16], k[16];
+};
+__device__ __forceinline__ double k_metal(const KTable& t, double k0, double T) {
+  if (t.n == 0) return k0;
+  if (T <= t.T[0]) return t.k[0];
+  for (int i = 1; i < t.n; ++i)
+    if (T <= t.T[i]) return t.k[i - 1] + (t.k[i] - t.k[i - 1]) * (T - t.T[i - 1]) / (t.T[i] - t.T[i - 1]);
+  return t.k[t.n - 1];
+}
 __global__ void k_cell_materials(int64_t Nc, const uint8_t* zone, MoldMat mm, uint8_t* metal, double* rcp,
                                  double* rL) {
   GS(c, Nc) {
@@ -606,20 +619,33 @@ __global__ void k_cell_materials(int64_t Nc, const uint8_t* zone, MoldMat mm, ui
     rL[c] = me ? mm.rho_L : 0.0;
   }
 }
-// kf: conductivity of the owner's zone; gint > 0 on a face between a metal
-// and a mold cell: A / (d_own/k_own + 1/h + d_nei/k_nei)
-__global__ void k_face_conductance(int64_t Nf, const int32_t* own, const int32_t* nei, const uint8_t* metal,
-                                   const double* A, const double* dof, const double* dnf, MoldMat mm, double* kf,
-                                   double* gint) {
+// kf: conductivity of the face (metal: k at the mean of the two cells' T, or
+// of the cell and a fixed wall value, when k depends on T; the mold: its
+// constant k); gint > 0 on a face between a metal and a mold cell:
+// A / (d_own/k_own + 1/h + d_nei/k_nei), and on a convective wall:
+// A / (d_own/k_own + 1/h_wall).  T may be null when k is constant.
+__global__ void k_face_conductance(int64_t Nf, const int32_t* own, const int32_t* nei, const int32_t* patch,
+                                   const int32_t* bc_type, const double* bc_T, const double* bc_h,
+                                   const uint8_t* metal, const double* A, const double* dof, const double* dnf,
+                                   MoldMat mm, KTable kt, const double* T, double* kf, double* gint) {
   GS(f, Nf) {
     const int32_t o = own[f], q = nei[f];
-    const double ko = metal[o] ? mm.k : mm.mold_k;
-    kf[f] = ko;
-    double g = 0.0;
-    if (q >= 0 && metal[o] != metal[q]) {
-      const double kq = metal[q] ? mm.k : mm.mold_k;
-      g = A[f] / (dof[f] / ko + 1.0 / mm.h + dnf[f] / kq);
+    const double To = T ? T[o] : 0.0;
+    const double ko = metal[o] ? k_metal(kt, mm.k, To) : mm.mold_k;
+    double k = ko, g = 0.0;
+    if (q >= 0) {
+      if (metal[o] != metal[q]) {
+        const double kq = metal[q] ? k_metal(kt, mm.k, T ? T[q] : 0.0) : mm.mold_k;
+        g = A[f] / (dof[f] / ko + 1.0 / mm.h + dnf[f] / kq);
+      } else if (metal[o] && T) {
+        k = k_metal(kt, mm.k, 0.5 * (To + T[q]));
+      }
+    } else {
+      const int32_t b = patch[f];
+      if (bc_type[b] == FVS_BC_CONVECTIVE) g = A[f] / (dof[f] / ko + 1.0 / bc_h[b]);
+      else if (bc_type[b] == FVS_BC_DIRICHLET && metal[o] && T) k = k_metal(kt, mm.k, 0.5 * (To + bc_T[b]));
     }
+    kf[f] = k;
     gint[f] = g;
   }
 }
@@ -704,6 +730,7 @@ fvs_status solver_alloc(fvs_solver s) {
 }
 
 static fvs_status apply_properties(fvs_solver s, const fvs_props* p);
+static fvs_status conduction_operator(fvs_solver s);
 
 fvs_status solver_set_properties(fvs_solver s, const fvs_props* p) {
   s->has_mold = false;   // new properties: every cell metal until fvs_set_mold
@@ -726,9 +753,13 @@ fvs_status solver_set_mold(fvs_solver s, double rho, double cp, double k, double
   s->mold_h = h;
   s->mold_T = T_init;
   std::vector<fvs_patch_bc> bc = s->bc;
+  const std::vector<double> kT(s->k_T, s->k_T + s->n_k), kv(s->k_val, s->k_val + s->n_k);
   fvs_props p = s->props;
   p.bc = bc.data();
   p.n_patches = (int32_t)bc.size();
+  p.n_k = s->n_k;
+  p.k_T = kT.data();
+  p.k_val = kv.data();
   return apply_properties(s, &p);
 }
 
@@ -769,9 +800,37 @@ static fvs_status apply_properties(fvs_solver s, const fvs_props* p) {
               "T_sol + T_eps < T_liq < T_f)", (int)mt.fs_model);
     return FVS_ERR_ARG;
   }
+  for (int i = 0; i < p->n_patches; ++i) {
+    const int t = p->bc[i].type;
+    if (t != FVS_BC_ADIABATIC && t != FVS_BC_DIRICHLET && t != FVS_BC_CONVECTIVE) {
+      set_error("patch %d: unknown wall type %d", i, t);
+      return FVS_ERR_ARG;
+    }
+    if (t == FVS_BC_CONVECTIVE && !(p->bc[i].h > 0)) {
+      set_error("patch %d: a convective wall needs h > 0", i);
+      return FVS_ERR_ARG;
+    }
+  }
+  if (p->n_k < 0 || p->n_k > 16 || (p->n_k > 0 && (!p->k_T || !p->k_val))) {
+    set_error("k(T) table: 0..16 points with both arrays given");
+    return FVS_ERR_ARG;
+  }
+  for (int i = 0; i < p->n_k; ++i) {
+    if (!(p->k_val[i] > 0) || (i > 0 && !(p->k_T[i] > p->k_T[i - 1]))) {
+      set_error("k(T) table: temperatures must increase and conductivities be positive");
+      return FVS_ERR_ARG;
+    }
+  }
   s->props = *p;
   s->bc.assign(p->bc, p->bc + p->n_patches);
   s->props.bc = nullptr;
+  s->n_k = p->n_k;
+  for (int i = 0; i < p->n_k; ++i) {
+    s->k_T[i] = p->k_T[i];
+    s->k_val[i] = p->k_val[i];
+  }
+  s->props.k_T = nullptr;
+  s->props.k_val = nullptr;
   if (s->props.max_krylov_iters <= 0) s->props.max_krylov_iters = 500;
   if (s->props.max_e_iters <= 0) s->props.max_e_iters = 40;
   if (!(s->props.p_rtol > 0)) s->props.p_rtol = 1e-8;
@@ -780,15 +839,20 @@ static fvs_status apply_properties(fvs_solver s, const fvs_props* p) {
   if (!(s->props.e_tol_T > 0)) s->props.e_tol_T = 1e-8;
   const int np = std::max(1, p->n_patches);
   std::vector<int32_t> ht(np, 0);
-  std::vector<double> hT(np, 0.0);
+  std::vector<double> hT(np, 0.0), hh(np, 0.0);
   for (int i = 0; i < p->n_patches; ++i) {
     ht[i] = p->bc[i].type;
     hT[i] = p->bc[i].T;
+    hh[i] = p->bc[i].h;
   }
   FVS_TRY(s->bc_type.alloc(np));
   FVS_TRY(s->bc_T.alloc(np));
+  FVS_TRY(s->bc_h.alloc(np));
   FVS_CUDA(cudaMemcpyAsync(s->bc_type.p, ht.data(), np * sizeof(int32_t), cudaMemcpyHostToDevice, s->stream));
   FVS_CUDA(cudaMemcpyAsync(s->bc_T.p, hT.data(), np * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  FVS_CUDA(cudaMemcpyAsync(s->bc_h.p, hh.data(), np * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  // the host vectors must outlive the copies
+  FVS_CUDA(cudaStreamSynchronize(s->stream));
   // materials per cell (zones count only with a mold material) and the
   // conductive operator: k_f times the face gradient, the series flux on
   // metal-mold faces
@@ -798,19 +862,36 @@ static fvs_status apply_properties(fvs_solver s, const fvs_props* p) {
                    s->mold_h};
   k_cell_materials<<<stride_grid(m->Nc, 256), 256, 0, s->stream>>>(m->Nc, m->zone, mm, s->metal, s->rcp, s->rL);
   FVS_COUNT_LAUNCH();
-  k_face_conductance<<<stride_grid(m->Nf, 256), 256, 0, s->stream>>>(m->Nf, m->own, m->nei, s->metal, m->A, m->dof,
-                                                                     m->dnf, mm, s->kface, s->gint);
+  s->have_props = true;
+  FVS_TRY(solver_set_state(s, nullptr, nullptr, 0));
+  return conduction_operator(s);
+}
+
+// conductive operator L (face conductivities inside; with k(T) those of the
+// current T) and Ke = -1/2 L with the same pattern
+static fvs_status conduction_operator(fvs_solver s) {
+  fvs_mesh m = s->mesh;
+  const fvs_material& mt = s->props.mat;
+  const MoldMat mm{s->has_mold ? 1 : 0, mt.rho, mt.cp, mt.k, mt.rho * mt.latent, s->mold_rho, s->mold_cp, s->mold_k,
+                   s->mold_h};
+  KTable kt;
+  kt.n = s->n_k;
+  for (int i = 0; i < s->n_k; ++i) {
+    kt.T[i] = s->k_T[i];
+    kt.k[i] = s->k_val[i];
+  }
+  k_face_conductance<<<stride_grid(m->Nf, 256), 256, 0, s->stream>>>(
+      m->Nf, m->own, m->nei, m->patch, s->bc_type, s->bc_T, s->bc_h, s->metal, m->A, m->dof, m->dnf, mm, kt,
+      s->n_k > 0 ? s->T.p : nullptr, s->kface, s->gint);
   FVS_COUNT_LAUNCH();
   FVS_TRY(assemble_temperature_operator(m, s->bc_type, s->bc_T, s->LT, s->lT, s->stream, s->kface, s->gint));
-  // Ke = -1/2 L (conductivities inside L) with the same pattern
   FVS_TRY(s->Ke.alloc(m->Nc, m->W));
   k_copy_i<<<stride_grid((int64_t)m->Nc * m->W, 256), 256, 0, s->stream>>>((int64_t)m->Nc * m->W, s->LT.col,
                                                                             s->Ke.col); FVS_COUNT_LAUNCH();
   k_scale_ell<<<stride_grid(m->Nc, 256), 256, 0, s->stream>>>(m->Nc, m->W, -0.5, s->LT.val, s->LT.diag,
                                                              s->Ke.val, s->Ke.diag); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
-  s->have_props = true;
-  return solver_set_state(s, nullptr, nullptr, 0);
+  return FVS_OK;
 }
 
 fvs_status solver_set_state(fvs_solver s, const double* T, const double* u, int on_device) {
@@ -1172,6 +1253,15 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
   int64_t na = s->nact;
   S.n_active = s->nlm;
 
+  // natural convection off: velocity, fluxes and pressure stay zero (they
+  // were zeroed with the state), only the energy equation runs
+  const bool flow_on = !s->props.no_flow;
+  if (!flow_on) {
+    na = 0;
+    FVS_TRY(s->u.zero(st));       // a velocity given to fvs_set_state does not move anything
+    FVS_TRY(s->uold.zero(st));
+  }
+
   // 2. momentum predictor
   FVS_TRY(s->M.alloc(na, m->W));
   FVS_TRY(s->mrhs.alloc(3 * na + 1));
@@ -1208,6 +1298,7 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
       }
     }
   }
+  if (flow_on) {
   k_scatter3<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, na, s->map, s->lm, s->mx, s->ustar); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
 
@@ -1278,6 +1369,10 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
   k_cell_correct<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, Nf, s->lm, m->cf, s->fcase, s->gradf, s->ustar, dt,
                                                        mt.rho, s->unew); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
+  }   // flow_on
+
+  // conductivities of T^n when k depends on T (both Crank-Nicolson halves)
+  if (s->n_k > 0) FVS_TRY(conduction_operator(s));
 
   // 5. energy: linearised latent heat, inner solve, enthalpy inversion
   k_energy_base<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, m->W, m->cf, m->cfs, m->own, m->nei, s->F, s->Fold, s->T,
@@ -1347,10 +1442,12 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
   dswap(s->Told, s->T);     // Told <- T^n
   dswap(s->T, s->Tnew);     // T <- T^{n+1}
   dswap(s->fs, s->fsnew);
-  dswap(s->uold, s->u);     // uold <- u^n
-  dswap(s->u, s->unew);     // u <- u^{n+1}
-  dswap(s->Fold, s->F);     // Fold <- F^n
-  dswap(s->F, s->Fnew);     // F <- F^{n+1}
+  if (flow_on) {
+    dswap(s->uold, s->u);     // uold <- u^n
+    dswap(s->u, s->unew);     // u <- u^{n+1}
+    dswap(s->Fold, s->F);     // Fold <- F^n
+    dswap(s->F, s->Fnew);     // F <- F^{n+1}
+  }
   FVS_CUDA(cudaStreamSynchronize(st));
   s->time += dt;
   s->nstep += 1;

@@ -66,7 +66,10 @@ struct fvs_solver_s {
 
   // wall data and the energy operator (-k/2 times the unit operator)
   fvs::DBuf<int32_t> bc_type;
-  fvs::DBuf<double> bc_T;
+  fvs::DBuf<double> bc_T, bc_h;
+  // k(T) of the metal: piecewise linear table (n_k = 0: constant mat.k)
+  int n_k = 0;
+  double k_T[16] = {0}, k_val[16] = {0};
   fvs::DBuf<uint8_t> metal;        // [Nc] 1 metal, 0 mold
   fvs::DBuf<double> rcp, rL;       // [Nc] rho cp and rho L (0 in the mold)
   fvs::DBuf<double> kface, gint;   // [Nf] face conductivity, interface conductance
@@ -117,6 +120,21 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* st);
 fvs_status solver_pressure_solve(fvs_solver s, const double* rhs, double* p_out, double rtol, int* iters,
                                  double* relres);
 fvs_status solver_query(fvs_solver s, fvs_field f, double* dst, int64_t len, int on_device);
+// What a plain UQ run computes besides the solves: the samples' liquidus
+// temperatures, which outputs, grain growth, and the optional final fields
+struct UqSpec {
+  std::vector<double> T_liq;            // per sample
+  int qoi_kind = FVS_QOI_MEANS;
+  double grain_kp = 0.0, grain_Ds = 0.0, grain_r0 = 0.0;
+  double* T_out = nullptr;              // host [n*Nc], input numbering (nullable)
+  double* u_out = nullptr;              // host [n*Nc*3]
+  double* p_out = nullptr;              // host [n*Nc]
+};
 fvs_status uq_batch(fvs_mesh mesh, const fvs_props* base, int64_t n, const double* inputs, double dt,
-                    int max_steps, int n_streams, double* qoi, int64_t* steps);
+                    int max_steps, int n_streams, const UqSpec& spec, double* qoi, int64_t* steps);
+fvs_status surrogate_dims(fvs_surrogate s, int* nin, int* nout);
+// FVS_UQ_SURROGATE: the ensemble answers the samples it can, plain solves
+// (lockstep or streams per opt->plain_mode) the rest
+fvs_status uq_surrogate(fvs_mesh mesh, const fvs_props* base, int64_t n, const double* inputs, double dt,
+                        int max_steps, const fvs_uq_options& opt, const UqSpec& spec, double* qoi, int64_t* steps);
 }  // namespace fvs

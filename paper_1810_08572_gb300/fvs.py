@@ -27,7 +27,7 @@ FVS_OK, FVS_ERR_ARG, FVS_ERR_MESH, FVS_ERR_CUDA, FVS_ERR_NOMEM, FVS_ERR_NOT_CONV
     FVS_ERR_TIMEOUT, FVS_ERR_STATE = range(8)
 STATUS = {0: "FVS_OK", 1: "FVS_ERR_ARG", 2: "FVS_ERR_MESH", 3: "FVS_ERR_CUDA", 4: "FVS_ERR_NOMEM",
           5: "FVS_ERR_NOT_CONVERGED", 6: "FVS_ERR_TIMEOUT", 7: "FVS_ERR_STATE"}
-FVS_BC_ADIABATIC, FVS_BC_DIRICHLET = 0, 1
+FVS_BC_ADIABATIC, FVS_BC_DIRICHLET, FVS_BC_CONVECTIVE = 0, 1, 2
 FVS_PREC_FP64, FVS_PREC_MIXED = 0, 1
 FVS_PSOLVER_AMG, FVS_PSOLVER_JACOBI = 0, 1
 FIELDS = dict(T=0, FS=1, U=2, P=3, FLUX=4, TAG=5, QOI=6, USTAR=7, CROSS=8, FACE_CASE=9, GRAIN=10)
@@ -48,14 +48,16 @@ class fvs_material(C.Structure):
 
 
 class fvs_patch_bc(C.Structure):
-    _fields_ = [("type", C.c_int32), ("T", C.c_double)]
+    _fields_ = [("type", C.c_int32), ("T", C.c_double), ("h", C.c_double)]
 
 
 class fvs_props(C.Structure):
     _fields_ = [("mat", fvs_material), ("n_patches", C.c_int32), ("bc", C.POINTER(fvs_patch_bc)),
                 ("T_init", C.c_double), ("p_rtol", C.c_double), ("mom_rtol", C.c_double),
                 ("e_rtol", C.c_double), ("e_tol_T", C.c_double), ("max_e_iters", C.c_int32),
-                ("max_krylov_iters", C.c_int32), ("precision", C.c_int32), ("p_solver", C.c_int32)]
+                ("max_krylov_iters", C.c_int32), ("precision", C.c_int32), ("p_solver", C.c_int32),
+                ("no_flow", C.c_int32), ("n_k", C.c_int32), ("k_T", C.POINTER(C.c_double)),
+                ("k_val", C.POINTER(C.c_double))]
 
 
 class fvs_step_stats(C.Structure):
@@ -76,6 +78,16 @@ class fvs_mesh_info(C.Structure):
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class fvs_uq_options(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("n_streams", C.c_int32), ("qoi_kind", C.c_int32),
+                ("liquidus_T0", C.c_double), ("liquidus_slope", C.c_double), ("grain_kp", C.c_double),
+                ("grain_Ds", C.c_double), ("grain_r0", C.c_double), ("n_models", C.c_int32),
+                ("models", C.POINTER(C.c_void_p)), ("box_lo", C.POINTER(C.c_double)),
+                ("box_hi", C.POINTER(C.c_double)), ("max_spread", C.c_double), ("plain_mode", C.c_int32),
+                ("used_plain", C.POINTER(C.c_int32)), ("T_out", C.POINTER(C.c_double)),
+                ("u_out", C.POINTER(C.c_double)), ("p_out", C.POINTER(C.c_double))]
 
 
 class fvs_kernel_time(C.Structure):
@@ -115,9 +127,19 @@ _SIGS = {
     "fvs_surrogate_train": ([_P, _P, _P, C.c_int64, C.c_int32, C.c_double, C.POINTER(C.c_double)], C.c_int),
     "fvs_surrogate_predict": ([_P, _P, _P, C.c_int64, C.c_int], C.c_int),
     "fvs_profile_enable": ([_P, C.c_int], C.c_int),
-    "fvs_uq_batch": ([_P, C.POINTER(fvs_props), C.c_int64, _P, C.c_double, C.c_int32, C.c_int32, C.c_int32, _P,
-                      _P], C.c_int),
+    "fvs_uq_batch": ([_P, C.POINTER(fvs_props), C.c_int64, _P, C.c_double, C.c_int32, C.POINTER(fvs_uq_options),
+                      _P, _P], C.c_int),
     "fvs_profile_read": ([_P, C.POINTER(fvs_kernel_time), C.c_int32, C.POINTER(C.c_int32)], C.c_int),
+    "fvs_measure_fp64_fma": ([C.c_int64, C.POINTER(C.c_double)], C.c_int),
+    "fvs_pce_create": ([C.c_int32, _P, _P, _P, C.c_int32, C.c_int32, _P, C.POINTER(_P)], C.c_int),
+    "fvs_pce_destroy": ([_P], C.c_int),
+    "fvs_pce_num_terms": ([_P], C.c_int64),
+    "fvs_pce_multi_indices": ([_P, _P, C.c_int64], C.c_int),
+    "fvs_pce_nodes": ([_P, C.c_int32, C.c_int32, _P, C.c_int64, C.POINTER(C.c_int64)], C.c_int),
+    "fvs_pce_fit": ([_P, _P, _P, C.c_int64, C.POINTER(C.c_double)], C.c_int),
+    "fvs_pce_eval": ([_P, _P, _P, C.c_int64, C.c_int], C.c_int),
+    "fvs_pce_coefficients": ([_P, _P, C.c_int64], C.c_int),
+    "fvs_pce_sensitivity": ([_P, _P, _P, _P, _P], C.c_int),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -166,12 +188,17 @@ def make_props(p):
                        int(m.get("fs_model", 0)), float(m.get("kp", 0.0)), float(m.get("T_f", 0.0)),
                        float(m.get("T_eps", 0.0)))
     walls = p["walls"]
-    bcs = (fvs_patch_bc * max(1, len(walls)))(*[fvs_patch_bc(int(t), float(T)) for t, T in walls])
+    bcs = (fvs_patch_bc * max(1, len(walls)))(*[fvs_patch_bc(int(w[0]), float(w[1]),
+                                                              float(w[2]) if len(w) > 2 else 0.0) for w in walls])
+    kt = p.get("k_table") or []
+    kT = (C.c_double * max(1, len(kt)))(*[float(a) for a, _ in kt])
+    kv = (C.c_double * max(1, len(kt)))(*[float(b) for _, b in kt])
     props = fvs_props(mat, len(walls), C.cast(bcs, C.POINTER(fvs_patch_bc)), p["T_init"], p["p_rtol"],
                       p.get("mom_rtol", 1e-10), p.get("e_rtol", 1e-10), p.get("e_tol_T", 1e-8),
                       int(p.get("max_e_iters", 40)), int(p.get("max_krylov_iters", 500)),
-                      int(p.get("precision", 0)), int(p.get("p_solver", 0)))
-    props._keep = bcs
+                      int(p.get("precision", 0)), int(p.get("p_solver", 0)), int(bool(p.get("no_flow", False))),
+                      len(kt), C.cast(kT, C.POINTER(C.c_double)), C.cast(kv, C.POINTER(C.c_double)))
+    props._keep = (bcs, kT, kv)
     return props
 
 
@@ -216,21 +243,68 @@ class Mesh:
             pass
 
 
-UQ_LOCKSTEP, UQ_STREAMS = 0, 1
+UQ_LOCKSTEP, UQ_STREAMS, UQ_SURROGATE = 0, 1, 2
+QOI_MEANS, QOI_EXTREMES = 0, 1
+# liquidus line of the synthetic cavity workloads: 913 K at 4 wt%, -5 K per wt%
+CAVITY_LIQUIDUS = (933.0, -5.0)
 
 
-def uq_batch(mesh, props, inputs, dt, max_steps, n_streams=0, mode=UQ_LOCKSTEP):
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def uq_batch(mesh, props, inputs, dt, max_steps, n_streams=0, mode=UQ_LOCKSTEP, **kw):
     """Plain batched UQ solves: inputs [S, 3] (T_melt, T_wall, C0) -> (qoi [S, 4], steps [S]).
     mode UQ_LOCKSTEP advances all samples together (one launch per phase);
-    UQ_STREAMS runs independent solves on n_streams CUDA streams."""
+    UQ_STREAMS runs independent solves on n_streams CUDA streams.  Other
+    options as in uq_run."""
+    q, st, _ = uq_run(mesh, props, inputs, dt, max_steps, n_streams=n_streams, mode=mode, **kw)
+    return q, st
+
+
+def uq_run(mesh, props, inputs, dt, max_steps, n_streams=0, mode=UQ_LOCKSTEP, qoi_kind=QOI_MEANS,
+           liquidus=CAVITY_LIQUIDUS, grain=None, models=None, box=None, max_spread=0.0,
+           plain_mode=UQ_LOCKSTEP, fields=False, allow_not_converged=False):
+    """fvs_uq_batch: inputs [S, 3] (T_melt, T_wall, C0) -> (qoi [S, 4], steps [S],
+    extras), extras holding used_plain and, with fields=True, the final T, U
+    and P of every plainly solved sample.  liquidus = (T at C0 = 0, slope in K per
+    wt%) or None to keep the material's; grain = dict(kp, D_s, r0); models:
+    Surrogate objects for mode UQ_SURROGATE, box = (lo[3], hi[3])."""
     inputs = np.ascontiguousarray(inputs, dtype=np.float64)
     n = len(inputs)
+    nc = mesh.n_cells
     qoi = np.empty((n, 4), dtype=np.float64)
     steps = np.empty(n, dtype=np.int64)
+    used = np.empty(n, dtype=np.int32)
+    opt = fvs_uq_options()
+    opt.mode, opt.n_streams, opt.qoi_kind = int(mode), int(n_streams), int(qoi_kind)
+    if liquidus is not None:
+        opt.liquidus_T0, opt.liquidus_slope = float(liquidus[0]), float(liquidus[1])
+    if grain is not None:
+        opt.grain_kp, opt.grain_Ds, opt.grain_r0 = float(grain["kp"]), float(grain["D_s"]), float(grain["r0"])
+    keep = []
+    if models:
+        hs = (C.c_void_p * len(models))(*[m.h.value for m in models])
+        lo = np.ascontiguousarray(box[0], dtype=np.float64)
+        hi = np.ascontiguousarray(box[1], dtype=np.float64)
+        keep += [hs, lo, hi]
+        opt.n_models = len(models)
+        opt.models = C.cast(hs, C.POINTER(C.c_void_p))
+        opt.box_lo, opt.box_hi = _dptr(lo), _dptr(hi)
+        opt.max_spread = float(max_spread)
+        opt.plain_mode = int(plain_mode)
+    opt.used_plain = used.ctypes.data_as(C.POINTER(C.c_int32))
+    extra = dict(used_plain=used)
+    if fields:
+        extra.update(T=np.full((n, nc), np.nan), U=np.full((n, nc, 3), np.nan), P=np.full((n, nc), np.nan))
+        opt.T_out, opt.u_out, opt.p_out = _dptr(extra["T"]), _dptr(extra["U"]), _dptr(extra["P"])
     pr = make_props(props)
-    check(fvs_uq_batch(mesh.h, C.byref(pr), n, _ptr(inputs), float(dt), int(max_steps), int(mode), int(n_streams),
-                       _ptr(qoi), _ptr(steps)), "fvs_uq_batch")
-    return qoi, steps
+    r = fvs_uq_batch(mesh.h, C.byref(pr), n, _ptr(inputs), float(dt), int(max_steps), C.byref(opt), _ptr(qoi),
+                     _ptr(steps))
+    if r != FVS_OK and not (allow_not_converged and r == FVS_ERR_NOT_CONVERGED):
+        raise FvsError(r, "fvs_uq_batch")
+    extra["used_plain"] = used.astype(bool)
+    return qoi, steps, extra
 
 
 class Surrogate:
@@ -289,6 +363,86 @@ class Surrogate:
     def close(self):
         if self.h:
             fvs_surrogate_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+PCE_NORMAL, PCE_UNIFORM = 0, 1
+
+
+def measure_fp64_fma(iters=1 << 16):
+    """Measured FP64 FMA rate (GFLOP/s) of the current GPU."""
+    g = C.c_double()
+    check(fvs_measure_fp64_fma(int(iters), C.byref(g)), "fvs_measure_fp64_fma")
+    return g.value
+
+
+class Pce:
+    """Owns an fvs_pce handle: polynomial chaos surrogate (Eq. 27-28)."""
+
+    def __init__(self, families, params, degree, n_out, stream=None):
+        fam = np.ascontiguousarray(families, dtype=np.int32)
+        p1 = np.ascontiguousarray([a for a, _ in params], dtype=np.float64)
+        p2 = np.ascontiguousarray([b for _, b in params], dtype=np.float64)
+        h = C.c_void_p()
+        check(fvs_pce_create(len(fam), _ptr(fam), _ptr(p1), _ptr(p2), int(degree), int(n_out), _stream_ptr(stream),
+                             C.byref(h)), "fvs_pce_create")
+        self.h = h
+        self.d, self.n_out = len(fam), int(n_out)
+
+    def num_terms(self):
+        return int(fvs_pce_num_terms(self.h))
+
+    def multi_indices(self):
+        a = np.empty(self.num_terms() * self.d, dtype=np.int32)
+        check(fvs_pce_multi_indices(self.h, _ptr(a), len(a)), "fvs_pce_multi_indices")
+        return a.reshape(-1, self.d)
+
+    def nodes(self, level, sparse=False):
+        n = C.c_int64()
+        check(fvs_pce_nodes(self.h, int(level), int(sparse), None, 0, C.byref(n)), "fvs_pce_nodes")
+        X = np.empty((n.value, self.d), dtype=np.float64)
+        check(fvs_pce_nodes(self.h, int(level), int(sparse), _ptr(X), n.value, C.byref(n)), "fvs_pce_nodes")
+        return X
+
+    def fit(self, X, Y):
+        X = np.ascontiguousarray(X, dtype=np.float64)
+        Y = np.ascontiguousarray(np.asarray(Y, dtype=np.float64).reshape(len(X), -1))
+        r = C.c_double()
+        check(fvs_pce_fit(self.h, _ptr(X), _ptr(Y), len(X), C.byref(r)), "fvs_pce_fit")
+        return r.value
+
+    def __call__(self, X, out=None):
+        if isinstance(X, np.ndarray):
+            X = np.ascontiguousarray(X, dtype=np.float64)
+            Y = np.empty((len(X), self.n_out), dtype=np.float64)
+            check(fvs_pce_eval(self.h, _ptr(X), _ptr(Y), len(X), 0), "fvs_pce_eval")
+            return Y
+        check(fvs_pce_eval(self.h, _ptr(X), _ptr(out), X.shape[0], 1), "fvs_pce_eval")
+        return out
+
+    def coefficients(self):
+        c = np.empty(self.num_terms() * self.n_out, dtype=np.float64)
+        check(fvs_pce_coefficients(self.h, _ptr(c), len(c)), "fvs_pce_coefficients")
+        return c.reshape(-1, self.n_out)
+
+    def sensitivity(self):
+        """(mean [n_out], var [n_out], total Sobol [n_out, d], first-order [n_out, d])."""
+        m = np.empty(self.n_out)
+        v = np.empty(self.n_out)
+        t = np.empty((self.n_out, self.d))
+        f = np.empty((self.n_out, self.d))
+        check(fvs_pce_sensitivity(self.h, _ptr(m), _ptr(v), _ptr(t), _ptr(f)), "fvs_pce_sensitivity")
+        return m, v, t, f
+
+    def close(self):
+        if self.h:
+            fvs_pce_destroy(self.h)
             self.h = None
 
     def __del__(self):

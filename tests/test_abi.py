@@ -43,7 +43,7 @@ def test_struct_layouts_match_header(lib, root, tmp_path):
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         pytest.skip("no C compiler")
-    structs = ["fvs_material", "fvs_patch_bc", "fvs_props", "fvs_step_stats", "fvs_mesh_info"]
+    structs = ["fvs_material", "fvs_patch_bc", "fvs_props", "fvs_step_stats", "fvs_mesh_info", "fvs_uq_options"]
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "fvs.h"', "int main(void) {"]
     for name in structs:
         lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')

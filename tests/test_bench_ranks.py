@@ -64,3 +64,4 @@ def test_reference_arm_line():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "active cell-steps/s"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+    assert line["steps"] == 1 and line["cpu_baseline"]["steps"] == 1 and line["cpu_baseline"]["host"]["nproc"] >= 1
