@@ -413,8 +413,19 @@ def run_shrink(fvs, c, args, stream, torch):
             ev1.record(stream)
             torch.cuda.synchronize()
             ms = ev0.elapsed_time(ev1)
+            # where the step goes: two more steps with per-kernel event timing,
+            # the sparse kernels summed by the system they work on
+            S.profile(True)
+            for _ in range(2):
+                S.step(c["dt"], 1, allow_not_converged=True)
+            by = {}
+            for r in S.profile_read():
+                sysname = r["name"].split("@")[-1]
+                by[sysname] = by.get(sysname, 0.0) + r["total_ms"] / 2.0
+            S.profile(False)
             row[prec] = dict(value=round(act / (ms / 1e3), 1), ms_per_step=round(ms / args.shrink_steps, 3),
-                             mean_active=round(act / args.shrink_steps), p_its=round(float(np.mean(p_its)), 1))
+                             mean_active=round(act / args.shrink_steps), p_its=round(float(np.mean(p_its)), 1),
+                             sparse_kernel_ms_per_step={k: round(v, 2) for k, v in sorted(by.items())})
             S.close()
         out.append(row)
     mesh.close()

@@ -119,8 +119,24 @@ __global__ void kb_final2(int nb, int Sp, const double* part, double* sc, int sl
 }
 
 // ---------------------------------------------------------------------------
-// operators: y = A x for (row, sample)
+// operators: y = A x for (row, sample).  The neighbour values come from a
+// gather functor: straight from x in global memory, or from the block's
+// staged copy in shared memory (XStage).
 // ---------------------------------------------------------------------------
+template <typename V>
+struct GatherGlobal {
+  const V* x;
+  const int32_t* col;
+  int Sp, s;
+  __device__ __forceinline__ V operator()(int64_t q) const { return x[(int64_t)col[q] * Sp + s]; }
+};
+template <typename V>
+struct GatherStaged {
+  const V* xs;          // [u][32] in shared memory
+  const uint8_t* li;
+  int lane;
+  __device__ __forceinline__ V operator()(int64_t q) const { return xs[(int)li[q] * 32 + lane]; }
+};
 // shared values: y = dg x + [mask] sum_k val[k][i] x[col]   (mask: solid rows keep dg x only)
 struct OpShared {
   int64_t n;
@@ -129,13 +145,14 @@ struct OpShared {
   const double* val;
   const double* dg;       // per (i, s), may be null
   const uint8_t* mask;    // per (i, s), may be null
-  __device__ __forceinline__ double row(int64_t i, int s, int Sp, const double* x) const {
+  template <class G>
+  __device__ __forceinline__ double row(int64_t i, int s, int Sp, const double* x, const G& g) const {
     const int64_t e = i * Sp + s;
     double acc = dg ? dg[e] * x[e] : 0.0;
     if (!mask || mask[e]) {
       for (int k = 0; k < w; ++k) {
         const int64_t q = (int64_t)k * n + i;
-        acc = fma(val[q], x[(int64_t)col[q] * Sp + s], acc);
+        acc = fma(val[q], g(q), acc);
       }
     }
     return acc;
@@ -152,7 +169,8 @@ struct OpPpe0T {
   const V* base;
   const int32_t* ovr;
   const V* mval;
-  __device__ __forceinline__ V row(int64_t i, int s, int Sp, const V* x) const {
+  template <class G>
+  __device__ __forceinline__ V row(int64_t i, int s, int Sp, const V* x, const G& g) const {
     const int64_t e = i * Sp + s;
     const int32_t o = ovr[e];
     if (o == -2) return x[e];
@@ -160,11 +178,11 @@ struct OpPpe0T {
     if (o < 0) {
       for (int k = 0; k < w; ++k) {
         const int64_t q = (int64_t)k * n + i;
-        acc = fma(base[q], x[(int64_t)col[q] * Sp + s], acc);
+        acc = fma(base[q], g(q), acc);
       }
     } else {
       const V* mv = mval + (int64_t)o * w;
-      for (int k = 0; k < w; ++k) acc = fma(mv[k], x[(int64_t)col[(int64_t)k * n + i] * Sp + s], acc);
+      for (int k = 0; k < w; ++k) acc = fma(mv[k], g((int64_t)k * n + i), acc);
     }
     return acc;
   }
@@ -178,12 +196,13 @@ struct OpCoarseT {
   const int32_t* col;
   const V* val;
   const int32_t* rlen;   // stored entries per row (padding after), shared by all samples
-  __device__ __forceinline__ V row(int64_t i, int s, int Sp, const V* x) const {
+  template <class G>
+  __device__ __forceinline__ V row(int64_t i, int s, int Sp, const V* x, const G& g) const {
     V acc = 0;
     const int len = rlen ? rlen[i] : w;
     for (int k = 0; k < len; ++k) {
       const int64_t q = (int64_t)k * n + i;
-      acc = fma(val[q * Sp + s], x[(int64_t)col[q] * Sp + s], acc);
+      acc = fma(val[q * Sp + s], g(q), acc);
     }
     return acc;
   }
@@ -194,9 +213,10 @@ using OpCoarse = OpCoarseT<double>;
 template <class Op, typename V>
 __global__ void kb_apply(Op op, int Sp, const V* x, const V* b, V* y, int mode, const V* dinv, V omega) {
   BSAMPLE;
+  const GatherGlobal<V> g{x, op.col, Sp, s};
   BROW(i, op.n) {
     const int64_t e = i * Sp + s;
-    const V ax = op.row(i, s, Sp, x);
+    const V ax = op.row(i, s, Sp, x, g);
     V out;
     if (mode == 0) out = ax;
     else if (mode == 1) out = b[e] - ax;
@@ -204,6 +224,31 @@ __global__ void kb_apply(Op op, int Sp, const V* x, const V* b, V* y, int mode, 
     y[e] = out;
   }
 }
+// the same with x staged: block (32 samples, R rows) handles rows
+// [R blockIdx.x, R blockIdx.x + R) and first loads x of the block's column
+// list into shared memory (dynamic, umax x 32 values)
+template <class Op, typename V>
+__global__ void kb_apply_st(Op op, int Sp, const V* x, const V* b, V* y, int mode, const V* dinv, V omega,
+                            const int32_t* uptr, const int32_t* ucol, const uint8_t* li) {
+  extern __shared__ __align__(16) unsigned char kb_smem[];
+  V* xs = reinterpret_cast<V*>(kb_smem);
+  BSAMPLE;
+  const int64_t blk = blockIdx.x;
+  const int32_t u0 = uptr[blk], nu = uptr[blk + 1] - u0;
+  for (int u = threadIdx.y; u < nu; u += blockDim.y) xs[u * 32 + threadIdx.x] = x[(int64_t)ucol[u0 + u] * Sp + s];
+  __syncthreads();
+  const int64_t i = blk * blockDim.y + threadIdx.y;
+  if (i >= op.n) return;
+  const GatherStaged<V> g{xs, li, (int)threadIdx.x};
+  const int64_t e = i * Sp + s;
+  const V ax = op.row(i, s, Sp, x, g);
+  V out;
+  if (mode == 0) out = ax;
+  else if (mode == 1) out = b[e] - ax;
+  else out = x[e] + omega * dinv[e] * (b[e] - ax);
+  y[e] = out;
+}
+
 
 // ---------------------------------------------------------------------------
 // Krylov vector updates with per-sample scalars; samples with act = 0 keep
@@ -573,10 +618,28 @@ static fvs_status read_counts(Batch& B, int* h, int n) {
   FVS_CUDA(cudaStreamSynchronize(B.stream));
   return FVS_OK;
 }
+// the staged kernel fits when a block's column list (x of 32 samples)
+// stays within the default 48 KB of dynamic shared memory
+template <typename V>
+static bool stage_fits(const XStage* st) {
+  return st && st->R > 0 && (size_t)st->umax * 32 * sizeof(V) <= 48 * 1024;
+}
+template <class Op, typename V>
+static void launch_apply(Batch& B, const Op& op, const V* x, const V* b, V* y, int mode, const V* dinv, V omega,
+                         const BShape* sh) {
+  const XStage* st = sh ? sh->stage : nullptr;
+  if (stage_fits<V>(st)) {
+    kb_apply_st<Op, V><<<dim3((unsigned)st->nblk, (unsigned)B.tiles, 1), dim3(32, st->R, 1),
+                         (size_t)st->umax * 32 * sizeof(V), B.stream>>>(op, B.Sp, x, b, y, mode, dinv, omega,
+                                                                        st->uptr, st->ucol, st->li);
+  } else {
+    kb_apply<Op, V><<<sgrid(op.n, B.tiles, sh), sblock(sh), 0, B.stream>>>(op, B.Sp, x, b, y, mode, dinv, omega);
+  }
+}
 template <class Op>
 static fvs_status bapply(Batch& B, const Op& op, const double* x, const double* b, double* y, int mode,
                          const double* dinv = nullptr, double omega = 0.0, const BShape* sh = nullptr) {
-  kb_apply<Op, double><<<sgrid(op.n, B.tiles, sh), sblock(sh), 0, B.stream>>>(op, B.Sp, x, b, y, mode, dinv, omega);
+  launch_apply<Op, double>(B, op, x, b, y, mode, dinv, omega, sh);
   FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   return FVS_OK;
@@ -584,7 +647,7 @@ static fvs_status bapply(Batch& B, const Op& op, const double* x, const double* 
 template <class Op>
 static fvs_status bapplyf(Batch& B, const Op& op, const float* x, const float* b, float* y, int mode,
                           const float* dinv = nullptr, float omega = 0.0f, const BShape* sh = nullptr) {
-  kb_apply<Op, float><<<sgrid(op.n, B.tiles, sh), sblock(sh), 0, B.stream>>>(op, B.Sp, x, b, y, mode, dinv, omega);
+  launch_apply<Op, float>(B, op, x, b, y, mode, dinv, omega, sh);
   FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   return FVS_OK;
@@ -597,29 +660,29 @@ static fvs_status bapplyf(Batch& B, const Op& op, const float* x, const float* b
 // harmless); the fastest shape is kept for that operator
 // ---------------------------------------------------------------------------
 template <class Op, typename V>
-static fvs_status tune_apply(Batch& B, const Op& op, const V* x, const V* b, V* y, const V* dinv, BShape& out) {
+static fvs_status tune_apply(Batch& B, const Op& op, const V* x, const V* b, V* y, const V* dinv, BShape& out,
+                             const XStage* stage = nullptr) {
   out = BShape();
   if (getenv("FVS_NO_TUNE") || op.n <= 0) return FVS_OK;
   cudaEvent_t e0, e1;
   FVS_CUDA(cudaEventCreate(&e0));
   FVS_CUDA(cudaEventCreate(&e1));
   float best = 1e30f;
-  for (int rows : {4, 8, 16, 32}) {
-    for (int per_sm : {8, 16, 32}) {
-      if (32 * rows * per_sm > 2048 * 4) continue;   // well past full occupancy
-      BShape sh{rows, per_sm};
-      kb_apply<Op, V><<<sgrid(op.n, B.tiles, &sh), sblock(&sh), 0, B.stream>>>(op, B.Sp, x, b, y, 2, dinv, (V)0.5);
-      if (cudaGetLastError() != cudaSuccess) continue;   // shape not launchable (registers): skip it
-      cudaEventRecord(e0, B.stream);
-      for (int r = 0; r < 3; ++r)
-        kb_apply<Op, V><<<sgrid(op.n, B.tiles, &sh), sblock(&sh), 0, B.stream>>>(op, B.Sp, x, b, y, 2, dinv,
-                                                                                 (V)0.5);
-      cudaEventRecord(e1, B.stream);
-      const cudaError_t e = cudaEventSynchronize(e1);
-      float ms = 0.0f;
-      if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-      if (e == cudaSuccess && ms < best) { best = ms; out = sh; }
-    }
+  std::vector<BShape> cand;
+  for (int rows : {4, 8, 16, 32})
+    for (int per_sm : {8, 16, 32})
+      if (32 * rows * per_sm <= 2048 * 4) cand.push_back(BShape{rows, per_sm, nullptr});   // past full occupancy: no
+  if (stage_fits<V>(stage)) cand.push_back(BShape{stage->R, 0, stage});
+  for (const BShape& sh : cand) {
+    launch_apply<Op, V>(B, op, x, b, y, 2, dinv, (V)0.5, &sh);
+    if (cudaGetLastError() != cudaSuccess) continue;   // shape not launchable (registers): skip it
+    cudaEventRecord(e0, B.stream);
+    for (int r = 0; r < 3; ++r) launch_apply<Op, V>(B, op, x, b, y, 2, dinv, (V)0.5, &sh);
+    cudaEventRecord(e1, B.stream);
+    const cudaError_t e = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    if (e == cudaSuccess && ms < best) { best = ms; out = sh; }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -670,6 +733,45 @@ template <typename T>
 static fvs_status upload(cudaStream_t s, const std::vector<T>& h, DBuf<T>& d) {
   FVS_TRY(d.alloc(h.size() + 1));
   if (!h.empty()) FVS_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  return FVS_OK;
+}
+
+// column lists of blocks of R consecutive rows (host, at set-up): every
+// stored column of the ELL pattern [k*n + i], k < w
+static fvs_status build_stage(cudaStream_t st, int64_t n, int w, const int32_t* dcol, int R, XStage& S) {
+  S.R = 0;
+  if (n <= 0) return FVS_OK;
+  std::vector<int32_t> col((size_t)n * w);
+  FVS_CUDA(cudaMemcpyAsync(col.data(), dcol, col.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  FVS_CUDA(cudaStreamSynchronize(st));
+  const int64_t nblk = (n + R - 1) / R;
+  std::vector<int32_t> uptr(nblk + 1, 0), ucol;
+  std::vector<uint8_t> li((size_t)n * w);
+  std::vector<int32_t> tmp;
+  int umax = 0;
+  for (int64_t b = 0; b < nblk; ++b) {
+    const int64_t r0 = b * R, r1 = std::min<int64_t>(n, r0 + R);
+    tmp.clear();
+    for (int64_t i = r0; i < r1; ++i)
+      for (int k = 0; k < w; ++k) tmp.push_back(col[(size_t)k * n + i]);
+    std::sort(tmp.begin(), tmp.end());
+    tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+    if (tmp.size() > 255) return FVS_OK;   // too many columns for a byte index: leave unstaged
+    umax = std::max(umax, (int)tmp.size());
+    for (int64_t i = r0; i < r1; ++i)
+      for (int k = 0; k < w; ++k)
+        li[(size_t)k * n + i] =
+            (uint8_t)(std::lower_bound(tmp.begin(), tmp.end(), col[(size_t)k * n + i]) - tmp.begin());
+    ucol.insert(ucol.end(), tmp.begin(), tmp.end());
+    uptr[b + 1] = (int32_t)ucol.size();
+  }
+  FVS_TRY(upload(st, uptr, S.uptr));
+  FVS_TRY(upload(st, ucol, S.ucol));
+  FVS_TRY(upload(st, li, S.li));
+  FVS_CUDA(cudaStreamSynchronize(st));
+  S.R = R;
+  S.nblk = nblk;
+  S.umax = umax;
   return FVS_OK;
 }
 
@@ -799,30 +901,35 @@ fvs_status batch_amg_setup(Batch& B) {
   // launch shapes of every level's operator, on the buffers of that level
   // (the fine rows all read their shared base row for the timing)
   FVS_CUDA(cudaMemsetAsync(B.ovr.p, 0xFF, (size_t)Nc * Sp * sizeof(int32_t), st));
+  constexpr int STAGE_ROWS = 8;
+  FVS_TRY(build_stage(st, Nc, W, B.K0.col.p, STAGE_ROWS, B.stage_p));
   for (int l = 0; l + 1 < L || (L == 1 && l == 0); ++l) {
     BLevel& F = *B.lv[l];
     const size_t nS = (size_t)F.n * Sp;
+    if (l >= 1) FVS_TRY(build_stage(st, F.n, F.w, F.col, STAGE_ROWS, F.stage));
+    const XStage* stg = l == 0 ? &B.stage_p : &F.stage;
     if (l >= 1) FVS_CUDA(cudaMemsetAsync(F.val.p, 0, (size_t)F.n * F.w * Sp * sizeof(double), st));
     if (B.fp32) {
       if (l >= 1) FVS_CUDA(cudaMemsetAsync(F.valf.p, 0, (size_t)F.n * F.w * Sp * sizeof(float), st));
       for (DBuf<float>* b : {&F.bf, &F.xf, &F.yf, &F.dinvf}) FVS_CUDA(cudaMemsetAsync(b->p, 0, nS * sizeof(float), st));
       if (l == 0)
         FVS_TRY(tune_apply(B, OpPpe0T<float>{Nc, W, B.K0.col.p, B.K0f.p, B.ovr.p, B.mvalf.p}, F.xf.p, F.bf.p, F.yf.p,
-                           F.dinvf.p, F.shape));
+                           F.dinvf.p, F.shape, stg));
       else
         FVS_TRY(tune_apply(B, OpCoarseT<float>{F.n, F.w, F.col, F.valf.p, F.rlen}, F.xf.p, F.bf.p, F.yf.p, F.dinvf.p,
-                           F.shape));
+                           F.shape, stg));
     } else {
       for (DBuf<double>* b : {&F.b, &F.x, &F.y, &F.dinv}) FVS_CUDA(cudaMemsetAsync(b->p, 0, nS * sizeof(double), st));
       if (l == 0)
         FVS_TRY(tune_apply(B, OpPpe0{Nc, W, B.K0.col.p, B.K0.val.p, B.ovr.p, B.mval.p}, F.x.p, F.b.p, F.y.p, F.dinv.p,
-                           F.shape));
+                           F.shape, stg));
       else
-        FVS_TRY(tune_apply(B, OpCoarse{F.n, F.w, F.col, F.val.p, F.rlen}, F.x.p, F.b.p, F.y.p, F.dinv.p, F.shape));
+        FVS_TRY(tune_apply(B, OpCoarse{F.n, F.w, F.col, F.val.p, F.rlen}, F.x.p, F.b.p, F.y.p, F.dinv.p, F.shape,
+                           stg));
     }
     if (getenv("FVS_DEBUG"))
-      fprintf(stderr, "[fvs batch] level %d (%lld rows): operator shape %d rows x %d per SM\n", l, (long long)F.n,
-              F.shape.rows, F.shape.per_sm);
+      fprintf(stderr, "[fvs batch] level %d (%lld rows): operator shape %d rows x %d per SM%s (stage umax %d)\n", l,
+              (long long)F.n, F.shape.rows, F.shape.per_sm, F.shape.stage ? ", staged" : "", stg->umax);
   }
   FVS_CUDA(cudaStreamSynchronize(st));
   B.amg_ok = true;
@@ -2202,10 +2309,12 @@ fvs_status batch_run(fvs_mesh mesh, const fvs_props* base, int64_t n, const doub
         FVS_TRY(B.kw.ensure(cs));
         for (DBuf<double>* b : {&B.kw.r, &B.kw.p, &B.kw.v, &B.mdiag, &B.edx})
           FVS_CUDA(cudaMemsetAsync(b->p, 0, cs * sizeof(double), st));
+        FVS_TRY(build_stage(st, Nc, W, mesh->Lu.col.p, 8, B.stage_m));
+        FVS_TRY(build_stage(st, Nc, W, B.LT.col.p, 8, B.stage_e));
         FVS_TRY(tune_apply(B, OpShared{Nc, W, mesh->Lu.col.p, B.moff.p, B.mdiag.p, nullptr}, B.kw.r.p, B.kw.p.p,
-                           B.kw.v.p, B.mdiag.p, B.shp_mom));
+                           B.kw.v.p, B.mdiag.p, B.shp_mom, &B.stage_m));
         FVS_TRY(tune_apply(B, OpShared{Nc, W, B.LT.col.p, B.kev.p, B.edx.p, nullptr}, B.kw.r.p, B.kw.p.p, B.kw.v.p,
-                           B.edx.p, B.shp_energy));
+                           B.edx.p, B.shp_energy, &B.stage_e));
         if (getenv("FVS_DEBUG"))
           fprintf(stderr, "[fvs batch] momentum shape %d x %d, energy shape %d x %d\n", B.shp_mom.rows,
                   B.shp_mom.per_sm, B.shp_energy.rows, B.shp_energy.per_sm);

@@ -28,11 +28,28 @@ enum BSlot {
   B_FIRST, B_T0, B_T1, B_T2, B_NSLOT
 };
 
+// Staging of x for a batched operator: the rows are cut into blocks of R
+// consecutive rows; block b lists the distinct columns its rows reference
+// (ucol[uptr[b] .. uptr[b+1])), and every stored entry q = k*n + i carries
+// its column's position in that list (li[q] < 256).  A kernel block loads
+// x of those columns for its 32 samples into shared memory once (all loads
+// independent) and gathers from there, instead of one dependent global
+// gather per entry.
+struct XStage {
+  int R = 0;                      // rows per block; 0: not built
+  int64_t nblk = 0;
+  int umax = 0;                   // largest column list of a block
+  DBuf<int32_t> uptr, ucol;
+  DBuf<uint8_t> li;
+};
+
 // launch shape of a batched operator kernel: blocks of 32 samples x rows,
-// at most per_sm blocks per SM (chosen by the autotuner)
+// at most per_sm blocks per SM, or the staged kernel over stage->R rows per
+// block (chosen by the autotuner)
 struct BShape {
   int rows = 8;
   int per_sm = 16;
+  const XStage* stage = nullptr;
 };
 
 // one level of the batched AMG hierarchy
@@ -53,6 +70,7 @@ struct BLevel {
   DBuf<float> bf, xf, rf, yf;
   DBuf<int32_t> lab;              // null-space labels [i*Sp + s] (levels used for label pull-down)
   BShape shape;                   // tuned launch shape of this level's operator
+  XStage stage;                   // levels >= 1: x staging of this level's pattern
 };
 
 // a device-driven Krylov loop captured as a graph (conditional while-node)
@@ -153,6 +171,7 @@ struct Batch {
   uint64_t batch_version = 0;     // bumped when operator or hierarchy buffers move
   BatchGraph gmom[3], gp, ge;     // captured solve loops
   BShape shp_mom, shp_energy;     // tuned launch shapes of the shared operators
+  XStage stage_p, stage_m, stage_e;   // x staging of the fine pressure, momentum and energy patterns
   BatchWork kw;
 
   ~Batch();
