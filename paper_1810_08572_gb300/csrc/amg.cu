@@ -845,12 +845,7 @@ __global__ void k_jac0(int64_t n, T omega, const T* dinv, const T* b, T* x) {
 template <typename T>
 __device__ __forceinline__ T fine_row(int64_t n, int w, const int32_t* __restrict__ col, const T* __restrict__ val,
                                       const T* __restrict__ x, int64_t i) {
-  T acc = 0;
-  for (int k = 0; k < w; ++k) {
-    const int64_t e = (int64_t)k * n + i;
-    acc = fma(val[e], x[col[e]], acc);
-  }
-  return acc;
+  return ell_row(n, w, col, val, x, i, (T)0);
 }
 
 // y = x + omega D^-1 (b - A x)

@@ -137,6 +137,26 @@ struct GatherStaged {
   int lane;
   __device__ __forceinline__ V operator()(int64_t q) const { return xs[(int)li[q] * 32 + lane]; }
 };
+// acc + sum_{k < len} vf(k) g(k n + i), in slot order: the gathers of CH
+// consecutive entries are issued before their multiply-adds, so a thread
+// waits on one round of loads per CH entries instead of one per entry (the
+// batched operators are bound by that latency: a warp serves one row of 32
+// samples, and its loads are few and small)
+constexpr int BCH = 9;
+template <typename V, class G, class VF>
+__device__ __forceinline__ V chunked_sum(int64_t n, int len, int64_t i, const G& g, const VF& vf, V acc) {
+  int k = 0;
+  for (; k + BCH <= len; k += BCH) {
+    V xv[BCH];
+#pragma unroll
+    for (int c = 0; c < BCH; ++c) xv[c] = g((int64_t)(k + c) * n + i);
+#pragma unroll
+    for (int c = 0; c < BCH; ++c) acc = fma(vf(k + c), xv[c], acc);
+  }
+  for (; k < len; ++k) acc = fma(vf(k), g((int64_t)k * n + i), acc);
+  return acc;
+}
+
 // shared values: y = dg x + [mask] sum_k val[k][i] x[col]   (mask: solid rows keep dg x only)
 struct OpShared {
   int64_t n;
@@ -150,10 +170,9 @@ struct OpShared {
     const int64_t e = i * Sp + s;
     double acc = dg ? dg[e] * x[e] : 0.0;
     if (!mask || mask[e]) {
-      for (int k = 0; k < w; ++k) {
-        const int64_t q = (int64_t)k * n + i;
-        acc = fma(val[q], g(q), acc);
-      }
+      const double* v = val;
+      const int64_t nn = n;
+      acc = chunked_sum(n, w, i, g, [v, nn, i](int k) { return v[(int64_t)k * nn + i]; }, acc);
     }
     return acc;
   }
@@ -176,13 +195,12 @@ struct OpPpe0T {
     if (o == -2) return x[e];
     V acc = 0;
     if (o < 0) {
-      for (int k = 0; k < w; ++k) {
-        const int64_t q = (int64_t)k * n + i;
-        acc = fma(base[q], g(q), acc);
-      }
+      const V* bv = base;
+      const int64_t nn = n;
+      acc = chunked_sum(n, w, i, g, [bv, nn, i](int k) { return bv[(int64_t)k * nn + i]; }, acc);
     } else {
       const V* mv = mval + (int64_t)o * w;
-      for (int k = 0; k < w; ++k) acc = fma(mv[k], g((int64_t)k * n + i), acc);
+      acc = chunked_sum(n, w, i, g, [mv](int k) { return mv[k]; }, acc);
     }
     return acc;
   }
@@ -198,13 +216,11 @@ struct OpCoarseT {
   const int32_t* rlen;   // stored entries per row (padding after), shared by all samples
   template <class G>
   __device__ __forceinline__ V row(int64_t i, int s, int Sp, const V* x, const G& g) const {
-    V acc = 0;
     const int len = rlen ? rlen[i] : w;
-    for (int k = 0; k < len; ++k) {
-      const int64_t q = (int64_t)k * n + i;
-      acc = fma(val[q * Sp + s], g(q), acc);
-    }
-    return acc;
+    const V* v = val;
+    const int64_t nn = n;
+    return chunked_sum(n, len, i, g, [v, nn, i, Sp, s](int k) { return v[((int64_t)k * nn + i) * Sp + s]; },
+                       (V)0);
   }
 };
 using OpCoarse = OpCoarseT<double>;

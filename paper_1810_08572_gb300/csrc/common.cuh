@@ -143,6 +143,24 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
   return v;
 }
 
+// One ELL row, acc + sum_k val[k*n + i] x[col[k*n + i]] in slot order: the
+// matrix streams through once per product, so its loads are marked
+// evict-first (ld.global.cs) to leave the cache to the x gathers; the slot
+// stride is a pointer increment rather than a 64-bit multiply per entry.
+template <typename T>
+__device__ __forceinline__ T ell_row(int64_t n, int w, const int32_t* __restrict__ col, const T* __restrict__ val,
+                                     const T* __restrict__ x, int64_t i, T acc) {
+  const int32_t* cp = col + i;
+  const T* vp = val + i;
+#pragma unroll 9
+  for (int k = 0; k < w; ++k) {
+    acc = fma(__ldcs(vp), x[__ldcs(cp)], acc);
+    cp += n;
+    vp += n;
+  }
+  return acc;
+}
+
 // 3x3 inverse by cofactors; returns the determinant.
 __device__ __forceinline__ double inv3(const double a[9], double r[9]) {
   const double c00 = a[4] * a[8] - a[5] * a[7];

@@ -15,11 +15,7 @@ __global__ void k_spmv(int64_t n, int w, const int32_t* __restrict__ col, const 
                        const double* __restrict__ x, double* __restrict__ y,
                        const double* __restrict__ dextra) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = dextra ? dextra[i] * x[i] : 0.0;
-    for (int k = 0; k < w; ++k) {
-      const int64_t e = (int64_t)k * n + i;
-      acc = fma(val[e], x[col[e]], acc);
-    }
+    const double acc = ell_row(n, w, col, val, x, i, dextra ? dextra[i] * x[i] : 0.0);
     y[i] = acc;
   }
 }
@@ -28,11 +24,7 @@ __global__ void k_residual(int64_t n, int w, const int32_t* __restrict__ col, co
                            const double* __restrict__ x, const double* __restrict__ b, double* __restrict__ r,
                            const double* __restrict__ dextra) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = dextra ? dextra[i] * x[i] : 0.0;
-    for (int k = 0; k < w; ++k) {
-      const int64_t e = (int64_t)k * n + i;
-      acc = fma(val[e], x[col[e]], acc);
-    }
+    const double acc = ell_row(n, w, col, val, x, i, dextra ? dextra[i] * x[i] : 0.0);
     r[i] = b[i] - acc;
   }
 }
@@ -281,11 +273,7 @@ __global__ void __launch_bounds__(256, 8) k_spmv_dot(int64_t n, int w, const int
                                                      unsigned int* ticket, double* sc) {
   double a = 0.0, b = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    double acc = DX ? dextra[i] * x[i] : 0.0;
-    for (int k = 0; k < w; ++k) {
-      const int64_t e = (int64_t)k * n + i;
-      acc = fma(val[e], x[col[e]], acc);
-    }
+    const double acc = ell_row(n, w, col, val, x, i, DX ? dextra[i] * x[i] : 0.0);
     y[i] = acc;
     a = fma(d[i], acc, a);
     if (YY) b = fma(acc, acc, b);
