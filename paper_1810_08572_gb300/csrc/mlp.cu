@@ -4,8 +4,8 @@
 // surrogate for the same role).
 //
 // A multilayer perceptron with GELU hidden layers and a linear output,
-// BF16 weights and activations, FP32 accumulation on the tensor cores
-// (mma.sync m16n8k16), FP32 master weights and Adam moments.  Every
+// BF16 weights and activations, FP32 accumulation in tensor memory on the
+// tcgen05 tensor cores, FP32 master weights and Adam moments.  Every
 // dimension is padded to a multiple of 16 with zeros that stay zero.
 #include <cuda_bf16.h>
 
@@ -19,18 +19,6 @@ namespace fvs {
 #define GS(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
 
 typedef __nv_bfloat16 bf16;
-
-__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
-  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-__device__ __forceinline__ void mma_bf16_16816(float c[4], const uint32_t a[4], const uint32_t b[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
 
 __device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
@@ -47,63 +35,137 @@ struct Epi {
   int ldo;
 };
 
-// C[M x N] = sum_k A(m, k) B(n, k) with A(m, k) = A[m*am + k*ak], B(n, k) = B[n*bn + k*bk].
-// One warp per 16-row tile, all N (<= 128) columns; K, N multiples of 16.
+// ---------------------------------------------------------------------------
+// C[M x N] = sum_k A(m, k) B(n, k) with A(m, k) = A[m*am + k*ak], B(n, k) =
+// B[n*bn + k*bk] (BF16), N <= 128, K a multiple of 16, on the
+// 5th-generation tensor cores (tcgen05) with a fused epilogue: one CTA of
+// four warps per 128 rows of C, all N (<= 128) columns in one tile, K in
+// chunks of 64.  Each chunk of A (128 x 64) and B (N x 64) is staged in
+// shared memory in the canonical K-major layout without swizzle (core
+// matrices of 8 rows x 16 bytes; 128 bytes between core matrices along K,
+// 1024 bytes between groups of 8 rows), one thread issues the chunk's
+// 128 x N x 16 BF16 MMAs into an FP32 accumulator in tensor memory and
+// commits them to an mbarrier, and after the last chunk every warp reads
+// its 32 accumulator lanes with tcgen05.ld for the fused epilogue.  Waits are
+// bounded: a wait that runs out sets *err and the CTA still frees its
+// tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int TC_KC = 64;
+constexpr int TC_COLS = 128;   // tensor-memory columns of a CTA (N <= 128)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ int tc_off(int r, int k) { return (r >> 3) * 1024 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2; }
+// shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (16-byte units), descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+  return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46);
+}
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase) {
+  uint32_t done = 0;
+  for (int it = 0; it < (1 << 22) && !done; ++it)
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(mbar), "r"(phase));
+  return done != 0;
+}
+
 template <int EPI>
-__global__ void k_mlp_gemm(int M, int N, int K, const bf16* __restrict__ A, int am, int ak,
-                           const bf16* __restrict__ B, int bn, int bk, Epi e) {
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int m0 = warp * 16;
-  if (m0 >= M) return;
-  const int g = lane >> 2, t = lane & 3;
-  float acc[16][4];
-#pragma unroll
-  for (int j = 0; j < 16; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+__global__ void __launch_bounds__(128, 1) k_mlp_gemm_tc(int M, int N, int K, const bf16* __restrict__ A, int am, int ak,
+                                                        const bf16* __restrict__ B, int bn, int bk, Epi e, int* err) {
+  __shared__ __align__(1024) unsigned char sa[128 * TC_KC * 2];
+  __shared__ __align__(1024) unsigned char sb[TC_COLS * TC_KC * 2];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * 128;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
+                 "r"(TC_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = taddr_s;
+  // kind::f16 instruction descriptor: FP32 accumulator, BF16 A and B, both
+  // K-major, N >> 3, M >> 4
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
   const bf16 zero = __float2bfloat16(0.f);
-  auto ldA = [&](int m, int k) -> bf16 { return m < M ? A[(int64_t)m * am + (int64_t)k * ak] : zero; };
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    uint32_t a[4];
-    a[0] = pack2(ldA(m0 + g, k0 + 2 * t), ldA(m0 + g, k0 + 2 * t + 1));
-    a[1] = pack2(ldA(m0 + g + 8, k0 + 2 * t), ldA(m0 + g + 8, k0 + 2 * t + 1));
-    a[2] = pack2(ldA(m0 + g, k0 + 2 * t + 8), ldA(m0 + g, k0 + 2 * t + 9));
-    a[3] = pack2(ldA(m0 + g + 8, k0 + 2 * t + 8), ldA(m0 + g + 8, k0 + 2 * t + 9));
-#pragma unroll
-    for (int j = 0; j < 16; ++j) {
-      if (j * 8 < N) {
-        const int n = j * 8 + g;
-        uint32_t b[2];
-        b[0] = pack2(B[(int64_t)n * bn + (int64_t)(k0 + 2 * t) * bk], B[(int64_t)n * bn + (int64_t)(k0 + 2 * t + 1) * bk]);
-        b[1] = pack2(B[(int64_t)n * bn + (int64_t)(k0 + 2 * t + 8) * bk],
-                     B[(int64_t)n * bn + (int64_t)(k0 + 2 * t + 9) * bk]);
-        mma_bf16_16816(acc[j], a, b);
-      }
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int k0 = 0; k0 < K && ok; k0 += TC_KC) {
+    const int kc = min(TC_KC, K - k0);
+    // stage A(m, k) and B(n, k); the index that is contiguous in memory runs fastest
+    for (int t = tid; t < 128 * kc; t += 128) {
+      const int r = ak == 1 ? t / kc : t % 128, k = ak == 1 ? t % kc : t / 128;
+      const int m = m0 + r;
+      *(bf16*)(sa + tc_off(r, k)) = m < M ? A[(int64_t)m * am + (int64_t)(k0 + k) * ak] : zero;
     }
+    for (int t = tid; t < N * kc; t += 128) {
+      const int r = bk == 1 ? t / kc : t % N, k = bk == 1 ? t % kc : t / N;
+      *(bf16*)(sb + tc_off(r, k)) = B[(int64_t)r * bn + (int64_t)(k0 + k) * bk];
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      for (int kk = 0; kk < kc / 16; ++kk) {
+        const uint64_t ad = tc_desc(smem_u32(sa) + kk * 256), bd = tc_desc(smem_u32(sb) + kk * 256);
+        const uint32_t accum = (k0 > 0 || kk > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar)));
+    }
+    if (!tc_wait(smem_u32(&mbar), phase)) {
+      ok = false;
+      if (lane == 0) atomicOr(err, 1);
+      tc_wait(smem_u32(&mbar), phase);   // give the MMAs in flight a second bounded chance
+    }
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
   }
-#pragma unroll
-  for (int j = 0; j < 16; ++j) {
-    if (j * 8 >= N) continue;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int m = m0 + g + (q >= 2 ? 8 : 0);
-      const int n = j * 8 + 2 * t + (q & 1);
+  if (ok) {
+    const int m = m0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (m >= M) continue;
-      const int64_t o = (int64_t)m * e.ldo + n;
-      float v = acc[j][q];
-      if (EPI == EPI_GELU) {
-        v += e.bias[n];
-        if (e.z) e.z[o] = v;
-        e.hout[o] = __float2bfloat16(gelu(v));
-      } else if (EPI == EPI_LINEAR) {
-        v += e.bias[n];
-        e.fout[o] = v;
-      } else if (EPI == EPI_DGRAD) {
-        e.hout[o] = __float2bfloat16(v * gelu_grad(e.z[o]));
-      } else {
-        e.fout[o] = v;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int n = c0 + j;
+        const int64_t o = (int64_t)m * e.ldo + n;
+        float v = __uint_as_float(r[j]);
+        if (EPI == EPI_GELU) {
+          v += e.bias[n];
+          if (e.z) e.z[o] = v;
+          e.hout[o] = __float2bfloat16(gelu(v));
+        } else if (EPI == EPI_LINEAR) {
+          v += e.bias[n];
+          e.fout[o] = v;
+        } else if (EPI == EPI_DGRAD) {
+          e.hout[o] = __float2bfloat16(v * gelu_grad(e.z[o]));
+        } else {
+          e.fout[o] = v;
+        }
       }
     }
   }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_COLS));
 }
 
 // inputs (double, [n x nin]) -> normalised BF16 rows padded to kin
@@ -225,6 +287,7 @@ struct fvs_surrogate_s {
   DBuf<bf16> d0, d1;
   DBuf<float> Y;
   DBuf<double> part, lossv, Xd, Td;
+  DBuf<int> tc_err;          // set by a tensor-core GEMM whose bounded wait ran out
   ~fvs_surrogate_s() {
     for (auto* p : H) delete p;
     for (auto* p : Z) delete p;
@@ -259,7 +322,7 @@ static fvs_status sg_work(fvs_surrogate_s* s, int64_t n) {
   return FVS_OK;
 }
 
-static int gemm_grid(int64_t M) { return (int)((M + 63) / 64); }
+static int tc_grid(int64_t M) { return (int)((M + 127) / 128); }
 
 // forward pass of n normalised BF16 rows already in H[0]; keep Z when training
 static fvs_status sg_forward(fvs_surrogate_s* s, int64_t n, bool keep) {
@@ -274,10 +337,10 @@ static fvs_status sg_forward(fvs_surrogate_s* s, int64_t n, bool keep) {
     if (l < L - 1) {
       e.z = keep ? s->Z[l]->p : nullptr;
       e.hout = s->H[l + 1]->p;
-      k_mlp_gemm<EPI_GELU><<<gemm_grid(n), 128, 0, st>>>((int)n, N, K, s->H[l]->p, K, 1, W, K, 1, e);
+      k_mlp_gemm_tc<EPI_GELU><<<tc_grid(n), 128, 0, st>>>((int)n, N, K, s->H[l]->p, K, 1, W, K, 1, e, s->tc_err.p);
     } else {
       e.fout = s->Y.p;
-      k_mlp_gemm<EPI_LINEAR><<<gemm_grid(n), 128, 0, st>>>((int)n, N, K, s->H[l]->p, K, 1, W, K, 1, e);
+      k_mlp_gemm_tc<EPI_LINEAR><<<tc_grid(n), 128, 0, st>>>((int)n, N, K, s->H[l]->p, K, 1, W, K, 1, e, s->tc_err.p);
     }
     FVS_COUNT_LAUNCH();
   }
@@ -305,8 +368,8 @@ static fvs_status sg_gradients(fvs_surrogate_s* s, int64_t n, double* loss_host)
     Epi e{};
     e.fout = s->g.p + s->woff[l];
     e.ldo = K;
-    k_mlp_gemm<EPI_WGRAD><<<gemm_grid(N), 128, 0, st>>>(N, K, (int)((n + 15) / 16 * 16), dcur, 1, N,
-                                                        s->H[l]->p, 1, K, e); FVS_COUNT_LAUNCH();
+    k_mlp_gemm_tc<EPI_WGRAD><<<tc_grid(N), 128, 0, st>>>(N, K, (int)((n + 15) / 16 * 16), dcur, 1, N,
+                                                         s->H[l]->p, 1, K, e, s->tc_err.p); FVS_COUNT_LAUNCH();
     k_bias_grad<<<(N + 127) / 128, 128, 0, st>>>((int)n, N, dcur, s->g.p + s->boff[l]); FVS_COUNT_LAUNCH();
     if (l > 0) {
       // delta_{l-1} = (delta_l W_l) * gelu'(Z_{l-1}): A(m=b, k=n) = delta[b*N + n], B(n'=k, k=n) = W[n*K + k]
@@ -314,7 +377,8 @@ static fvs_status sg_gradients(fvs_surrogate_s* s, int64_t n, double* loss_host)
       d.z = s->Z[l - 1]->p;
       d.hout = dnext;
       d.ldo = K;
-      k_mlp_gemm<EPI_DGRAD><<<gemm_grid(n), 128, 0, st>>>((int)n, K, N, dcur, N, 1, s->wb.p + s->woff[l], 1, K, d);
+      k_mlp_gemm_tc<EPI_DGRAD><<<tc_grid(n), 128, 0, st>>>((int)n, K, N, dcur, N, 1, s->wb.p + s->woff[l], 1, K, d,
+                                                          s->tc_err.p);
       FVS_COUNT_LAUNCH();
       std::swap(dcur, dnext);
     }
@@ -412,9 +476,11 @@ FVS_API fvs_status fvs_surrogate_create(int32_t n_in, int32_t n_hidden, int32_t 
   if (r == FVS_OK) r = s->sd_in.alloc(128);
   if (r == FVS_OK) r = s->mu_out.alloc(128);
   if (r == FVS_OK) r = s->sd_out.alloc(128);
+  if (r == FVS_OK) r = s->tc_err.alloc(1);
   if (r != FVS_OK) { delete s; return r; }
   s->w32.zero(s->stream); s->m.zero(s->stream); s->v.zero(s->stream); s->g.zero(s->stream);
   s->mask.zero(s->stream);
+  s->tc_err.zero(s->stream);
   for (int l = 0; l < L; ++l) {
     const int64_t n = (int64_t)s->kd[l + 1] * s->kd[l];
     const float lim = sqrtf(6.0f / (float)s->real[l]);
@@ -529,6 +595,20 @@ FVS_API fvs_status fvs_surrogate_params(fvs_surrogate s, double* inout, int64_t 
   return FVS_OK;
 }
 
+// FVS_ERR_TIMEOUT if a tensor-core GEMM gave up waiting on its MMAs (the
+// flag is cleared for the next call)
+static fvs_status tc_check(fvs_surrogate s) {
+  int h = 0;
+  FVS_CUDA(cudaMemcpyAsync(&h, s->tc_err.p, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  FVS_CUDA(cudaStreamSynchronize(s->stream));
+  if (h) {
+    s->tc_err.zero(s->stream);
+    set_error("surrogate: a tensor-core GEMM timed out waiting for its MMAs");
+    return FVS_ERR_TIMEOUT;
+  }
+  return FVS_OK;
+}
+
 FVS_API fvs_status fvs_surrogate_gradients(fvs_surrogate s, const double* X, const double* T, int64_t n,
                                            double* grad, int64_t grad_len, double* loss) {
   if (!s || !X || !T || !grad || n <= 0) {
@@ -549,6 +629,7 @@ FVS_API fvs_status fvs_surrogate_gradients(fvs_surrogate s, const double* X, con
   std::vector<float> h(s->nparam);
   FVS_CUDA(cudaMemcpyAsync(h.data(), s->g.p, s->nparam * sizeof(float), cudaMemcpyDeviceToHost, s->stream));
   FVS_CUDA(cudaStreamSynchronize(s->stream));
+  FVS_TRY(tc_check(s));
   for (size_t i = 0; i < idx.size(); ++i) grad[i] = (double)h[idx[i]];
   return FVS_OK;
 }
@@ -579,6 +660,7 @@ FVS_API fvs_status fvs_surrogate_train(fvs_surrogate s, const double* X, const d
   FVS_LAUNCH_CHECK();
   double l = 0.0;
   FVS_TRY(sg_gradients(s, n, &l));
+  FVS_TRY(tc_check(s));
   if (final_loss) *final_loss = l;
   return FVS_OK;
 }
@@ -612,5 +694,5 @@ FVS_API fvs_status fvs_surrogate_predict(fvs_surrogate s, const double* X, doubl
   FVS_LAUNCH_CHECK();
   if (!on_device) FVS_CUDA(cudaMemcpyAsync(Y, Yd, n * s->nout * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   FVS_CUDA(cudaStreamSynchronize(s->stream));
-  return FVS_OK;
+  return tc_check(s);
 }
