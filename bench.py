@@ -404,12 +404,14 @@ def run_shrink(fvs, c, args, stream, torch):
                 S.step(c["dt"], 1, allow_not_converged=True)
             torch.cuda.synchronize()
             ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            act, p_its = 0, []
+            act, p_its, setup, rebuilt = 0, [], [], []
             ev0.record(stream)
             for _ in range(args.shrink_steps):
                 st = S.step(c["dt"], 1, allow_not_converged=True)
                 act += st["n_active"]
                 p_its.append(st["p_its"])
+                setup.append(st["setup_ms"])
+                rebuilt.append(st["p_rebuilt"])
             ev1.record(stream)
             torch.cuda.synchronize()
             ms = ev0.elapsed_time(ev1)
@@ -425,6 +427,7 @@ def run_shrink(fvs, c, args, stream, torch):
             S.profile(False)
             row[prec] = dict(value=round(act / (ms / 1e3), 1), ms_per_step=round(ms / args.shrink_steps, 3),
                              mean_active=round(act / args.shrink_steps), p_its=round(float(np.mean(p_its)), 1),
+                             pressure_setup_ms_per_step=round(float(np.mean(setup)), 2), p_rebuilt=rebuilt,
                              sparse_kernel_ms_per_step={k: round(v, 2) for k, v in sorted(by.items())})
             S.close()
         out.append(row)

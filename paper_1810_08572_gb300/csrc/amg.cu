@@ -1120,6 +1120,7 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
   opt.npost = (int)env_num("FVS_AMG_NPOST", opt.npost);
   opt.coarsest = (int)env_num("FVS_AMG_COARSEST", opt.coarsest);
   opt.mis2_ratio = env_num("FVS_AMG_MIS2_RATIO", opt.mis2_ratio);
+  opt.mis2_from = (int)env_num("FVS_AMG_MIS2_FROM", opt.mis2_from);
   if (opt.npre < 1) opt.npre = 1;
   if (opt.npost < 1) opt.npost = 1;
   DBuf<int> err, cnt;
@@ -1174,8 +1175,9 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
     // attempts 0-2: distance-1 independent sets on ever wider strength
     // graphs; attempt 3, only where those would stall the coarsening: the
     // distance-2 set on the first graph
-    for (int attempt = 0; attempt < 4; ++attempt) {
-      if (attempt == 3 && (double)nc <= opt.mis2_ratio * (double)n) break;   // keep the distance-1 result
+    const int first = l >= opt.mis2_from ? 3 : 0;
+    for (int attempt = first; attempt < 4; ++attempt) {
+      if (first == 0 && attempt == 3 && (double)nc <= opt.mis2_ratio * (double)n) break;   // keep the distance-1 result
       mis2 = attempt == 3;
       const double theta = (attempt == 0 || mis2) ? opt.theta : 0.0;
       const int absval = attempt == 2 ? 1 : 0;
@@ -1326,7 +1328,8 @@ fvs_status Amg::coarsest_setup(cudaStream_t s) {
     set_error("AMG coarsest level too large (%d rows)", nc);
     return FVS_ERR_NOT_CONVERGED;
   }
-  DBuf<int> err, ncd;
+  DBuf<int>& err = c_err;
+  DBuf<int>& ncd = c_ncd;
   FVS_TRY(Ainv.alloc((size_t)nc * nc + 1));
   FVS_TRY(clab.alloc(nc + 1));
   FVS_TRY(csing.alloc(nc + 1));
@@ -1349,8 +1352,9 @@ fvs_status Amg::coarsest_setup(cudaStream_t s) {
       k_coarsest_smem<<<1, 1024, sh, s>>>(nc, A.w, A.col, A.val, Ainv, clab, csing, ncd, err, 1);
       FVS_COUNT_LAUNCH();
     } else {
-      DBuf<double> fac;
-      DBuf<int32_t> perm, order;
+      DBuf<double>& fac = gj_fac;
+      DBuf<int32_t>& perm = gj_perm;
+      DBuf<int32_t> order;
       FVS_TRY(fac.alloc(nc)); FVS_TRY(perm.alloc(nc)); FVS_TRY(order.alloc(nc));
       FVS_CUDA(cudaMemsetAsync(Ainv.p, 0, (size_t)nc * nc * sizeof(double), s));
       k_dense_fill<<<stride_grid(nc, 128), 128, 0, s>>>(nc, A.w, A.col, A.val, Ainv); FVS_COUNT_LAUNCH();
@@ -1364,9 +1368,40 @@ fvs_status Amg::coarsest_setup(cudaStream_t s) {
       }
       k_dense_parts<<<1, 1024, dense_parts_smem(nc), s>>>(nc, Ainv, clab, csing, order, ncd); FVS_COUNT_LAUNCH();
       const int eb = std::min(nc, 4 * sm_count());
-      for (int k = 0; k < nc; ++k) {
-        k_gj_pivot<<<1, 256, 0, s>>>(nc, k, Ainv, fac, perm, err); FVS_COUNT_LAUNCH();
-        k_gj_elim<<<eb, 128, 0, s>>>(nc, k, Ainv, fac, err); FVS_COUNT_LAUNCH();
+      // 2 nc launches whose cost is mostly launch latency: capture them once
+      // per level size and buffer set, then replay the graph
+      const uint64_t key = ((uint64_t)nc << 40) ^ (uint64_t)(uintptr_t)Ainv.p ^ ((uint64_t)(uintptr_t)fac.p << 1) ^
+                           ((uint64_t)(uintptr_t)perm.p << 2) ^ ((uint64_t)(uintptr_t)err.p << 3) ^ (uint64_t)eb;
+      bool replayed = false;
+      if (graphs_enabled() && s != nullptr) {
+        if (!gj_exec || gj_key != key) {
+          if (gj_exec) cudaGraphExecDestroy(gj_exec);
+          gj_exec = nullptr;
+          gj_key = 0;
+          cudaGraph_t g = nullptr;
+          if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            for (int k = 0; k < nc; ++k) {
+              k_gj_pivot<<<1, 256, 0, s>>>(nc, k, Ainv, fac, perm, err);
+              k_gj_elim<<<eb, 128, 0, s>>>(nc, k, Ainv, fac, err);
+            }
+            if (cudaStreamEndCapture(s, &g) == cudaSuccess && g) {
+              if (cudaGraphInstantiate(&gj_exec, g, 0) != cudaSuccess) gj_exec = nullptr;
+              cudaGraphDestroy(g);
+            }
+          }
+          cudaGetLastError();   // a failed capture leaves the eager launches below
+          if (gj_exec) gj_key = key;
+        }
+        if (gj_exec && cudaGraphLaunch(gj_exec, s) == cudaSuccess) {
+          replayed = true;
+          __atomic_add_fetch(&g_launches, 2ULL * (unsigned long long)nc, __ATOMIC_RELAXED);
+        }
+      }
+      if (!replayed) {
+        for (int k = 0; k < nc; ++k) {
+          k_gj_pivot<<<1, 256, 0, s>>>(nc, k, Ainv, fac, perm, err); FVS_COUNT_LAUNCH();
+          k_gj_elim<<<eb, 128, 0, s>>>(nc, k, Ainv, fac, err); FVS_COUNT_LAUNCH();
+        }
       }
       k_gj_unswap<<<stride_grid(nc, 128), 128, 0, s>>>(nc, Ainv, perm, err); FVS_COUNT_LAUNCH();
       k_dense_fold<true><<<stride_grid(nc, 128), 128, 0, s>>>(nc, Ainv, clab, csing, order, ncd, err);

@@ -38,6 +38,7 @@ struct AmgOptions {
   int coarsest = 160;      // stop coarsening at or below this size (shared-memory inverse)
   int npre = 1, npost = 1;
   double mis2_ratio = 0.85; // distance-2 aggregation where distance-1 sets keep more than this share of rows
+  int mis2_from = 1 << 30;  // levels from this one on aggregate by distance-2 sets directly
   bool fp32 = false;       // V-cycle in single precision
 };
 
@@ -72,6 +73,15 @@ struct Amg : Precond {
   fvs_status refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe);
   fvs_status apply(cudaStream_t s, const double* r, double* z) override;
   uint64_t version = 0;          // bumped by every setup
+  // coarsest inverse above the shared-memory size: one pivot and one
+  // elimination launch per column, replayed as a captured graph (kept while
+  // the level size and buffers stay the same)
+  DBuf<double> gj_fac;
+  DBuf<int32_t> gj_perm;
+  DBuf<int> c_err, c_ncd;
+  cudaGraphExec_t gj_exec = nullptr;
+  uint64_t gj_key = 0;
+  ~Amg() { if (gj_exec) cudaGraphExecDestroy(gj_exec); }
   uint64_t signature() const override {
     return version * 2654435761ULL + (opt.fp32 ? 1 : 0) + (masked ? 2 : 0);
   }
