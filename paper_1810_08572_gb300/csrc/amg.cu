@@ -120,6 +120,19 @@ __global__ void k_count_isolated(int64_t n, const uint64_t* mask, int* out) {
   }
   if (c) atomicAdd(out, c);
 }
+// fine rows without a nonzero coupling (identity rows of cells that carry no
+// pressure: frozen or not yet melted cells of the numbering) take no part in
+// the aggregation: state 3, no aggregate, no null-space label
+__global__ void k_mark_decoupled(int64_t n, int w, const int32_t* col, const double* val, uint8_t* st) {
+  GS(i, n) {
+    bool any = false;
+    for (int k = 0; k < w && !any; ++k) {
+      const int64_t e = (int64_t)k * n + i;
+      any = col[e] != (int32_t)i && val[e] != 0.0;
+    }
+    if (!any) st[i] = 3;
+  }
+}
 __global__ void k_is_root(int64_t n, const uint8_t* st, int32_t* flag) {
   GS(i, n) flag[i] = st[i] == 1 ? 1 : 0;
 }
@@ -128,6 +141,7 @@ __global__ void k_assign(int64_t n, int w, const int32_t* col, const double* val
                          const uint8_t* st, const int32_t* rid, int32_t* agg, int* err, int lenient = 0) {
   GS(i, n) {
     if (st[i] == 1) { agg[i] = rid[i]; continue; }
+    if (st[i] == 3) { agg[i] = -1; continue; }
     double best = -1e300;
     int32_t bj = -1;
     for (int q = 0; q < SMASK_WORDS; ++q) {
@@ -240,11 +254,11 @@ __global__ void k_mis2_remove(int64_t n, const int32_t* col, const uint64_t* mas
 // nodes two hops from their root join the aggregate of their strongest
 // assigned strong neighbour (reads one snapshot, writes another)
 __global__ void k_assign_near(int64_t n, const int32_t* col, const double* val, const uint64_t* mask,
-                              const int32_t* agg_in, int32_t* agg_out, int* left) {
+                              const uint8_t* st, const int32_t* agg_in, int32_t* agg_out, int* left) {
   int cnt = 0;
   GS(i, n) {
     int32_t a = agg_in[i];
-    if (a < 0) {
+    if (a < 0 && st[i] != 3) {
       double best = -1e300;
       int32_t bj = -1;
       for (int q = 0; q < SMASK_WORDS; ++q) {
@@ -277,13 +291,33 @@ __global__ void k_fill_members(int64_t n, const int32_t* agg, const int32_t* ptr
     if (a >= 0) idx[ptr[a] + atomicAdd(&cur[a], 1)] = (int32_t)i;
   }
 }
-// refresh: rows whose cells carry no pressure leave their aggregates (a row
-// regaining pressure would need a new aggregation: flagged)
-__global__ void k_mask_agg(int64_t n, const int32_t* act, const uint8_t* ppe, int32_t* agg, int* err) {
+// refresh: a row carrying pressure without an aggregate (its cell melted
+// again, or first melted in a margin row of the numbering) joins the
+// aggregate of its most strongly coupled neighbour that has one; reads one
+// snapshot, writes another
+__global__ void k_join_agg(int64_t n, int w, const int32_t* col, const double* val, const int32_t* act,
+                           const uint8_t* ppe, const int32_t* agg_in, int32_t* agg_out) {
   GS(i, n) {
-    if (!ppe[act[i]]) agg[i] = -1;
-    else if (agg[i] < 0) atomicOr(err, 8);
+    int32_t a = agg_in[i];
+    if (a < 0 && ppe[act[i]]) {
+      double best = 0.0;
+      for (int k = 0; k < w; ++k) {
+        const int64_t e = (int64_t)k * n + i;
+        const int32_t j = col[e];
+        if (j == (int32_t)i || val[e] == 0.0 || agg_in[j] < 0) continue;
+        const double v = fabs(val[e]);
+        if (v > best) { best = v; a = agg_in[j]; }
+      }
+    }
+    agg_out[i] = a;
   }
+}
+// refresh: rows whose cells carry no pressure leave their aggregates; a row
+// that carries pressure and found no aggregate stays outside every aggregate
+// (smoothed on the fine level only, its couplings lumped into the coarse
+// diagonals)
+__global__ void k_mask_agg(int64_t n, const int32_t* act, const uint8_t* ppe, int32_t* agg) {
+  GS(i, n) if (!ppe[act[i]]) agg[i] = -1;
 }
 __global__ void k_sort_members(int64_t nc, const int32_t* ptr, int32_t* idx) {
   GS(I, nc) {
@@ -305,6 +339,10 @@ __global__ void k_sort_members(int64_t nc, const int32_t* ptr, int32_t* idx) {
 // warp each (many warps per block); larger rows take a whole block.  With a
 // 'dirty' mask only the marked coarse rows are recomputed (refresh).
 // ---------------------------------------------------------------------------
+// a coupling to a row without an aggregate (a cell that carries pressure
+// again since the aggregation was formed) lumps into the coarse diagonal, so
+// coarse row sums -- and the constant null vectors -- are kept
+__device__ __forceinline__ int32_t gal_key(int32_t a, int64_t I) { return a >= 0 ? a : (int32_t)I; }
 // gather and zero-pad to P (a power of two), then sort; T threads, SYNC()
 // the barrier among them
 #define GAL_GATHER_SORT(T, t, SYNC)                                                \
@@ -314,7 +352,7 @@ __global__ void k_sort_members(int64_t nc, const int32_t* ptr, int32_t* idx) {
       const int32_t i = midx[lo + m];                                             \
       const int64_t ei = (int64_t)k * n + i;                                      \
       const double a = val[ei];                                                   \
-      key[e] = a != 0.0 ? agg[col[ei]] : INT_MAX;                                 \
+      key[e] = a != 0.0 ? gal_key(agg[col[ei]], I) : INT_MAX;                     \
       v[e] = a;                                                                   \
     } else {                                                                      \
       key[e] = INT_MAX;                                                           \
@@ -452,7 +490,7 @@ __global__ void __launch_bounds__(256) k_galerkin_wide(int64_t nc, int64_t n, in
       for (int k = threadIdx.x; k < len; k += blockDim.x) {
         const int64_t ei = (int64_t)k * n + i;
         const double a = val[ei];
-        key[base + k] = a != 0.0 ? agg[col[ei]] : INT_MAX;
+        key[base + k] = a != 0.0 ? gal_key(agg[col[ei]], I) : INT_MAX;
         v[base + k] = a;
       }
       base += len;
@@ -875,9 +913,9 @@ __global__ void k_resid(int64_t n, int w, const int32_t* __restrict__ col, const
 // lanes than one thread per row does, and short serial chains keep the small
 // levels (latency-bound) from waiting on one gather after another.
 constexpr int CG = 4;
-template <typename T>
+template <typename T, class X>
 __device__ __forceinline__ T coarse_part(int64_t n, const int32_t* __restrict__ col, const T* __restrict__ val,
-                                         const T* __restrict__ x, int len, int64_t i, int q) {
+                                         const X& x, int len, int64_t i, int q) {
   T acc = 0;
   int k = q;
   for (; k + 3 * CG < len; k += 4 * CG) {
@@ -885,7 +923,7 @@ __device__ __forceinline__ T coarse_part(int64_t n, const int32_t* __restrict__ 
                   e3 = e2 + (int64_t)CG * n;
     const int32_t c0 = col[e0], c1 = col[e1], c2 = col[e2], c3 = col[e3];
     const T v0 = val[e0], v1 = val[e1], v2 = val[e2], v3 = val[e3];
-    const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+    const T x0 = x(c0), x1 = x(c1), x2 = x(c2), x3 = x(c3);
     acc = fma(v0, x0, acc);
     acc = fma(v1, x1, acc);
     acc = fma(v2, x2, acc);
@@ -893,10 +931,16 @@ __device__ __forceinline__ T coarse_part(int64_t n, const int32_t* __restrict__ 
   }
   for (; k < len; k += CG) {
     const int64_t e = (int64_t)k * n + i;
-    acc = fma(val[e], x[col[e]], acc);
+    acc = fma(val[e], x(col[e]), acc);
   }
   return acc;
 }
+// x of a sweep, gathered by column
+template <typename T>
+struct XVec {
+  const T* __restrict__ x;
+  __device__ __forceinline__ T operator()(int32_t c) const { return x[c]; }
+};
 template <typename T>
 __device__ __forceinline__ T lanes_sum(T v) {
 #pragma unroll
@@ -914,7 +958,7 @@ __global__ void k_resid_g(int64_t n, const int32_t* __restrict__ col, const T* _
   for (int64_t i0 = warp * (32 / CG); i0 < n; i0 += nw * (32 / CG)) {
     const int64_t i = i0 + lane / CG;
     const bool ok = i < n;
-    T acc = ok ? coarse_part(n, col, val, x, rlen[i], i, q) : (T)0;
+    T acc = ok ? coarse_part(n, col, val, XVec<T>{x}, rlen[i], i, q) : (T)0;
     acc = lanes_sum(acc);
     if (ok && q == 0) r[i] = b[i] - acc;
   }
@@ -930,7 +974,7 @@ __global__ void k_jac_g(int64_t n, const int32_t* __restrict__ col, const T* __r
   for (int64_t i0 = warp * (32 / CG); i0 < n; i0 += nw * (32 / CG)) {
     const int64_t i = i0 + lane / CG;
     const bool ok = i < n;
-    T acc = ok ? coarse_part(n, col, val, x, rlen[i], i, q) : (T)0;
+    T acc = ok ? coarse_part(n, col, val, XVec<T>{x}, rlen[i], i, q) : (T)0;
     acc = lanes_sum(acc);
     if (ok && q == 0) y[i] = x[i] + omega * dinv[i] * (b[i] - acc);
   }
@@ -1010,6 +1054,48 @@ __global__ void k_sub_scalar(int64_t n, const double* mean, const int32_t* lab, 
 // refresh: rows whose cells no longer carry pressure leave the null-space labels
 __global__ void k_mask_labels(int64_t n, const int32_t* act, const uint8_t* ppe, int32_t* lab) {
   GS(i, n) if (!ppe[act[i]]) lab[i] = -1;
+}
+// refresh: a row carrying pressure without a label takes the label of the
+// labelled rows it couples to; left[0] counts rows still without one,
+// left[1] rows that took one; two different labels flag err (the row joins
+// two parts)
+__global__ void k_adopt_labels(int64_t n, int w, const int32_t* col, const double* val, const int32_t* act,
+                               const uint8_t* ppe, const int32_t* lab_in, int32_t* lab_out, int* left, int* err) {
+  int still = 0, took = 0;
+  GS(i, n) {
+    int32_t l = lab_in[i];
+    if (l < 0 && ppe[act[i]]) {
+      for (int k = 0; k < w; ++k) {
+        const int64_t e = (int64_t)k * n + i;
+        const int32_t j = col[e];
+        if (j == (int32_t)i || val[e] == 0.0) continue;
+        const int32_t lj = lab_in[j];
+        if (lj < 0) continue;
+        if (l < 0) l = lj;
+        else if (l != lj) atomicOr(err, 16);
+      }
+      if (l < 0) ++still;
+      else ++took;
+    }
+    lab_out[i] = l;
+  }
+  if (still) atomicAdd(left, still);
+  if (took) atomicAdd(left + 1, took);
+}
+// a coupling between two labelled rows of different parts flags err
+__global__ void k_label_conflicts(int64_t n, int w, const int32_t* col, const double* val, const int32_t* lab,
+                                  int* err) {
+  GS(i, n) {
+    const int32_t l = lab[i];
+    if (l < 0) continue;
+    for (int k = 0; k < w; ++k) {
+      const int64_t e = (int64_t)k * n + i;
+      const int32_t j = col[e];
+      if (j == (int32_t)i || val[e] == 0.0) continue;
+      const int32_t lj = lab[j];
+      if (lj >= 0 && lj != l) { atomicOr(err, 32); break; }
+    }
+  }
 }
 // 64-bit fingerprint of each ELL row (columns and value bits); with 'old'
 // given, rows whose fingerprint changed are marked dirty
@@ -1182,6 +1268,10 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
       const double theta = (attempt == 0 || mis2) ? opt.theta : 0.0;
       const int absval = attempt == 2 ? 1 : 0;
       FVS_TRY(st.zero(s));
+      if (l == 0) {
+        k_mark_decoupled<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, st);
+        FVS_COUNT_LAUNCH();
+      }
       k_strong<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->w, cur->col, cur->val, mo, theta, absval, mask);
       FVS_COUNT_LAUNCH();
       FVS_LAUNCH_CHECK();
@@ -1242,7 +1332,7 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
       int left = 0;
       for (int pass = 0; pass < 3; ++pass) {
         FVS_TRY(cnt.zero(s));
-        k_assign_near<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->col, cur->val, mask, L->agg, agg2, cnt);
+        k_assign_near<<<stride_grid(n, 256), 256, 0, s>>>(n, cur->col, cur->val, mask, st, L->agg, agg2, cnt);
         FVS_COUNT_LAUNCH();
         FVS_CUDA(cudaMemcpyAsync(L->agg.p, agg2.p, n * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
         FVS_TRY(read_int(s, cnt, &left));
@@ -1447,6 +1537,7 @@ fvs_status Amg::coarsest_setup(cudaStream_t s) {
   FVS_TRY(cpart.alloc(1025));
   FVS_LAUNCH_CHECK();
   FVS_CUDA(cudaStreamSynchronize(s));
+  masked = true;   // decoupled rows (label -1) stay out of the projection
   return FVS_OK;
 }
 
@@ -1472,10 +1563,11 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
     tph[k] += std::chrono::duration<double, std::milli>(now - t_last).count();
     t_last = now;
   };
-  DBuf<int> err;
+  DBuf<int> err, cnt2;
   DBuf<double> mo;
   FVS_TRY(err.alloc(1));
   FVS_TRY(err.zero(s));
+  FVS_TRY(cnt2.alloc(2));
   FVS_TRY(mo.alloc(n0 + 1));
   for (auto& L : lv) {
     FVS_TRY(L->dirty.alloc(L->n + 1));
@@ -1492,8 +1584,21 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
     // without pressure leave them), then rebuild the member lists
     AmgLevel* L = lv[0].get();
     const int64_t nc = lv[1]->n;
+    {
+      // rows that carry pressure again join the aggregate of the row they
+      // couple to most strongly (two passes for chains of such rows); the
+      // Galerkin pass below checks that the coarse rows still fit
+      const Ell& A = *L->A;
+      DBuf<int32_t> agg2;
+      FVS_TRY(agg2.alloc(n0 + 1));
+      for (int pass = 0; pass < 2; ++pass) {
+        k_join_agg<<<stride_grid(n0, 256), 256, 0, s>>>(n0, A.w, A.col, A.val, act, ppe, L->agg, agg2);
+        FVS_COUNT_LAUNCH();
+        FVS_CUDA(cudaMemcpyAsync(L->agg.p, agg2.p, n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      }
+    }
     k_dirty_up<<<stride_grid(n0, 256), 256, 0, s>>>(n0, L->agg, L->dirty, lv[1]->dirty); FVS_COUNT_LAUNCH();
-    k_mask_agg<<<stride_grid(n0, 256), 256, 0, s>>>(n0, act, ppe, L->agg, err); FVS_COUNT_LAUNCH();
+    k_mask_agg<<<stride_grid(n0, 256), 256, 0, s>>>(n0, act, ppe, L->agg); FVS_COUNT_LAUNCH();
     DBuf<int32_t> mc;
     FVS_TRY(mc.alloc(nc + 1));
     FVS_TRY(mc.zero(s));
@@ -1506,7 +1611,8 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
   }
   tick(0);
   // Galerkin rows of the dirty aggregates, level by level on the kept
-  // aggregation; rows can only lose entries, so the widths still hold (checked)
+  // aggregation; a coarse row that no longer fits its level's width (a row
+  // that joined an aggregate brought new couplings) flags a new setup
   for (size_t l = 0; l < lv.size(); ++l) {
     AmgLevel* L = lv[l].get();
     const Ell* cur = L->A;
@@ -1545,6 +1651,33 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
   tick(2);
   if (n0 > 0) {
     k_mask_labels<<<stride_grid(n0, 256), 256, 0, s>>>(n0, act, ppe, fine_lab); FVS_COUNT_LAUNCH();
+    // rows that carry pressure again take the label of the rows they couple
+    // to (a few passes for chains of such rows); a row between two parts, or
+    // one left without a label, needs a new setup
+    const Ell& A = *lv[0]->A;
+    DBuf<int32_t> lab2;
+    FVS_TRY(lab2.alloc(n0 + 1));
+    int left = 0;
+    for (int pass = 0; pass < 4; ++pass) {
+      FVS_TRY(cnt2.zero(s));
+      k_adopt_labels<<<stride_grid(n0, 256), 256, 0, s>>>(n0, A.w, A.col, A.val, act, ppe, fine_lab, lab2, cnt2,
+                                                          err);
+      FVS_COUNT_LAUNCH();
+      FVS_CUDA(cudaMemcpyAsync(fine_lab.p, lab2.p, n0 * sizeof(int32_t), cudaMemcpyDeviceToDevice, s));
+      int h[2] = {0, 0};
+      FVS_CUDA(cudaMemcpyAsync(h, cnt2.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+      FVS_CUDA(cudaStreamSynchronize(s));
+      left = h[0];
+      if (left == 0 || h[1] == 0) break;   // done, or no progress
+    }
+    // rows labelled in the same pass from different sides may now couple two parts
+    k_label_conflicts<<<stride_grid(n0, 256), 256, 0, s>>>(n0, A.w, A.col, A.val, fine_lab, err); FVS_COUNT_LAUNCH();
+    int e = 0;
+    FVS_TRY(read_int(s, err, &e));
+    if (e || left) {
+      set_error("AMG refresh: rows carrying pressure again need a new setup (flags 0x%x, %d unlabelled)", e, left);
+      return FVS_ERR_NOT_CONVERGED;
+    }
     FVS_TRY(ccnt.zero(s));
     k_comp_count<<<stride_grid(n0, 256), 256, 0, s>>>(n0, fine_lab, ccnt); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
@@ -1614,10 +1747,6 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
   const char* n_jac0 = f32 ? (cl ? "jacobi0_f32_coarse" : "jacobi0_f32") : (cl ? "jacobi0_coarse" : "jacobi0");
   const char* n_jac = f32 ? (cl ? "jacobi_f32_coarse" : "jacobi_f32") : (cl ? "jacobi_coarse" : "jacobi");
   const char* n_res = f32 ? (cl ? "residual_f32_coarse" : "residual_f32") : (cl ? "residual_vc_coarse" : "residual_vc");
-  {
-    ProfScope ps(pkey, n_jac0, 3.0 * vb * (double)n, s);
-    k_jac0<T><<<g, 256, 0, s>>>(n, (T)opt.omega, dinv, b, xa); FVS_COUNT_LAUNCH();
-  }
   const int gg = stride_grid(n * CG, 256);   // coarse levels: CG lanes per row
   auto jac = [&](T* xin, T* xout) {
     ProfScope ps(pkey, n_jac, jac_bytes, s);
@@ -1625,6 +1754,10 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
     else k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xin, xout);
     FVS_COUNT_LAUNCH();
   };
+  {
+    ProfScope ps(pkey, n_jac0, 3.0 * vb * (double)n, s);
+    k_jac0<T><<<g, 256, 0, s>>>(n, (T)opt.omega, dinv, b, xa); FVS_COUNT_LAUNCH();
+  }
   for (int k = 1; k < opt.npre; ++k) {
     jac(xa, xb);
     T* t = xa; xa = xb; xb = t;

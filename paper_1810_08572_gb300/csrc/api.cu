@@ -303,6 +303,7 @@ FVS_API fvs_status fvs_profile_enable(fvs_solver s, int on) {
   s->prof.reset();
   s->prof.on = on != 0;
   s->prof.label(&s->K, "pressure");
+  s->prof.label(&s->Kp, "pressure");   // the V-cycle on the compact operator
   s->prof.label(&s->Ke, "energy");
   s->prof.label(&s->M, "momentum");
   return FVS_OK;

@@ -98,15 +98,38 @@ __global__ void __launch_bounds__(128, 1) k_mlp_gemm_tc(int M, int N, int K, con
   bool ok = true;
   for (int k0 = 0; k0 < K && ok; k0 += TC_KC) {
     const int kc = min(TC_KC, K - k0);
-    // stage A(m, k) and B(n, k); the index that is contiguous in memory runs fastest
-    for (int t = tid; t < 128 * kc; t += 128) {
-      const int r = ak == 1 ? t / kc : t % 128, k = ak == 1 ? t % kc : t / 128;
-      const int m = m0 + r;
-      *(bf16*)(sa + tc_off(r, k)) = m < M ? A[(int64_t)m * am + (int64_t)(k0 + k) * ak] : zero;
+    // stage A(m, k) and B(n, k).  Rows contiguous in k go as 16-byte core
+    // matrix rows (eight consecutive threads take the eight rows of one core
+    // matrix: one 128-byte shared-memory wavefront, no bank conflicts);
+    // otherwise element by element with the index that is contiguous in
+    // memory running fastest.
+    const int nch = kc >> 3;
+    if (ak == 1 && (am & 7) == 0) {
+      for (int t = tid; t < 128 * nch; t += 128) {
+        const int q = t >> 3, ch = q % nch, r = (q / nch) * 8 + (t & 7);
+        const int m = m0 + r;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (m < M) v = *reinterpret_cast<const uint4*>(A + (int64_t)m * am + k0 + ch * 8);
+        *reinterpret_cast<uint4*>(sa + tc_off(r, ch * 8)) = v;
+      }
+    } else {
+      for (int t = tid; t < 128 * kc; t += 128) {
+        const int r = ak == 1 ? t / kc : t % 128, k = ak == 1 ? t % kc : t / 128;
+        const int m = m0 + r;
+        *(bf16*)(sa + tc_off(r, k)) = m < M ? A[(int64_t)m * am + (int64_t)(k0 + k) * ak] : zero;
+      }
     }
-    for (int t = tid; t < N * kc; t += 128) {
-      const int r = bk == 1 ? t / kc : t % N, k = bk == 1 ? t % kc : t / N;
-      *(bf16*)(sb + tc_off(r, k)) = B[(int64_t)r * bn + (int64_t)(k0 + k) * bk];
+    if (bk == 1 && (bn & 7) == 0) {
+      for (int t = tid; t < N * nch; t += 128) {
+        const int q = t >> 3, ch = q % nch, r = (q / nch) * 8 + (t & 7);
+        *reinterpret_cast<uint4*>(sb + tc_off(r, ch * 8)) =
+            *reinterpret_cast<const uint4*>(B + (int64_t)r * bn + k0 + ch * 8);
+      }
+    } else {
+      for (int t = tid; t < N * kc; t += 128) {
+        const int r = bk == 1 ? t / kc : t % N, k = bk == 1 ? t % kc : t / N;
+        *(bf16*)(sb + tc_off(r, k)) = B[(int64_t)r * bn + (int64_t)(k0 + k) * bk];
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
@@ -143,10 +166,48 @@ __global__ void __launch_bounds__(128, 1) k_mlp_gemm_tc(int M, int N, int K, con
           : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
       if (m >= M) continue;
+      const int64_t o0 = (int64_t)m * e.ldo + c0;
+      if ((e.ldo & 7) == 0) {
+        // a lane's 16 columns as 16-byte vectors (row offsets are multiples of 8 elements)
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+        if (EPI == EPI_GELU || EPI == EPI_LINEAR) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] += e.bias[c0 + j];
+        }
+        if (EPI == EPI_DGRAD) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4) {
+            const float4 z = *reinterpret_cast<const float4*>(e.z + o0 + j);
+            v[j] *= gelu_grad(z.x); v[j + 1] *= gelu_grad(z.y); v[j + 2] *= gelu_grad(z.z); v[j + 3] *= gelu_grad(z.w);
+          }
+        }
+        float* f32out = EPI == EPI_GELU ? e.z : e.fout;
+        if ((EPI == EPI_LINEAR || EPI == EPI_WGRAD || EPI == EPI_GELU) && f32out) {
+#pragma unroll
+          for (int j = 0; j < 16; j += 4)
+            *reinterpret_cast<float4*>(f32out + o0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+        }
+        if (EPI == EPI_GELU || EPI == EPI_DGRAD) {
+          uint32_t h[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float a = EPI == EPI_GELU ? gelu(v[2 * j]) : v[2 * j];
+            const float b = EPI == EPI_GELU ? gelu(v[2 * j + 1]) : v[2 * j + 1];
+            const __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
+            h[j] = *reinterpret_cast<const uint32_t*>(&hb);
+          }
+          uint4* dst = reinterpret_cast<uint4*>(e.hout + o0);
+          dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+          dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+        }
+        continue;
+      }
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const int n = c0 + j;
-        const int64_t o = (int64_t)m * e.ldo + n;
+        const int64_t o = o0 + j;
         float v = __uint_as_float(r[j]);
         if (EPI == EPI_GELU) {
           v += e.bias[n];

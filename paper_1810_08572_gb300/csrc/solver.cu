@@ -15,6 +15,8 @@
 #include "fslaw.cuh"
 #include "solver.cuh"
 
+extern "C" const char* fvs_last_error(void);
+
 namespace fvs {
 
 #define GS(i, n) for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
@@ -62,9 +64,25 @@ __global__ void k_tag(int64_t Nc, const double* T, double Ts, uint8_t* lm, int32
   if (dead) atomicAdd(counts + 3, dead);
   if (nlm) atomicAdd(counts + 4, nlm);
 }
-__global__ void k_compact(int64_t Nc, const uint8_t* lm, const int32_t* excl, int32_t* map, int32_t* act) {
+// a numbering also takes the metal cells across a face from an LM cell: a
+// solid cell at the front that melts again then already has a row (an
+// identity row until it carries pressure) and the numbering and the AMG
+// hierarchy built for it stay in use
+__global__ void k_margin(int64_t Nc, const int32_t* cf, const int32_t* own, const int32_t* nei, const uint8_t* lm,
+                         const uint8_t* metal, int32_t* flag) {
   GS(c, Nc) {
-    if (lm[c]) {
+    if (lm[c] || !metal[c]) continue;
+    for (int s = 0; s < 6; ++s) {
+      const int32_t f = cf[s * Nc + c];
+      const int32_t o = own[f], q = nei[f];
+      const int32_t j = o == c ? q : o;
+      if (j >= 0 && lm[j]) { flag[c] = 1; break; }
+    }
+  }
+}
+__global__ void k_compact(int64_t Nc, const int32_t* flag, const int32_t* excl, int32_t* map, int32_t* act) {
+  GS(c, Nc) {
+    if (flag[c]) {
       map[c] = excl[c];
       act[excl[c]] = (int32_t)c;
     } else {
@@ -329,6 +347,48 @@ __global__ void k_ppe_matrix(PpeCtx x, int32_t* col, double* val, double* diag, 
       val[(int64_t)k * x.nact + r] = v;
     }
     diag[r] = dg;
+  }
+}
+
+// Operator the pressure preconditioner is built on: each row of K keeps its
+// diagonal and its couplings to the cells across its six faces; the
+// couplings that the vertex interpolation of the non-orthogonal face
+// gradients adds (the other 20 of a 27-point row) are lumped into the
+// diagonal.  Row sums are unchanged, so every liquid pocket keeps the
+// constant as its null vector.  Slot 0 holds the diagonal, slot 1 + s the
+// neighbour across face s (the row itself with a zero where there is none).
+__global__ void k_ppe_compact(int64_t nact, int64_t Nc, int W, const int32_t* act, const int32_t* map,
+                              const uint8_t* ppe, const int32_t* cf, const int32_t* own, const int32_t* nei,
+                              const int32_t* col, const double* val, int32_t* ccol, double* cval, double* cdiag) {
+  GS(r, nact) {
+    const int32_t c = act[r];
+    int32_t fcol[6];
+    double fval[6];
+    double d = 0.0;
+    for (int s = 0; s < 6; ++s) {
+      const int32_t f = cf[s * Nc + c];
+      const int32_t o = own[f], q = nei[f];
+      const int32_t j = o == c ? q : o;
+      fcol[s] = (ppe[c] && j >= 0 && map[j] >= 0 && ppe[j]) ? map[j] : -1;
+      fval[s] = 0.0;
+    }
+    for (int k = 0; k < W; ++k) {
+      const int32_t cc = col[(int64_t)k * nact + r];
+      const double v = val[(int64_t)k * nact + r];
+      int hit = -1;
+      if (cc != (int32_t)r)
+        for (int s = 0; s < 6; ++s)
+          if (hit < 0 && fcol[s] == cc) hit = s;
+      if (hit >= 0) fval[hit] += v;
+      else d += v;
+    }
+    ccol[r] = (int32_t)r;
+    cval[r] = d;
+    for (int s = 0; s < 6; ++s) {
+      ccol[(int64_t)(1 + s) * nact + r] = fcol[s] >= 0 ? fcol[s] : (int32_t)r;
+      cval[(int64_t)(1 + s) * nact + r] = fval[s];
+    }
+    cdiag[r] = d;
   }
 }
 
@@ -943,13 +1003,19 @@ static fvs_status renumber_lm(fvs_solver s) {
   fvs_mesh m = s->mesh;
   cudaStream_t st = s->stream;
   const int64_t Nc = m->Nc;
+  const char* mg = getenv("FVS_MARGIN");
+  if (!(mg && *mg == '0')) {
+    k_margin<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, m->cf, m->own, m->nei, s->lm, s->metal, s->flag);
+    FVS_COUNT_LAUNCH();
+  }
   FVS_TRY(exclusive_scan(st, s->sw, Nc + 1, s->flag, s->excl));
-  k_compact<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->lm, s->excl, s->map, s->act); FVS_COUNT_LAUNCH();
+  k_compact<<<stride_grid(Nc, 256), 256, 0, st>>>(Nc, s->flag, s->excl, s->map, s->act); FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   int32_t na = 0;
   FVS_CUDA(cudaMemcpyAsync(&na, s->excl.p + Nc, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   FVS_CUDA(cudaStreamSynchronize(st));
   s->nact = na;
+  s->nmargin = std::max<int64_t>(0, (int64_t)na - s->nlm);
   s->numbered = true;
   s->renumbered = true;
   s->k_valid = false;
@@ -970,14 +1036,16 @@ static fvs_status classify(fvs_solver s) {
   FVS_CUDA(cudaMemcpyAsync(tc, s->cnt.p, 5 * sizeof(int), cudaMemcpyDeviceToHost, st));
   FVS_CUDA(cudaStreamSynchronize(st));
   s->nlm = tc[4];
-  // The system numbering (LM cells when it was made) is kept while cells only
-  // freeze and the frozen share stays small: frozen rows become identity
-  // rows, so the AMG hierarchy built for that numbering keeps serving as the
-  // preconditioner (refreshed on its fine level).  A melted cell, a larger
-  // frozen share, or the rebuild policy renumbers.
+  // The system numbering (LM cells when it was made, and the solid metal
+  // cells across a face from them) is kept while cells freeze or the cells
+  // of that margin melt, and the frozen share stays small: rows of cells
+  // without pressure are identity rows, so the AMG hierarchy built for that
+  // numbering keeps serving as the preconditioner (refreshed).  A cell that
+  // melts outside the numbering, a larger frozen share, or the rebuild
+  // policy renumbers.
   const char* rf = getenv("FVS_REFRESH_FRACTION");   // frozen share kept on one numbering
   const double frac = (rf && *rf) ? atof(rf) : 0.01;
-  const int64_t dead_cap = std::max<int64_t>(64, (int64_t)(frac * (double)s->nact));
+  const int64_t dead_cap = std::max<int64_t>(64, (int64_t)(frac * (double)s->nact)) + s->nmargin;
   const bool renumber = !s->numbered || tc[2] > 0 || tc[3] > dead_cap || s->force_full;
   s->renumbered = false;
   if (renumber) FVS_TRY(renumber_lm(s));
@@ -1048,7 +1116,19 @@ static fvs_status assemble_pressure(fvs_solver s) {
   // (new diagonal, rows of frozen cells left out of the null-space
   // projection); otherwise build the hierarchy anew.
   const double t_matrix = dbg ? lap() : 0.0;
+  // the preconditioner's operator: K itself, or its face-coupling part
+  // (decided at each full setup; a refresh keeps the choice)
+  auto fill_compact = [&]() -> fvs_status {
+    FVS_TRY(s->Kp.alloc(s->nact, 7));
+    k_ppe_compact<<<stride_grid(s->nact, 256), 256, 0, st>>>(s->nact, m->Nc, m->W, s->act, s->map, s->ppe, m->cf,
+                                                              m->own, m->nei, s->K.col, s->K.val, s->Kp.col,
+                                                              s->Kp.val, s->Kp.diag);
+    FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
+    return FVS_OK;
+  };
   if (!s->renumbered && s->amg_ok && !s->force_full && s->nact > 0) {
+    if (s->pc_compact) FVS_TRY(fill_compact());
     const fvs_status r = s->amg.refresh(st, s->act, s->ppe);
     if (r == FVS_OK) {
       s->amg_full = false;
@@ -1056,6 +1136,7 @@ static fvs_status assemble_pressure(fvs_solver s) {
       return FVS_OK;
     }
     if (r != FVS_ERR_NOT_CONVERGED) return r;
+    if (dbg) fprintf(stderr, "[fvs step] refresh refused: %s\n", fvs_last_error());
     // the kept aggregation no longer fits: number the LM cells anew
     FVS_TRY(renumber_lm(s));
     return assemble_pressure(s);
@@ -1075,11 +1156,21 @@ static fvs_status assemble_pressure(fvs_solver s) {
     // is one matrix-vector product per V-cycle, cheaper than the several
     // latency-bound launches per level that the small levels below it cost
     s->amg.opt.coarsest = SOLVER_COARSEST;
-    fvs_status r = s->amg.setup(st, s->K);
+    // the vertex-interpolation couplings are small next to the face
+    // couplings; leaving them out of the hierarchy cuts the bytes of every
+    // V-cycle sweep (7 instead of 27 entries a fine row, narrower Galerkin
+    // rows below) while the Krylov method keeps the full K
+    const char* pc = getenv("FVS_PC_COMPACT");
+    s->pc_compact = m->W > 7 && !(pc && *pc == '0');
+    if (s->pc_compact) FVS_TRY(fill_compact());
+    fvs_status r = s->amg.setup(st, s->pc_compact ? s->Kp : s->K);
     if (r == FVS_OK) {
       s->amg_ok = true;
       s->amg_levels = s->amg.levels();
-      s->ncomp = s->amg.ncomp;
+      // liquid pockets: the singular parts (identity rows of cells without
+      // pressure are parts of their own when the whole system is one level)
+      s->ncomp = 0;
+      for (uint8_t g : s->amg.sing_host) s->ncomp += g ? 1 : 0;
     } else if (r != FVS_ERR_NOT_CONVERGED) {
       return r;
     }
@@ -1326,6 +1417,9 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
     if (!s->amg_full && s->amg_ok && r.converged &&
         r.iters > std::max(s->p_its_ref * 3 / 2, s->p_its_ref + 6))
       s->force_full = true;
+    if (getenv("FVS_DEBUG") && !s->amg_full && s->amg_ok && (!r.converged || s->force_full))
+      fprintf(stderr, "[fvs step] refreshed solve %s: %d iterations (reference %d)\n",
+              r.converged ? "slow" : "stalled", r.iters, s->p_its_ref);
     if (!s->amg_full && s->amg_ok && !r.converged) {
       const auto t0 = std::chrono::steady_clock::now();
       FVS_TRY(renumber_lm(s));

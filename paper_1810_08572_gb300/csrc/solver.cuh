@@ -81,11 +81,14 @@ struct fvs_solver_s {
   fvs::DBuf<uint8_t> lm, ppe, flow, fcase;
   fvs::DBuf<int32_t> flag, excl, map, act, nS;
   int64_t nact = 0, nppe = 0;
+  int64_t nmargin = 0;    // rows of the numbering beyond the LM cells when it was made
   fvs::ScanWork sw;
 
   // compact systems
   fvs::Ell M;             // momentum predictor on LM cells
   fvs::Ell K;             // pressure: K = -A on LM cells (identity rows for non-flowing)
+  fvs::Ell Kp;            // K's diagonal and face couplings, the rest lumped (AMG operator)
+  bool pc_compact = false;        // the hierarchy was built on Kp
   fvs::DBuf<double> mrhs, mx;     // [3*nact]
   fvs::DBuf<double> prhs, px;     // [nact]
   fvs::DBuf<double> pv, fSv;      // vertex pressure sums / solid fractions [Nv]

@@ -354,6 +354,49 @@ def test_refreshed_hierarchy_while_cells_freeze(fvs, monkeypatch, precision):
     compare(o, S, 1e-9, fields=("U", "P", "FLUX"))
 
 
+def remelt_field(m, full_band):
+    """Melt at 940 K with a two-cell solid band just below the solidus (it
+    re-melts in the first step), either across the whole mesh (two pockets
+    that merge when it melts) or across half of it (one pocket)."""
+    ijk = m["cell_ijk"]
+    nx, ny, _ = m["shape"]
+    rng = np.random.default_rng(11)
+    T = 940.0 - rng.uniform(0.0, 5.0, len(ijk))
+    band = (ijk[:, 0] >= nx // 2) & (ijk[:, 0] <= nx // 2 + 1)
+    if not full_band:
+        band &= ijk[:, 1] < ny // 2
+    T[band] = cases.AL_ALLOY["T_sol"] - 1e-3
+    return T, band
+
+
+@pytest.mark.parametrize("full_band", [False, True])
+def test_margin_cells_that_melt(fvs, full_band):
+    """The numbering also holds the solid cells across a face from the melt.
+    When they melt (here a band just below the solidus, heated from both
+    sides) their rows join the aggregates of their neighbours and the
+    hierarchy is refreshed, not rebuilt (p_rebuilt == 2), unless they join
+    two pockets: then the labels conflict and the step rebuilds
+    (p_rebuilt == 1).  Both against the oracle at 1e-10."""
+    m = box_mesh(24, 24, 4, cases.CAVITY, jitter=0.2, jitter_seed=71, permute_seed=72)
+    T0, band = remelt_field(m, full_band)
+    props = cases.props(**TIGHT)
+    o, M, S = make_pair(fvs, m, props, T0)
+    st = S.step(1e-3)
+    o.step(1e-3)
+    assert st["p_rebuilt"] == 1 and st["n_components"] == (2 if full_band else 1)
+    assert (S.query("T")[band] > cases.AL_ALLOY["T_sol"]).all()
+    st = S.step(1e-3)
+    o.step(1e-3)
+    assert st["p_rebuilt"] == (1 if full_band else 2), st["p_rebuilt"]
+    assert st["n_components"] == 1 and st["p_relres"] <= 1e-12
+    compare(o, S, 1e-10)
+    for _ in range(3):
+        st = S.step(1e-3)
+        o.step(1e-3)
+        assert st["p_relres"] <= 1e-12
+    compare(o, S, 1e-10)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_graph_replayed_iterations_on_a_stream(fvs, precision):
     """On a non-default stream the Krylov iterations are captured once and
