@@ -98,7 +98,7 @@ fvs_status fvs_mesh_set_zones(fvs_mesh mesh, const int32_t* zone);
 
 typedef struct {
   int64_t n_cells, n_faces, n_nodes, n_interior_faces;
-  int32_t max_cell_neighbours; /* width of the vertex-neighbour stencil       */
+  int32_t max_cell_neighbours; /* stencil width: cells sharing a vertex (27), or a face (7) on orthogonal meshes */
   int32_t max_face_neighbours; /* largest neighbour set N(f) of a face        */
   int32_t n_patches;           /* 1 + largest patch id                        */
   int32_t orthogonal;          /* 1 if no face carries cross diffusion        */

@@ -1018,8 +1018,21 @@ __global__ void k_comp_count(int64_t n, const int32_t* lab, double* cnt) {
     if (c >= 0 && (int)(threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&cnt[c], (double)__popc(peers));
   }
 }
+// per-part sums; a warp whose rows all lie in one part adds once
 __global__ void k_comp_sum(int64_t n, const int32_t* lab, const double* v, double* s) {
-  GS(i, n) if (lab[i] >= 0) atomicAdd(&s[lab[i]], v[i]);
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = b + threadIdx.x;
+    const int32_t c = i < n ? lab[i] : -1;
+    double x = c >= 0 ? v[i] : 0.0;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    if (peers == 0xffffffffu) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if ((threadIdx.x & 31) == 0 && c >= 0) atomicAdd(&s[c], x);
+    } else if (c >= 0) {
+      atomicAdd(&s[c], x);
+    }
+  }
 }
 __global__ void k_comp_sub(int64_t n, const int32_t* lab, const uint8_t* sing, const double* s, const double* cnt,
                            double* v) {
@@ -1030,10 +1043,14 @@ __global__ void k_comp_sub(int64_t n, const int32_t* lab, const uint8_t* sing, c
 }
 // single component: deterministic mean via block partials (lab, when given,
 // masks rows out; cnt_dev, when given, holds the row count)
-__global__ void k_sum_part(int64_t n, const double* v, const int32_t* lab, double* part) {
+// (want >= 0: only the rows labelled want)
+__device__ __forceinline__ bool in_part(const int32_t* lab, int want, int64_t i) {
+  return !lab || (want < 0 ? lab[i] >= 0 : lab[i] == want);
+}
+__global__ void k_sum_part(int64_t n, const double* v, const int32_t* lab, int want, double* part) {
   __shared__ double sh[32];
   double a = 0.0;
-  GS(i, n) if (!lab || lab[i] >= 0) a += v[i];
+  GS(i, n) if (in_part(lab, want, i)) a += v[i];
   a = block_sum(a, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = a;
 }
@@ -1047,9 +1064,9 @@ __global__ void k_mean_final(int nb, const double* part, double cnt, const doubl
     *mean = c > 0.0 ? a / c : 0.0;
   }
 }
-__global__ void k_sub_scalar(int64_t n, const double* mean, const int32_t* lab, double* v) {
+__global__ void k_sub_scalar(int64_t n, const double* mean, const int32_t* lab, int want, double* v) {
   const double m = *mean;
-  GS(i, n) if (!lab || lab[i] >= 0) v[i] -= m;
+  GS(i, n) if (in_part(lab, want, i)) v[i] -= m;
 }
 // refresh: rows whose cells no longer carry pressure leave the null-space labels
 __global__ void k_mask_labels(int64_t n, const int32_t* act, const uint8_t* ppe, int32_t* lab) {
@@ -1695,14 +1712,20 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
 fvs_status Amg::project(cudaStream_t s, double* v) {
   const int64_t n = lv[0]->n;
   if (n == 0 || ncomp == 0) return FVS_OK;
-  if (ncomp == 1) {
-    if (!sing_host[0]) return FVS_OK;
+  int nsing = 0, first = -1;
+  for (int c = 0; c < ncomp; ++c)
+    if (sing_host[c]) { ++nsing; if (first < 0) first = c; }
+  if (nsing == 0) return FVS_OK;
+  if (nsing == 1) {
+    // one singular part (the usual case; the other parts, if any, are rows
+    // without pressure): deterministic mean through block partials
     const int nb = std::min(1024, 2 * sm_count());
-    const int32_t* mask = masked ? fine_lab.p : nullptr;
-    k_sum_part<<<nb, 256, 0, s>>>(n, v, mask, cpart); FVS_COUNT_LAUNCH();
-    k_mean_final<<<1, 1024, 0, s>>>(nb, cpart, (double)n, masked ? ccnt.p : nullptr, cpart.p + 1024);
+    const int32_t* mask = (masked || ncomp > 1) ? fine_lab.p : nullptr;
+    const int want = ncomp > 1 ? first : -1;
+    k_sum_part<<<nb, 256, 0, s>>>(n, v, mask, want, cpart); FVS_COUNT_LAUNCH();
+    k_mean_final<<<1, 1024, 0, s>>>(nb, cpart, (double)n, mask ? ccnt.p + first : nullptr, cpart.p + 1024);
     FVS_COUNT_LAUNCH();
-    k_sub_scalar<<<stride_grid(n, 256), 256, 0, s>>>(n, cpart.p + 1024, mask, v); FVS_COUNT_LAUNCH();
+    k_sub_scalar<<<stride_grid(n, 256), 256, 0, s>>>(n, cpart.p + 1024, mask, want, v); FVS_COUNT_LAUNCH();
     FVS_LAUNCH_CHECK();
     return FVS_OK;
   }

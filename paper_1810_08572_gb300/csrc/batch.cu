@@ -1575,7 +1575,8 @@ __global__ void kb_ppe_rows(BPpe x, int32_t* ovr, double* mval, double* dinv, in
           const int32_t j = x.fnb[(int64_t)k * x.Nf + f];
           if (!x.ppe[(int64_t)j * x.Sp + s]) continue;
           const int p = find_sorted(nbl, 1, nn, j);
-          if (p >= 0) acc[p] += add; else atomicOr(err, 2);
+          if (p >= 0) acc[p] += add;
+          else if (add != 0.0) atomicOr(err, 2);   // a zero share may miss a face-only stencil
         }
       }
     }

@@ -234,6 +234,32 @@ __global__ void k_cell_nb(int64_t Nc, const int32_t* cn, const int32_t* ptr, con
     if (nb) for (int k = 0; k < W; ++k) nb[k * Nc + c] = k < n ? buf[k] : buf[0];
   }
 }
+// face-neighbour stencil of an orthogonal mesh: the cell and the cells across
+// its faces, sorted (every cross-diffusion weight is zero there, so no
+// coefficient reaches a cell that shares only an edge or a vertex)
+__global__ void k_cell_nb_faces(int64_t Nc, const int32_t* cf, const int32_t* own, const int32_t* nei, int W,
+                                int32_t* nb, int32_t* nnb) {
+  GS(c, Nc) {
+    int32_t buf[7];
+    int n = 1;
+    buf[0] = (int32_t)c;
+    for (int s = 0; s < 6; ++s) {
+      const int32_t f = cf[s * Nc + c];
+      const int32_t o = own[f], q = nei[f];
+      const int32_t j = o == (int32_t)c ? q : o;
+      if (j < 0) continue;
+      bool dup = false;
+      for (int k = 0; k < n; ++k) dup |= buf[k] == j;
+      if (!dup) buf[n++] = j;
+    }
+    for (int a = 1; a < n; ++a)
+      for (int b = a; b > 0 && buf[b - 1] > buf[b]; --b) {
+        const int32_t t = buf[b]; buf[b] = buf[b - 1]; buf[b - 1] = t;
+      }
+    nnb[c] = n;
+    if (nb) for (int k = 0; k < W; ++k) nb[k * Nc + c] = k < n ? buf[k] : buf[0];
+  }
+}
 __global__ void k_face_nb(int64_t Nf, const int32_t* fv, const int32_t* ptr, const int32_t* idx, int WF,
                           int32_t* fnb, int32_t* nfnb, int* err) {
   int32_t buf[FVS_MAX_FNB];
@@ -693,6 +719,28 @@ fvs_status mesh_build(fvs_mesh m, const double* nodes, int64_t Nv, const int32_t
     FVS_TRY(red.fetch(s));
     m->total_volume = red.host[S_TMP0];
     m->orthogonal = red.host[S_TMP1] < 1e-10 ? 1 : 0;
+  }
+  const char* full_st = getenv("FVS_FULL_STENCIL");   // keep the vertex-neighbour stencil
+  if (m->orthogonal && !(full_st && *full_st && *full_st != '0')) {
+    // orthogonal mesh: the cross-diffusion weights vanish, so every operator
+    // couples a cell to the cells across its faces only.  The stencil drops
+    // to those (7 slots instead of 27: a quarter of the bytes and FMAs of
+    // every operator row) and the weights are set to exact zeros.
+    FVS_TRY(m->ce.zero(s));
+    FVS_TRY(m->cz.zero(s));
+    FVS_TRY(mx.zero(s));
+    k_cell_nb_faces<<<stride_grid(Nc, 256), 256, 0, s>>>(Nc, m->cf, m->own, m->nei, 0, nullptr, m->nnb);
+    FVS_COUNT_LAUNCH();
+    k_max_i32<<<stride_grid(Nc, 256), 256, 0, s>>>(Nc, m->nnb, mx.p); FVS_COUNT_LAUNCH();
+    int w = 0;
+    FVS_CUDA(cudaMemcpyAsync(&w, mx.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FVS_CUDA(cudaStreamSynchronize(s));
+    m->W = w;
+    m->nb.release();
+    FVS_TRY(m->nb.alloc((size_t)m->W * Nc));
+    k_cell_nb_faces<<<stride_grid(Nc, 256), 256, 0, s>>>(Nc, m->cf, m->own, m->nei, m->W, m->nb, m->nnb);
+    FVS_COUNT_LAUNCH();
+    FVS_LAUNCH_CHECK();
   }
   // counts
   {

@@ -327,7 +327,8 @@ __global__ void k_ppe_matrix(PpeCtx x, int32_t* col, double* val, double* diag, 
           const int32_t j = x.fnb[(int64_t)k * x.Nf + f];
           if (!x.ppe[j]) continue;
           const int p = find_sorted(nbl, 1, nn, j);
-          if (p >= 0) acc[p] += add; else atomicOr(err, 2);
+          if (p >= 0) acc[p] += add;
+          else if (add != 0.0) atomicOr(err, 2);   // a zero share may miss a face-only stencil
         }
       }
     }
