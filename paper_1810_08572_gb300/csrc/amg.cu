@@ -729,37 +729,55 @@ __global__ void __launch_bounds__(1024) k_coarsest_smem(int n, int w, const int3
   for (int i = threadIdx.x; i < n; i += blockDim.x)
     for (int k = 0; k < w; ++k) M[i * n + col[(int64_t)k * n + i]] += val[((int64_t)k * n + i) * vs + smp];
   __syncthreads();
-  if (threadIdx.x == 0) {
-    // connected parts (breadth-first over the symmetric pattern), queue in 'order'
-    for (int i = 0; i < n; ++i) lb[i] = -1;
-    int nc = 0;
-    for (int s0 = 0; s0 < n; ++s0) {
-      if (lb[s0] >= 0) continue;
-      int qh = 0, qt = 0;
-      order[qt++] = s0;
-      lb[s0] = nc;
-      while (qh < qt) {
-        const int i = order[qh++];
-        for (int j = 0; j < n; ++j)
-          if (lb[j] < 0 && (M[i * n + j] != 0.0 || M[j * n + i] != 0.0)) {
-            lb[j] = nc;
-            order[qt++] = j;
-          }
-      }
-      ++nc;
+  // connected parts of the symmetric pattern: every row starts with its own
+  // index as label and takes the smallest label among the rows it couples
+  // to, one warp per row, until no label changes (at most n rounds)
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) lb[i] = i;
+  __syncthreads();
+  for (int round = 0; round < n; ++round) {
+    if (threadIdx.x == 0) ncs = 0;
+    __syncthreads();
+    for (int i = wid; i < n; i += nwarp) {
+      int m = lb[i];
+      for (int j = lane; j < n; j += 32)
+        if (M[i * n + j] != 0.0 || M[j * n + i] != 0.0) m = min(m, lb[j]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = min(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane == 0 && m < lb[i]) { lb[i] = m; ncs = 1; }
     }
+    __syncthreads();
+    const int changed = ncs;
+    __syncthreads();
+    if (!changed) break;
+  }
+  // row sums and diagonals for the singular test
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double rs = 0.0;
+    for (int j = 0; j < n; ++j) rs += M[i * n + j];
+    fac[i] = rs;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // parts numbered by their smallest row; a singular part (zero row sums)
+    // pins its first row
+    int nc = 0;
+    for (int i = 0; i < n; ++i) {
+      if (lb[i] == i) perm[i] = nc++;
+    }
+    for (int i = 0; i < n; ++i) lb[i] = perm[lb[i]];
     for (int c = 0; c < nc; ++c) {
       double rs = 0.0, sc = 0.0;
       int first = -1;
       for (int i = 0; i < n; ++i) {
         if (lb[i] != c) continue;
         if (first < 0) first = i;
-        for (int j = 0; j < n; ++j) rs += M[i * n + j];
+        rs += fac[i];
         sc += fabs(M[i * n + i]);
       }
-      const bool s = fabs(rs) <= 1e-9 * sc;
-      sg[c] = s ? 1 : 0;
-      if (s) {
+      const bool sgl = fabs(rs) <= 1e-9 * sc;
+      sg[c] = sgl ? 1 : 0;
+      if (sgl) {
         for (int j = 0; j < n; ++j) M[first * n + j] = 0.0;
         M[first * n + first] = 1.0;
       }
@@ -772,18 +790,27 @@ __global__ void __launch_bounds__(1024) k_coarsest_smem(int n, int w, const int3
     ncomp_out[smp] = nc;
   }
   __syncthreads();
-  // in-place Gauss-Jordan with partial (row) pivoting
+  // in-place Gauss-Jordan with partial (row) pivoting; the pivot search is
+  // one warp's, the update a 32 x 32 tiling of the matrix
   for (int k = 0; k < n; ++k) {
-    if (threadIdx.x == 0) {
+    if (wid == 0) {
       int p = k;
-      double best = fabs(M[k * n + k]);
-      for (int i = k + 1; i < n; ++i) {
+      double best = -1.0;
+      for (int i = k + lane; i < n; i += 32) {
         const double a = fabs(M[i * n + k]);
         if (a > best) { best = a; p = i; }
       }
-      piv = p;
-      perm[k] = p;
-      pval = best;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (ob > best || (ob == best && op < p)) { best = ob; p = op; }
+      }
+      if (lane == 0) {
+        piv = p;
+        perm[k] = p;
+        pval = best;
+      }
     }
     __syncthreads();
     if (!(pval > 1e-300)) {
@@ -805,9 +832,10 @@ __global__ void __launch_bounds__(1024) k_coarsest_smem(int n, int w, const int3
     for (int i = threadIdx.x; i < n; i += blockDim.x)
       if (i != k) M[i * n + k] = 0.0;
     __syncthreads();
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int i = e / n, j = e - i * n;
-      if (i != k) M[e] -= fac[i] * M[k * n + j];
+    for (int i = wid; i < n; i += nwarp) {
+      if (i == k) continue;
+      const double f = fac[i];
+      for (int j = lane; j < n; j += 32) M[i * n + j] -= f * M[k * n + j];
     }
     __syncthreads();
   }
@@ -905,22 +933,21 @@ __global__ void k_resid(int64_t n, int w, const int32_t* __restrict__ col, const
   }
 }
 
-// Coarse levels, CG lanes per row: lane q of a row sums the stored entries
-// q, q + CG, q + 2 CG, ... (four loads in flight), then the row's lanes add
-// their partial sums by shuffles.  The 32 / CG rows of a warp are
-// consecutive, so with slot-major storage every slot's values and columns of
-// those rows fill whole 32-byte sectors, rows of uneven length idle fewer
-// lanes than one thread per row does, and short serial chains keep the small
-// levels (latency-bound) from waiting on one gather after another.
-constexpr int CG = 4;
-template <typename T, class X>
+// Coarse levels, G lanes per row (1, 2 or 4; two unless a level's rows are
+// very short): lane q of a row sums the stored entries q, q + G,
+// q + 2G, ... (four loads in flight), then the row's lanes add their partial
+// sums by shuffles.  The 32 / G rows of a warp are consecutive, so with
+// slot-major storage every slot's values and columns of those rows fill
+// whole 32-byte sectors; several lanes per row idle fewer lanes on rows of
+// uneven length and shorten the serial chain of gathers on wide rows.
+template <typename T, int G, class X>
 __device__ __forceinline__ T coarse_part(int64_t n, const int32_t* __restrict__ col, const T* __restrict__ val,
                                          const X& x, int len, int64_t i, int q) {
   T acc = 0;
   int k = q;
-  for (; k + 3 * CG < len; k += 4 * CG) {
-    const int64_t e0 = (int64_t)k * n + i, e1 = e0 + (int64_t)CG * n, e2 = e1 + (int64_t)CG * n,
-                  e3 = e2 + (int64_t)CG * n;
+  for (; k + 3 * G < len; k += 4 * G) {
+    const int64_t e0 = (int64_t)k * n + i, e1 = e0 + (int64_t)G * n, e2 = e1 + (int64_t)G * n,
+                  e3 = e2 + (int64_t)G * n;
     const int32_t c0 = col[e0], c1 = col[e1], c2 = col[e2], c3 = col[e3];
     const T v0 = val[e0], v1 = val[e1], v2 = val[e2], v3 = val[e3];
     const T x0 = x(c0), x1 = x(c1), x2 = x(c2), x3 = x(c3);
@@ -929,7 +956,7 @@ __device__ __forceinline__ T coarse_part(int64_t n, const int32_t* __restrict__ 
     acc = fma(v2, x2, acc);
     acc = fma(v3, x3, acc);
   }
-  for (; k < len; k += CG) {
+  for (; k < len; k += G) {
     const int64_t e = (int64_t)k * n + i;
     acc = fma(val[e], x(col[e]), acc);
   }
@@ -941,43 +968,57 @@ struct XVec {
   const T* __restrict__ x;
   __device__ __forceinline__ T operator()(int32_t c) const { return x[c]; }
 };
-template <typename T>
+template <typename T, int G>
 __device__ __forceinline__ T lanes_sum(T v) {
 #pragma unroll
-  for (int o = 1; o < CG; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 1; o < G; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 // r = b - A x on a coarse level (warp-uniform loop over groups of rows)
-template <typename T>
+template <typename T, int G>
 __global__ void k_resid_g(int64_t n, const int32_t* __restrict__ col, const T* __restrict__ val,
                           const T* __restrict__ x, const T* __restrict__ b, T* __restrict__ r,
                           const int32_t* __restrict__ rlen) {
-  const int lane = threadIdx.x & 31, q = lane & (CG - 1);
+  const int lane = threadIdx.x & 31, q = lane & (G - 1);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i0 = warp * (32 / CG); i0 < n; i0 += nw * (32 / CG)) {
-    const int64_t i = i0 + lane / CG;
+  for (int64_t i0 = warp * (32 / G); i0 < n; i0 += nw * (32 / G)) {
+    const int64_t i = i0 + lane / G;
     const bool ok = i < n;
-    T acc = ok ? coarse_part(n, col, val, XVec<T>{x}, rlen[i], i, q) : (T)0;
-    acc = lanes_sum(acc);
+    T acc = ok ? coarse_part<T, G>(n, col, val, XVec<T>{x}, rlen[i], i, q) : (T)0;
+    acc = lanes_sum<T, G>(acc);
     if (ok && q == 0) r[i] = b[i] - acc;
   }
 }
 // y = x + omega D^-1 (b - A x) on a coarse level
-template <typename T>
+template <typename T, int G>
 __global__ void k_jac_g(int64_t n, const int32_t* __restrict__ col, const T* __restrict__ val, T omega,
                         const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
                         T* __restrict__ y, const int32_t* __restrict__ rlen) {
-  const int lane = threadIdx.x & 31, q = lane & (CG - 1);
+  const int lane = threadIdx.x & 31, q = lane & (G - 1);
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t i0 = warp * (32 / CG); i0 < n; i0 += nw * (32 / CG)) {
-    const int64_t i = i0 + lane / CG;
+  for (int64_t i0 = warp * (32 / G); i0 < n; i0 += nw * (32 / G)) {
+    const int64_t i = i0 + lane / G;
     const bool ok = i < n;
-    T acc = ok ? coarse_part(n, col, val, XVec<T>{x}, rlen[i], i, q) : (T)0;
-    acc = lanes_sum(acc);
+    T acc = ok ? coarse_part<T, G>(n, col, val, XVec<T>{x}, rlen[i], i, q) : (T)0;
+    acc = lanes_sum<T, G>(acc);
     if (ok && q == 0) y[i] = x[i] + omega * dinv[i] * (b[i] - acc);
   }
+}
+// lanes per row of a coarse level from its mean stored row length
+// (FVS_AMG_LANES forces one count)
+static int coarse_lanes(const AmgLevel& L) {
+  static const int forced = [] {
+    const char* e = getenv("FVS_AMG_LANES");
+    const int v = e ? atoi(e) : 0;
+    return (v == 1 || v == 2 || v == 4) ? v : 0;
+  }();
+  if (forced) return forced;
+  // two lanes measured fastest on every coarse level of the 128^3 cavity
+  // (mean stored lengths 12-33; one lane: +3 %, four lanes: +4 % step time)
+  const double mean = L.n > 0 ? L.stored / (double)L.n : 0.0;
+  return mean < 6.0 ? 1 : 2;
 }
 
 template <typename T>
@@ -1770,11 +1811,14 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
   const char* n_jac0 = f32 ? (cl ? "jacobi0_f32_coarse" : "jacobi0_f32") : (cl ? "jacobi0_coarse" : "jacobi0");
   const char* n_jac = f32 ? (cl ? "jacobi_f32_coarse" : "jacobi_f32") : (cl ? "jacobi_coarse" : "jacobi");
   const char* n_res = f32 ? (cl ? "residual_f32_coarse" : "residual_f32") : (cl ? "residual_vc_coarse" : "residual_vc");
-  const int gg = stride_grid(n * CG, 256);   // coarse levels: CG lanes per row
+  const int G = rl ? coarse_lanes(*L) : 1;   // coarse levels: G lanes per row
+  const int gg = stride_grid(n * G, 256);
   auto jac = [&](T* xin, T* xout) {
     ProfScope ps(pkey, n_jac, jac_bytes, s);
-    if (rl) k_jac_g<T><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
-    else k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xin, xout);
+    if (!rl) k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xin, xout);
+    else if (G == 1) k_jac_g<T, 1><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
+    else if (G == 2) k_jac_g<T, 2><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
+    else k_jac_g<T, 4><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
     FVS_COUNT_LAUNCH();
   };
   {
@@ -1787,8 +1831,10 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
   }
   {
     ProfScope ps(pkey, n_res, res_bytes, s);
-    if (rl) k_resid_g<T><<<gg, 256, 0, s>>>(n, A.col, val, xa, b, r, rl);
-    else k_resid<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, xa, b, r);
+    if (!rl) k_resid<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, xa, b, r);
+    else if (G == 1) k_resid_g<T, 1><<<gg, 256, 0, s>>>(n, A.col, val, xa, b, r, rl);
+    else if (G == 2) k_resid_g<T, 2><<<gg, 256, 0, s>>>(n, A.col, val, xa, b, r, rl);
+    else k_resid_g<T, 4><<<gg, 256, 0, s>>>(n, A.col, val, xa, b, r, rl);
     FVS_COUNT_LAUNCH();
   }
   k_restrict<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cb); FVS_COUNT_LAUNCH();

@@ -67,8 +67,8 @@ __global__ void kb_dot2(int64_t n, int Sp, const double* a, const double* b, con
   if (threadIdx.y == 0) {
     double u = 0.0, v = 0.0;
     for (int k = 0; k < 8; ++k) { u += sh[0][k][threadIdx.x]; v += sh[1][k][threadIdx.x]; }
-    part[(int64_t)s * gridDim.x + blockIdx.x] = u;
-    part[((int64_t)Sp + s) * gridDim.x + blockIdx.x] = v;
+    part[(int64_t)blockIdx.x * Sp + s] = u;
+    part[((int64_t)gridDim.x + blockIdx.x) * Sp + s] = v;
   }
 }
 // max |a - b| and max |c - d| per sample
@@ -88,19 +88,21 @@ __global__ void kb_maxdiff2(int64_t n, int Sp, const double* a, const double* b,
   if (threadIdx.y == 0) {
     double u = 0.0, v = 0.0;
     for (int k = 0; k < 8; ++k) { u = fmax(u, sh[0][k][threadIdx.x]); v = fmax(v, sh[1][k][threadIdx.x]); }
-    part[(int64_t)s * gridDim.x + blockIdx.x] = u;
-    part[((int64_t)Sp + s) * gridDim.x + blockIdx.x] = v;
+    part[(int64_t)blockIdx.x * Sp + s] = u;
+    part[((int64_t)gridDim.x + blockIdx.x) * Sp + s] = v;
   }
 }
 // sc[slot0*Sp + s] = sum (or max) of the partials of output 0, likewise
 // slot1; block (32 samples, 8 lanes), lane y takes blocks y, y+8, ... and the
-// lanes combine in fixed order
+// lanes combine in fixed order.  Partials are stored [output][block][sample],
+// so the 32 samples of one block's partial are one coalesced load.
 __global__ void kb_final2(int nb, int Sp, const double* part, double* sc, int slot0, int slot1, int take_max) {
   __shared__ double sh[2][8][33];
   const int s = blockIdx.x * 32 + threadIdx.x;
   double u = 0.0, v = 0.0;
+#pragma unroll 4
   for (int b = threadIdx.y; b < nb; b += 8) {
-    const double pu = part[(int64_t)s * nb + b], pv = part[((int64_t)Sp + s) * nb + b];
+    const double pu = part[(int64_t)b * Sp + s], pv = part[((int64_t)nb + b) * Sp + s];
     if (take_max) { u = fmax(u, pu); v = fmax(v, pv); } else { u += pu; v += pv; }
   }
   sh[0][threadIdx.y][threadIdx.x] = u;
@@ -554,7 +556,7 @@ __global__ void kb_proj_part(int64_t n, int Sp, int nc, const int32_t* lab, cons
     for (int k = 0; k < BATCH_NCM; ++k) {
       double u = 0.0;
       for (int y = 0; y < 8; ++y) u += sh[k][y][threadIdx.x];
-      part[((int64_t)k * Sp + s) * gridDim.x + blockIdx.x] = u;
+      part[((int64_t)k * gridDim.x + blockIdx.x) * Sp + s] = u;
     }
   }
 }
@@ -565,7 +567,8 @@ __global__ void kb_proj_final(int nb, int Sp, const double* part, const double* 
     const double c = ccnt[s * BATCH_NCM + k];
     double u = 0.0;
     if (c > 0.0)
-      for (int b = threadIdx.y; b < nb; b += 8) u += part[((int64_t)k * Sp + s) * nb + b];
+#pragma unroll 4
+      for (int b = threadIdx.y; b < nb; b += 8) u += part[((int64_t)k * nb + b) * Sp + s];
     sh[threadIdx.y][threadIdx.x] = u;
     __syncthreads();
     if (threadIdx.y == 0) {
