@@ -933,8 +933,8 @@ __global__ void k_resid(int64_t n, int w, const int32_t* __restrict__ col, const
   }
 }
 
-// Coarse levels, G lanes per row (1, 2 or 4; two unless a level's rows are
-// very short): lane q of a row sums the stored entries q, q + G,
+// Coarse levels, G lanes per row (1, 2, 4 or 8 by the level's size and row
+// length): lane q of a row sums the stored entries q, q + G,
 // q + 2G, ... (four loads in flight), then the row's lanes add their partial
 // sums by shuffles.  The 32 / G rows of a warp are consecutive, so with
 // slot-major storage every slot's values and columns of those rows fill
@@ -1012,13 +1012,17 @@ static int coarse_lanes(const AmgLevel& L) {
   static const int forced = [] {
     const char* e = getenv("FVS_AMG_LANES");
     const int v = e ? atoi(e) : 0;
-    return (v == 1 || v == 2 || v == 4) ? v : 0;
+    return (v == 1 || v == 2 || v == 4 || v == 8) ? v : 0;
   }();
   if (forced) return forced;
-  // two lanes measured fastest on every coarse level of the 128^3 cavity
-  // (mean stored lengths 12-33; one lane: +3 %, four lanes: +4 % step time)
+  // large levels are bandwidth-bound: two lanes keep whole sectors per slot
+  // and most lanes busy; small levels are latency-bound: more lanes per row
+  // shorten each lane's chain of dependent gathers (128^3 cavity, cold
+  // launches: 905k-row level 37/43 us with two lanes against 47/69 us with
+  // four; 6k-row level 12 us with two against 8 us with four)
   const double mean = L.n > 0 ? L.stored / (double)L.n : 0.0;
-  return mean < 6.0 ? 1 : 2;
+  if (mean < 6.0) return 1;
+  return L.n >= 65536 ? 2 : (L.n >= 8192 ? 4 : 8);
 }
 
 template <typename T>
@@ -1700,12 +1704,15 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
       return FVS_ERR_NOT_CONVERGED;
     }
   }
-  // the coarsest inverse (a dense O(n^3) factorisation) is redone on every
-  // few refreshes only; in between the V-cycle's coarsest solve uses the
-  // previous one (the coarse rows above it are exact Galerkin products)
+  // the coarsest inverse (a dense O(n^3) factorisation) is kept from the last
+  // full setup: the coarse rows above it are exact Galerkin products, and a
+  // refreshed solve that slows down rebuilds the hierarchy (redoing the
+  // inverse on every fourth refresh measured slower at 128^3: 52.0 against
+  // 50.2 ms a step over 20 steps with freezing).  FVS_AMG_COARSEST_EVERY=k
+  // redoes it on every k-th refresh.
   tick(1);
-  const int every = std::max(1, (int)env_num("FVS_AMG_COARSEST_EVERY", 4));
-  if (++refreshes % every == 0) FVS_TRY(coarsest_setup(s));
+  const int every = (int)env_num("FVS_AMG_COARSEST_EVERY", 0);
+  if (every > 0 && ++refreshes % every == 0) FVS_TRY(coarsest_setup(s));
   tick(2);
   if (n0 > 0) {
     k_mask_labels<<<stride_grid(n0, 256), 256, 0, s>>>(n0, act, ppe, fine_lab); FVS_COUNT_LAUNCH();
@@ -1818,7 +1825,8 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
     if (!rl) k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xin, xout);
     else if (G == 1) k_jac_g<T, 1><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
     else if (G == 2) k_jac_g<T, 2><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
-    else k_jac_g<T, 4><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
+    else if (G == 4) k_jac_g<T, 4><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
+    else k_jac_g<T, 8><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
     FVS_COUNT_LAUNCH();
   };
   {
@@ -1834,7 +1842,8 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
     if (!rl) k_resid<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, xa, b, r);
     else if (G == 1) k_resid_g<T, 1><<<gg, 256, 0, s>>>(n, A.col, val, xa, b, r, rl);
     else if (G == 2) k_resid_g<T, 2><<<gg, 256, 0, s>>>(n, A.col, val, xa, b, r, rl);
-    else k_resid_g<T, 4><<<gg, 256, 0, s>>>(n, A.col, val, xa, b, r, rl);
+    else if (G == 4) k_resid_g<T, 4><<<gg, 256, 0, s>>>(n, A.col, val, xa, b, r, rl);
+    else k_resid_g<T, 8><<<gg, 256, 0, s>>>(n, A.col, val, xa, b, r, rl);
     FVS_COUNT_LAUNCH();
   }
   k_restrict<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cb); FVS_COUNT_LAUNCH();
