@@ -155,7 +155,16 @@ __device__ __forceinline__ V chunked_sum(int64_t n, int len, int64_t i, const G&
 #pragma unroll
     for (int c = 0; c < BCH; ++c) acc = fma(vf(k + c), xv[c], acc);
   }
-  for (; k < len; ++k) acc = fma(vf(k), g((int64_t)k * n + i), acc);
+  if (k < len) {
+    // the last, partial chunk (every row of a face-only stencil, 7 < BCH):
+    // its gathers are issued together too, the missing slots re-read slot 0
+    V xv[BCH - 1];
+#pragma unroll
+    for (int c = 0; c < BCH - 1; ++c) xv[c] = g((int64_t)(k + c < len ? k + c : 0) * n + i);
+#pragma unroll
+    for (int c = 0; c < BCH - 1; ++c)
+      if (k + c < len) acc = fma(vf(k + c), xv[c], acc);
+  }
   return acc;
 }
 
