@@ -1033,6 +1033,18 @@ __global__ void k_restrict(int64_t nc, const int32_t* mptr, const int32_t* midx,
     bc[I] = s;
   }
 }
+// restriction and the next level's first Jacobi iterate: bc = R r,
+// xc = omega Dc^-1 bc
+template <typename T>
+__global__ void k_restrict_jac0(int64_t nc, const int32_t* mptr, const int32_t* midx, const T* r, T* bc, T omega,
+                                const T* dinvc, T* xc) {
+  GS(I, nc) {
+    T s = 0;
+    for (int32_t m = mptr[I]; m < mptr[I + 1]; ++m) s += r[midx[m]];
+    bc[I] = s;
+    xc[I] = omega * dinvc[I] * s;
+  }
+}
 template <typename T>
 __global__ void k_prolong(int64_t n, const int32_t* agg, const T* yc, T scale, T* x) {
   GS(i, n) {
@@ -1785,7 +1797,7 @@ fvs_status Amg::project(cudaStream_t s, double* v) {
 }
 
 template <typename T>
-fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
+fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y, bool x0_ready) {
   AmgLevel* L = lv[l].get();
   const Ell& A = *L->A;
   const int64_t n = L->n;
@@ -1829,7 +1841,7 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
     else k_jac_g<T, 8><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
     FVS_COUNT_LAUNCH();
   };
-  {
+  if (!x0_ready) {
     ProfScope ps(pkey, n_jac0, 3.0 * vb * (double)n, s);
     k_jac0<T><<<g, 256, 0, s>>>(n, (T)opt.omega, dinv, b, xa); FVS_COUNT_LAUNCH();
   }
@@ -1846,9 +1858,20 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y) {
     else k_resid_g<T, 8><<<gg, 256, 0, s>>>(n, A.col, val, xa, b, r, rl);
     FVS_COUNT_LAUNCH();
   }
-  k_restrict<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cb); FVS_COUNT_LAUNCH();
+  // restriction; above a level that is not the coarsest it also forms that
+  // level's first Jacobi iterate from zero (row by row, no second launch)
+  const bool next_sweeps = l + 2 < (int)lv.size();
+  if (next_sweeps) {
+    T* cx = f32 ? (T*)C->xf.p : (T*)C->x.p;
+    const T* cdinv = f32 ? (const T*)C->dinvf.p : (const T*)C->dinv.p;
+    k_restrict_jac0<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cb, (T)opt.omega, cdinv,
+                                                             cx);
+  } else {
+    k_restrict<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cb);
+  }
+  FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
-  FVS_TRY(vcycle_t<T>(s, l + 1, cb, cy));
+  FVS_TRY(vcycle_t<T>(s, l + 1, cb, cy, next_sweeps));
   k_prolong<T><<<g, 256, 0, s>>>(n, L->agg, cy, (T)opt.coarse_scale, xa); FVS_COUNT_LAUNCH();
   for (int k = 0; k < opt.npost; ++k) {
     T* out = (k == opt.npost - 1) ? y : xb;

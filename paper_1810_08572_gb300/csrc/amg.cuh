@@ -91,7 +91,9 @@ struct Amg : Precond {
 
  private:
   template <typename T>
-  fvs_status vcycle_t(cudaStream_t s, int l, const T* b, T* y);
+  // x0_ready: the level's first Jacobi iterate from zero is already in its x
+  // (formed by the restriction from the level above)
+  fvs_status vcycle_t(cudaStream_t s, int l, const T* b, T* y, bool x0_ready = false);
   fvs_status coarsest_setup(cudaStream_t s);
   fvs_status setup_fp32(cudaStream_t s);
 };

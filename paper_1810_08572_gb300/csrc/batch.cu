@@ -434,6 +434,19 @@ __global__ void kb_restrict(int64_t nc, int Sp, const int32_t* mptr, const int32
     bc[I * Sp + s] = a;
   }
 }
+// restriction and the next level's first Jacobi iterate (xc = omega Dc^-1 bc)
+template <typename V>
+__global__ void kb_restrict_jac0(int64_t nc, int Sp, const int32_t* mptr, const int32_t* midx, const V* r, V* bc,
+                                 V omega, const V* dinvc, V* xc) {
+  BSAMPLE;
+  BROW(I, nc) {
+    V a = 0;
+    for (int32_t m = mptr[I]; m < mptr[I + 1]; ++m) a += r[(int64_t)midx[m] * Sp + s];
+    const int64_t e = I * Sp + s;
+    bc[e] = a;
+    xc[e] = omega * dinvc[e] * a;
+  }
+}
 // x += scale P yc (rows with ovr == -2 at the fine level take no correction)
 template <typename V>
 __global__ void kb_prolong(int64_t n, int Sp, const int32_t* agg, const int32_t* ovr, const V* yc, V scale, V* x) {
@@ -1061,7 +1074,7 @@ static fvs_status level_applyf(Batch& B, int l, const float* x, const float* b, 
 // transfers with over-correction, pinned dense coarsest inverse); V = double,
 // or float for the mixed-precision path (FP32 copies of every level)
 template <typename V>
-static fvs_status bvcycle_t(Batch& B, int l, const V* b, V* y) {
+static fvs_status bvcycle_t(Batch& B, int l, const V* b, V* y, bool x0_ready = false) {
   const int L = (int)B.lv.size();
   BLevel& F = *B.lv[l];
   const int Sp = B.Sp;
@@ -1079,11 +1092,23 @@ static fvs_status bvcycle_t(Batch& B, int l, const V* b, V* y) {
   V* cb = f32 ? (V*)C.bf.p : (V*)C.b.p;
   V* cy = f32 ? (V*)C.yf.p : (V*)C.y.p;
   const V* dinv = f32 ? (const V*)F.dinvf.p : (const V*)F.dinv.p;
-  kb_jac0<V><<<bgrid(F.n, B.tiles), bblock(), 0, st>>>(F.n, Sp, om, dinv, b, x); FVS_COUNT_LAUNCH();
+  if (!x0_ready) {
+    kb_jac0<V><<<bgrid(F.n, B.tiles), bblock(), 0, st>>>(F.n, Sp, om, dinv, b, x); FVS_COUNT_LAUNCH();
+  }
   if (f32) FVS_TRY(level_applyf(B, l, (const float*)x, (const float*)b, (float*)r, 1, nullptr, 0.0f));
   else FVS_TRY(level_apply(B, l, (const double*)x, (const double*)b, (double*)r, 1, nullptr, 0.0));
-  kb_restrict<V><<<bgrid(C.n, B.tiles), bblock(), 0, st>>>(C.n, Sp, F.mptr, F.midx, r, cb); FVS_COUNT_LAUNCH();
-  FVS_TRY(bvcycle_t<V>(B, l + 1, cb, cy));
+  // above a level that is not the coarsest the restriction also forms that
+  // level's first Jacobi iterate
+  const bool next_sweeps = l + 2 < L;
+  if (next_sweeps) {
+    V* cx = f32 ? (V*)C.xf.p : (V*)C.x.p;
+    const V* cdinv = f32 ? (const V*)C.dinvf.p : (const V*)C.dinv.p;
+    kb_restrict_jac0<V><<<bgrid(C.n, B.tiles), bblock(), 0, st>>>(C.n, Sp, F.mptr, F.midx, r, cb, om, cdinv, cx);
+  } else {
+    kb_restrict<V><<<bgrid(C.n, B.tiles), bblock(), 0, st>>>(C.n, Sp, F.mptr, F.midx, r, cb);
+  }
+  FVS_COUNT_LAUNCH();
+  FVS_TRY(bvcycle_t<V>(B, l + 1, cb, cy, next_sweeps));
   kb_prolong<V><<<bgrid(F.n, B.tiles), bblock(), 0, st>>>(F.n, Sp, F.agg, l == 0 ? B.ovr.p : nullptr, cy,
                                                           (V)B.aopt.coarse_scale, x); FVS_COUNT_LAUNCH();
   if (f32) FVS_TRY(level_applyf(B, l, (const float*)x, (const float*)b, (float*)y, 2, (const float*)dinv, (float)om));
