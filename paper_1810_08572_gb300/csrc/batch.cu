@@ -51,8 +51,44 @@ static inline void dswap_b(DBuf<T>& a, DBuf<T>& b) {
 // deterministic per-sample reductions: block partials (fixed order over the
 // 8 row lanes), then one pass per sample over the blocks in fixed order
 // ---------------------------------------------------------------------------
+// The block of a tile (group of 32 samples) that finishes last adds the
+// tile's partials in fixed block order -- lane y takes blocks y, y+8, ...,
+// then the lanes combine in fixed order, whatever block is last -- writes
+// sc[slot*Sp + s] and resets the tile's counter (so graph replays start from
+// zero).  Partials are read past L1 (other SMs wrote them).
+__device__ __forceinline__ void kb_last_block_final(int Sp, const double* part, double* sc, int slot0, int slot1,
+                                                    int take_max, int* cnt, double (*sh)[8][33]) {
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) last = atomicAdd(&cnt[blockIdx.y], 1) == (int)gridDim.x - 1 ? 1 : 0;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int nb = (int)gridDim.x;
+  const int s = blockIdx.y * 32 + threadIdx.x;
+  double u = 0.0, v = 0.0;
+  for (int b = threadIdx.y; b < nb; b += 8) {
+    const double pu = __ldcg(part + (int64_t)b * Sp + s), pv = __ldcg(part + ((int64_t)nb + b) * Sp + s);
+    if (take_max) { u = fmax(u, pu); v = fmax(v, pv); } else { u += pu; v += pv; }
+  }
+  sh[0][threadIdx.y][threadIdx.x] = u;
+  sh[1][threadIdx.y][threadIdx.x] = v;
+  __syncthreads();
+  if (threadIdx.y == 0) {
+    u = sh[0][0][threadIdx.x];
+    v = sh[1][0][threadIdx.x];
+    for (int k = 1; k < 8; ++k) {
+      if (take_max) { u = fmax(u, sh[0][k][threadIdx.x]); v = fmax(v, sh[1][k][threadIdx.x]); }
+      else { u += sh[0][k][threadIdx.x]; v += sh[1][k][threadIdx.x]; }
+    }
+    if (slot0 >= 0) sc[slot0 * Sp + s] = u;
+    if (slot1 >= 0) sc[slot1 * Sp + s] = v;
+  }
+  if (threadIdx.x == 0 && threadIdx.y == 0) cnt[blockIdx.y] = 0;
+}
 __global__ void kb_dot2(int64_t n, int Sp, const double* a, const double* b, const double* c, const double* d,
-                        double* part) {
+                        double* part, double* sc, int slot0, int slot1, int* cnt) {
   __shared__ double sh[2][8][33];
   BSAMPLE;
   double x = 0.0, y = 0.0;
@@ -70,10 +106,12 @@ __global__ void kb_dot2(int64_t n, int Sp, const double* a, const double* b, con
     part[(int64_t)blockIdx.x * Sp + s] = u;
     part[((int64_t)gridDim.x + blockIdx.x) * Sp + s] = v;
   }
+  __syncthreads();
+  kb_last_block_final(Sp, part, sc, slot0, slot1, 0, cnt, sh);
 }
 // max |a - b| and max |c - d| per sample
 __global__ void kb_maxdiff2(int64_t n, int Sp, const double* a, const double* b, const double* c, const double* d,
-                            double* part) {
+                            double* part, double* sc, int slot0, int slot1, int* cnt) {
   __shared__ double sh[2][8][33];
   BSAMPLE;
   double x = 0.0, y = 0.0;
@@ -91,33 +129,8 @@ __global__ void kb_maxdiff2(int64_t n, int Sp, const double* a, const double* b,
     part[(int64_t)blockIdx.x * Sp + s] = u;
     part[((int64_t)gridDim.x + blockIdx.x) * Sp + s] = v;
   }
-}
-// sc[slot0*Sp + s] = sum (or max) of the partials of output 0, likewise
-// slot1; block (32 samples, 8 lanes), lane y takes blocks y, y+8, ... and the
-// lanes combine in fixed order.  Partials are stored [output][block][sample],
-// so the 32 samples of one block's partial are one coalesced load.
-__global__ void kb_final2(int nb, int Sp, const double* part, double* sc, int slot0, int slot1, int take_max) {
-  __shared__ double sh[2][8][33];
-  const int s = blockIdx.x * 32 + threadIdx.x;
-  double u = 0.0, v = 0.0;
-#pragma unroll 4
-  for (int b = threadIdx.y; b < nb; b += 8) {
-    const double pu = part[(int64_t)b * Sp + s], pv = part[((int64_t)nb + b) * Sp + s];
-    if (take_max) { u = fmax(u, pu); v = fmax(v, pv); } else { u += pu; v += pv; }
-  }
-  sh[0][threadIdx.y][threadIdx.x] = u;
-  sh[1][threadIdx.y][threadIdx.x] = v;
   __syncthreads();
-  if (threadIdx.y == 0) {
-    u = sh[0][0][threadIdx.x];
-    v = sh[1][0][threadIdx.x];
-    for (int k = 1; k < 8; ++k) {
-      if (take_max) { u = fmax(u, sh[0][k][threadIdx.x]); v = fmax(v, sh[1][k][threadIdx.x]); }
-      else { u += sh[0][k][threadIdx.x]; v += sh[1][k][threadIdx.x]; }
-    }
-    if (slot0 >= 0) sc[slot0 * Sp + s] = u;
-    if (slot1 >= 0) sc[slot1 * Sp + s] = v;
-  }
+  kb_last_block_final(Sp, part, sc, slot0, slot1, 1, cnt, sh);
 }
 
 // ---------------------------------------------------------------------------
@@ -635,8 +648,8 @@ static int red_blocks(int64_t n, int tiles) {
 static fvs_status bdot2(Batch& B, int64_t n, const double* a, const double* b, const double* c, const double* d,
                         int slot0, int slot1) {
   const int nb = red_blocks(n, B.tiles);
-  kb_dot2<<<dim3(nb, B.tiles), bblock(), 0, B.stream>>>(n, B.Sp, a, b, c, d, B.part); FVS_COUNT_LAUNCH();
-  kb_final2<<<B.tiles, bblock(), 0, B.stream>>>(nb, B.Sp, B.part, B.sc, slot0, c ? slot1 : -1, 0);
+  kb_dot2<<<dim3(nb, B.tiles), bblock(), 0, B.stream>>>(n, B.Sp, a, b, c, d, B.part, B.sc, slot0, c ? slot1 : -1,
+                                                        B.redcnt);
   FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   return FVS_OK;
@@ -644,8 +657,9 @@ static fvs_status bdot2(Batch& B, int64_t n, const double* a, const double* b, c
 static fvs_status bmaxdiff2(Batch& B, int64_t n, const double* a, const double* b, const double* c, const double* d,
                             int slot0, int slot1) {
   const int nb = red_blocks(n, B.tiles);
-  kb_maxdiff2<<<dim3(nb, B.tiles), bblock(), 0, B.stream>>>(n, B.Sp, a, b, c, d, B.part); FVS_COUNT_LAUNCH();
-  kb_final2<<<B.tiles, bblock(), 0, B.stream>>>(nb, B.Sp, B.part, B.sc, slot0, slot1, 1); FVS_COUNT_LAUNCH();
+  kb_maxdiff2<<<dim3(nb, B.tiles), bblock(), 0, B.stream>>>(n, B.Sp, a, b, c, d, B.part, B.sc, slot0, slot1,
+                                                            B.redcnt);
+  FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
   return FVS_OK;
 }
@@ -2339,6 +2353,8 @@ fvs_status batch_run(fvs_mesh mesh, const fvs_props* base, int64_t n, const doub
         const int64_t rows = std::max<int64_t>(std::max(Nc, Nf), Nv);
         const int nbm = red_blocks(rows, B.tiles);
         FVS_TRY(B.part.alloc((size_t)std::max(BATCH_NCM, 5) * Sp * nbm + 1));
+        FVS_TRY(B.redcnt.alloc((size_t)Sp / 32 + 1));
+        FVS_TRY(B.redcnt.zero(B.stream));
       }
       B.ocap = std::max<int64_t>(1024, Nc * Sp / 16);
       FVS_TRY(B.mval.alloc((size_t)B.ocap * W + 1));

@@ -161,6 +161,7 @@ struct Batch {
   // reductions
   int nb = 0;                     // row blocks of the reduction kernels
   DBuf<double> part;              // [2 * Sp * nb] (and BATCH_NCM * Sp * nb for parts)
+  DBuf<int> redcnt;               // [tiles] finished blocks of a reduction (the last one resets it)
   DBuf<double> sc;                // [B_NSLOT * Sp]
   DBuf<uint8_t> kact;             // Krylov: sample still iterating
   DBuf<uint8_t> krestart;         // Krylov: sample restarts (breakdown)
