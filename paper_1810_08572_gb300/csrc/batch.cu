@@ -569,7 +569,7 @@ __global__ void kb_part_ids(int Sp, int nc, const int* count, const uint8_t* sin
   }
 }
 __global__ void kb_proj_part(int64_t n, int Sp, int nc, const int32_t* lab, const int32_t* cid, const double* v,
-                             double* part) {
+                             double* part, const double* ccnt, double* mean, int* cnt) {
   __shared__ double sh[BATCH_NCM][8][33];
   BSAMPLE;
   double a[BATCH_NCM];
@@ -594,25 +594,30 @@ __global__ void kb_proj_part(int64_t n, int Sp, int nc, const int32_t* lab, cons
       part[((int64_t)k * gridDim.x + blockIdx.x) * Sp + s] = u;
     }
   }
-}
-__global__ void kb_proj_final(int nb, int Sp, const double* part, const double* ccnt, double* mean) {
-  __shared__ double sh[8][33];
-  const int s = blockIdx.x * 32 + threadIdx.x;
+  // the tile's last block forms the per-part means (fixed block order)
+  __shared__ int last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) last = atomicAdd(&cnt[blockIdx.y], 1) == (int)gridDim.x - 1 ? 1 : 0;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int nb = (int)gridDim.x;
   for (int k = 0; k < BATCH_NCM; ++k) {
     const double c = ccnt[s * BATCH_NCM + k];
     double u = 0.0;
     if (c > 0.0)
-#pragma unroll 4
-      for (int b = threadIdx.y; b < nb; b += 8) u += part[((int64_t)k * nb + b) * Sp + s];
-    sh[threadIdx.y][threadIdx.x] = u;
+      for (int b = threadIdx.y; b < nb; b += 8) u += __ldcg(part + ((int64_t)k * nb + b) * Sp + s);
+    sh[0][threadIdx.y][threadIdx.x] = u;
     __syncthreads();
     if (threadIdx.y == 0) {
       double t = 0.0;
-      for (int y = 0; y < 8; ++y) t += sh[y][threadIdx.x];
+      for (int y = 0; y < 8; ++y) t += sh[0][y][threadIdx.x];
       mean[s * BATCH_NCM + k] = c > 0.0 ? t / c : 0.0;
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0 && threadIdx.y == 0) cnt[blockIdx.y] = 0;
 }
 __global__ void kb_proj_sub(int64_t n, int Sp, int nc, const int32_t* lab, const int32_t* cid, const double* mean,
                             double* v) {
@@ -1053,9 +1058,9 @@ fvs_status batch_amg_values(Batch& B) {
 static fvs_status bproject(Batch& B, double* v) {
   const int64_t n = B.mesh->Nc;
   const int nb = red_blocks(n, B.tiles);
-  kb_proj_part<<<dim3(nb, B.tiles), bblock(), 0, B.stream>>>(n, B.Sp, B.nc, B.lv[0]->lab, B.cid, v, B.part);
+  kb_proj_part<<<dim3(nb, B.tiles), bblock(), 0, B.stream>>>(n, B.Sp, B.nc, B.lv[0]->lab, B.cid, v, B.part, B.ccnt,
+                                                             B.csum, B.redcnt);
   FVS_COUNT_LAUNCH();
-  kb_proj_final<<<B.tiles, bblock(), 0, B.stream>>>(nb, B.Sp, B.part, B.ccnt, B.csum); FVS_COUNT_LAUNCH();
   kb_proj_sub<<<bgrid(n, B.tiles), bblock(), 0, B.stream>>>(n, B.Sp, B.nc, B.lv[0]->lab, B.cid, B.csum, v);
   FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
