@@ -1,7 +1,9 @@
 """Solver paths beyond the default one: the single-grid pressure solve on a
-system of several liquid pockets, a refused non-finite right side, and the
-bench workload's jittered mesh at a size no oracle can follow, checked
-through identities that hold at any size."""
+system of several liquid pockets, a refused non-finite right side, the
+bench workload's jittered mesh at a size no oracle can follow (checked
+through identities that hold at any size), and the two operator reductions
+that must not change the answer: face-only stencils on orthogonal meshes
+and the AMG hierarchy built on the face couplings of the pressure matrix."""
 import numpy as np
 import pytest
 
@@ -196,3 +198,54 @@ def test_jittered_full_size_identities(fvs):
     assert np.abs(out[1]["T"] - out[0]["T"]).max() <= 1e-6
     assert rel(out[1]["U"], out[0]["U"]) <= 1e-6
     assert rel(out[1]["P"], out[0]["P"]) <= 1e-6
+
+
+def _run(fvs, m, props, T0, u0, steps, dt=1e-3):
+    M = fvs.Mesh(m)
+    S = fvs.Solver(M, props)
+    S.set_state(T0, u0)
+    for _ in range(steps):
+        st = S.step(dt)
+        assert st["status"] == 0 and st["fallback"] == 0
+    out = {k: S.query(k) for k in ("T", "U", "P", "FLUX")}
+    width = M.info["max_cell_neighbours"]
+    S.close()
+    M.close()
+    return out, width
+
+
+def test_face_only_stencil_changes_nothing(fvs, monkeypatch):
+    """On an orthogonal mesh the neighbour lists keep only the cells across
+    the faces (7 slots); the couplings left out were exact zeros, so three
+    steps with convection and a frozen band equal the 27-slot stencil's to
+    rounding of the Krylov iterates (both solved to 1e-13)."""
+    m = box_mesh(12, 10, 6, cases.CAVITY, permute_seed=5)
+    ijk = m["cell_ijk"]
+    rng = np.random.default_rng(9)
+    T0 = 940.0 - rng.uniform(0.0, 10.0, len(ijk))
+    T0[ijk[:, 0] == 5] = 800.0
+    u0 = rng.normal(scale=2e-3, size=(len(T0), 3))
+    props = cases.props(**TIGHT)
+    face, wf = _run(fvs, m, props, T0, u0, 3)
+    monkeypatch.setenv("FVS_FULL_STENCIL", "1")
+    full, ww = _run(fvs, m, props, T0, u0, 3)
+    assert wf == 7 and ww == 27
+    for k in ("T", "U", "P", "FLUX"):
+        assert rel(face[k], full[k]) <= 1e-11, k
+
+
+def test_hierarchy_on_face_couplings_changes_only_the_iterations(fvs, monkeypatch):
+    """The AMG hierarchy built on the face-coupling part of the pressure
+    matrix (vertex couplings lumped into the diagonal) preconditions the same
+    Krylov solve as one built on the full matrix: on a jittered mesh with
+    two pockets, three steps agree to the solve tolerance."""
+    m = box_mesh(40, 36, 2, cases.CAVITY, jitter=0.2, jitter_seed=81, permute_seed=82)
+    T0 = pockets_field(m, seed=4)
+    rng = np.random.default_rng(10)
+    u0 = rng.normal(scale=2e-3, size=(len(T0), 3))
+    props = cases.props(**TIGHT)
+    compact, _ = _run(fvs, m, props, T0, u0, 3)
+    monkeypatch.setenv("FVS_PC_COMPACT", "0")
+    full, _ = _run(fvs, m, props, T0, u0, 3)
+    for k in ("T", "U", "P", "FLUX"):
+        assert rel(compact[k], full[k]) <= 1e-10, k
