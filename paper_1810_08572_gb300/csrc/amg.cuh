@@ -58,18 +58,22 @@ struct Amg : Precond {
   ScanWork sw;
   bool ready = false;
 
-  bool masked = false;            // some fine rows carry label -1 (refreshed)
+  bool masked = false;            // the projection reads the fine labels (rows with label -1 take no part)
   int refreshes = 0;              // refreshes since the setup
 
   fvs_status setup(cudaStream_t s, const Ell& A);
   fvs_status count_stored(cudaStream_t s);   // AmgLevel::stored of every level
-  // The operator's values changed on the same rows (cells frozen since the
-  // setup became identity rows): rows of cells without pressure
-  // (ppe[act[i]] == 0) leave their aggregates and the null-space labels, and
-  // the Galerkin rows of every aggregate whose member rows changed (row
-  // fingerprints) are recomputed on the kept aggregation, level by level,
-  // followed by the coarsest inverse.  FVS_ERR_NOT_CONVERGED: the kept
-  // aggregation does not fit any more (a new setup is needed).
+  // The operator's values changed on the same rows: rows of cells without
+  // pressure (ppe[act[i]] == 0: frozen since the setup) leave their
+  // aggregates and the null-space labels; rows that carry pressure without
+  // an aggregate (cells melted again, or margin rows melted for the first
+  // time) join the aggregate of their most strongly coupled neighbour and
+  // take its label; the Galerkin rows of every aggregate whose member rows
+  // changed (row fingerprints) are recomputed on the kept aggregation, level
+  // by level.  The coarsest inverse of the setup is kept.
+  // FVS_ERR_NOT_CONVERGED: the kept aggregation does not fit any more (a
+  // coarse row outgrew its width, a row found no label, or two parts met),
+  // so a new setup is needed.
   fvs_status refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe);
   fvs_status apply(cudaStream_t s, const double* r, double* z) override;
   uint64_t version = 0;          // bumped by every setup
@@ -90,9 +94,9 @@ struct Amg : Precond {
   int levels() const { return (int)lv.size(); }
 
  private:
-  template <typename T>
   // x0_ready: the level's first Jacobi iterate from zero is already in its x
   // (formed by the restriction from the level above)
+  template <typename T>
   fvs_status vcycle_t(cudaStream_t s, int l, const T* b, T* y, bool x0_ready = false);
   fvs_status coarsest_setup(cudaStream_t s);
   fvs_status setup_fp32(cudaStream_t s);
