@@ -71,6 +71,82 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t phase) {
   return done != 0;
 }
 
+// fused epilogue of one 128-row tile: warp group `warp` (0-3) reads its 32
+// accumulator lanes (rows m0 + 32 warp + lane) from tensor memory, 16
+// columns at a time from c_begin in steps of c_step (two warps of the same
+// group split the columns by starting 16 apart with a step of 32)
+template <int EPI>
+__device__ __forceinline__ void tc_epilogue(uint32_t taddr, int warp, int lane, int m0, int M, int N, const Epi& e,
+                                            int c_begin = 0, int c_step = 16) {
+  const int m = m0 + warp * 32 + lane;
+  for (int c0 = c_begin; c0 < N; c0 += c_step) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    if (m >= M) continue;
+    const int64_t o0 = (int64_t)m * e.ldo + c0;
+    if ((e.ldo & 7) == 0) {
+      // a lane's 16 columns as 16-byte vectors (row offsets are multiples of 8 elements)
+      float v[16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+      if (EPI == EPI_GELU || EPI == EPI_LINEAR) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] += e.bias[c0 + j];
+      }
+      if (EPI == EPI_DGRAD) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+          const float4 z = *reinterpret_cast<const float4*>(e.z + o0 + j);
+          v[j] *= gelu_grad(z.x); v[j + 1] *= gelu_grad(z.y); v[j + 2] *= gelu_grad(z.z); v[j + 3] *= gelu_grad(z.w);
+        }
+      }
+      float* f32out = EPI == EPI_GELU ? e.z : e.fout;
+      if ((EPI == EPI_LINEAR || EPI == EPI_WGRAD || EPI == EPI_GELU) && f32out) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 4)
+          *reinterpret_cast<float4*>(f32out + o0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+      }
+      if (EPI == EPI_GELU || EPI == EPI_DGRAD) {
+        uint32_t h[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const float a = EPI == EPI_GELU ? gelu(v[2 * j]) : v[2 * j];
+          const float b = EPI == EPI_GELU ? gelu(v[2 * j + 1]) : v[2 * j + 1];
+          const __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
+          h[j] = *reinterpret_cast<const uint32_t*>(&hb);
+        }
+        uint4* dst = reinterpret_cast<uint4*>(e.hout + o0);
+        dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
+        dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
+      }
+      continue;
+    }
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int n = c0 + j;
+      const int64_t o = o0 + j;
+      float v = __uint_as_float(r[j]);
+      if (EPI == EPI_GELU) {
+        v += e.bias[n];
+        if (e.z) e.z[o] = v;
+        e.hout[o] = __float2bfloat16(gelu(v));
+      } else if (EPI == EPI_LINEAR) {
+        v += e.bias[n];
+        e.fout[o] = v;
+      } else if (EPI == EPI_DGRAD) {
+        e.hout[o] = __float2bfloat16(v * gelu_grad(e.z[o]));
+      } else {
+        e.fout[o] = v;
+      }
+    }
+  }
+}
+
 template <int EPI>
 __global__ void __launch_bounds__(128, 1) k_mlp_gemm_tc(int M, int N, int K, const bf16* __restrict__ A, int am, int ak,
                                                         const bf16* __restrict__ B, int bn, int bk, Epi e, int* err) {
@@ -155,75 +231,124 @@ __global__ void __launch_bounds__(128, 1) k_mlp_gemm_tc(int M, int N, int K, con
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
   }
-  if (ok) {
-    const int m = m0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      uint32_t r[16];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
-      asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (m >= M) continue;
-      const int64_t o0 = (int64_t)m * e.ldo + c0;
-      if ((e.ldo & 7) == 0) {
-        // a lane's 16 columns as 16-byte vectors (row offsets are multiples of 8 elements)
-        float v[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
-        if (EPI == EPI_GELU || EPI == EPI_LINEAR) {
-#pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] += e.bias[c0 + j];
-        }
-        if (EPI == EPI_DGRAD) {
-#pragma unroll
-          for (int j = 0; j < 16; j += 4) {
-            const float4 z = *reinterpret_cast<const float4*>(e.z + o0 + j);
-            v[j] *= gelu_grad(z.x); v[j + 1] *= gelu_grad(z.y); v[j + 2] *= gelu_grad(z.z); v[j + 3] *= gelu_grad(z.w);
-          }
-        }
-        float* f32out = EPI == EPI_GELU ? e.z : e.fout;
-        if ((EPI == EPI_LINEAR || EPI == EPI_WGRAD || EPI == EPI_GELU) && f32out) {
-#pragma unroll
-          for (int j = 0; j < 16; j += 4)
-            *reinterpret_cast<float4*>(f32out + o0 + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        }
-        if (EPI == EPI_GELU || EPI == EPI_DGRAD) {
-          uint32_t h[8];
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const float a = EPI == EPI_GELU ? gelu(v[2 * j]) : v[2 * j];
-            const float b = EPI == EPI_GELU ? gelu(v[2 * j + 1]) : v[2 * j + 1];
-            const __nv_bfloat162 hb = __floats2bfloat162_rn(a, b);
-            h[j] = *reinterpret_cast<const uint32_t*>(&hb);
-          }
-          uint4* dst = reinterpret_cast<uint4*>(e.hout + o0);
-          dst[0] = make_uint4(h[0], h[1], h[2], h[3]);
-          dst[1] = make_uint4(h[4], h[5], h[6], h[7]);
-        }
-        continue;
-      }
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int n = c0 + j;
-        const int64_t o = o0 + j;
-        float v = __uint_as_float(r[j]);
-        if (EPI == EPI_GELU) {
-          v += e.bias[n];
-          if (e.z) e.z[o] = v;
-          e.hout[o] = __float2bfloat16(gelu(v));
-        } else if (EPI == EPI_LINEAR) {
-          v += e.bias[n];
-          e.fout[o] = v;
-        } else if (EPI == EPI_DGRAD) {
-          e.hout[o] = __float2bfloat16(v * gelu_grad(e.z[o]));
-        } else {
-          e.fout[o] = v;
-        }
-      }
+  if (ok) tc_epilogue<EPI>(taddr, warp, lane, m0, M, N, e);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_COLS));
+}
+
+// ---------------------------------------------------------------------------
+// Forward GEMM (activations A [M x K] row-major times weights B [N x K],
+// K <= 128, N <= 128) as a persistent kernel: each CTA stages the weights
+// once, allocates its tensor-memory accumulator once, and walks the 128-row
+// tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... with eight warps (two per
+// accumulator lane group in the epilogue)  The A tile of the next
+// tile is copied into the other of two shared-memory buffers (cp.async,
+// 16-byte core-matrix rows, zero fill past M) while the current tile's MMAs
+// and epilogue run.  Layouts, descriptors and the epilogue are those of
+// k_mlp_gemm_tc; every wait on the MMAs is bounded and the decision to stop
+// is taken by the whole CTA (__syncthreads_or), which then drains its copies
+// and frees its tensor memory.
+// ---------------------------------------------------------------------------
+constexpr int TC_CHUNK_BYTES = 128 * TC_KC * 2;   // one K chunk of 128 rows
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+}
+// rows of A's tile m0 into buffer sa (K in chunks of TC_KC, 16-byte pieces)
+__device__ __forceinline__ void tc_stage_a_async(unsigned char* sa, const bf16* A, int M, int K, int m0, int tid,
+                                                 int nthr) {
+  const int nchunk = (K + TC_KC - 1) / TC_KC;
+  for (int c = 0; c < nchunk; ++c) {
+    const int k0 = c * TC_KC, kc = min(TC_KC, K - k0), nch = kc >> 3;
+    unsigned char* base = sa + c * TC_CHUNK_BYTES;
+    for (int t = tid; t < 128 * nch; t += nthr) {
+      const int q = t >> 3, ch = q % nch, r = (q / nch) * 8 + (t & 7);
+      const int m = m0 + r;
+      const bf16* src = m < M ? A + (int64_t)m * K + k0 + ch * 8 : A;
+      cp_async16(smem_u32(base + tc_off(r, ch * 8)), src, m < M ? 16 : 0);
     }
   }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int EPI>
+__global__ void __launch_bounds__(256, 1) k_mlp_fwd_tc(int M, int N, int K, const bf16* __restrict__ A,
+                                                       const bf16* __restrict__ B, Epi e, int* err) {
+  extern __shared__ __align__(1024) unsigned char tc_dyn[];
+  const int nchunk = (K + TC_KC - 1) / TC_KC;
+  unsigned char* sb = tc_dyn;                               // nchunk chunks
+  unsigned char* sa0 = tc_dyn + nchunk * TC_CHUNK_BYTES;    // 2 x nchunk chunks
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t taddr_s;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntiles = (M + 127) / 128;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&taddr_s)),
+                 "r"(TC_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+  // the weights, once
+  for (int c = 0; c < nchunk; ++c) {
+    const int k0 = c * TC_KC, kc = min(TC_KC, K - k0), nch = kc >> 3;
+    for (int t = tid; t < N * nch; t += blockDim.x) {
+      const int q = t >> 3, ch = q % nch, r = (q / nch) * 8 + (t & 7);
+      *reinterpret_cast<uint4*>(sb + c * TC_CHUNK_BYTES + tc_off(r, ch * 8)) =
+          *reinterpret_cast<const uint4*>(B + (int64_t)r * K + k0 + ch * 8);
+    }
+  }
+  if (blockIdx.x < ntiles) tc_stage_a_async(sa0, A, M, K, blockIdx.x * 128, tid, blockDim.x);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = taddr_s;
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+  uint32_t phase = 0;
+  int buf = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int next = tile + gridDim.x;
+    if (next < ntiles) {
+      tc_stage_a_async(sa0 + (buf ^ 1) * nchunk * TC_CHUNK_BYTES, A, M, K, next * 128, tid, blockDim.x);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const unsigned char* sa = sa0 + buf * nchunk * TC_CHUNK_BYTES;
+      for (int c = 0; c < nchunk; ++c) {
+        const int kc = min(TC_KC, K - c * TC_KC);
+        for (int kk = 0; kk < kc / 16; ++kk) {
+          const uint64_t ad = tc_desc(smem_u32(sa + c * TC_CHUNK_BYTES) + kk * 256);
+          const uint64_t bd = tc_desc(smem_u32(sb + c * TC_CHUNK_BYTES) + kk * 256);
+          const uint32_t accum = (c > 0 || kk > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(taddr),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(&mbar)));
+    }
+    const bool late = __syncthreads_or(!tc_wait(smem_u32(&mbar), phase) ? 1 : 0);
+    if (late) {
+      if (tid == 0) atomicOr(err, 1);
+      tc_wait(smem_u32(&mbar), phase);   // the MMAs in flight get a second bounded chance
+      break;
+    }
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // eight warps: warp w reads accumulator lanes 32 (w % 4) .. +31, the
+    // 16-column blocks starting at 16 (w / 4), every other one
+    tc_epilogue<EPI>(taddr, warp & 3, lane, tile * 128, M, N, e, 16 * (warp >> 2), 32);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();   // accumulator read before the next tile's MMAs; buffer free for reuse
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    buf ^= 1;
+  }
+  asm volatile("cp.async.wait_all;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_COLS));
@@ -385,6 +510,36 @@ static fvs_status sg_work(fvs_surrogate_s* s, int64_t n) {
 
 static int tc_grid(int64_t M) { return (int)((M + 127) / 128); }
 
+// forward layer C = A W^T with the fused epilogue: the persistent kernel
+// (up to four CTAs per SM, weights staged once per CTA, next A tile copied
+// while the current one is multiplied) where K and N fit one tile, else one
+// CTA a tile
+template <int EPI>
+static fvs_status tc_forward(cudaStream_t st, int64_t n, int N, int K, const bf16* A, const bf16* W, const Epi& e,
+                             int* err) {
+  if (K <= 128 && N <= 128) {
+    const int nchunk = (K + TC_KC - 1) / TC_KC;
+    const size_t smem = (size_t)3 * nchunk * TC_CHUNK_BYTES;
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+      FVS_CUDA(cudaFuncSetAttribute(k_mlp_fwd_tc<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    3 * 2 * TC_CHUNK_BYTES));
+      attr_set[dev] = true;
+    }
+    // CTAs per SM: tensor memory allows four (128 columns each), shared memory
+    // 227 KB / (smem + 1 KB)
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227 * 1024) / (smem + 1024)));
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tc_grid(n), (int64_t)per_sm * sm_count()));
+    k_mlp_fwd_tc<EPI><<<grid, 256, smem, st>>>((int)n, N, K, A, W, e, err);
+  } else {
+    k_mlp_gemm_tc<EPI><<<tc_grid(n), 128, 0, st>>>((int)n, N, K, A, K, 1, W, K, 1, e, err);
+  }
+  FVS_COUNT_LAUNCH();
+  return FVS_OK;
+}
+
 // forward pass of n normalised BF16 rows already in H[0]; keep Z when training
 static fvs_status sg_forward(fvs_surrogate_s* s, int64_t n, bool keep) {
   const int L = (int)s->kd.size() - 1;
@@ -398,12 +553,11 @@ static fvs_status sg_forward(fvs_surrogate_s* s, int64_t n, bool keep) {
     if (l < L - 1) {
       e.z = keep ? s->Z[l]->p : nullptr;
       e.hout = s->H[l + 1]->p;
-      k_mlp_gemm_tc<EPI_GELU><<<tc_grid(n), 128, 0, st>>>((int)n, N, K, s->H[l]->p, K, 1, W, K, 1, e, s->tc_err.p);
+      FVS_TRY(tc_forward<EPI_GELU>(st, n, N, K, s->H[l]->p, W, e, s->tc_err.p));
     } else {
       e.fout = s->Y.p;
-      k_mlp_gemm_tc<EPI_LINEAR><<<tc_grid(n), 128, 0, st>>>((int)n, N, K, s->H[l]->p, K, 1, W, K, 1, e, s->tc_err.p);
+      FVS_TRY(tc_forward<EPI_LINEAR>(st, n, N, K, s->H[l]->p, W, e, s->tc_err.p));
     }
-    FVS_COUNT_LAUNCH();
   }
   FVS_LAUNCH_CHECK();
   return FVS_OK;
