@@ -65,3 +65,19 @@ def test_reference_arm_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["unit"] == "active cell-steps/s"
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
     assert line["steps"] == 1 and line["cpu_baseline"]["steps"] == 1 and line["cpu_baseline"]["host"]["nproc"] >= 1
+
+
+def test_casting_bands():
+    """The casting study's binning: shares 1.0 and 0.8 fall in the top band,
+    0.79 in the next, steps with no active cell in none; per band the mean
+    step time, iterations, full setups and active cell-steps per second."""
+    sys.path.insert(0, ROOT)
+    import bench
+    n = 1000
+    rows = [(0.010, 1000, 20, 1), (0.012, 800, 22, 2), (0.008, 790, 18, 2), (0.004, 150, 10, 1), (0.002, 0, 0, 0)]
+    b = bench.active_share_bands(rows, n)
+    assert [x["active_share"] for x in b] == ["0.8-1.0", "0.6-0.8", "0.0-0.2"]
+    assert [x["steps"] for x in b] == [2, 1, 1]
+    assert b[0]["ms_per_step"] == 11.0 and b[0]["p_its"] == 21.0 and b[0]["rebuilds"] == 1
+    assert abs(b[0]["active_cell_steps_per_s"] - 1800 / 0.022) < 0.1
+    assert b[2]["rebuilds"] == 1 and abs(b[2]["active_cell_steps_per_s"] - 150 / 0.004) < 0.1
