@@ -495,3 +495,27 @@ def test_grain_growth_matches_oracle(fvs, material):
     r = S.query("GRAIN")
     assert rel(r, o.grain_radius()) <= 1e-10
     assert (r > 1.001e-6).any() and np.isclose(r, 1e-6, rtol=1e-14, atol=0).any()
+
+
+def test_heated_slot_against_the_cubic_and_the_oracle(fvs):
+    """The buoyant flow between a hot and a cold wall of
+    ``tests/test_oracle_convection.py`` (32 cells across, 80 steps of 8 ms
+    from rest): every field of the GPU path matches the oracle, and its
+    mid-height profile is the closed-form cubic of the fully developed flow
+    to the discretisation error the oracle shows (0.72 % of the peak)."""
+    from tests.test_oracle_convection import T_C, T_H, T_REF, D, mid_rows, slot_case, slot_exact
+    mesh, mat, walls = slot_case(32)
+    props = cases.props(material=mat, walls=walls, T_init=T_REF, **dict(TIGHT, p_rtol=1e-12))
+    o = Oracle(mesh, props)
+    T0 = T_C + (T_H - T_C) * o.g.xc[:, 0] / D
+    set_state(o, T0)
+    S = fvs.Solver(fvs.Mesh(mesh), props)
+    S.set_state(T0)
+    for _ in range(80):
+        o.step(8e-3)
+    S.step(8e-3, 80)
+    compare(o, S, 1e-7, fields=("T", "U", "P"))
+    v_ex = slot_exact(o.g.xc[:, 0], mat)
+    mid = mid_rows(mesh)
+    err = np.abs(S.query("U")[mid, 1] - v_ex[mid]).max() / np.abs(v_ex).max()
+    assert err < 0.008, err
