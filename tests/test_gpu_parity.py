@@ -519,3 +519,38 @@ def test_heated_slot_against_the_cubic_and_the_oracle(fvs):
     mid = mid_rows(mesh)
     err = np.abs(S.query("U")[mid, 1] - v_ex[mid]).max() / np.abs(v_ex).max()
     assert err < 0.008, err
+
+
+def test_freezing_out_and_fully_solid(fvs):
+    """Degenerate active sets: a small cavity with cold walls freezes out
+    within ten steps of 2 ms and is stepped on with no liquid or mushy cell
+    (empty momentum and pressure systems, pure conduction); a cavity that
+    starts below the solidus has no active cell from its first step.  The
+    active counts follow the oracle's step by step, the flow fields are zero
+    once nothing is active, and the temperatures match."""
+    m = box_mesh(8, 8, 2, (0.01, 0.01, 0.0025))
+    props = cases.props(walls=cases.all_walls(500.0), T_init=915.0, **TIGHT)
+    o, M, S = make_pair(fvs, m, props)
+    counts = []
+    for _ in range(16):
+        st_o = o.step(2e-3)
+        st = S.step(2e-3)
+        assert st["n_active"] == st_o["n_active"] == int(o.lm.sum())
+        counts.append(st["n_active"])
+    assert counts[0] > 0 and counts[-6:] == [0] * 6, counts
+    assert rel(S.query("T"), o.T) <= 1e-10
+    for name in ("U", "P", "FLUX"):
+        assert np.abs(S.query(name)).max() == 0.0, name
+    q, ref = S.query("QOI"), o.qoi()
+    assert np.isfinite(ref["t_f"]).all() and np.isfinite(q[:, 0]).all()
+    assert rel(q[:, 0], ref["t_f"]) < 1e-8
+
+    props = cases.props(walls=cases.all_walls(700.0), T_init=800.0, **TIGHT)
+    o, M, S = make_pair(fvs, m, props)
+    for _ in range(3):
+        o.step(2e-3)
+        st = S.step(2e-3)
+        assert st["n_active"] == 0 and st["n_ppe"] == 0
+    assert rel(S.query("T"), o.T) <= 1e-10
+    for name in ("U", "P", "FLUX"):
+        assert np.abs(S.query(name)).max() == 0.0, name
