@@ -200,6 +200,62 @@ def test_jittered_full_size_identities(fvs):
     assert rel(out[1]["P"], out[0]["P"]) <= 1e-6
 
 
+def test_bench_workload_in_its_launch_configuration(fvs):
+    """The timed workload itself: the 128^3 jittered, permuted cavity with the
+    solver settings, side stream and CUDA graphs of the step benchmark, 3 + 20
+    steps (cells start to freeze at step 11, after which the hierarchy is
+    refreshed).  Every step converges (no step of the measured run is taken
+    unconverged) without the fallback; in each of the last three the flux
+    carries no divergence beyond the pressure residual (Eq. 17), only flowing
+    faces carry flux and solid cells do not move.  After the 23 steps the
+    mixed-precision fields are within 1e-6 of the FP64 ones."""
+    import torch
+    c = cases.config_jittered(n=128)
+    m, dt = c["mesh"], c["dt"]
+    own = np.asarray(m["face_cells"])[:, 0]
+    nei = np.asarray(m["face_cells"])[:, 1]
+    inner = nei >= 0
+    X = np.asarray(m["nodes"])
+    fc = np.asarray(m["faces"])[inner]
+    Sf = 0.5 * np.cross(X[fc[:, 2]] - X[fc[:, 0]], X[fc[:, 3]] - X[fc[:, 1]])
+    oi, ni = own[inner], nei[inner]
+    nc = len(m["cells"])
+    out = {}
+    for precision in (0, 1):
+        # the step benchmark's settings
+        props = cases.props(p_rtol=1e-8, mom_rtol=1e-10, e_rtol=1e-10, e_tol_T=1e-6, max_e_iters=40,
+                            max_krylov_iters=1000, precision=precision)
+        stream = torch.cuda.Stream()
+        M = fvs.Mesh(m, stream=stream)
+        S = fvs.Solver(M, props, stream=stream)
+        refreshed = 0
+        for k in range(23):
+            T0 = S.query("T") if k >= 20 else None
+            st = S.step(dt)
+            assert st["status"] == 0 and st["fallback"] == 0 and st["p_relres"] <= 1e-8, (k, st)
+            refreshed += st["p_rebuilt"] == 2
+            if T0 is None:
+                continue
+            U, US, F, case = S.query("U"), S.query("USTAR"), S.query("FLUX"), S.query("FACE_CASE")
+            assert np.abs(U[T0 <= cases.AL_ALLOY["T_sol"]]).max(initial=0.0) == 0.0
+            flowing = (case == 1) | (case == 2)
+            assert np.abs(F[~flowing]).max(initial=0.0) == 0.0
+            flow = flowing[inner]
+            Fstar = np.einsum("fi,fi->f", Sf[flow], 0.5 * (US[oi[flow]] + US[ni[flow]]))
+            divF = np.bincount(own, weights=F, minlength=nc) - np.bincount(ni, weights=F[inner], minlength=nc)
+            divS = (np.bincount(oi[flow], weights=Fstar, minlength=nc)
+                    - np.bincount(ni[flow], weights=Fstar, minlength=nc))
+            assert np.linalg.norm(divF) <= 1.05e-8 * np.linalg.norm(divS)
+        assert refreshed > 0 and (S.query("TAG") == 0).any()
+        out[precision] = {k: S.query(k) for k in ("T", "U", "P")}
+        S.close()
+        M.close()
+    # measured on this workload by the step benchmark: 3.3e-7 K, 2.5e-7, 1.4e-8
+    assert np.abs(out[1]["T"] - out[0]["T"]).max() <= 1e-6
+    assert rel(out[1]["U"], out[0]["U"]) <= 1e-6
+    assert rel(out[1]["P"], out[0]["P"]) <= 1e-6
+
+
 def _run(fvs, m, props, T0, u0, steps, dt=1e-3):
     M = fvs.Mesh(m)
     S = fvs.Solver(M, props)
