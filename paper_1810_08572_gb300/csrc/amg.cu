@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <chrono>
 #include <climits>
+#include <cmath>
 #include <cstdlib>
+#include <cstring>
 
 #include "amg.cuh"
 
@@ -1006,6 +1008,58 @@ __global__ void k_jac_g(int64_t n, const int32_t* __restrict__ col, const T* __r
     if (ok && q == 0) y[i] = x[i] + omega * dinv[i] * (b[i] - acc);
   }
 }
+// Chebyshev sweep (three-term recurrence of the Chebyshev polynomials in
+// D^-1 A): y = x + beta (x - xp) + alpha D^-1 (b - A x), xp the iterate
+// before x (nullptr: zero).  xp and y may be the same array (each row reads
+// its own xp entry before writing y); x is gathered and must differ from y.
+template <typename T>
+__global__ void k_cheb(int64_t n, int w, const int32_t* __restrict__ col, const T* __restrict__ val, T alpha,
+                       T beta, const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x,
+                       const T* xp, T* y) {
+  GS(i, n) {
+    const T acc = fine_row(n, w, col, val, x, i);
+    const T xi = x[i];
+    const T d = xp ? xi - xp[i] : xi;
+    y[i] = xi + beta * d + alpha * dinv[i] * (b[i] - acc);
+  }
+}
+template <typename T, int G>
+__global__ void k_cheb_g(int64_t n, const int32_t* __restrict__ col, const T* __restrict__ val, T alpha, T beta,
+                         const T* __restrict__ dinv, const T* __restrict__ b, const T* __restrict__ x, const T* xp,
+                         T* y, const int32_t* __restrict__ rlen) {
+  const int lane = threadIdx.x & 31, q = lane & (G - 1);
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i0 = warp * (32 / G); i0 < n; i0 += nw * (32 / G)) {
+    const int64_t i = i0 + lane / G;
+    const bool ok = i < n;
+    T acc = ok ? coarse_part<T, G>(n, col, val, XVec<T>{x}, rlen[i], i, q) : (T)0;
+    acc = lanes_sum<T, G>(acc);
+    if (ok && q == 0) {
+      const T xi = x[i];
+      const T d = xp ? xi - xp[i] : xi;
+      y[i] = xi + beta * d + alpha * dinv[i] * (b[i] - acc);
+    }
+  }
+}
+// Gershgorin bound of the spectrum of D^-1 A: every eigenvalue lies in a disc
+// about 1 of radius sum_{j != i} |a_ij| / |a_ii|, so the largest real part is
+// at most max_i |D^-1_ii| sum_j |a_ij|.  The stored slots of a row are summed
+// (padding holds zeros); one atomic per warp, on the bit patterns, which order
+// non-negative doubles as their values.
+__global__ void k_gershgorin(int64_t n, int w, const double* __restrict__ val, const double* __restrict__ dinv,
+                             const int32_t* __restrict__ rlen, unsigned long long* out) {
+  double m = 0.0;
+  GS(i, n) {
+    const int len = rlen ? rlen[i] : w;
+    double s = 0.0;
+    for (int k = 0; k < len; ++k) s += fabs(val[(int64_t)k * n + i]);
+    m = fmax(m, s * fabs(dinv[i]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
 // lanes per row of a coarse level from its mean stored row length
 // (FVS_AMG_LANES forces one count)
 static int coarse_lanes(const AmgLevel& L) {
@@ -1281,6 +1335,10 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
   opt.coarsest = (int)env_num("FVS_AMG_COARSEST", opt.coarsest);
   opt.mis2_ratio = env_num("FVS_AMG_MIS2_RATIO", opt.mis2_ratio);
   opt.mis2_from = (int)env_num("FVS_AMG_MIS2_FROM", opt.mis2_from);
+  opt.smoother = (int)env_num("FVS_AMG_SMOOTHER", opt.smoother);
+  opt.cheb_ratio = env_num("FVS_AMG_CHEB_RATIO", opt.cheb_ratio);
+  if (opt.smoother != 1) opt.smoother = 0;
+  if (!(opt.cheb_ratio > 1.0)) opt.cheb_ratio = 4.0;
   if (opt.npre < 1) opt.npre = 1;
   if (opt.npost < 1) opt.npost = 1;
   DBuf<int> err, cnt;
@@ -1480,8 +1538,40 @@ fvs_status Amg::setup(cudaStream_t s, const Ell& A) {
             "coarsest %.2f fp32 %.2f\n", nc, ncomp, tph[0], tph[1], tph[2], tph[3], tph[4], tph[5], tph[6]);
   }
   FVS_TRY(count_stored(s));
+  if (opt.smoother == 1) FVS_TRY(cheb_bounds(s));
   ready = true;
   return FVS_OK;
+}
+
+fvs_status Amg::cheb_bounds(cudaStream_t s) {
+  const int nl = (int)lv.size();
+  FVS_TRY(gbound.alloc(nl + 1));
+  FVS_CUDA(cudaMemsetAsync(gbound.p, 0, sizeof(unsigned long long) * nl, s));
+  for (int l = 0; l + 1 < nl; ++l) {   // the coarsest level is solved, not smoothed
+    AmgLevel* L = lv[l].get();
+    if (L->n == 0) continue;
+    k_gershgorin<<<stride_grid(L->n, 256), 256, 0, s>>>(L->n, L->A->w, L->A->val, L->dinv,
+                                                       L->rlen.n ? L->rlen.p : nullptr, gbound.p + l);
+    FVS_COUNT_LAUNCH();
+  }
+  FVS_LAUNCH_CHECK();
+  std::vector<unsigned long long> h(nl, 0ULL);
+  FVS_CUDA(cudaMemcpyAsync(h.data(), gbound.p, sizeof(unsigned long long) * nl, cudaMemcpyDeviceToHost, s));
+  FVS_CUDA(cudaStreamSynchronize(s));
+  for (int l = 0; l < nl; ++l) {
+    double v;
+    memcpy(&v, &h[l], sizeof(v));
+    lv[l]->cheb_b = std::isfinite(v) ? v : 0.0;
+  }
+  ++bound_epoch;
+  return FVS_OK;
+}
+
+// the first sweep from a given iterate: weighted Jacobi, or the first step
+// of the Chebyshev recurrence (weight 1 / theta, theta the interval's centre)
+double Amg::first_weight(const AmgLevel& L) const {
+  if (opt.smoother != 1 || !(L.cheb_b > 0.0)) return opt.omega;
+  return 2.0 / (L.cheb_b * (1.0 + 1.0 / opt.cheb_ratio));
 }
 
 fvs_status Amg::coarsest_setup(cudaStream_t s) {
@@ -1765,6 +1855,7 @@ fvs_status Amg::refresh(cudaStream_t s, const int32_t* act, const uint8_t* ppe) 
             tph[0], tph[1], tph[2], tph[3]);
   masked = true;
   FVS_TRY(count_stored(s));
+  if (opt.smoother == 1) FVS_TRY(cheb_bounds(s));
   ready = true;
   return FVS_OK;
 }
@@ -1814,7 +1905,7 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y, bool x0_ready)
   T* xa = f32 ? (T*)L->xf.p : (T*)L->x.p;
   T* xb = f32 ? (T*)L->tf.p : (T*)L->t.p;
   T* r = f32 ? (T*)L->rf.p : (T*)L->r.p;
-  T* cb = f32 ? (T*)C->bf.p : (T*)C->b.p;
+  T* cbv = f32 ? (T*)C->bf.p : (T*)C->b.p;
   T* cy = f32 ? (T*)C->yf.p : (T*)C->y.p;
   const double vb = (double)sizeof(T);
   // kernel timing: every level is credited to the hierarchy's fine operator,
@@ -1832,22 +1923,49 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y, bool x0_ready)
   const char* n_res = f32 ? (cl ? "residual_f32_coarse" : "residual_f32") : (cl ? "residual_vc_coarse" : "residual_vc");
   const int G = rl ? coarse_lanes(*L) : 1;   // coarse levels: G lanes per row
   const int gg = stride_grid(n * G, 256);
+  const T w0 = (T)first_weight(*L);
   auto jac = [&](T* xin, T* xout) {
     ProfScope ps(pkey, n_jac, jac_bytes, s);
-    if (!rl) k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, (T)opt.omega, dinv, b, xin, xout);
-    else if (G == 1) k_jac_g<T, 1><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
-    else if (G == 2) k_jac_g<T, 2><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
-    else if (G == 4) k_jac_g<T, 4><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
-    else k_jac_g<T, 8><<<gg, 256, 0, s>>>(n, A.col, val, (T)opt.omega, dinv, b, xin, xout, rl);
+    if (!rl) k_jac<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, w0, dinv, b, xin, xout);
+    else if (G == 1) k_jac_g<T, 1><<<gg, 256, 0, s>>>(n, A.col, val, w0, dinv, b, xin, xout, rl);
+    else if (G == 2) k_jac_g<T, 2><<<gg, 256, 0, s>>>(n, A.col, val, w0, dinv, b, xin, xout, rl);
+    else if (G == 4) k_jac_g<T, 4><<<gg, 256, 0, s>>>(n, A.col, val, w0, dinv, b, xin, xout, rl);
+    else k_jac_g<T, 8><<<gg, 256, 0, s>>>(n, A.col, val, w0, dinv, b, xin, xout, rl);
+    FVS_COUNT_LAUNCH();
+  };
+  // Chebyshev smoother: interval [cb / ratio, cb], centre th, half-width de;
+  // step k >= 1 of the recurrence has rho_k = 1 / (2 th / de - rho_{k-1}),
+  // rho_0 = de / th, alpha = 2 rho_k / de, beta = rho_k rho_{k-1}
+  const bool cheb = opt.smoother == 1 && L->cheb_b > 0.0;
+  const double cb = L->cheb_b, th = 0.5 * (cb + cb / opt.cheb_ratio), de = 0.5 * (cb - cb / opt.cheb_ratio);
+  auto cheb_step = [&](T* xin, const T* xprev, T* xout, double& rho) {
+    const double rn = 1.0 / (2.0 * th / de - rho);
+    const T alpha = (T)(2.0 * rn / de), beta = (T)(rn * rho);
+    rho = rn;
+    ProfScope ps(pkey, n_jac, jac_bytes + vb * (double)n, s);
+    if (!rl) k_cheb<T><<<g, 256, 0, s>>>(n, A.w, A.col, val, alpha, beta, dinv, b, xin, xprev, xout);
+    else if (G == 1) k_cheb_g<T, 1><<<gg, 256, 0, s>>>(n, A.col, val, alpha, beta, dinv, b, xin, xprev, xout, rl);
+    else if (G == 2) k_cheb_g<T, 2><<<gg, 256, 0, s>>>(n, A.col, val, alpha, beta, dinv, b, xin, xprev, xout, rl);
+    else if (G == 4) k_cheb_g<T, 4><<<gg, 256, 0, s>>>(n, A.col, val, alpha, beta, dinv, b, xin, xprev, xout, rl);
+    else k_cheb_g<T, 8><<<gg, 256, 0, s>>>(n, A.col, val, alpha, beta, dinv, b, xin, xprev, xout, rl);
     FVS_COUNT_LAUNCH();
   };
   if (!x0_ready) {
     ProfScope ps(pkey, n_jac0, 3.0 * vb * (double)n, s);
-    k_jac0<T><<<g, 256, 0, s>>>(n, (T)opt.omega, dinv, b, xa); FVS_COUNT_LAUNCH();
+    k_jac0<T><<<g, 256, 0, s>>>(n, w0, dinv, b, xa); FVS_COUNT_LAUNCH();
   }
-  for (int k = 1; k < opt.npre; ++k) {
-    jac(xa, xb);
-    T* t = xa; xa = xb; xb = t;
+  {
+    double rho = cheb ? de / th : 0.0;
+    const T* xprev = nullptr;   // the pre-smoothing starts from zero
+    for (int k = 1; k < opt.npre; ++k) {
+      if (cheb) {
+        cheb_step(xa, xprev, xb, rho);
+        xprev = xa;
+      } else {
+        jac(xa, xb);
+      }
+      T* t = xa; xa = xb; xb = t;
+    }
   }
   {
     ProfScope ps(pkey, n_res, res_bytes, s);
@@ -1864,20 +1982,24 @@ fvs_status Amg::vcycle_t(cudaStream_t s, int l, const T* b, T* y, bool x0_ready)
   if (next_sweeps) {
     T* cx = f32 ? (T*)C->xf.p : (T*)C->x.p;
     const T* cdinv = f32 ? (const T*)C->dinvf.p : (const T*)C->dinv.p;
-    k_restrict_jac0<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cb, (T)opt.omega, cdinv,
-                                                             cx);
+    k_restrict_jac0<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cbv,
+                                                             (T)first_weight(*C), cdinv, cx);
   } else {
-    k_restrict<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cb);
+    k_restrict<T><<<stride_grid(C->n, 256), 256, 0, s>>>(C->n, L->mptr, L->midx, r, cbv);
   }
   FVS_COUNT_LAUNCH();
   FVS_LAUNCH_CHECK();
-  FVS_TRY(vcycle_t<T>(s, l + 1, cb, cy, next_sweeps));
+  FVS_TRY(vcycle_t<T>(s, l + 1, cbv, cy, next_sweeps));
   k_prolong<T><<<g, 256, 0, s>>>(n, L->agg, cy, (T)opt.coarse_scale, xa); FVS_COUNT_LAUNCH();
-  for (int k = 0; k < opt.npost; ++k) {
-    T* out = (k == opt.npost - 1) ? y : xb;
-    jac(xa, out);
-    xb = xa;
-    xa = out;
+  {
+    double rho = cheb ? de / th : 0.0;
+    for (int k = 0; k < opt.npost; ++k) {
+      T* out = (k == opt.npost - 1) ? y : xb;
+      if (cheb && k > 0) cheb_step(xa, xb, out, rho);   // xb holds the iterate before xa
+      else jac(xa, out);
+      xb = xa;
+      xa = out;
+    }
   }
   FVS_LAUNCH_CHECK();
   return FVS_OK;

@@ -28,6 +28,7 @@ struct AmgLevel {
   DBuf<uint8_t> dirty;  // rows changed since the last setup or refresh
   int64_t n = 0;
   double stored = 0.0;  // operator entries the V-cycle reads (coarse levels: sum of rlen)
+  double cheb_b = 0.0;  // Chebyshev smoother: Gershgorin bound of the spectrum of D^-1 A
 };
 
 struct AmgOptions {
@@ -40,6 +41,12 @@ struct AmgOptions {
   double mis2_ratio = 0.85; // distance-2 aggregation where distance-1 sets keep more than this share of rows
   int mis2_from = 1 << 30;  // levels from this one on aggregate by distance-2 sets directly
   bool fp32 = false;       // V-cycle in single precision
+  // smoother: 0 weighted Jacobi (omega), 1 Chebyshev polynomial in D^-1 A
+  // on [b / cheb_ratio, b] with b each level's Gershgorin bound (degree npre
+  // before and npost after the coarse correction; degree 1 is Jacobi with
+  // the weight 2 / (b + b / cheb_ratio))
+  int smoother = 0;
+  double cheb_ratio = 4.0;
 };
 
 struct Amg : Precond {
@@ -87,7 +94,9 @@ struct Amg : Precond {
   uint64_t gj_key = 0;
   ~Amg() { if (gj_exec) cudaGraphExecDestroy(gj_exec); }
   uint64_t signature() const override {
-    return version * 2654435761ULL + (opt.fp32 ? 1 : 0) + (masked ? 2 : 0);
+    // Chebyshev weights are launch arguments: new bounds need a new graph
+    return version * 2654435761ULL + (opt.fp32 ? 1 : 0) + (masked ? 2 : 0) +
+           (opt.smoother == 1 ? bound_epoch * 4 : 0);
   }
   // subtract the component mean on every singular component (fine level)
   fvs_status project(cudaStream_t s, double* v);
@@ -100,6 +109,12 @@ struct Amg : Precond {
   fvs_status vcycle_t(cudaStream_t s, int l, const T* b, T* y, bool x0_ready = false);
   fvs_status coarsest_setup(cudaStream_t s);
   fvs_status setup_fp32(cudaStream_t s);
+  // Chebyshev smoother: Gershgorin bounds of every smoothed level (after a
+  // setup or a refresh, when the operator values are final)
+  fvs_status cheb_bounds(cudaStream_t s);
+  double first_weight(const AmgLevel& L) const;   // weight of the first sweep
+  DBuf<unsigned long long> gbound;
+  uint64_t bound_epoch = 0;
 };
 
 struct AmgProjector : Projector {

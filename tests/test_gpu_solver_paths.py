@@ -1,9 +1,10 @@
 """Solver paths beyond the default one: the single-grid pressure solve on a
 system of several liquid pockets, a refused non-finite right side, the
 bench workload's jittered mesh at a size no oracle can follow (checked
-through identities that hold at any size), and the two operator reductions
-that must not change the answer: face-only stencils on orthogonal meshes
-and the AMG hierarchy built on the face couplings of the pressure matrix."""
+through identities that hold at any size), and three choices that must not
+change the answer: face-only stencils on orthogonal meshes, the AMG
+hierarchy built on the face couplings of the pressure matrix, and the
+Chebyshev smoother in place of weighted Jacobi."""
 import numpy as np
 import pytest
 
@@ -305,3 +306,42 @@ def test_hierarchy_on_face_couplings_changes_only_the_iterations(fvs, monkeypatc
     full, _ = _run(fvs, m, props, T0, u0, 3)
     for k in ("T", "U", "P", "FLUX"):
         assert rel(compact[k], full[k]) <= 1e-10, k
+
+
+def _steps_with_stats(fvs, m, props, T0, u0, steps, dt=1e-3):
+    M = fvs.Mesh(m)
+    S = fvs.Solver(M, props)
+    S.set_state(T0, u0)
+    its = []
+    for _ in range(steps):
+        st = S.step(dt)
+        assert st["status"] == 0 and st["fallback"] == 0 and st["p_relres"] <= 1e-12
+        assert st["amg_levels"] >= 2
+        its.append(st["p_its"])
+    out = {k: S.query(k) for k in ("T", "U", "P", "FLUX")}
+    S.close()
+    M.close()
+    return out, its
+
+
+@pytest.mark.parametrize("jitter,precision", [(0.2, 0), (0.2, 1), (0.0, 0)])
+def test_chebyshev_smoother_changes_only_the_iterations(fvs, monkeypatch, jitter, precision):
+    """The Chebyshev smoother (FVS_AMG_SMOOTHER=1: on every level a
+    Chebyshev polynomial in D^-1 A on [b/4, b], b the level's Gershgorin
+    bound; degree 1 before and 2 after the coarse correction under BiCGStab,
+    1 and 1 under CG) preconditions the same solves as weighted Jacobi: three
+    steps of a multi-level hierarchy with three liquid pockets agree to the
+    solve tolerance, jittered (BiCGStab, FP64 and the FP32 V-cycle) and
+    orthogonal (CG), with a comparable number of iterations."""
+    m = box_mesh(32, 32, 8, cases.CAVITY, jitter=jitter, jitter_seed=91, permute_seed=92)
+    T0 = pockets_field(m, seed=5)
+    rng = np.random.default_rng(11)
+    u0 = rng.normal(scale=2e-3, size=(len(T0), 3))
+    props = cases.props(precision=precision, **TIGHT)
+    jac, its_j = _steps_with_stats(fvs, m, props, T0, u0, 3)
+    monkeypatch.setenv("FVS_AMG_SMOOTHER", "1")
+    che, its_c = _steps_with_stats(fvs, m, props, T0, u0, 3)
+    tol = 1e-10 if precision == 0 else 1e-8
+    for k in ("T", "U", "P"):
+        assert rel(che[k], jac[k]) <= tol, (k, rel(che[k], jac[k]))
+    assert sum(its_c) <= 2 * sum(its_j), (its_c, its_j)
