@@ -105,6 +105,37 @@ struct JacobiPrecond : Precond {
   }
 };
 
+// Line preconditioner: z = P^-1 r with P the diagonal (plus dextra) and the
+// couplings along chains of cells, each cell joined to the neighbours it is
+// most strongly coupled to where that choice is mutual (a row's two largest
+// off-diagonal magnitudes).  Strongly anisotropic cells (thin in one
+// direction) make those chains lines across the thin direction, where
+// Jacobi converges slowly.  P restricted to one chain is tridiagonal and is
+// solved exactly; cells on no chain take the Jacobi step.  The chains are
+// found once from the operator (build) and stored 32 lines to a group,
+// position-major within the group, so a warp's loads at one position are
+// contiguous; factor() recomputes the tridiagonal factors from the current
+// values, apply() does one forward and one backward substitution per line.
+struct LinePrecond : Precond {
+  const Ell* A = nullptr;
+  const double* dextra = nullptr;   // extra diagonal at factor() time (or null)
+  int64_t n = 0;
+  int w = 0;
+  const int32_t* built_from = nullptr;   // column array the chains were found in
+  int64_t nlines = 0, ngroups = 0, padded = 0;
+  int max_len = 0;
+  DBuf<int64_t> goff;      // [ngroups] first entry of each group
+  DBuf<int32_t> llen;      // [ngroups * 32] length of each line (0: no line)
+  DBuf<int32_t> cell;      // [padded] cell at (group, position, lane)
+  DBuf<int8_t> sprev, snext;   // slot of the previous / next cell of the line in the cell's row (-1: none)
+  DBuf<double> lo, inv, cp;    // sub-diagonal, 1 / pivot, super-diagonal / pivot
+  bool ready = false;
+  fvs_status build(cudaStream_t s, const Ell& A);
+  fvs_status factor(cudaStream_t s);
+  fvs_status apply(cudaStream_t s, const double* r, double* z) override;
+  uint64_t signature() const override { return (uint64_t)(uintptr_t)inv.p * 29u + (uint64_t)n; }
+};
+
 struct KrylovWork {
   DBuf<double> r, rh, p, ph, v, sv, sh, t, z, q;
   fvs_status ensure(int64_t n);

@@ -1485,6 +1485,13 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
     J.A = &s->Ke;
     J.dextra = s->edx;
     J.dinv = s->jinv_e;
+    const char* el = getenv("FVS_ENERGY_LINES");
+    const bool lines = el && *el == '1';
+    if (lines && (!s->eline.ready || s->eline.built_from != s->Ke.col.p || s->eline.n != s->Ke.n ||
+                  s->eline.w != s->Ke.w))
+      FVS_TRY(s->eline.build(st, s->Ke));
+    s->eline.dextra = s->edx;
+    Precond& PE = lines ? static_cast<Precond&>(s->eline) : static_cast<Precond&>(J);
     // Tnew / fsnew hold the iterate m; Tlin the linear solution
     DBuf<double>& Tm = s->Tnew;
     DBuf<double>& fsm = s->fsnew;
@@ -1500,8 +1507,9 @@ fvs_status solver_step(fvs_solver s, double dt, fvs_step_stats* stats) {
                                                           s->jinv_e);
       FVS_COUNT_LAUNCH();
       FVS_LAUNCH_CHECK();
+      if (lines) FVS_TRY(s->eline.factor(st));
       SolveResult r;
-      FVS_TRY(bicgstab(st, s->red, s->kw, s->Ke, s->edx, J, s->erhs, s->Tlin, rtol_m,
+      FVS_TRY(bicgstab(st, s->red, s->kw, s->Ke, s->edx, PE, s->erhs, s->Tlin, rtol_m,
                        s->props.max_krylov_iters, nullptr, r, 0.0, &s->g_e));
       S.e_lin_its += r.iters;
       if (!r.converged) {

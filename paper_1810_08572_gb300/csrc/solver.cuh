@@ -55,6 +55,9 @@ struct fvs_solver_s {
   // inverse Jacobi diagonals of the energy system (per latent-heat pass) and
   // of the momentum system (per step)
   fvs::DBuf<double> jinv_e, jinv_m;
+  // line preconditioner of the energy system (FVS_ENERGY_LINES=1 instead of
+  // Jacobi): chains found once from the energy operator, factors per pass
+  fvs::LinePrecond eline;
   double time = 0.0;
   int64_t nstep = 0;
 
