@@ -26,10 +26,10 @@ struct LineLayout {
 // `strong` times the first (so that the chains of a thin direction do not
 // join at their ends through a weak coupling); i and j are joined where
 // each chose the other, so every cell has at most two partners and the
-// chains are paths and cycles.  Paths are walked from an end, cycles from their
-// first cell; a walk longer than max_line starts a new line.  Lines are
-// sorted by decreasing length and stored 32 to a group, each group padded
-// to its longest line, position-major inside the group.
+// chains are paths and cycles.  Paths are walked from an end, cycles from
+// their first cell; a walk longer than max_line starts a new line.  Lines
+// are sorted by decreasing length and stored 32 to a group, each group
+// padded to its longest line, position-major inside the group.
 inline void build_line_layout(const int32_t* col, const double* val, int64_t n, int w, int max_line,
                               LineLayout& L, double strong = 0.25) {
   L = LineLayout();
