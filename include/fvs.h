@@ -176,7 +176,7 @@ typedef struct {
                                    and the energy equation is conduction with
                                    latent heat.  0: the full method            */
   int32_t n_k;                  /* points of a piecewise-linear conductivity
-                                   k(T) of the metal (Section 4 uses a table;
+                                   k(T) of the metal (Section 3 uses a table;
                                    0: the constant mat.k), at most 16          */
   const double* k_T;            /* host [n_k] increasing temperatures (K)       */
   const double* k_val;          /* host [n_k] conductivities (W/m K), held

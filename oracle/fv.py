@@ -39,7 +39,7 @@ Readings of points the paper leaves open:
    carries the orthogonal flux A (T_inf - T_C1)/(d_1/k_1 + 1/h) through the
    half cell and the film, d_1 the distance from the cell centre to the face
    centre; its vertices are free (cell means), as on adiabatic walls
- * a temperature-dependent conductivity k(T) of the metal (Section 4 uses a
+ * a temperature-dependent conductivity k(T) of the metal (Section 3 uses a
    table; piecewise linear here, held constant outside it) is evaluated per
    face at the start of each step, at the mean of the two owner temperatures
    T^n (a fixed-temperature wall: the mean of the cell and wall values; a
@@ -72,9 +72,11 @@ BC_CONVECTIVE = 2
 # Geometry (Section 2.3, Fig. 1, Eq. 11-12)
 # ----------------------------------------------------------------------------
 class Geometry:
-    """Face and cell geometry of an unstructured hexahedral mesh."""
+    """Face and cell geometry of an unstructured hexahedral mesh.
+    Section 2.3 (Fig. 1), the geometry behind Eq. 11-12."""
 
     def __init__(self, nodes, cells, faces, face_cells, patch):
+        """Section 2.3: face vectors, centres, volumes and the local Jacobian of Eq. 12."""
         X = np.asarray(nodes, dtype=np.float64)
         self.nodes = X
         self.cells = np.asarray(cells, dtype=np.int64)
@@ -148,6 +150,7 @@ class Geometry:
         self.boundary_vertex[self.faces[~self.interior].ravel()] = True
 
     def _vdiff(self, a, b):
+        """Differences along a face's two diagonals: the eta and zeta derivatives of Eq. 12."""
         fi = np.arange(self.Nf)
         r = np.concatenate([fi, fi])
         c = np.concatenate([self.faces[:, a], self.faces[:, b]])
@@ -156,7 +159,8 @@ class Geometry:
 
     # -- face normal derivative (Eq. 11) -------------------------------------
     def normal_derivative_rows(self, Dxi, Deta, Dzeta):
-        """A_f (n . grad phi)_f as rows over cells, from the three local differences."""
+        """A_f (n . grad phi)_f as rows over cells, from the three local differences.
+        Eq. 11 with the local derivatives of Eq. 12."""
         A = self.Af
         return (sp.diags(A * (1.0 / self.ndotd + self.w[:, 0])) @ Dxi
                 + sp.diags(A * self.w[:, 1]) @ Deta
@@ -168,7 +172,8 @@ class Geometry:
 # ----------------------------------------------------------------------------
 def vertex_operator(g, fixed_mask, fixed_value):
     """phi_v = mean of the cells around v, or a fixed wall value where masked.
-    Returns (P [Nv x Nc], c [Nv]) with phi_v = P phi + c."""
+    Returns (P [Nv x Nc], c [Nv]) with phi_v = P phi + c.
+    Section 2.3: a vertex value is the mean of the cells around the vertex."""
     keep = sp.diags((~fixed_mask).astype(np.float64))
     return (keep @ g.Pavg).tocsr(), np.where(fixed_mask, fixed_value, 0.0)
 
@@ -176,7 +181,8 @@ def vertex_operator(g, fixed_mask, fixed_value):
 def diffusion_operator(g, face_mask, vP, vc, phi_b):
     """Affine operator L phi + l = sum over masked faces of sigma A_f (n . grad phi)_f.
 
-    ``phi_b`` is the value at boundary faces (C2 := face centre)."""
+    ``phi_b`` is the value at boundary faces (C2 := face centre).
+    Eq. 11-12: direct and cross diffusion through the local Jacobian."""
     Deta = g.E31 @ vP
     Dzeta = g.E42 @ vP
     N = g.normal_derivative_rows(g.Dxi, Deta, Dzeta)
@@ -187,14 +193,16 @@ def diffusion_operator(g, face_mask, vP, vc, phi_b):
 
 
 def velocity_diffusion(g):
-    """No-slip walls: wall vertices and wall faces carry u = 0."""
+    """No-slip walls: wall vertices and wall faces carry u = 0.
+    The diffusion term of Eq. 6, discretised as in Section 2.3."""
     vP, vc = vertex_operator(g, g.boundary_vertex, 0.0)
     return diffusion_operator(g, np.ones(g.Nf, bool), vP, vc, np.zeros(g.Nf))
 
 
 def wall_data(g, walls):
     """Per face: wall type (-1 interior), wall temperature (or ambient
-    temperature of a convective wall) and film coefficient h."""
+    temperature of a convective wall) and film coefficient h.
+    Boundary data only (the wall conditions of Sections 3-4); no method arithmetic."""
     btype = np.full(g.Nf, -1)
     bval = np.zeros(g.Nf)
     bh = np.zeros(g.Nf)
@@ -215,7 +223,8 @@ def temperature_diffusion(g, walls, k_face=None, interface=None, G_int=None, G_c
     (a metal cell against a mold cell) carry only the orthogonal flux
     G_int (T_C2 - T_C1) through the series resistance of the two half cells
     and the interface coefficient; convective wall faces carry
-    G_conv (T_inf - T_C1) (no cross terms on either)."""
+    G_conv (T_inf - T_C1) (no cross terms on either).
+    The conduction term of Eq. 4, discretised by Eq. 11-12."""
     btype, bval, bh = wall_data(g, walls)
     dir_face = btype == BC_DIRICHLET
     conv_face = btype == BC_CONVECTIVE
@@ -261,7 +270,8 @@ def temperature_diffusion(g, walls, k_face=None, interface=None, G_int=None, G_c
 # ----------------------------------------------------------------------------
 def scheil_law(m):
     """(kp, T_f, T_eps) of the smeared Gulliver-Scheil law if the material
-    selects it (fs_model = 1), else None (linear solid fraction)."""
+    selects it (fs_model = 1), else None (linear solid fraction).
+    Eq. 5 and its smeared form, Eq. 21."""
     if int(m.get("fs_model", 0)) == 1:
         return (float(m["kp"]), float(m["T_f"]), float(m["T_eps"]))
     return None
@@ -291,7 +301,8 @@ def solid_fraction(T, T_sol, T_liq, scheil=None):
 
 
 def solid_fraction_slope(T, T_sol, T_liq, scheil=None):
-    """dfs/dT, taken at each kink from the side nearer the mushy interior."""
+    """dfs/dT, taken at each kink from the side nearer the mushy interior.
+    Slope of Eq. 5 / Eq. 21, used by the latent-heat linearisation of Eq. 18-20."""
     T = np.asarray(T, dtype=np.float64)
     if scheil is None:
         return np.where((T >= T_sol) & (T <= T_liq), -1.0 / (T_liq - T_sol), 0.0)
@@ -330,6 +341,7 @@ def grain_update(r2, fs_a, fs_b, dt, kp, D_s):
 
 
 def darcy_coefficient(fs, C, eps):
+    """Eq. 3: the Blake-Kozeny drag coefficient of Section 2.1."""
     return C * fs * fs / ((1.0 - fs) ** 3 + eps)
 
 
@@ -347,12 +359,14 @@ def yield_strength_mpa(sdas):
 # Linear solves
 # ----------------------------------------------------------------------------
 def solve(A, b):
+    """Library primitive: a sparse direct solve (no method arithmetic)."""
     x = spla.spsolve(A.tocsc(), b)
     return np.atleast_1d(x)
 
 
 def pressure_components(App):
-    """Connected parts of the pressure system (symmetric closure of its pattern)."""
+    """Connected parts of the pressure system (symmetric closure of its pattern).
+    Section 2.5: the disjoint liquid pockets of the pressure system."""
     S = (abs(App) + abs(App).T).tocsr()
     S.eliminate_zeros()
     return connected_components(S, directed=False)
@@ -388,9 +402,11 @@ def solve_singular(App, b):
 # The solver state and one time step (Section 2.2, steps 1-5)
 # ----------------------------------------------------------------------------
 class Oracle:
-    """One deterministic run of the method on one mesh."""
+    """One deterministic run of the method on one mesh.
+    Section 2.2: the fractional-step algorithm, one step at a time."""
 
     def __init__(self, mesh, props):
+        """Base operators of Section 2.3 and the material data of Section 2.1."""
         self.g = g = Geometry(mesh["nodes"], mesh["cells"], mesh["faces"],
                               mesh["face_cells"], mesh["patch"])
         self.m = dict(props["material"])
@@ -443,7 +459,8 @@ class Oracle:
 
     # -- helpers ---------------------------------------------------------------
     def k_metal(self, T):
-        """Conductivity of the metal at temperatures T."""
+        """Conductivity of the metal at temperatures T.
+        k(T) of Section 3 (the validation ingot's table), piecewise linear between table points."""
         if self.k_table is None:
             return np.full(np.shape(T), float(self.m["k"]))
         return np.interp(T, self.k_table[0], self.k_table[1])
@@ -451,7 +468,8 @@ class Oracle:
     def conduction(self, T):
         """Conductive operator (L T + l = sum over faces of the conductive
         flux) with the conductivities of the temperature field T (only read
-        with a k(T) table)."""
+        with a k(T) table).
+        The conduction term of Eq. 4 (Eq. 11-12), with the mold of Section 4."""
         g, m, mold = self.g, self.m, self.mold
         metal = self.metal
         q = np.maximum(g.neigh, 0)
@@ -475,20 +493,24 @@ class Oracle:
                                      G_conv=G_conv)
 
     def reset_grain(self):
+        """Initial grain radius of the growth law, Eq. 24-26."""
         r0 = self.grain["r0"] if self.grain else 0.0
         self.r2 = np.where(self.metal, r0 * r0, 0.0)
 
     def grain_radius(self):
-        """Grain radius per cell (m); 0 in the mold."""
+        """Grain radius per cell (m); 0 in the mold.
+        Eq. 24-26."""
         return np.sqrt(self.r2)
 
     def fs_of(self, T):
-        """Solid fraction of every cell at temperatures T (0 in the mold)."""
+        """Solid fraction of every cell at temperatures T (0 in the mold).
+        Eq. 5 / Eq. 21, or the linear law between solidus and liquidus."""
         m = self.m
         return np.where(self.metal, solid_fraction(T, m["T_sol"], m["T_liq"], self.scheil), 0.0)
 
     def conv(self, phi, F):
-        """Conv(phi, F)_c = sum_f sigma F_f (phi_C1 + phi_C2)/2 (walls carry F = 0)."""
+        """Conv(phi, F)_c = sum_f sigma F_f (phi_C1 + phi_C2)/2 (walls carry F = 0).
+        The convection term of Eq. 6, discretised as in Section 2.3."""
         return self.g.Div @ (F * (self.g.Avg @ phi))
 
     def face_cases(self, lm):
@@ -532,6 +554,7 @@ class Oracle:
 
     # -- the step ------------------------------------------------------------------
     def step(self, dt):
+        """Section 2.2: tags, predictor (Eq. 6), pressure (Eq. 9), correction (Eq. 8, 17), energy (Eq. 4, 18-20)."""
         g, m = self.g, self.m
         rho, mu = m["rho"], m["mu"]
         T_n, fs_n = self.T, self.fs
@@ -634,7 +657,8 @@ class Oracle:
         return u_star, u_new, F_new, p, case, ppe, b_full
 
     def energy_residual(self, T, dt, T_n, fs_n, T_o, F_n, F_o):
-        """R(T) of the discrete energy equation (all terms moved to the left)."""
+        """R(T) of the discrete energy equation (all terms moved to the left).
+        Eq. 4 in the discrete form of Eq. 18-20."""
         g, m = self.g, self.m
         rcp, rL = self.rcp, self.rL
         conv = 1.5 * self.conv(T_n, F_n) - 0.5 * self.conv(T_o, F_o)
@@ -678,6 +702,7 @@ class Oracle:
         return T, fs, it
 
     def update_crossings(self, T_n, T_new, dt):
+        """Crossing times behind Eq. 22 (local solidification time and cooling rate)."""
         m = self.m
         for which, Tc in (("t_liq", m["T_liq"]), ("t_sol", m["T_sol"])):
             arr = getattr(self, which)
@@ -687,7 +712,8 @@ class Oracle:
 
     def qoi(self):
         """Local solidification time, cooling rate, SDAS and yield strength
-        per cell (NaN where the cell has not yet passed the solidus)."""
+        per cell (NaN where the cell has not yet passed the solidus).
+        Eq. 22-23."""
         m = self.m
         done = self.metal & (self.t_sol >= 0) & (self.t_liq >= 0)
         tf = np.where(done, self.t_sol - self.t_liq, np.nan)
@@ -712,6 +738,7 @@ class Oracle:
         return np.array([t_total, lam, ys, self.grain_radius()[metal].max()])
 
     def run(self, dt, nsteps):
+        """Repeated steps of Section 2.2."""
         for _ in range(nsteps):
             self.step(dt)
         return self
@@ -732,6 +759,7 @@ def temperature_from_enthalpy(H, cp, L, T_sol, T_liq, scheil=None):
     T1, T2 = T_sol - T_eps, T_sol + T_eps
 
     def enthalpy(T):
+        """H(T) of Eq. 4-5."""
         return cp * T + L * (1.0 - solid_fraction(T, T_sol, T_liq, scheil))
 
     H1, H2, H3 = cp * T1, float(enthalpy(T2)), cp * T_liq + L

@@ -17,10 +17,12 @@ from scipy.special import erf
 
 
 def gelu(z):
+    """GELU(x) = x Phi(x), the surrogate's activation (the surrogate is not in the paper; it stands in for the collocation fits of Section 2.7 inside the Monte Carlo loop)."""
     return 0.5 * z * (1.0 + erf(z / np.sqrt(2.0)))
 
 
 def gelu_grad(z):
+    """Derivative of GELU: Phi(x) + x phi(x)."""
     return 0.5 * (1.0 + erf(z / np.sqrt(2.0))) + z * np.exp(-0.5 * z * z) / np.sqrt(2.0 * np.pi)
 
 
@@ -48,6 +50,7 @@ def forward(params, X):
 
 
 def loss(params, X, Y):
+    """Mean squared error over batch and outputs."""
     out, _ = forward(params, X)
     return np.mean((out - Y) ** 2)
 
@@ -67,10 +70,12 @@ def backward(params, X, Y):
 
 
 def flatten(params):
+    """Parameter packing (no arithmetic)."""
     return np.concatenate([np.concatenate([W.ravel(), b]) for W, b in params])
 
 
 def unflatten(vec, sizes):
+    """Parameter unpacking (no arithmetic)."""
     params, k = [], 0
     for a, b in zip(sizes[:-1], sizes[1:]):
         W = vec[k:k + a * b].reshape(b, a)

@@ -32,7 +32,8 @@ def basis_1d(family, xi, nmax):
     """Orthonormal 1-D polynomials psi_0..psi_nmax at xi: probabilists'
     Hermite He_n/sqrt(n!) (He_{n+1} = xi He_n - n He_{n-1}) or Legendre
     sqrt(2n+1) P_n ((n+1) P_{n+1} = (2n+1) xi P_n - n P_{n-1}), both
-    normalised to unit variance under their distribution."""
+    normalised to unit variance under their distribution.
+    Eq. 27."""
     xi = np.asarray(xi, dtype=np.float64)
     P = np.zeros((nmax + 1,) + xi.shape)
     P[0] = 1.0
@@ -49,7 +50,8 @@ def basis_1d(family, xi, nmax):
 
 
 def multi_indices(d, p):
-    """All alpha in N^d with |alpha| <= p, graded by total degree (alpha = 0 first)."""
+    """All alpha in N^d with |alpha| <= p, graded by total degree (alpha = 0 first).
+    The total-degree truncation of Eq. 27."""
     out = []
     for deg in range(p + 1):
         for a in itertools.product(range(deg + 1), repeat=d):
@@ -59,9 +61,11 @@ def multi_indices(d, p):
 
 
 class PCE:
-    """Polynomial chaos expansion of n_out outputs in d inputs, total degree p."""
+    """Polynomial chaos expansion of n_out outputs in d inputs, total degree p.
+    Eq. 27-28."""
 
     def __init__(self, families, params, degree):
+        """Eq. 27-28."""
         self.fam = list(families)
         self.par = [tuple(map(float, q)) for q in params]
         self.d = len(self.fam)
@@ -70,6 +74,7 @@ class PCE:
         self.coef = None
 
     def standardise(self, X):
+        """Section 2.7: inputs mapped to the standard variables of Eq. 27."""
         X = np.atleast_2d(np.asarray(X, dtype=np.float64))
         xi = np.empty_like(X)
         for j, (f, (a, b)) in enumerate(zip(self.fam, self.par)):
@@ -94,23 +99,28 @@ class PCE:
         return self
 
     def __call__(self, X):
+        """Eq. 27 evaluated at new inputs."""
         return self.vandermonde(X) @ self.coef
 
     def mean(self):
+        """Mean of the expansion of Eq. 27 (its constant term)."""
         return self.coef[0]
 
     def variance(self):
+        """Variance of the expansion of Eq. 27 (sum of squared non-constant terms)."""
         return (self.coef[1:] ** 2).sum(axis=0)
 
     def sobol_total(self):
         """Total index of input j: the variance share of every term with
-        alpha_j > 0.  Returns [n_out, d]."""
+        alpha_j > 0.  Returns [n_out, d].
+        Section 5, Fig. 13."""
         v = self.variance()
         c2 = self.coef ** 2
         return np.stack([c2[self.alpha[:, j] > 0].sum(axis=0) / v for j in range(self.d)], axis=1)
 
     def sobol_first(self):
-        """First-order index of input j: terms in alpha_j alone.  [n_out, d]."""
+        """First-order index of input j: terms in alpha_j alone.  [n_out, d].
+        Section 5, Fig. 13."""
         v = self.variance()
         c2 = self.coef ** 2
         only = [(self.alpha[:, j] > 0) & (self.alpha.sum(axis=1) == self.alpha[:, j]) for j in range(self.d)]
@@ -119,7 +129,8 @@ class PCE:
 
 def rule_1d(family, n):
     """n roots of the degree-n basis polynomial (Gauss points) and weights
-    summing to 1, in the standardised variable."""
+    summing to 1, in the standardised variable.
+    Section 2.7: the Gauss points the collocation samples."""
     if family == NORMAL:
         x, w = hermegauss(n)
     else:
@@ -128,7 +139,8 @@ def rule_1d(family, n):
 
 
 def tensor_nodes(families, level):
-    """Tensor product of level-point Gauss rules: level^d points."""
+    """Tensor product of level-point Gauss rules: level^d points.
+    Section 2.7, Table 2 (27 and 216 points)."""
     rules = [rule_1d(f, level)[0] for f in families]
     return np.array(list(itertools.product(*rules)))
 
@@ -137,7 +149,8 @@ def smolyak_nodes(families, level):
     """Smolyak's sparse grid on the level-i Gauss rules with i points: the
     union of the tensor grids X_i1 x ... x X_id over the multi-indices with
     i_j >= 1 and max(d, level) <= |i| <= level + d - 1 (Smolyak 1963; the
-    non-nested Gaussian form of Heiss and Winschel)."""
+    non-nested Gaussian form of Heiss and Winschel).
+    Section 2.7, Table 1."""
     d = len(families)
     pts = {}
     for idx in itertools.product(range(1, level + 1), repeat=d):
@@ -149,7 +162,8 @@ def smolyak_nodes(families, level):
 
 
 def from_standard(families, params, xi):
-    """Map standardised points back to the inputs' own units."""
+    """Map standardised points back to the inputs' own units.
+    Section 2.7."""
     xi = np.atleast_2d(xi)
     X = np.empty_like(xi)
     for j, (f, (a, b)) in enumerate(zip(families, params)):
@@ -159,7 +173,8 @@ def from_standard(families, params, xi):
 
 def latin_hypercube(families, params, n, seed):
     """n Latin-hypercube samples of the inputs (one point per equal-probability
-    stratum of every marginal, strata paired by random permutations)."""
+    stratum of every marginal, strata paired by random permutations).
+    Sections 3 and 5: the Latin-hypercube test sets."""
     from scipy.stats import norm
     rng = np.random.default_rng(seed)
     d = len(families)

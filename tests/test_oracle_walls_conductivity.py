@@ -11,7 +11,7 @@ and natural-convection-off mode.
   temperatures is exactly (Phi(T_2) - Phi(T_1))/distance, so the discrete
   steady state equals Phi^-1 of the linear potential at every cell centre.
   Evaluating k at one owner instead of the mean fails (planted and checked).
-  The conductivity table is the paper's Sn-Bi one (Section 4).
+  The conductivity table is the paper's Sn-Bi one (Section 3).
 * The global energy balance with both features, computed from wall fluxes
   written out independently of the oracle's operator.
 * Natural convection off (Section 4) equals the full method whenever the
@@ -22,7 +22,7 @@ import numpy as np
 from fvs_inputs import box_mesh, cases, strip_mesh
 from oracle.fv import BC_ADIABATIC, BC_CONVECTIVE, BC_DIRICHLET, Oracle
 
-# Section 4, Sn-Bi validation: mean conductivity (W/m K) at four temperatures (K)
+# Section 3, Sn-Bi validation: mean conductivity (W/m K) at four temperatures (K)
 SN_BI_K = [(273.2, 61.282), (373.2, 57.42), (573.2, 30.1), (973.2, 37.7)]
 HOT = dict(cases.AL_ALLOY, beta=0.0, T_sol=300.0, T_liq=310.0, latent=0.0)   # liquid throughout, no latent heat
 
