@@ -201,3 +201,53 @@ def test_cycles_are_cut_and_ties_stay_valid(shim):
     z = replay_solve(L, col, val, diag, np.zeros(216), r, 216)
     P = tridiagonal_matrix(L, col, val, diag, np.zeros(216), 216)
     np.testing.assert_allclose(P @ z, r, rtol=0, atol=1e-12 * np.abs(r).max())
+
+
+def test_lines_on_the_energy_operator_of_thin_jittered_cells(shim):
+    """The oracle's energy operator (rho cp V / dt plus half the conduction
+    operator of Eq. 4, 27 couplings a row) on a jittered, permuted 6 x 6 x 48
+    strip of the bench mesh's thin cells, stored as a slot-major ELL the way
+    the library stores it: the chains are the z columns, and BiCGStab
+    preconditioned by the kernels' line substitutions (replayed) needs a
+    third or less of the iterations point-Jacobi needs."""
+    from fvs_inputs import box_mesh, cases
+    from oracle.fv import Oracle
+    n_side, nz = 6, 48
+    h = 0.1 / 128
+    m = box_mesh(n_side, n_side, nz, (n_side * h, n_side * h, nz * 0.0125 / 128), jitter=0.2, jitter_seed=31,
+                 permute_seed=32)
+    o = Oracle(m, cases.props())
+    A = (-0.5 * o.LTk + sp.diags(o.rcp * o.g.V / 1e-3)).tocsr()
+    A.sort_indices()
+    n = A.shape[0]
+    w = int(np.diff(A.indptr).max())
+    col = np.repeat(np.arange(n, dtype=np.int32)[None, :], w, 0)
+    val = np.zeros((w, n))
+    for i in range(n):
+        lo, hi = A.indptr[i], A.indptr[i + 1]
+        col[: hi - lo, i] = A.indices[lo:hi]
+        val[: hi - lo, i] = A.data[lo:hi]
+    col, val = np.ascontiguousarray(col.ravel()), np.ascontiguousarray(val.ravel())
+    diag = A.diagonal()
+    L = layout(shim, col, val, n, w, 512)
+    check_layout(L, col, n, w)
+    ijk = m["cell_ijk"]
+    for t, idx in lines_of(L):
+        c = L["cell"][idx]
+        d = np.diff(ijk[c], axis=0)
+        assert (d[:, :2] == 0).all() and (np.abs(d[:, 2]) == 1).all()
+    assert sorted(L["llen"][: L["nlines"]].tolist()) == [nz] * (n_side * n_side)
+    rng = np.random.default_rng(33)
+    b = A @ (950.0 + rng.normal(size=n))
+
+    def iterations(apply):
+        count = [0]
+        x, info = sla.bicgstab(A, b, rtol=1e-10, atol=0.0, maxiter=500,
+                               M=sla.LinearOperator(A.shape, matvec=apply),
+                               callback=lambda xk: count.__setitem__(0, count[0] + 1))
+        assert info == 0 and np.linalg.norm(b - A @ x) <= 1e-9 * np.linalg.norm(b)
+        return count[0]
+
+    its_j = iterations(lambda v: v / diag)
+    its_l = iterations(lambda v: replay_solve(L, col, val, diag, np.zeros(n), v, n))
+    assert its_l * 3 <= its_j, (its_l, its_j)
